@@ -1,0 +1,384 @@
+"""Benchmark: decoded information Gbit/s of the punctured-eMBB receive path on GB300.
+
+One step = one pass of the whole path over one batch: puncture flushing +
+max-log demap -> layered offset-min-sum decode -> TB CRC-24, goodput and
+reward.  Default workload: 4096 BG1-shaped code blocks, Z = 384 (K = 8448),
+rate 1/2, 16-QAM, Es/N0 cycling 6..12 dB, URLLC preempting 1-3 mini-slots on
+4-12 PRBs per slot, 10 iterations with early termination, float32.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun each rank decodes its own replica of the
+workload (independent code blocks: no collective on the data path) and the
+value is all ranks' decoded bits over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "decoded info Gbit/s + % HBM roofline; served p99 slot latency vs 125 µs, INT8 vs FP32"
+OPS_PER_EDGE = 10  # algorithmic lane-ops per lifted edge update ("Roofline")
+SAT = {"f32": None, "i8": (63, 63, 127), "i16": (1023, 1023, 32767)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def _oracle_chunk(args):
+    """Worker: run the oracle path on a sub-workload; returns (info bits, failed TBs)."""
+    w, mode, max_iter, et = args
+    from oracle import path as opath
+    out = opath.run(w, mode, max_iter, et)
+    return int(sum(w.bgs[int(c["bg"])].kb * int(c["Z"]) for c in w.cbs)), int((out["d"] == 0).sum())
+
+
+def make_workload(name: str, rank: int = 0):
+    from workload import large_fp32, mixed, tiny_fp32
+    if name == "large":
+        return large_fp32(seed=2 + 1000 * rank)
+    if name == "mixed":
+        return mixed(seed=3 + 1000 * rank)
+    if name == "tiny":
+        return tiny_fp32(seed=1000 * rank)
+    raise ValueError(name)
+
+
+def oracle_sample(w, n_tb: int, n_chunks: int):
+    from workload.configs import subset
+    idx = np.arange(min(n_tb, w.n_tb))
+    return [subset(w, part) for part in np.array_split(idx, n_chunks) if part.size]
+
+
+def time_oracle(pool, chunks, mode, max_iter, et):
+    t = time.perf_counter()
+    res = pool.map(_oracle_chunk, [(c, mode, max_iter, et) for c in chunks])
+    dt = time.perf_counter() - t
+    return sum(r[0] for r in res), dt
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = [ln.split(",") for ln in open(self.path) if ln.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def edge_updates(w, status: np.ndarray) -> int:
+    """Lifted edge updates the decoder performed: sum over blocks of iterations x edges in m_eff rows x Z."""
+    total = 0
+    cache = {}
+    for i, c in enumerate(w.cbs):
+        bg, Z, t0, m_eff, n_eff = w.cb_geometry(i)
+        key = (int(c["bg"]), m_eff)
+        if key not in cache:
+            cache[key] = int(np.sum(bg.row < m_eff))
+        total += int(status[i] & 0xFFFF) * cache[key] * Z
+    return total
+
+
+def hbm_bytes(w, mode: str) -> dict:
+    """Algorithmic DRAM bytes per step for each kernel (read + write)."""
+    esz = {"f32": 4, "i8": 1, "i16": 2}[mode]
+    sym = w.sym.size * 8
+    mask = w.mask.size * 4
+    llr = w.llr_len * esz
+    bits = w.bits_words * 4
+    status = w.n_cb * 4
+    return {"demap": sym + mask + llr, "decode": llr + bits + status,
+            "crc": bits + w.n_tb * 1 + w.n_slots * 16}
+
+
+def peak_alu_gops(num_sms: int, mhz: float) -> float:
+    """FP32/INT32 lane-ops per second: SMs x 128 lanes x clock."""
+    return num_sms * 128 * mhz * 1e6 / 1e9
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured", float(d.get("sm_max_mhz", 2070.0))
+    return 6800.0, "fallback", 2070.0
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = make_workload(args.config)
+    mi, et = w.meta["max_iter"], bool(w.meta["early_term"])
+    mode = "f64"
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    per_step_tb = args.ref_tb
+    with ctx.Pool(cores) as pool:
+        chunks = oracle_sample(w, per_step_tb, cores)
+        for _ in range(args.warmup):
+            time_oracle(pool, chunks, mode, mi, et)
+        bits = 0
+        dt = 0.0
+        for _ in range(args.steps):
+            b, t = time_oracle(pool, chunks, mode, mi, et)
+            bits += b
+            dt += t
+    v = bits / dt / 1e9
+    sample = f"first {per_step_tb} TBs of the {args.config} workload per step, float64 oracle, {cores} processes"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.config},
+            "cpu_baseline": {"value": v, "unit": "Gbit/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large", choices=["large", "mixed", "tiny"])
+    ap.add_argument("--mode", default=None, choices=["f32", "i8", "i16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-int8", action="store_true")
+    ap.add_argument("--cpu-tb", type=int, default=768, help="TBs in the timed CPU-oracle sample")
+    ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    # the oracle pool starts before any CUDA call (spawned workers)
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cores)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2506_00167_gb300 import Session
+
+    w = make_workload(args.config, rank)
+    mode = args.mode or w.meta.get("mode", "f32")
+    mi, et = w.meta["max_iter"], bool(w.meta["early_term"])
+    dev = torch.device("cuda", local)
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    hbm_peak, peak_kind, sm_max_nominal = load_peaks()
+
+    sym_h = torch.from_numpy(np.ascontiguousarray(w.sym, dtype=np.complex64)).pin_memory()
+    mask_h = torch.from_numpy(np.ascontiguousarray(w.mask).view(np.int32)).pin_memory()
+    sym = sym_h.to(dev)
+    mask = mask_h.to(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(mode_):
+        s = Session(w.bgs, w.z_set, mode=mode_, max_iter=mi, early_term=et, sat=SAT[mode_])
+        b = s.batch(w.cbs, w.tbs, w.slot_N)
+        out = b.alloc_outputs(local)
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(args.warmup):
+            s.run(b, sym, mask, out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            e_a, e_b, e_c, e_d = ev[k]
+            e_a.record(stream)
+            s.puncture_demap(b, sym, mask, out["llr"])
+            e_b.record(stream)
+            s.decode_batch(b, out["llr"], out["bits"], out["status"])
+            e_c.record(stream)
+            s.tb_crc_goodput(b, out["bits"], out["d"], out["goodput_bits"], out["goodput_sc"], out["reward"])
+            e_d.record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = t0.elapsed_time(t1)
+        k_ms = {"demap": statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                "decode": statistics.mean(e[1].elapsed_time(e[2]) for e in ev),
+                "crc": statistics.mean(e[2].elapsed_time(e[3]) for e in ev)}
+        status = out["status"].cpu().numpy()
+        errs = s.device_errors()
+        if errs:
+            raise RuntimeError(f"device error word {errs:#x}")
+        return s, b, out, ms, k_ms, status
+
+    clk = ClockSampler(str(getattr(torch.cuda.get_device_properties(dev), "uuid", local)))
+    if not str(clk.gpu_id).startswith("GPU-") and clk.gpu_id.count("-") >= 4:
+        clk.gpu_id = "GPU-" + clk.gpu_id
+    clk.start()
+    s, b, out, ms, k_ms, status = timed(mode)
+    clocks = clk.stop()
+
+    # max over ranks
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    info_bits = w.info_bits_total()
+    value = world * info_bits * args.steps / (ms / 1e3) / 1e9
+    ms_step = ms / args.steps
+
+    # ---- end to end through the public API from pinned host buffers
+    res_h = {k: torch.empty_like(out[k], device="cpu").pin_memory() for k in ("d", "goodput_bits", "reward")}
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        sym.copy_(sym_h, non_blocking=True)
+        mask.copy_(mask_h, non_blocking=True)
+        s.run(b, sym, mask, out)
+        for k in res_h:
+            res_h[k].copy_(out[k], non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sym.copy_(sym_h, non_blocking=True)
+        mask.copy_(mask_h, non_blocking=True)
+        s.run(b, sym, mask, out)
+        for k in res_h:
+            res_h[k].copy_(out[k], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_e2e = float(tt.item())
+    e2e_val = world * info_bits * args.steps / (ms_e2e / 1e3) / 1e9
+    h2d = sym_h.numel() * 8 + mask_h.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in res_h.values())
+
+    # ---- roofline of the dominant kernel (the decoder)
+    eu = edge_updates(w, status)
+    mhz = (clocks or {}).get("sm_mhz") or sm_max_nominal
+    peak_g = peak_alu_gops(num_sms, mhz)
+    achieved_g = OPS_PER_EDGE * eu / (k_ms["decode"] / 1e3) / 1e9
+    hb = hbm_bytes(w, mode)
+    roof = {"bound": "alu", "achieved": achieved_g, "peak": peak_g, "unit": "Glaneop/s",
+            "frac": achieved_g / peak_g, "traffic": None,
+            "kernel": "oms_decode_kernel", "launch_ms": k_ms["decode"],
+            "edge_updates_per_launch": eu, "ops_per_edge_update": OPS_PER_EDGE,
+            "peak_basis": f"{num_sms} SMs x 128 lanes x {mhz:.0f} MHz (median SM clock sampled in the timed region)",
+            "hbm_achieved_gbs": hb["decode"] / (k_ms["decode"] / 1e3) / 1e9,
+            "hbm_peak_gbs": hbm_peak, "hbm_frac": hb["decode"] / (k_ms["decode"] / 1e3) / 1e9 / hbm_peak,
+            "hbm_peak_kind": peak_kind}
+    demap_gbs = hb["demap"] / (k_ms["demap"] / 1e3) / 1e9
+    kernels = {k: {"ms": v, "share": v / sum(k_ms.values())} for k, v in k_ms.items()}
+    kernels["demap"]["hbm_gbs"] = demap_gbs
+    kernels["demap"]["hbm_frac"] = demap_gbs / hbm_peak
+
+    # ---- INT8 on the same workload
+    int8 = None
+    if not args.no_int8 and mode != "i8":
+        s8, b8, out8, ms8, k8, st8 = timed("i8")
+        int8 = {"value": world * info_bits * args.steps / (ms8 / 1e3) / 1e9, "unit": "Gbit/s",
+                "ms_per_step": ms8 / args.steps, "decode_ms": k8["decode"],
+                "mean_iters": float(np.mean(st8 & 0xFFFF))}
+        del s8, b8, out8
+
+    # ---- CPU baseline: the oracle on a bounded sample, all host cores
+    cpu = None
+    if pool is not None:
+        chunks = oracle_sample(w, args.cpu_tb, cores)
+        bits, dt = time_oracle(pool, chunks, "f64", mi, et)
+        pool.close()
+        cpu = {"value": bits / dt / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {min(args.cpu_tb, w.n_tb)} TBs of the workload, float64 oracle "
+                         f"(demap + decode + CRC), {cores} spawned processes, {dt:.1f} s wall"}
+
+    gpu_launches = args.steps * (2 + len(set(int(z) for z in w.cbs["Z"])))
+    line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"f32": "f32", "i8": "i8", "i16": "i16"}[mode],
+            "data": "synthetic (seeded Tx chain: CRC-24, QC-LDPC encode, 16-QAM, AWGN, URLLC puncture masks)",
+            "config": {"workload": {"large": "4096 x BG1-shaped Z=384 K=8448 R=1/2 16-QAM, Es/N0 6-12 dB, "
+                                             "<=10 iter + ET",
+                                    "mixed": "512 slots x 8 UEs mixed BG/Z/R/Qm",
+                                    "tiny": "8x16 Z=16 QPSK"}[args.config],
+                       "code_blocks": w.n_cb, "transport_blocks": w.n_tb, "info_bits_per_step": info_bits,
+                       "mean_iters": float(np.mean(status & 0xFFFF)),
+                       "l2": "inputs larger than L2 (symbols %.0f MB + LLRs %.0f MB per step)"
+                             % (w.sym.size * 8 / 1e6, hb["decode"] / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "codewords_per_s": world * w.n_cb * args.steps / (ms / 1e3),
+            "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "int8": int8,
+            "e2e": {"value": e2e_val, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * ldpcgb -- GB300 (sm_103a) receive path for URLLC-punctured eMBB transport
+ * blocks: puncture flushing + max-log soft demapping, layered offset-min-sum
+ * decoding of NR-style quasi-cyclic LDPC codes, and the transport-block CRC-24
+ * check that yields d_e, the goodput (paper Sec. III-B, eq. 1) and the reward
+ * r(t) (paper Sec. V-A, eq. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns 0 (LDPC_OK) or a negative LDPC_E* code; on failure
+ *   ldpc_last_error() returns a thread-local message.  No C++ exception and no
+ *   abort crosses this interface.
+ * - Compute calls only ENQUEUE work on the session's CUDA stream and return;
+ *   results are ready once that stream is synchronised.
+ * - "_dev" pointers are device memory OWNED BY THE CALLER (e.g. PyTorch
+ *   tensors); the library never frees them.  Host pointers (descriptor
+ *   arrays, base-graph tables) are read during the call and may be freed when
+ *   it returns.  The library owns the session (shift tables, workspace, error
+ *   word) and batch objects; destroy them with the matching *_destroy call.
+ * - A session is bound to the device that was current at create time and to
+ *   one stream; it is not thread-safe.
+ * - Buffer sizes: ldpc_batch_info() reports how many elements each caller
+ *   buffer must hold for a batch; the library cannot see allocation sizes and
+ *   trusts the caller to provide at least that much.
+ * - Device-side waits are bounded.  A kernel that gives up sets a bit in the
+ *   session's device error word (read with ldpc_device_errors()) and returns.
+ */
+#ifndef LDPCGB_H
+#define LDPCGB_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LDPC_API __attribute__((visibility("default")))
+#else
+#define LDPC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LDPC_OK 0
+#define LDPC_EINVAL (-1)   /* bad argument or descriptor (Z not allowed, E too large, misaligned offset) */
+#define LDPC_ENOMEM (-2)   /* device-memory budget exceeded or cudaMalloc failed */
+#define LDPC_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define LDPC_ETIMEOUT (-4) /* a bounded device wait gave up (serving) */
+#define LDPC_EBUSY (-5)    /* serving ring full / not started */
+
+/* Bits of the device error word. */
+#define LDPC_DEVERR_TMA_TIMEOUT 0x1u   /* a bulk-copy wait hit its iteration limit */
+#define LDPC_DEVERR_BAD_ITEM 0x2u      /* a work item failed its device-side check */
+#define LDPC_DEVERR_SERVE_TIMEOUT 0x4u /* the serving loop's doorbell wait gave up */
+
+typedef struct ldpc_session ldpc_session; /* opaque, owned by the library */
+typedef struct ldpc_batch ldpc_batch;     /* opaque, owned by the library */
+
+typedef enum { LDPC_F32 = 0, LDPC_I8 = 1, LDPC_I16 = 2 } ldpc_mode;
+
+/*
+ * One base matrix.  Edges are listed in row-major (row, col) order; at most
+ * one edge per (row, col).  Row k of the Z x Z block at (row, col) with raw
+ * shift V connects to column (k + V mod Z) mod Z.  Columns [0, kb) carry
+ * information, the next mc columns core parity (rows [0, mc) are the core
+ * rows), the rest extension parity, one per extension row.  The first
+ * n_punct_cols information columns are never transmitted.  The paper gives
+ * no code parameters (Sec. III-B, Sec. IV "Tx Signal Processing"); callers
+ * supply seeded matrices.  Host pointers, copied at ldpc_session_create.
+ */
+typedef struct {
+  int32_t mb, nb, kb, mc;
+  int32_t n_punct_cols;
+  int32_t n_edges;
+  const int16_t *row;
+  const int16_t *col;
+  const int16_t *V; /* raw shift in [0, 32767]; the lifted shift is V mod Z */
+} ldpc_base_graph;
+
+typedef struct {
+  int32_t n_bg;
+  const ldpc_base_graph *bgs; /* host array of n_bg */
+  int32_t n_z;
+  const int32_t *z_set;       /* allowed lifting sizes: 16 or a multiple of 32, <= 384 */
+  int32_t mode;               /* ldpc_mode */
+  int32_t max_iter;           /* 1..64 */
+  int32_t early_term;         /* 1: stop a code block at the first zero syndrome */
+  float offset_f32;           /* beta for LDPC_F32 (e.g. 0.5) */
+  int32_t offset_lsb;         /* beta for the integer modes, in LSB (e.g. 1) */
+  float q_scale;              /* integer modes: LSB per LLR unit (e.g. 4) */
+  int32_t llr_sat;            /* |channel LLR| clamp after quantising (INT8 63, INT16 1023) */
+  int32_t msg_sat;            /* |Q| clamp before the minimum (INT8 63, INT16 1023) */
+  int32_t post_sat;           /* |Q|, |L| saturation (INT8 127, INT16 32767) */
+  int32_t interleave;         /* 1: Qm-row block interleaver between rate matching and mapping */
+  uint64_t device_mem_budget; /* bytes the session and its batches may allocate; 0 = unlimited */
+  void *cuda_stream;          /* cudaStream_t; NULL = the legacy default stream */
+} ldpc_session_desc;
+
+/*
+ * One code block.  Transmitted bits are codeword positions [t0, t0 + E) with
+ * t0 = n_punct_cols * Z; the decoder works on n_eff = kb + m_eff columns with
+ * m_eff = min(mb, max(mc, ceil((E + t0) / Z) - kb)) rows.
+ *   re_offset        first complex symbol (float2) of the block, E / Qm of them
+ *   mask_word_offset first uint32 of its puncture mask: bit r % 32 of word
+ *                    r / 32 set = resource element r was taken by URLLC
+ *   llr_offset       first element of its n_eff * Z LLRs; a multiple of 16
+ *   bits_word_offset first uint32 of its kb * Z / 32 decoded information
+ *                    words: bit i of the block is bit i % 32 of word i / 32
+ *   inv_sigma2       1 / noise variance per symbol
+ */
+typedef struct {
+  int32_t bg, Z, Qm, E;
+  int64_t re_offset;
+  int64_t mask_word_offset;
+  int64_t llr_offset;
+  int64_t bits_word_offset;
+  float inv_sigma2;
+  int32_t reserved; /* must be 0 */
+} ldpc_cb_desc;
+
+/*
+ * One transport block (one eMBB user in one slot): code blocks
+ * [first_cb, first_cb + n_cb) carry its payload_bits + 24 CRC bits in order;
+ * n_sc is n_e, the user's subcarriers; slot indexes the slot_N array.
+ */
+typedef struct {
+  int32_t first_cb, n_cb, n_sc, slot, payload_bits;
+} ldpc_tb_desc;
+
+typedef struct {
+  int64_t sym_elems;    /* float2 symbols the sym buffer must hold */
+  int64_t mask_words;   /* uint32 mask words */
+  int64_t llr_elems;    /* LLR elements (float / int8 / int16 by mode) */
+  int64_t bits_words;   /* uint32 decoded-bit words */
+  int32_t n_cb, n_tb, n_slots;
+  int32_t n_items;      /* decoder work items (codeword groups) */
+  int64_t info_bits;    /* sum of K over the code blocks */
+} ldpc_batch_info;
+
+/* Create a session: validates the base graphs (row degree 2..27, one entry per
+ * (row, col)), builds the shift tables for every (base graph, Z) pair, and
+ * allocates its workspace on the current device. */
+LDPC_API int ldpc_session_create(const ldpc_session_desc *d, ldpc_session **out);
+LDPC_API int ldpc_session_destroy(ldpc_session *s);
+/* Rebind the session to another stream of the same device (NULL = legacy default). */
+LDPC_API int ldpc_session_set_stream(ldpc_session *s, void *cuda_stream);
+
+/* Validate host descriptor arrays and plan a batch: per-block geometry, the
+ * decoder's work items (codeword groups of one shape), demap tiles and the
+ * slot-to-TB lists.  cbs/tbs/slot_N are host arrays; slot_N[s] is N, the
+ * subcarriers of slot s (the reward's normaliser).  n_tb may be 0 (decode
+ * only); then tb_crc_goodput rejects the batch. */
+LDPC_API int ldpc_batch_create(ldpc_session *s, const ldpc_cb_desc *cbs, int32_t n_cb,
+                      const ldpc_tb_desc *tbs, int32_t n_tb, int32_t n_slots,
+                      const int32_t *slot_N, ldpc_batch **out);
+LDPC_API int ldpc_batch_destroy(ldpc_batch *b);
+LDPC_API int ldpc_batch_info_get(const ldpc_batch *b, ldpc_batch_info *out);
+
+/*
+ * Puncture flushing + max-log soft demapping + rate dematching (paper
+ * Sec. IV "UE": the LLRs of bits on punctured resource elements are set to 0
+ * after the soft demodulator; the demapper algorithm is not stated there,
+ * this library uses max-log).  For each resource element r of each block:
+ * if its mask bit is set all Qm LLRs are 0, otherwise
+ *   lambda_i = inv_sigma2 * (min_{s: b_i=1} |y-s|^2 - min_{s: b_i=0} |y-s|^2)
+ * over NR-style Gray QAM (Qm = 2, 4, 6, 8), written to codeword position
+ * t0 + i * (E/Qm) + r (interleaved) or t0 + r * Qm + i.  Positions never
+ * transmitted are written 0.  Integer modes store
+ * clamp(round_half_away(q_scale * lambda), -llr_sat, llr_sat).
+ *   sym_dev  float2 (re, im) symbols; mask_dev uint32 words;
+ *   llr_dev  float (F32) / int8 (I8) / int16 (I16), batch info llr_elems.
+ */
+LDPC_API int puncture_demap(ldpc_session *s, const ldpc_batch *b, const void *sym_dev,
+                   const uint32_t *mask_dev, void *llr_dev);
+
+/*
+ * Layered offset-min-sum decoding of every code block of the batch from the
+ * LLR buffer.  Rows 0..m_eff-1 in order each iteration; check (l, k) over
+ * edges j: Q_j = L[v_j] - R_j; R'_j = sign * max(min_{i != j} |Q_i| - beta, 0)
+ * with sign the product of the other edges' signs (Q = 0 counts positive);
+ * L[v_j] = Q_j + R'_j.  Integer modes saturate Q and L at post_sat and clamp
+ * |Q| at msg_sat before the minimum.  After every iteration the hard decision
+ * [L < 0] is checked against the m_eff rows; with early termination a block
+ * stops at the first zero syndrome.  Writes each block's kb*Z information bits
+ * to bits_dev and status_dev[cb] = iterations | (syndrome_zero << 16).
+ * The paper's decoder is a toolbox function (Sec. IV "UE"); this is the
+ * algorithm this library fixes in its place.
+ */
+LDPC_API int decode_batch(ldpc_session *s, const ldpc_batch *b, const void *llr_dev,
+                 uint32_t *bits_dev, int32_t *status_dev);
+
+/*
+ * Transport-block CRC-24 check and per-slot goodput and reward.  d_e = 1 iff
+ * the TB's (payload_bits + 24) decoded bits are a multiple of
+ * g(x) = 0x1864CFB (register from 0, first bit highest degree) -- the same
+ * test as comparing received and recomputed CRC bits (Sec. IV "UE Feedback").
+ * Per slot t:  goodput_bits[t] = sum_e d_e * payload_bits_e;
+ *              goodput_sc[t]   = sum_e d_e * n_e               (eq. 1)
+ *              reward[t]       = (1/N_t) * sum_e (d_e - 1) n_e  (eq. 2)
+ * d_dev: uint8 per TB; the other outputs one element per slot.
+ */
+LDPC_API int tb_crc_goodput(ldpc_session *s, const ldpc_batch *b, const uint32_t *bits_dev,
+                   uint8_t *d_dev, uint64_t *goodput_bits_dev, uint32_t *goodput_sc_dev,
+                   float *reward_dev);
+
+/* Synchronise the session stream and return (then clear) the device error word. */
+LDPC_API int ldpc_device_errors(ldpc_session *s, uint32_t *flags_out);
+
+/* Thread-local message for the last non-zero return on this thread. */
+LDPC_API const char *ldpc_last_error(void);
+
+/* Library version string. */
+LDPC_API const char *ldpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPCGB_H */

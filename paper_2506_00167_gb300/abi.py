@@ -1,0 +1,123 @@
+"""ctypes binding of the ldpcgb C-ABI (``include/ldpcgb.h``).
+
+Argument marshalling only: every step of the receive path runs in the CUDA
+kernels behind ``libldpcgb.so``.  PyTorch supplies device memory and the
+current stream; buffers are passed as raw device pointers.  There is no CPU
+fallback: if the library is missing or was built for another GPU, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libldpcgb.so")
+
+LDPC_F32, LDPC_I8, LDPC_I16 = 0, 1, 2
+MODES = {"f32": LDPC_F32, "i8": LDPC_I8, "i16": LDPC_I16}
+ERRORS = {-1: "LDPC_EINVAL", -2: "LDPC_ENOMEM", -3: "LDPC_ECUDA", -4: "LDPC_ETIMEOUT", -5: "LDPC_EBUSY"}
+
+EXPORTED = [
+    "ldpc_session_create", "ldpc_session_destroy", "ldpc_session_set_stream",
+    "ldpc_batch_create", "ldpc_batch_destroy", "ldpc_batch_info_get",
+    "puncture_demap", "decode_batch", "tb_crc_goodput",
+    "ldpc_device_errors", "ldpc_last_error", "ldpc_version",
+]
+
+
+class BaseGraphC(ctypes.Structure):
+    _fields_ = [("mb", ctypes.c_int32), ("nb", ctypes.c_int32), ("kb", ctypes.c_int32), ("mc", ctypes.c_int32),
+                ("n_punct_cols", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("row", ctypes.POINTER(ctypes.c_int16)), ("col", ctypes.POINTER(ctypes.c_int16)),
+                ("V", ctypes.POINTER(ctypes.c_int16))]
+
+
+class SessionDescC(ctypes.Structure):
+    _fields_ = [("n_bg", ctypes.c_int32), ("bgs", ctypes.POINTER(BaseGraphC)),
+                ("n_z", ctypes.c_int32), ("z_set", ctypes.POINTER(ctypes.c_int32)),
+                ("mode", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("early_term", ctypes.c_int32),
+                ("offset_f32", ctypes.c_float), ("offset_lsb", ctypes.c_int32), ("q_scale", ctypes.c_float),
+                ("llr_sat", ctypes.c_int32), ("msg_sat", ctypes.c_int32), ("post_sat", ctypes.c_int32),
+                ("interleave", ctypes.c_int32), ("device_mem_budget", ctypes.c_uint64),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class CbDescC(ctypes.Structure):
+    _fields_ = [("bg", ctypes.c_int32), ("Z", ctypes.c_int32), ("Qm", ctypes.c_int32), ("E", ctypes.c_int32),
+                ("re_offset", ctypes.c_int64), ("mask_word_offset", ctypes.c_int64),
+                ("llr_offset", ctypes.c_int64), ("bits_word_offset", ctypes.c_int64),
+                ("inv_sigma2", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+class TbDescC(ctypes.Structure):
+    _fields_ = [("first_cb", ctypes.c_int32), ("n_cb", ctypes.c_int32), ("n_sc", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("payload_bits", ctypes.c_int32)]
+
+
+class BatchInfoC(ctypes.Structure):
+    _fields_ = [("sym_elems", ctypes.c_int64), ("mask_words", ctypes.c_int64), ("llr_elems", ctypes.c_int64),
+                ("bits_words", ctypes.c_int64), ("n_cb", ctypes.c_int32), ("n_tb", ctypes.c_int32),
+                ("n_slots", ctypes.c_int32), ("n_items", ctypes.c_int32), ("info_bits", ctypes.c_int64)]
+
+
+def _np_dtype(struct) -> np.dtype:
+    """NumPy structured dtype with the exact field offsets of a ctypes struct."""
+    conv = {ctypes.c_int32: "<i4", ctypes.c_int64: "<i8", ctypes.c_float: "<f4"}
+    names, formats, offsets = [], [], []
+    for name, ct in struct._fields_:
+        names.append(name)
+        formats.append(conv[ct])
+        offsets.append(getattr(struct, name).offset)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(struct)})
+
+
+CB_NP = _np_dtype(CbDescC)
+TB_NP = _np_dtype(TbDescC)
+
+_lib = None
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libldpcgb.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libldpcgb.so not found at {p}; run paper_2506_00167_gb300.build.build() first")
+    lib = ctypes.CDLL(p)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.ldpc_session_create.argtypes = [ctypes.POINTER(SessionDescC), ctypes.POINTER(vp)]
+    lib.ldpc_session_destroy.argtypes = [vp]
+    lib.ldpc_session_set_stream.argtypes = [vp, vp]
+    lib.ldpc_batch_create.argtypes = [vp, vp, i32, vp, i32, i32, vp, ctypes.POINTER(vp)]
+    lib.ldpc_batch_destroy.argtypes = [vp]
+    lib.ldpc_batch_info_get.argtypes = [vp, ctypes.POINTER(BatchInfoC)]
+    lib.puncture_demap.argtypes = [vp, vp, vp, vp, vp]
+    lib.decode_batch.argtypes = [vp, vp, vp, vp, vp]
+    lib.tb_crc_goodput.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.ldpc_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    lib.ldpc_last_error.restype = ctypes.c_char_p
+    lib.ldpc_version.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        f = getattr(lib, name)
+        if f.restype is None or f.restype is ctypes.c_int:
+            f.restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(rc: int, where: str) -> None:
+    if rc != 0:
+        msg = load().ldpc_last_error().decode(errors="replace")
+        raise LdpcError(rc, where, msg)

@@ -1,0 +1,187 @@
+// Internal types and device helpers shared by the ldpcgb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ldpcgb.h"
+
+namespace ldpcgb {
+
+constexpr int kMaxDeg = 27;      // sign bits 0..26 + 5-bit argmin index in one word
+constexpr int kMaxZ = 384;
+constexpr int kMaxSmem = 232448; // 227 KB dynamic shared memory per block (sm_100 family)
+constexpr int kCrcBlock = 256;
+
+// One (base graph, Z) pair.  Its table in the session's edge buffer is
+// [n_edges words: (col * Z) | (shift << 16)] [pad to 4] [mb + 1 row starts] [pad to 4].
+struct ShapeDev {
+  int32_t bg, Z, mb, nb, kb, mc, npc;
+  int32_t tab_off;    // first word of this shape's table
+  int32_t row_off;    // row starts, relative to tab_off
+  int32_t tab_words;  // multiple of 4 (whole table, 16-byte granules)
+};
+
+// Per code block geometry, computed on the host at batch creation.
+struct CbDev {
+  int32_t shape, Z, Qm, E;
+  int32_t t0, m_eff, n_eff, n_re;
+  int32_t kb, pad0;
+  int64_t re_off, mask_off, llr_off, bits_off;
+  float inv_sigma2;
+  int32_t pad1;
+};
+
+// One decoder work item: `count` code blocks of one shape, listed from
+// item_cbs[first]; each is decoded by its own group of Z threads.
+struct DecodeItem {
+  int32_t shape, first, count, pad;
+};
+
+struct DemapTile {
+  int32_t cb, re_start;
+};
+
+struct TbDev {
+  int32_t first_cb, n_cb, n_sc, slot, payload_bits, words;
+};
+
+struct DecodeArgs {
+  const ShapeDev* shapes;
+  const uint32_t* tabs;
+  const CbDev* cbs;
+  const int32_t* item_cbs;
+  const DecodeItem* items;
+  int32_t n_items;
+  int32_t Z;
+  const void* llr;
+  uint32_t* bits;
+  int32_t* status;
+  uint32_t* err;
+  uint8_t* rscratch;        // R records in global memory (RGLOBAL variant)
+  int64_t rscratch_group;   // bytes per (block, group) slot
+  int32_t G;                // groups per block
+  int32_t hdr_bytes;        // shape table + mbarrier, 16-byte multiple
+  int32_t region_bytes;     // per-group shared region
+  int32_t L_bytes;          // per-group posterior array (padded)
+  int32_t rec_cap;          // records per group (max m_eff * Z)
+  int32_t max_iter, early_term;
+  float beta, msg_sat, post_sat;
+};
+
+struct DemapArgs {
+  const CbDev* cbs;
+  const DemapTile* tiles;
+  const float2* sym;
+  const uint32_t* mask;
+  void* llr;
+  int32_t interleave;
+  float q_scale, llr_sat;
+};
+
+struct CrcArgs {
+  const TbDev* tbs;
+  const CbDev* cbs;
+  const int32_t* slot_start;  // n_slots + 1
+  const int32_t* slot_tbs;
+  const int32_t* slot_N;
+  const uint32_t* crc_table;  // 256 entries
+  const uint32_t* xpow32;     // x^(32 m) mod g, m = 0..max_words
+  const uint32_t* bits;
+  uint8_t* d;
+  uint64_t* goodput_bits;
+  uint32_t* goodput_sc;
+  float* reward;
+};
+
+// ---------------------------------------------------------------- host side
+void set_error(const std::string& msg);
+
+// Kernel launchers (defined next to their kernels).
+cudaError_t launch_decode(int mode, bool rglobal, dim3 grid, dim3 block, int smem, cudaStream_t st,
+                          const DecodeArgs& a);
+cudaError_t decode_occupancy(int mode, bool rglobal, int block, int smem, int* blocks_per_sm);
+cudaError_t decode_prepare(int mode);  // raise the dynamic shared-memory limit
+cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
+cudaError_t launch_crc(int n_slots, cudaStream_t st, const CrcArgs& a);
+
+constexpr int kDemapBlock = 256;
+
+}  // namespace ldpcgb
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+namespace ldpcgb {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make generic-proxy shared-memory traffic visible to / ordered with the
+// async (bulk-copy) proxy.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk (TMA engine) copy global -> this CTA's shared memory, completing on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll may itself suspend
+// for a short hardware-defined time).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Barrier over `nthreads` threads on barrier `id` that also ORs `pred`.
+__device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+}  // namespace ldpcgb
+#endif

@@ -1,0 +1,616 @@
+// Host side of the C-ABI: sessions, batch planning and the entry points.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct ldpc_session {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int mode = LDPC_F32;
+  int max_iter = 10;
+  int early_term = 1;
+  float beta_f32 = 0.5f;
+  int offset_lsb = 1;
+  float q_scale = 4.0f;
+  int llr_sat = 63, msg_sat = 63, post_sat = 127;
+  int interleave = 1;
+  uint64_t budget = 0;
+  uint64_t allocated = 0;
+  int num_sms = 0;
+  struct Bg {
+    int mb, nb, kb, mc, npc;
+    std::vector<int> row, col, V;
+    std::vector<int> maxcol_upto;  // largest column used by rows 0..r
+  };
+  std::vector<Bg> bgs;
+  std::vector<int> zset;
+  std::vector<ldpcgb::ShapeDev> shapes;
+  std::map<std::pair<int, int>, int> shape_index;  // (bg, Z) -> shape
+  uint32_t* d_tabs = nullptr;
+  ldpcgb::ShapeDev* d_shapes = nullptr;
+  uint32_t* d_crc_table = nullptr;
+  uint32_t* d_err = nullptr;
+};
+
+namespace {
+
+struct Launch {
+  int Z = 0, G = 1, block = 0, smem = 0, grid = 0;
+  bool rglobal = false;
+  int item_begin = 0, item_count = 0;
+  int hdr_bytes = 0, region_bytes = 0, L_bytes = 0, rec_cap = 0;
+  int64_t rscratch_group = 0;
+  int64_t rscratch_off = 0;  // into the batch's scratch buffer
+};
+
+}  // namespace
+
+struct ldpc_batch {
+  ldpc_session* s = nullptr;
+  ldpc_batch_info info{};
+  std::vector<ldpcgb::CbDev> cbs;
+  ldpcgb::CbDev* d_cbs = nullptr;
+  std::vector<Launch> launches;
+  ldpcgb::DecodeItem* d_items = nullptr;
+  int32_t* d_item_cbs = nullptr;
+  uint8_t* d_rscratch = nullptr;
+  int64_t rscratch_bytes = 0;
+  ldpcgb::DemapTile* d_tiles = nullptr;
+  int n_tiles = 0;
+  ldpcgb::TbDev* d_tbs = nullptr;
+  int32_t* d_slot_start = nullptr;
+  int32_t* d_slot_tbs = nullptr;
+  int32_t* d_slot_N = nullptr;
+  uint32_t* d_xpow32 = nullptr;
+  std::vector<void*> owned;
+  uint64_t bytes = 0;
+};
+
+namespace ldpcgb {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace ldpcgb
+
+using namespace ldpcgb;
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(LDPC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Device allocation charged against the session budget.
+template <typename T>
+int dev_alloc(ldpc_session* s, T** p, size_t count, std::vector<void*>* owned, uint64_t* charged) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  bytes = (bytes + 255) & ~size_t(255);
+  if (s->budget && s->allocated + bytes > s->budget)
+    return fail(LDPC_ENOMEM, "device-memory budget exceeded (" + std::to_string(s->allocated + bytes) + " > " +
+                                 std::to_string(s->budget) + " bytes)");
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) return fail(LDPC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  s->allocated += bytes;
+  if (owned) owned->push_back(*p);
+  if (charged) *charged += bytes;
+  return LDPC_OK;
+}
+
+template <typename T>
+int upload(ldpc_session* s, T** p, const std::vector<T>& v, std::vector<void*>* owned, uint64_t* charged) {
+  int rc = dev_alloc(s, p, v.size(), owned, charged);
+  if (rc) return rc;
+  if (!v.empty()) {
+    cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  }
+  return LDPC_OK;
+}
+
+int align16(int x) { return (x + 15) & ~15; }
+
+bool z_supported(int Z) { return Z == 16 || (Z >= 32 && Z <= kMaxZ && Z % 32 == 0); }
+
+uint32_t crc_byte_entry(uint32_t v) {
+  uint32_t r = v << 16;
+  for (int i = 0; i < 8; ++i) r = (r & 0x800000u) ? (((r << 1) ^ 0x864CFBu) & 0xFFFFFFu) : ((r << 1) & 0xFFFFFFu);
+  return r;
+}
+
+// x^(32 m) mod g for m = 0..n.
+std::vector<uint32_t> xpow32_table(int n) {
+  std::vector<uint32_t> t(n + 1);
+  uint32_t cur = 1;  // x^0
+  for (int m = 0; m <= n; ++m) {
+    t[m] = cur;
+    for (int i = 0; i < 32; ++i) {  // multiply by x^32, one bit at a time
+      cur <<= 1;
+      if (cur & 0x1000000u) cur ^= 0x1864CFBu;
+    }
+  }
+  return t;
+}
+
+int session_free(ldpc_session* s) {
+  if (!s) return LDPC_OK;
+  cudaSetDevice(s->device);
+  cudaFree(s->d_tabs);
+  cudaFree(s->d_shapes);
+  cudaFree(s->d_crc_table);
+  cudaFree(s->d_err);
+  delete s;
+  return LDPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ldpc_last_error(void) { return g_err.c_str(); }
+
+const char* ldpc_version(void) { return "ldpcgb 0.1 sm_103a"; }
+
+int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
+  try {
+    if (!d || !out) return fail(LDPC_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->mode < LDPC_F32 || d->mode > LDPC_I16) return fail(LDPC_EINVAL, "unknown mode");
+    if (d->max_iter < 1 || d->max_iter > 64) return fail(LDPC_EINVAL, "max_iter must be 1..64");
+    if (d->n_bg < 1 || !d->bgs) return fail(LDPC_EINVAL, "no base graphs");
+    if (d->n_z < 1 || !d->z_set) return fail(LDPC_EINVAL, "empty Z set");
+    if (d->mode != LDPC_F32) {
+      const int lim = d->mode == LDPC_I8 ? 127 : 32767;
+      if (d->post_sat < 1 || d->post_sat > lim || d->msg_sat < 1 || d->msg_sat > d->post_sat ||
+          d->llr_sat < 1 || d->llr_sat > d->post_sat || d->offset_lsb < 0 || !(d->q_scale > 0.f))
+        return fail(LDPC_EINVAL, "integer-mode saturation/offset/scale out of range");
+    } else if (!(d->offset_f32 >= 0.f)) {
+      return fail(LDPC_EINVAL, "offset_f32 must be >= 0");
+    }
+    auto* s = new (std::nothrow) ldpc_session();
+    if (!s) return fail(LDPC_ENOMEM, "host allocation");
+    cudaGetDevice(&s->device);
+    s->stream = static_cast<cudaStream_t>(d->cuda_stream);
+    s->mode = d->mode;
+    s->max_iter = d->max_iter;
+    s->early_term = d->early_term ? 1 : 0;
+    s->beta_f32 = d->offset_f32;
+    s->offset_lsb = d->offset_lsb;
+    s->q_scale = d->q_scale;
+    s->llr_sat = d->llr_sat;
+    s->msg_sat = d->msg_sat;
+    s->post_sat = d->post_sat;
+    s->interleave = d->interleave ? 1 : 0;
+    s->budget = d->device_mem_budget;
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+
+    for (int i = 0; i < d->n_z; ++i) {
+      if (!z_supported(d->z_set[i])) {
+        session_free(s);
+        return fail(LDPC_EINVAL, "Z=" + std::to_string(d->z_set[i]) + " unsupported (16 or a multiple of 32 <= 384)");
+      }
+      s->zset.push_back(d->z_set[i]);
+    }
+    for (int b = 0; b < d->n_bg; ++b) {
+      const ldpc_base_graph& g = d->bgs[b];
+      ldpc_session::Bg h{g.mb, g.nb, g.kb, g.mc, g.n_punct_cols, {}, {}, {}, {}};
+      if (g.mb < 1 || g.nb <= g.mb || g.kb != g.nb - g.mb || g.mc < 1 || g.mc > g.mb || g.n_punct_cols < 0 ||
+          g.n_punct_cols > g.kb || g.n_edges < 1 || !g.row || !g.col || !g.V) {
+        session_free(s);
+        return fail(LDPC_EINVAL, "base graph " + std::to_string(b) + ": bad sizes (need kb = nb - mb)");
+      }
+      std::vector<int> deg(g.mb, 0);
+      int prev_r = -1, prev_c = -1;
+      for (int e = 0; e < g.n_edges; ++e) {
+        const int r = g.row[e], c = g.col[e], v = g.V[e];
+        if (r < 0 || r >= g.mb || c < 0 || c >= g.nb || v < 0 || (r < prev_r) || (r == prev_r && c <= prev_c)) {
+          session_free(s);
+          return fail(LDPC_EINVAL, "base graph " + std::to_string(b) + ": edges must be row-major, unique, in range");
+        }
+        prev_r = r;
+        prev_c = c;
+        deg[r]++;
+        h.row.push_back(r);
+        h.col.push_back(c);
+        h.V.push_back(v);
+      }
+      h.maxcol_upto.assign(g.mb, 0);
+      for (int e = 0; e < g.n_edges; ++e) h.maxcol_upto[g.row[e]] = std::max(h.maxcol_upto[g.row[e]], int(g.col[e]));
+      for (int r = 1; r < g.mb; ++r) h.maxcol_upto[r] = std::max(h.maxcol_upto[r], h.maxcol_upto[r - 1]);
+      for (int r = 0; r < g.mb; ++r)
+        if (deg[r] < 2 || deg[r] > kMaxDeg) {
+          session_free(s);
+          return fail(LDPC_EINVAL, "base graph " + std::to_string(b) + ": row degree must be 2.." +
+                                       std::to_string(kMaxDeg));
+        }
+      if ((g.kb * 16) % 32 && std::find(s->zset.begin(), s->zset.end(), 16) != s->zset.end()) {
+        session_free(s);
+        return fail(LDPC_EINVAL, "Z=16 needs an even number of information columns");
+      }
+      s->bgs.push_back(h);
+    }
+
+    // ---- shift tables per (bg, Z)
+    std::vector<uint32_t> tabs;
+    for (int b = 0; b < static_cast<int>(s->bgs.size()); ++b) {
+      const auto& g = s->bgs[b];
+      for (int Z : s->zset) {
+        ShapeDev sh{};
+        sh.bg = b;
+        sh.Z = Z;
+        sh.mb = g.mb;
+        sh.nb = g.nb;
+        sh.kb = g.kb;
+        sh.mc = g.mc;
+        sh.npc = g.npc;
+        sh.tab_off = static_cast<int32_t>(tabs.size());
+        const int ne = static_cast<int>(g.row.size());
+        for (int e = 0; e < ne; ++e)
+          tabs.push_back(static_cast<uint32_t>(g.col[e] * Z) | (static_cast<uint32_t>(g.V[e] % Z) << 16));
+        while ((tabs.size() - sh.tab_off) % 4) tabs.push_back(0);
+        sh.row_off = static_cast<int32_t>(tabs.size() - sh.tab_off);
+        int acc = 0;
+        for (int r = 0; r <= g.mb; ++r) {
+          tabs.push_back(static_cast<uint32_t>(acc));
+          if (r < g.mb)
+            acc += static_cast<int>(std::count(g.row.begin(), g.row.end(), r));
+        }
+        while ((tabs.size() - sh.tab_off) % 4) tabs.push_back(0);
+        sh.tab_words = static_cast<int32_t>(tabs.size() - sh.tab_off);
+        s->shape_index[{b, Z}] = static_cast<int>(s->shapes.size());
+        s->shapes.push_back(sh);
+      }
+    }
+    std::vector<uint32_t> crc_tab(256);
+    for (uint32_t v = 0; v < 256; ++v) crc_tab[v] = crc_byte_entry(v);
+    int rc;
+    if ((rc = upload(s, &s->d_tabs, tabs, nullptr, nullptr)) ||
+        (rc = upload(s, &s->d_shapes, s->shapes, nullptr, nullptr)) ||
+        (rc = upload(s, &s->d_crc_table, crc_tab, nullptr, nullptr)) ||
+        (rc = upload(s, &s->d_err, std::vector<uint32_t>(4, 0u), nullptr, nullptr))) {
+      session_free(s);
+      return rc;
+    }
+    cudaError_t e = decode_prepare(s->mode);
+    if (e != cudaSuccess) {
+      session_free(s);
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    *out = s;
+    return LDPC_OK;
+  } catch (...) {
+    return fail(LDPC_EINVAL, "unexpected host exception");
+  }
+}
+
+int ldpc_session_destroy(ldpc_session* s) { return session_free(s); }
+
+int ldpc_session_set_stream(ldpc_session* s, void* stream) {
+  if (!s) return fail(LDPC_EINVAL, "null session");
+  s->stream = static_cast<cudaStream_t>(stream);
+  return LDPC_OK;
+}
+
+int ldpc_batch_destroy(ldpc_batch* b) {
+  if (!b) return LDPC_OK;
+  cudaSetDevice(b->s->device);
+  for (void* p : b->owned) cudaFree(p);
+  b->s->allocated -= std::min(b->s->allocated, b->bytes);
+  delete b;
+  return LDPC_OK;
+}
+
+int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, const ldpc_tb_desc* tbs,
+                      int32_t n_tb, int32_t n_slots, const int32_t* slot_N, ldpc_batch** out) {
+  try {
+    if (!s || !out || (n_cb > 0 && !cbs) || n_cb < 0 || n_tb < 0 || (n_tb > 0 && !tbs) || n_slots < 0 ||
+        (n_slots > 0 && !slot_N))
+      return fail(LDPC_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    auto* b = new (std::nothrow) ldpc_batch();
+    if (!b) return fail(LDPC_ENOMEM, "host allocation");
+    b->s = s;
+    auto bail = [&](int code, const std::string& msg) {
+      ldpc_batch_destroy(b);
+      return fail(code, msg);
+    };
+    const int esz = s->mode == LDPC_F32 ? 4 : (s->mode == LDPC_I8 ? 1 : 2);
+    int64_t sym_end = 0, mask_end = 0, llr_end = 0, bits_end = 0, info_bits = 0;
+    b->cbs.resize(n_cb);
+    for (int i = 0; i < n_cb; ++i) {
+      const ldpc_cb_desc& c = cbs[i];
+      const std::string at = "code block " + std::to_string(i) + ": ";
+      if (c.bg < 0 || c.bg >= static_cast<int>(s->bgs.size())) return bail(LDPC_EINVAL, at + "bad base graph");
+      auto it = s->shape_index.find({c.bg, c.Z});
+      if (it == s->shape_index.end()) return bail(LDPC_EINVAL, at + "Z not in the session's Z set");
+      if (c.Qm != 2 && c.Qm != 4 && c.Qm != 6 && c.Qm != 8) return bail(LDPC_EINVAL, at + "Qm must be 2/4/6/8");
+      const auto& g = s->bgs[c.bg];
+      const int t0 = g.npc * c.Z;
+      if (c.E <= 0 || c.E % c.Qm || t0 + c.E > g.nb * c.Z)
+        return bail(LDPC_EINVAL, at + "E must be a positive multiple of Qm with t0 + E <= nb*Z");
+      if (c.re_offset < 0 || c.mask_word_offset < 0 || c.llr_offset < 0 || c.bits_word_offset < 0 || c.reserved)
+        return bail(LDPC_EINVAL, at + "negative offset or nonzero reserved field");
+      if ((c.llr_offset * esz) % 16) return bail(LDPC_EINVAL, at + "llr_offset must be 16-byte aligned");
+      if ((g.kb * c.Z) % 32) return bail(LDPC_EINVAL, at + "kb*Z must be a multiple of 32");
+      if (!(c.inv_sigma2 >= 0.f)) return bail(LDPC_EINVAL, at + "inv_sigma2 must be >= 0");
+      const int cols = (c.E + t0 + c.Z - 1) / c.Z;
+      const int m_eff = std::min(g.mb, std::max(g.mc, cols - g.kb));
+      if (g.maxcol_upto[m_eff - 1] >= g.kb + m_eff)
+        return bail(LDPC_EINVAL, at + "a decoded row uses a column beyond the decoded ones (base graph order)");
+      CbDev d{};
+      d.shape = it->second;
+      d.Z = c.Z;
+      d.Qm = c.Qm;
+      d.E = c.E;
+      d.t0 = t0;
+      d.m_eff = m_eff;
+      d.n_eff = g.kb + m_eff;
+      d.n_re = c.E / c.Qm;
+      d.kb = g.kb;
+      d.re_off = c.re_offset;
+      d.mask_off = c.mask_word_offset;
+      d.llr_off = c.llr_offset;
+      d.bits_off = c.bits_word_offset;
+      d.inv_sigma2 = c.inv_sigma2;
+      b->cbs[i] = d;
+      sym_end = std::max<int64_t>(sym_end, c.re_offset + d.n_re);
+      mask_end = std::max<int64_t>(mask_end, c.mask_word_offset + (d.n_re + 31) / 32);
+      llr_end = std::max<int64_t>(llr_end, c.llr_offset + static_cast<int64_t>(d.n_eff) * c.Z);
+      bits_end = std::max<int64_t>(bits_end, c.bits_word_offset + g.kb * c.Z / 32);
+      info_bits += static_cast<int64_t>(g.kb) * c.Z;
+    }
+    int rc = upload(s, &b->d_cbs, b->cbs, &b->owned, &b->bytes);
+    if (rc) return bail(rc, g_err);
+
+    // ---- decoder plan: one launch per Z, items of G same-shape code blocks
+    std::map<int, std::vector<int>> by_z;
+    for (int i = 0; i < n_cb; ++i) by_z[b->cbs[i].Z].push_back(i);
+    std::vector<DecodeItem> items;
+    std::vector<int32_t> item_cbs;
+    int64_t scratch_total = 0;
+    for (auto& kv : by_z) {
+      const int Z = kv.first;
+      auto& idx = kv.second;
+      // same shape together, larger m_eff first
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        if (b->cbs[x].shape != b->cbs[y].shape) return b->cbs[x].shape < b->cbs[y].shape;
+        return b->cbs[x].m_eff > b->cbs[y].m_eff;
+      });
+      int max_n = 0, max_m = 0, tab_words = 0;
+      for (int i : idx) {
+        max_n = std::max(max_n, b->cbs[i].n_eff);
+        max_m = std::max(max_m, b->cbs[i].m_eff);
+        tab_words = std::max(tab_words, s->shapes[b->cbs[i].shape].tab_words);
+      }
+      const int msz = s->mode == LDPC_F32 ? 4 : (s->mode == LDPC_I8 ? 1 : 2);
+      Launch L;
+      L.Z = Z;
+      L.rec_cap = max_m * Z;
+      L.L_bytes = align16(max_n * Z * esz);
+      const int rec_bytes = 2 * align16(L.rec_cap * msz) + align16(L.rec_cap * 4);
+      L.hdr_bytes = align16(tab_words * 4) + 16;
+      int G = std::max(1, 256 / Z);
+      if (Z > 32) G = std::min(G, 15);
+      L.rglobal = false;
+      while (G > 1 && L.hdr_bytes + G * (L.L_bytes + rec_bytes) > kMaxSmem) --G;
+      if (Z == 16 && G > 1 && (G & 1)) --G;
+      if (L.hdr_bytes + G * (L.L_bytes + rec_bytes) > kMaxSmem) L.rglobal = true;
+      L.region_bytes = L.rglobal ? L.L_bytes : L.L_bytes + rec_bytes;
+      if (L.hdr_bytes + G * L.region_bytes > kMaxSmem)
+        return bail(LDPC_EINVAL, "Z=" + std::to_string(Z) + ": code block too large for shared memory");
+      L.G = G;
+      L.block = G * Z;
+      L.smem = L.hdr_bytes + G * L.region_bytes;
+      L.item_begin = static_cast<int>(items.size());
+      for (size_t p = 0; p < idx.size();) {
+        DecodeItem it{};
+        it.shape = b->cbs[idx[p]].shape;
+        it.first = static_cast<int32_t>(item_cbs.size());
+        int cnt = 0;
+        while (p < idx.size() && cnt < G && b->cbs[idx[p]].shape == it.shape) {
+          item_cbs.push_back(idx[p]);
+          ++p;
+          ++cnt;
+        }
+        it.count = cnt;
+        items.push_back(it);
+      }
+      L.item_count = static_cast<int>(items.size()) - L.item_begin;
+      int per_sm = 0;
+      cudaError_t e = decode_occupancy(s->mode, L.rglobal, L.block, L.smem, &per_sm);
+      if (e != cudaSuccess) return bail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+      if (per_sm < 1) return bail(LDPC_EINVAL, "decoder launch does not fit an SM");
+      L.grid = std::min(L.item_count, per_sm * s->num_sms);
+      if (L.rglobal) {
+        L.rscratch_group = rec_bytes;
+        L.rscratch_off = scratch_total;
+        scratch_total += static_cast<int64_t>(L.grid) * G * rec_bytes;
+      }
+      b->launches.push_back(L);
+    }
+    if ((rc = upload(s, &b->d_items, items, &b->owned, &b->bytes)) ||
+        (rc = upload(s, &b->d_item_cbs, item_cbs, &b->owned, &b->bytes)))
+      return bail(rc, g_err);
+    if (scratch_total > 0) {
+      if ((rc = dev_alloc(s, &b->d_rscratch, static_cast<size_t>(scratch_total), &b->owned, &b->bytes)))
+        return bail(rc, g_err);
+      b->rscratch_bytes = scratch_total;
+    }
+
+    // ---- demap tiles
+    std::vector<DemapTile> tiles;
+    for (int i = 0; i < n_cb; ++i)
+      for (int r = 0; r < std::max(1, b->cbs[i].n_re); r += kDemapBlock) tiles.push_back({i, r});
+    b->n_tiles = static_cast<int>(tiles.size());
+    if ((rc = upload(s, &b->d_tiles, tiles, &b->owned, &b->bytes))) return bail(rc, g_err);
+
+    // ---- transport blocks and slots
+    if (n_tb > 0) {
+      std::vector<TbDev> tv(n_tb);
+      std::vector<std::vector<int>> per_slot(n_slots);
+      int max_words = 0;
+      for (int t = 0; t < n_tb; ++t) {
+        const ldpc_tb_desc& x = tbs[t];
+        const std::string at = "transport block " + std::to_string(t) + ": ";
+        if (x.first_cb < 0 || x.n_cb < 1 || x.first_cb + x.n_cb > n_cb || x.slot < 0 || x.slot >= n_slots ||
+            x.n_sc < 0)
+          return bail(LDPC_EINVAL, at + "bad code-block range, slot or n_sc");
+        int64_t bits = 0;
+        for (int i = x.first_cb; i < x.first_cb + x.n_cb; ++i)
+          bits += static_cast<int64_t>(b->cbs[i].kb) * b->cbs[i].Z;
+        if (x.payload_bits != bits - 24) return bail(LDPC_EINVAL, at + "payload_bits must be sum(K) - 24");
+        tv[t] = TbDev{x.first_cb, x.n_cb, x.n_sc, x.slot, x.payload_bits, static_cast<int32_t>(bits / 32)};
+        max_words = std::max(max_words, static_cast<int>(bits / 32));
+        per_slot[x.slot].push_back(t);
+      }
+      std::vector<int32_t> start(n_slots + 1, 0), list;
+      for (int sl = 0; sl < n_slots; ++sl) {
+        start[sl] = static_cast<int32_t>(list.size());
+        for (int t : per_slot[sl]) list.push_back(t);
+        if (slot_N[sl] <= 0) return bail(LDPC_EINVAL, "slot_N must be positive");
+      }
+      start[n_slots] = static_cast<int32_t>(list.size());
+      std::vector<int32_t> sn(slot_N, slot_N + n_slots);
+      if ((rc = upload(s, &b->d_tbs, tv, &b->owned, &b->bytes)) ||
+          (rc = upload(s, &b->d_slot_start, start, &b->owned, &b->bytes)) ||
+          (rc = upload(s, &b->d_slot_tbs, list, &b->owned, &b->bytes)) ||
+          (rc = upload(s, &b->d_slot_N, sn, &b->owned, &b->bytes)) ||
+          (rc = upload(s, &b->d_xpow32, xpow32_table(max_words), &b->owned, &b->bytes)))
+        return bail(rc, g_err);
+    }
+
+    b->info.sym_elems = sym_end;
+    b->info.mask_words = mask_end;
+    b->info.llr_elems = llr_end;
+    b->info.bits_words = bits_end;
+    b->info.n_cb = n_cb;
+    b->info.n_tb = n_tb;
+    b->info.n_slots = n_tb > 0 ? n_slots : 0;
+    b->info.n_items = static_cast<int32_t>(items.size());
+    b->info.info_bits = info_bits;
+    *out = b;
+    return LDPC_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(LDPC_ENOMEM, "host allocation");
+  } catch (...) {
+    return fail(LDPC_EINVAL, "unexpected host exception");
+  }
+}
+
+int ldpc_batch_info_get(const ldpc_batch* b, ldpc_batch_info* out) {
+  if (!b || !out) return fail(LDPC_EINVAL, "null argument");
+  *out = b->info;
+  return LDPC_OK;
+}
+
+int puncture_demap(ldpc_session* s, const ldpc_batch* b, const void* sym_dev, const uint32_t* mask_dev,
+                   void* llr_dev) {
+  if (!s || !b || b->s != s) return fail(LDPC_EINVAL, "batch does not belong to this session");
+  if (b->info.n_cb == 0) return LDPC_OK;
+  if (!sym_dev || !mask_dev || !llr_dev) return fail(LDPC_EINVAL, "null buffer");
+  if (reinterpret_cast<uintptr_t>(sym_dev) % 8) return fail(LDPC_EINVAL, "symbol buffer must be 8-byte aligned");
+  DemapArgs a{};
+  a.cbs = b->d_cbs;
+  a.tiles = b->d_tiles;
+  a.sym = static_cast<const float2*>(sym_dev);
+  a.mask = mask_dev;
+  a.llr = llr_dev;
+  a.interleave = s->interleave;
+  a.q_scale = s->q_scale;
+  a.llr_sat = static_cast<float>(s->llr_sat);
+  cudaError_t e = launch_demap(s->mode, b->n_tiles, s->stream, a);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "puncture_demap launch");
+}
+
+int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint32_t* bits_dev,
+                 int32_t* status_dev) {
+  if (!s || !b || b->s != s) return fail(LDPC_EINVAL, "batch does not belong to this session");
+  if (b->info.n_cb == 0) return LDPC_OK;
+  if (!llr_dev || !bits_dev || !status_dev) return fail(LDPC_EINVAL, "null buffer");
+  if (reinterpret_cast<uintptr_t>(llr_dev) % 16) return fail(LDPC_EINVAL, "LLR buffer must be 16-byte aligned");
+  for (const Launch& L : b->launches) {
+    DecodeArgs a{};
+    a.shapes = s->d_shapes;
+    a.tabs = s->d_tabs;
+    a.cbs = b->d_cbs;
+    a.item_cbs = b->d_item_cbs;
+    a.items = b->d_items + L.item_begin;
+    a.n_items = L.item_count;
+    a.Z = L.Z;
+    a.llr = llr_dev;
+    a.bits = bits_dev;
+    a.status = status_dev;
+    a.err = s->d_err;
+    a.rscratch = b->d_rscratch ? b->d_rscratch + L.rscratch_off : nullptr;
+    a.rscratch_group = L.rscratch_group;
+    a.G = L.G;
+    a.hdr_bytes = L.hdr_bytes;
+    a.region_bytes = L.region_bytes;
+    a.L_bytes = L.L_bytes;
+    a.rec_cap = L.rec_cap;
+    a.max_iter = s->max_iter;
+    a.early_term = s->early_term;
+    if (s->mode == LDPC_F32) {
+      a.beta = s->beta_f32;
+      a.msg_sat = 3.0e38f;
+      a.post_sat = 3.0e38f;
+    } else {
+      a.beta = static_cast<float>(s->offset_lsb);
+      a.msg_sat = static_cast<float>(s->msg_sat);
+      a.post_sat = static_cast<float>(s->post_sat);
+    }
+    cudaError_t e = launch_decode(s->mode, L.rglobal, dim3(L.grid), dim3(L.block), L.smem, s->stream, a);
+    if (e != cudaSuccess) return cuda_fail(e, "decode_batch launch");
+  }
+  return LDPC_OK;
+}
+
+int tb_crc_goodput(ldpc_session* s, const ldpc_batch* b, const uint32_t* bits_dev, uint8_t* d_dev,
+                   uint64_t* goodput_bits_dev, uint32_t* goodput_sc_dev, float* reward_dev) {
+  if (!s || !b || b->s != s) return fail(LDPC_EINVAL, "batch does not belong to this session");
+  if (b->info.n_tb == 0) return fail(LDPC_EINVAL, "batch has no transport blocks");
+  if (!bits_dev || !d_dev || !goodput_bits_dev || !goodput_sc_dev || !reward_dev)
+    return fail(LDPC_EINVAL, "null buffer");
+  CrcArgs a{};
+  a.tbs = b->d_tbs;
+  a.cbs = b->d_cbs;
+  a.slot_start = b->d_slot_start;
+  a.slot_tbs = b->d_slot_tbs;
+  a.slot_N = b->d_slot_N;
+  a.crc_table = s->d_crc_table;
+  a.xpow32 = b->d_xpow32;
+  a.bits = bits_dev;
+  a.d = d_dev;
+  a.goodput_bits = goodput_bits_dev;
+  a.goodput_sc = goodput_sc_dev;
+  a.reward = reward_dev;
+  cudaError_t e = launch_crc(b->info.n_slots, s->stream, a);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "tb_crc_goodput launch");
+}
+
+int ldpc_device_errors(ldpc_session* s, uint32_t* flags_out) {
+  if (!s || !flags_out) return fail(LDPC_EINVAL, "null argument");
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  uint32_t v = 0;
+  e = cudaMemcpy(&v, s->d_err, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  *flags_out = v;
+  if (v) cudaMemset(s->d_err, 0, sizeof(uint32_t));
+  return LDPC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+"""Python-side handles for ldpcgb sessions and batches.
+
+``Session`` owns an ``ldpc_session`` (shift tables, workspace, error word) on
+the current CUDA device; ``Batch`` owns an ``ldpc_batch`` (validated
+descriptors and the decoder's work plan).  Compute methods take torch CUDA
+tensors, check their dtype, device and size against the batch, bind the
+session to torch's current stream and call the C-ABI.  Nothing here computes
+any step of the receive path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import abi
+
+LLR_TORCH = {"f32": torch.float32, "i8": torch.int8, "i16": torch.int16}
+DEFAULT_SAT = {"f32": (0, 0, 0), "i8": (63, 63, 127), "i16": (1023, 1023, 32767)}
+
+
+def _as_struct_array(arr: np.ndarray, np_dtype: np.dtype) -> np.ndarray:
+    a = np.ascontiguousarray(arr)
+    if a.dtype.itemsize != np_dtype.itemsize or set(a.dtype.names or ()) - {"_pad"} - set(np_dtype.names):
+        raise TypeError("descriptor array does not match the C layout")
+    out = np.zeros(a.shape[0], dtype=np_dtype)
+    for name in np_dtype.names:
+        src = "_pad" if (name == "reserved" and "reserved" not in a.dtype.names) else name
+        out[name] = a[src]
+    return out
+
+
+def _check_tensor(t: torch.Tensor, dtype, min_elems: int, name: str, device) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if t.device.type != "cuda" or (device is not None and t.device.index != device):
+        raise ValueError(f"{name}: must live on cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() < min_elems:
+        raise ValueError(f"{name}: {t.numel()} elements, the batch needs {min_elems}")
+    return t.data_ptr()
+
+
+class Batch:
+    def __init__(self, session: "Session", handle: int, info: abi.BatchInfoC):
+        self.session = session
+        self.handle = handle
+        self.info = info
+
+    def close(self) -> None:
+        if self.handle:
+            abi.check(abi.load().ldpc_batch_destroy(self.handle), "ldpc_batch_destroy")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # sizes the caller's buffers must have
+    @property
+    def n_cb(self) -> int:
+        return self.info.n_cb
+
+    @property
+    def info_bits(self) -> int:
+        return self.info.info_bits
+
+    def alloc_outputs(self, device=None) -> dict:
+        dev = torch.device("cuda", self.session.device if device is None else device)
+        i = self.info
+        return dict(
+            llr=torch.empty(i.llr_elems, dtype=LLR_TORCH[self.session.mode], device=dev),
+            bits=torch.empty(i.bits_words, dtype=torch.int32, device=dev),
+            status=torch.empty(i.n_cb, dtype=torch.int32, device=dev),
+            d=torch.empty(max(i.n_tb, 1), dtype=torch.uint8, device=dev),
+            goodput_bits=torch.empty(max(i.n_slots, 1), dtype=torch.int64, device=dev),
+            goodput_sc=torch.empty(max(i.n_slots, 1), dtype=torch.int32, device=dev),
+            reward=torch.empty(max(i.n_slots, 1), dtype=torch.float32, device=dev),
+        )
+
+
+class Session:
+    """One decoder configuration on one CUDA device."""
+
+    def __init__(self, base_graphs, z_set, mode: str = "f32", max_iter: int = 10, early_term: bool = True,
+                 offset_f32: float = 0.5, offset_lsb: int = 1, q_scale: float = 4.0, sat=None,
+                 interleave: bool = True, mem_budget: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("ldpcgb needs a CUDA device; there is no CPU path")
+        lib = abi.load()
+        self.mode = mode
+        self.device = torch.cuda.current_device()
+        llr_sat, msg_sat, post_sat = DEFAULT_SAT[mode] if sat is None else sat
+        self._keep = []
+        bgs = (abi.BaseGraphC * len(base_graphs))()
+        for i, g in enumerate(base_graphs):
+            row = np.ascontiguousarray(g.row, dtype=np.int16)
+            col = np.ascontiguousarray(g.col, dtype=np.int16)
+            V = np.ascontiguousarray(g.V, dtype=np.int16)
+            self._keep += [row, col, V]
+            p16 = ctypes.POINTER(ctypes.c_int16)
+            bgs[i] = abi.BaseGraphC(g.mb, g.nb, g.kb, g.mc, g.n_punct_cols, row.size,
+                                    row.ctypes.data_as(p16), col.ctypes.data_as(p16), V.ctypes.data_as(p16))
+        zs = (ctypes.c_int32 * len(z_set))(*[int(z) for z in z_set])
+        desc = abi.SessionDescC(len(base_graphs), bgs, len(z_set), zs, abi.MODES[mode], int(max_iter),
+                                int(bool(early_term)), float(offset_f32), int(offset_lsb), float(q_scale),
+                                int(llr_sat), int(msg_sat), int(post_sat), int(bool(interleave)),
+                                int(mem_budget), None)
+        h = ctypes.c_void_p()
+        abi.check(lib.ldpc_session_create(ctypes.byref(desc), ctypes.byref(h)), "ldpc_session_create")
+        self.handle = h.value
+        self._keep = []
+
+    def close(self) -> None:
+        if getattr(self, "handle", 0):
+            abi.check(abi.load().ldpc_session_destroy(self.handle), "ldpc_session_destroy")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self) -> None:
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        abi.check(abi.load().ldpc_session_set_stream(self.handle, s), "ldpc_session_set_stream")
+
+    def batch(self, cbs: np.ndarray, tbs: np.ndarray | None = None, slot_N=None) -> Batch:
+        lib = abi.load()
+        c = _as_struct_array(cbs, abi.CB_NP)
+        t = _as_struct_array(tbs, abi.TB_NP) if tbs is not None and len(tbs) else np.zeros(0, abi.TB_NP)
+        sn = np.ascontiguousarray(np.zeros(0) if slot_N is None else slot_N, dtype=np.int32)
+        h = ctypes.c_void_p()
+        abi.check(lib.ldpc_batch_create(self.handle, c.ctypes.data, c.size, t.ctypes.data if t.size else None,
+                                        t.size, sn.size, sn.ctypes.data if sn.size else None, ctypes.byref(h)),
+                  "ldpc_batch_create")
+        info = abi.BatchInfoC()
+        abi.check(lib.ldpc_batch_info_get(h.value, ctypes.byref(info)), "ldpc_batch_info_get")
+        return Batch(self, h.value, info)
+
+    # ------------------------------------------------------------------ compute
+    def puncture_demap(self, b: Batch, sym: torch.Tensor, mask: torch.Tensor, llr: torch.Tensor) -> None:
+        i = b.info
+        ps = _check_tensor(sym, torch.complex64, i.sym_elems, "sym", self.device)
+        pm = _check_tensor(mask, torch.int32, i.mask_words, "mask", self.device)
+        pl = _check_tensor(llr, LLR_TORCH[self.mode], i.llr_elems, "llr", self.device)
+        self._bind_stream()
+        abi.check(abi.load().puncture_demap(self.handle, b.handle, ps, pm, pl), "puncture_demap")
+
+    def decode_batch(self, b: Batch, llr: torch.Tensor, bits: torch.Tensor, status: torch.Tensor) -> None:
+        i = b.info
+        pl = _check_tensor(llr, LLR_TORCH[self.mode], i.llr_elems, "llr", self.device)
+        pb = _check_tensor(bits, torch.int32, i.bits_words, "bits", self.device)
+        pst = _check_tensor(status, torch.int32, i.n_cb, "status", self.device)
+        self._bind_stream()
+        abi.check(abi.load().decode_batch(self.handle, b.handle, pl, pb, pst), "decode_batch")
+
+    def tb_crc_goodput(self, b: Batch, bits: torch.Tensor, d: torch.Tensor, goodput_bits: torch.Tensor,
+                       goodput_sc: torch.Tensor, reward: torch.Tensor) -> None:
+        i = b.info
+        pb = _check_tensor(bits, torch.int32, i.bits_words, "bits", self.device)
+        pd = _check_tensor(d, torch.uint8, i.n_tb, "d", self.device)
+        pg = _check_tensor(goodput_bits, torch.int64, i.n_slots, "goodput_bits", self.device)
+        pgs = _check_tensor(goodput_sc, torch.int32, i.n_slots, "goodput_sc", self.device)
+        pr = _check_tensor(reward, torch.float32, i.n_slots, "reward", self.device)
+        self._bind_stream()
+        abi.check(abi.load().tb_crc_goodput(self.handle, b.handle, pb, pd, pg, pgs, pr), "tb_crc_goodput")
+
+    def run(self, b: Batch, sym: torch.Tensor, mask: torch.Tensor, out: dict) -> dict:
+        """The whole path: puncture_demap -> decode_batch -> tb_crc_goodput (if the batch has TBs)."""
+        self.puncture_demap(b, sym, mask, out["llr"])
+        self.decode_batch(b, out["llr"], out["bits"], out["status"])
+        if b.info.n_tb:
+            self.tb_crc_goodput(b, out["bits"], out["d"], out["goodput_bits"], out["goodput_sc"], out["reward"])
+        return out
+
+    def device_errors(self) -> int:
+        v = ctypes.c_uint32()
+        abi.check(abi.load().ldpc_device_errors(self.handle, ctypes.byref(v)), "ldpc_device_errors")
+        return int(v.value)

@@ -378,3 +378,43 @@ def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int 
               noiseless=noiseless)
     w.meta.update(dict(max_iter=10, early_term=1, mode="i8", offset=0.5))
     return w
+
+
+def subset(w: Workload, tb_index) -> Workload:
+    """A workload holding only the listed transport blocks (offsets re-based, slots renumbered)."""
+    tb_index = list(tb_index)
+    cb_rows, tb_rows, slots = [], [], {}
+    sym, mask, info = [], [], []
+    re_off = mask_off = llr_off = bits_off = 0
+    snr = []
+    for t in tb_index:
+        tb = w.tbs[t]
+        s_new = slots.setdefault(int(tb["slot"]), len(slots))
+        tb_rows.append((len(cb_rows), int(tb["n_cb"]), int(tb["n_sc"]), s_new, int(tb["payload_bits"])))
+        for i in range(int(tb["first_cb"]), int(tb["first_cb"]) + int(tb["n_cb"])):
+            c = w.cbs[i]
+            bg, Z, t0, m_eff, n_eff = w.cb_geometry(i)
+            n_re = int(c["E"]) // int(c["Qm"])
+            nmw = -(-n_re // 32)
+            kw = bg.kb * Z // 32
+            sym.append(w.sym[int(c["re_offset"]):int(c["re_offset"]) + n_re])
+            mask.append(w.mask[int(c["mask_word_offset"]):int(c["mask_word_offset"]) + nmw])
+            info.append(w.info_words[int(c["bits_word_offset"]):int(c["bits_word_offset"]) + kw])
+            cb_rows.append((int(c["bg"]), Z, int(c["Qm"]), int(c["E"]), re_off, mask_off, llr_off, bits_off,
+                            c["inv_sigma2"], 0))
+            if w.snr_db is not None:
+                snr.append(w.snr_db[i])
+            re_off += n_re
+            mask_off += nmw
+            llr_off += n_eff * Z
+            bits_off += kw
+    slot_N = np.zeros(len(slots), dtype=np.int32)
+    for old, new in slots.items():
+        slot_N[new] = w.slot_N[old]
+    out = Workload(w.name + "_subset", w.bgs, w.z_set, np.array(cb_rows, dtype=CB_DTYPE),
+                   np.array(tb_rows, dtype=TB_DTYPE), slot_N,
+                   np.concatenate(sym) if sym else np.zeros(0, np.complex64),
+                   np.concatenate(mask) if mask else np.zeros(0, np.uint32),
+                   np.concatenate(info) if info else np.zeros(0, np.uint32), llr_off, bits_off,
+                   snr_db=np.array(snr) if snr else None, meta=dict(w.meta))
+    return out
