@@ -43,12 +43,12 @@ def _oracle_chunk(args):
     return int(sum(w.bgs[int(c["bg"])].kb * int(c["Z"]) for c in w.cbs)), int((out["d"] == 0).sum())
 
 
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rank: int = 0, n: int | None = None):
     from workload import large_fp32, mixed, tiny_fp32
     if name == "large":
-        return large_fp32(seed=2 + 1000 * rank)
+        return large_fp32(n_cw=n or 4096, seed=2 + 1000 * rank)
     if name == "mixed":
-        return mixed(seed=3 + 1000 * rank)
+        return mixed(n_slots=n or 512, seed=3 + 1000 * rank)
     if name == "tiny":
         return tiny_fp32(seed=1000 * rank)
     raise ValueError(name)
@@ -189,7 +189,10 @@ def main():
     ap.add_argument("--mode", default=None, choices=["f32", "i8", "i16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-int8", action="store_true")
-    ap.add_argument("--cpu-tb", type=int, default=768, help="TBs in the timed CPU-oracle sample")
+    ap.add_argument("--cpu-tb", type=int, default=1536, help="TBs in the timed CPU-oracle sample")
+    ap.add_argument("--n", type=int, default=None, help="workload size (code blocks / slots); default full")
+    ap.add_argument("--min-warmup-s", type=float, default=1.0,
+                    help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -216,7 +219,7 @@ def main():
 
     from paper_2506_00167_gb300 import Session
 
-    w = make_workload(args.config, rank)
+    w = make_workload(args.config, rank, args.n)
     mode = args.mode or w.meta.get("mode", "f32")
     mi, et = w.meta["max_iter"], bool(w.meta["early_term"])
     dev = torch.device("cuda", local)
@@ -240,6 +243,11 @@ def main():
         for _ in range(args.warmup):
             s.run(b, sym, mask, out)
         torch.cuda.synchronize()
+        t_w = time.perf_counter()
+        while time.perf_counter() - t_w < args.min_warmup_s:
+            for _ in range(4):
+                s.run(b, sym, mask, out)
+            torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]

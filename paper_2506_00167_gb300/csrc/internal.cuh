@@ -12,16 +12,21 @@
 namespace ldpcgb {
 
 constexpr int kMaxDeg = 27;      // sign bits 0..26 + 5-bit argmin index in one word
+constexpr int kMaxChunks = 7;    // edges are processed four at a time: 7 * 4 >= kMaxDeg
 constexpr int kMaxZ = 384;
 constexpr int kMaxSmem = 232448; // 227 KB dynamic shared memory per block (sm_100 family)
 constexpr int kCrcBlock = 256;
 
-// One (base graph, Z) pair.  Its table in the session's edge buffer is
-// [n_edges words: (col * Z) | (shift << 16)] [pad to 4] [mb + 1 row starts] [pad to 4].
+// One (base graph, Z) pair as one decoder launch sees it.  Its edge table is,
+// per row, chunks of four edges as 8 words: four column bases (col * Z) then
+// four shifts (V mod Z); a row's last chunk is padded with edges whose base
+// is the launch's dummy slot and whose shift is 0.  Then one word per row,
+// start | (degree << 16) (start in words from the table base); then padding
+// to a multiple of 4 words.
 struct ShapeDev {
   int32_t bg, Z, mb, nb, kb, mc, npc;
   int32_t tab_off;    // first word of this shape's table
-  int32_t row_off;    // row starts, relative to tab_off
+  int32_t row_off;    // row words, relative to tab_off
   int32_t tab_words;  // multiple of 4 (whole table, 16-byte granules)
 };
 
@@ -67,7 +72,9 @@ struct DecodeArgs {
   int32_t hdr_bytes;        // shape table + mbarrier, 16-byte multiple
   int32_t region_bytes;     // per-group shared region
   int32_t L_bytes;          // per-group posterior array (padded)
+  int32_t hb_bytes;         // per-group hard-decision bitmap (Z % 32 == 0), padded
   int32_t rec_cap;          // records per group (max m_eff * Z)
+  int32_t dummy_base;       // element index of the group's dummy posteriors (Z of them)
   int32_t max_iter, early_term;
   float beta, msg_sat, post_sat;
 };

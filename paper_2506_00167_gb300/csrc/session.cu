@@ -33,8 +33,6 @@ struct ldpc_session {
   std::vector<int> zset;
   std::vector<ldpcgb::ShapeDev> shapes;
   std::map<std::pair<int, int>, int> shape_index;  // (bg, Z) -> shape
-  uint32_t* d_tabs = nullptr;
-  ldpcgb::ShapeDev* d_shapes = nullptr;
   uint32_t* d_crc_table = nullptr;
   uint32_t* d_err = nullptr;
 };
@@ -45,7 +43,7 @@ struct Launch {
   int Z = 0, G = 1, block = 0, smem = 0, grid = 0;
   bool rglobal = false;
   int item_begin = 0, item_count = 0;
-  int hdr_bytes = 0, region_bytes = 0, L_bytes = 0, rec_cap = 0;
+  int hdr_bytes = 0, region_bytes = 0, L_bytes = 0, hb_bytes = 0, rec_cap = 0, dummy_base = 0;
   int64_t rscratch_group = 0;
   int64_t rscratch_off = 0;  // into the batch's scratch buffer
 };
@@ -59,6 +57,8 @@ struct ldpc_batch {
   ldpcgb::CbDev* d_cbs = nullptr;
   std::vector<Launch> launches;
   ldpcgb::DecodeItem* d_items = nullptr;
+  ldpcgb::ShapeDev* d_shapes = nullptr;  // per (launch, shape) edge tables
+  uint32_t* d_tabs = nullptr;
   int32_t* d_item_cbs = nullptr;
   uint8_t* d_rscratch = nullptr;
   int64_t rscratch_bytes = 0;
@@ -145,11 +145,37 @@ std::vector<uint32_t> xpow32_table(int n) {
   return t;
 }
 
+// Edge table of base graph g at lifting Z for a launch whose dummy slot is at
+// element `dummy`: per row, chunks of 4 edges (4 bases, 4 shifts), the last
+// chunk padded with (dummy, 0); then one word per row: start | deg << 16.
+void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh) {
+  sh.tab_off = static_cast<int32_t>(tabs.size());
+  std::vector<uint32_t> row_info;
+  const int ne = static_cast<int>(g.row.size());
+  int e = 0;
+  for (int r = 0; r < g.mb; ++r) {
+    std::vector<int> cols, sh_;
+    for (; e < ne && g.row[e] == r; ++e) {
+      cols.push_back(g.col[e] * Z);
+      sh_.push_back(g.V[e] % Z);
+    }
+    const int deg = static_cast<int>(cols.size());
+    const int start = static_cast<int>(tabs.size()) - sh.tab_off;
+    for (int c = 0; c < (deg + 3) / 4; ++c) {
+      for (int i = 0; i < 4; ++i) tabs.push_back(static_cast<uint32_t>(4 * c + i < deg ? cols[4 * c + i] : dummy));
+      for (int i = 0; i < 4; ++i) tabs.push_back(static_cast<uint32_t>(4 * c + i < deg ? sh_[4 * c + i] : 0));
+    }
+    row_info.push_back(static_cast<uint32_t>(start) | (static_cast<uint32_t>(deg) << 16));
+  }
+  sh.row_off = static_cast<int32_t>(tabs.size()) - sh.tab_off;
+  for (uint32_t ri : row_info) tabs.push_back(ri);
+  while ((tabs.size() - sh.tab_off) % 4) tabs.push_back(0u);
+  sh.tab_words = static_cast<int32_t>(tabs.size()) - sh.tab_off;
+}
+
 int session_free(ldpc_session* s) {
   if (!s) return LDPC_OK;
   cudaSetDevice(s->device);
-  cudaFree(s->d_tabs);
-  cudaFree(s->d_shapes);
   cudaFree(s->d_crc_table);
   cudaFree(s->d_err);
   delete s;
@@ -243,8 +269,7 @@ int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
       s->bgs.push_back(h);
     }
 
-    // ---- shift tables per (bg, Z)
-    std::vector<uint32_t> tabs;
+    // ---- (base graph, Z) pairs; their edge tables are built per batch launch
     for (int b = 0; b < static_cast<int>(s->bgs.size()); ++b) {
       const auto& g = s->bgs[b];
       for (int Z : s->zset) {
@@ -256,20 +281,6 @@ int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
         sh.kb = g.kb;
         sh.mc = g.mc;
         sh.npc = g.npc;
-        sh.tab_off = static_cast<int32_t>(tabs.size());
-        const int ne = static_cast<int>(g.row.size());
-        for (int e = 0; e < ne; ++e)
-          tabs.push_back(static_cast<uint32_t>(g.col[e] * Z) | (static_cast<uint32_t>(g.V[e] % Z) << 16));
-        while ((tabs.size() - sh.tab_off) % 4) tabs.push_back(0);
-        sh.row_off = static_cast<int32_t>(tabs.size() - sh.tab_off);
-        int acc = 0;
-        for (int r = 0; r <= g.mb; ++r) {
-          tabs.push_back(static_cast<uint32_t>(acc));
-          if (r < g.mb)
-            acc += static_cast<int>(std::count(g.row.begin(), g.row.end(), r));
-        }
-        while ((tabs.size() - sh.tab_off) % 4) tabs.push_back(0);
-        sh.tab_words = static_cast<int32_t>(tabs.size() - sh.tab_off);
         s->shape_index[{b, Z}] = static_cast<int>(s->shapes.size());
         s->shapes.push_back(sh);
       }
@@ -277,9 +288,7 @@ int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
     std::vector<uint32_t> crc_tab(256);
     for (uint32_t v = 0; v < 256; ++v) crc_tab[v] = crc_byte_entry(v);
     int rc;
-    if ((rc = upload(s, &s->d_tabs, tabs, nullptr, nullptr)) ||
-        (rc = upload(s, &s->d_shapes, s->shapes, nullptr, nullptr)) ||
-        (rc = upload(s, &s->d_crc_table, crc_tab, nullptr, nullptr)) ||
+    if ((rc = upload(s, &s->d_crc_table, crc_tab, nullptr, nullptr)) ||
         (rc = upload(s, &s->d_err, std::vector<uint32_t>(4, 0u), nullptr, nullptr))) {
       session_free(s);
       return rc;
@@ -380,6 +389,8 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
     for (int i = 0; i < n_cb; ++i) by_z[b->cbs[i].Z].push_back(i);
     std::vector<DecodeItem> items;
     std::vector<int32_t> item_cbs;
+    std::vector<ShapeDev> lshapes;  // (launch, shape) tables
+    std::vector<uint32_t> tabs;
     int64_t scratch_total = 0;
     for (auto& kv : by_z) {
       const int Z = kv.first;
@@ -393,22 +404,35 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       for (int i : idx) {
         max_n = std::max(max_n, b->cbs[i].n_eff);
         max_m = std::max(max_m, b->cbs[i].m_eff);
-        tab_words = std::max(tab_words, s->shapes[b->cbs[i].shape].tab_words);
+      }
+      // this launch's tables: padding edges point at the dummy slot after L
+      std::map<int, int> local;  // session shape -> batch shape
+      for (int i : idx) {
+        const int sh = b->cbs[i].shape;
+        if (local.count(sh)) continue;
+        ShapeDev d = s->shapes[sh];
+        build_table(s->bgs[d.bg], Z, max_n * Z, tabs, d);
+        tab_words = std::max(tab_words, d.tab_words);
+        local[sh] = static_cast<int>(lshapes.size());
+        lshapes.push_back(d);
       }
       const int msz = s->mode == LDPC_F32 ? 4 : (s->mode == LDPC_I8 ? 1 : 2);
       Launch L;
       L.Z = Z;
       L.rec_cap = max_m * Z;
-      L.L_bytes = align16(max_n * Z * esz);
+      L.dummy_base = max_n * Z;
+      L.L_bytes = align16((max_n + 1) * Z * esz);
+      L.hb_bytes = (Z % 32 == 0) ? align16(max_n * (Z / 32) * 4) : 0;
       const int rec_bytes = 2 * align16(L.rec_cap * msz) + align16(L.rec_cap * 4);
       L.hdr_bytes = align16(tab_words * 4) + 16;
       int G = std::max(1, 256 / Z);
       if (Z > 32) G = std::min(G, 15);
       L.rglobal = false;
-      while (G > 1 && L.hdr_bytes + G * (L.L_bytes + rec_bytes) > kMaxSmem) --G;
+      const int base_bytes = L.L_bytes + L.hb_bytes;
+      while (G > 1 && L.hdr_bytes + G * (base_bytes + rec_bytes) > kMaxSmem) --G;
       if (Z == 16 && G > 1 && (G & 1)) --G;
-      if (L.hdr_bytes + G * (L.L_bytes + rec_bytes) > kMaxSmem) L.rglobal = true;
-      L.region_bytes = L.rglobal ? L.L_bytes : L.L_bytes + rec_bytes;
+      if (L.hdr_bytes + G * (base_bytes + rec_bytes) > kMaxSmem) L.rglobal = true;
+      L.region_bytes = L.rglobal ? base_bytes : base_bytes + rec_bytes;
       if (L.hdr_bytes + G * L.region_bytes > kMaxSmem)
         return bail(LDPC_EINVAL, "Z=" + std::to_string(Z) + ": code block too large for shared memory");
       L.G = G;
@@ -417,10 +441,11 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       L.item_begin = static_cast<int>(items.size());
       for (size_t p = 0; p < idx.size();) {
         DecodeItem it{};
-        it.shape = b->cbs[idx[p]].shape;
+        const int sshape = b->cbs[idx[p]].shape;
+        it.shape = local[sshape];
         it.first = static_cast<int32_t>(item_cbs.size());
         int cnt = 0;
-        while (p < idx.size() && cnt < G && b->cbs[idx[p]].shape == it.shape) {
+        while (p < idx.size() && cnt < G && b->cbs[idx[p]].shape == sshape) {
           item_cbs.push_back(idx[p]);
           ++p;
           ++cnt;
@@ -442,7 +467,9 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       b->launches.push_back(L);
     }
     if ((rc = upload(s, &b->d_items, items, &b->owned, &b->bytes)) ||
-        (rc = upload(s, &b->d_item_cbs, item_cbs, &b->owned, &b->bytes)))
+        (rc = upload(s, &b->d_item_cbs, item_cbs, &b->owned, &b->bytes)) ||
+        (rc = upload(s, &b->d_shapes, lshapes, &b->owned, &b->bytes)) ||
+        (rc = upload(s, &b->d_tabs, tabs, &b->owned, &b->bytes)))
       return bail(rc, g_err);
     if (scratch_total > 0) {
       if ((rc = dev_alloc(s, &b->d_rscratch, static_cast<size_t>(scratch_total), &b->owned, &b->bytes)))
@@ -543,8 +570,8 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
   if (reinterpret_cast<uintptr_t>(llr_dev) % 16) return fail(LDPC_EINVAL, "LLR buffer must be 16-byte aligned");
   for (const Launch& L : b->launches) {
     DecodeArgs a{};
-    a.shapes = s->d_shapes;
-    a.tabs = s->d_tabs;
+    a.shapes = b->d_shapes;
+    a.tabs = b->d_tabs;
     a.cbs = b->d_cbs;
     a.item_cbs = b->d_item_cbs;
     a.items = b->d_items + L.item_begin;
@@ -560,6 +587,8 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
     a.hdr_bytes = L.hdr_bytes;
     a.region_bytes = L.region_bytes;
     a.L_bytes = L.L_bytes;
+    a.hb_bytes = L.hb_bytes;
+    a.dummy_base = L.dummy_base;
     a.rec_cap = L.rec_cap;
     a.max_iter = s->max_iter;
     a.early_term = s->early_term;
