@@ -30,7 +30,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "decoded info Gbit/s + % HBM roofline; served p99 slot latency vs 125 µs, INT8 vs FP32"
-OPS_PER_EDGE = 10  # algorithmic lane-ops per lifted edge update ("Roofline")
+ALU_OPS_PER_EDGE = 8   # minimal ALU-pipe lane-ops per lifted edge update
+ALU_LANES_PER_SM = 64  # ALU pipe (min/max/compare/select/logic): 64 lanes per clock per SM
 SAT = {"f32": None, "i8": (63, 63, 127), "i16": (1023, 1023, 32767)}
 
 
@@ -135,8 +136,8 @@ def hbm_bytes(w, mode: str) -> dict:
 
 
 def peak_alu_gops(num_sms: int, mhz: float) -> float:
-    """FP32/INT32 lane-ops per second: SMs x 128 lanes x clock."""
-    return num_sms * 128 * mhz * 1e6 / 1e9
+    """ALU-pipe lane-ops per second: SMs x 64 lanes x clock."""
+    return num_sms * ALU_LANES_PER_SM * mhz * 1e6 / 1e9
 
 
 def load_peaks():
@@ -330,13 +331,14 @@ def main():
     eu = edge_updates(w, status)
     mhz = (clocks or {}).get("sm_mhz") or sm_max_nominal
     peak_g = peak_alu_gops(num_sms, mhz)
-    achieved_g = OPS_PER_EDGE * eu / (k_ms["decode"] / 1e3) / 1e9
+    achieved_g = ALU_OPS_PER_EDGE * eu / (k_ms["decode"] / 1e3) / 1e9
     hb = hbm_bytes(w, mode)
     roof = {"bound": "alu", "achieved": achieved_g, "peak": peak_g, "unit": "Glaneop/s",
             "frac": achieved_g / peak_g, "traffic": None,
             "kernel": "oms_decode_kernel", "launch_ms": k_ms["decode"],
-            "edge_updates_per_launch": eu, "ops_per_edge_update": OPS_PER_EDGE,
-            "peak_basis": f"{num_sms} SMs x 128 lanes x {mhz:.0f} MHz (median SM clock sampled in the timed region)",
+            "edge_updates_per_launch": eu, "alu_ops_per_edge_update": ALU_OPS_PER_EDGE,
+            "peak_basis": f"ALU pipe: {num_sms} SMs x {ALU_LANES_PER_SM} lanes x {mhz:.0f} MHz "
+                          "(median SM clock sampled from warm-up through the timed region)",
             "hbm_achieved_gbs": hb["decode"] / (k_ms["decode"] / 1e3) / 1e9,
             "hbm_peak_gbs": hbm_peak, "hbm_frac": hb["decode"] / (k_ms["decode"] / 1e3) / 1e9 / hbm_peak,
             "hbm_peak_kind": peak_kind}
