@@ -202,6 +202,34 @@ LDPC_API int tb_crc_goodput(ldpc_session *s, const ldpc_batch *b, const uint32_t
                    uint8_t *d_dev, uint64_t *goodput_bits_dev, uint32_t *goodput_sc_dev,
                    float *reward_dev);
 
+/*
+ * Decode n_cb code blocks of one shape WITHOUT ALLOCATING any memory (the
+ * paper has no counterpart; this is a deployment entry point).  For callers
+ * that cannot call cudaMalloc: code running while a CUDA graph is captured or
+ * replayed, under a memory pool that forbids growth, or in a real-time loop
+ * where an allocation's latency or failure is unacceptable.  It needs no
+ * session or batch: the base graph `g` (host arrays) and the decoder settings
+ * are passed directly, with the same meaning and limits as in
+ * ldpc_session_desc and ldpc_cb_desc.  Code block i's n_eff * Z LLRs start at
+ * element i * n_eff * Z of llr_dev (float / int8 / int16 by `mode`, 16-byte
+ * aligned); its kb*Z/32 information words are written at word
+ * i * (kb*Z/32) of bits_dev and its status at status_dev[i], both as in
+ * decode_batch.  Results equal decode_batch's for the same blocks.
+ * Scratch: one fixed 24 MiB __device__ array inside the library, held by
+ * every GPU that loads it until the process exits.  The first call on a
+ * device looks up that array's address (make it before any stream capture).
+ * n_cb above 32768, or a shape whose per-block message state does not fit
+ * the array, is rejected with LDPC_EINVAL before any launch.  All calls share
+ * the array and leave their contents in it: calls that overlap on the GPU
+ * (other streams, other threads) race -- serialise them.  Enqueued on
+ * `cuda_stream` (NULL = legacy default); never calls cudaMalloc/cudaFree.
+ */
+LDPC_API int decode_uniform_noalloc(const ldpc_base_graph *g, int32_t Z, int32_t E, int32_t n_cb,
+                                    int32_t mode, int32_t max_iter, int32_t early_term,
+                                    float offset_f32, int32_t offset_lsb, int32_t msg_sat,
+                                    int32_t post_sat, const void *llr_dev, uint32_t *bits_dev,
+                                    int32_t *status_dev, void *cuda_stream);
+
 /* Synchronise the session stream and return (then clear) the device error word. */
 LDPC_API int ldpc_device_errors(ldpc_session *s, uint32_t *flags_out);
 

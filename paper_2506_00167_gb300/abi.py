@@ -24,7 +24,7 @@ EXPORTED = [
     "ldpc_session_create", "ldpc_session_destroy", "ldpc_session_set_stream",
     "ldpc_batch_create", "ldpc_batch_destroy", "ldpc_batch_info_get",
     "puncture_demap", "decode_batch", "tb_crc_goodput",
-    "ldpc_device_errors", "ldpc_last_error", "ldpc_version",
+    "ldpc_device_errors", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
 ]
 
 
@@ -106,6 +106,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.decode_batch.argtypes = [vp, vp, vp, vp, vp]
     lib.tb_crc_goodput.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.ldpc_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    lib.decode_uniform_noalloc.argtypes = [ctypes.POINTER(BaseGraphC), i32, i32, i32, i32, i32, i32,
+                                           ctypes.c_float, i32, i32, i32, vp, vp, vp, vp]
     lib.ldpc_last_error.restype = ctypes.c_char_p
     lib.ldpc_version.restype = ctypes.c_char_p
     for name in EXPORTED:
