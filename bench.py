@@ -295,6 +295,22 @@ def main():
     value = world * info_bits * args.steps / (ms / 1e3) / 1e9
     ms_step = ms / args.steps
 
+    # ---- the same step as one captured CUDA graph per step
+    from paper_2506_00167_gb300 import Graph
+    graph = Graph(s, b, sym, mask, out)
+    for _ in range(3):
+        graph.launch()
+    torch.cuda.synchronize()
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(torch.cuda.current_stream(dev))
+    for _ in range(args.steps):
+        graph.launch()
+    g1.record(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1)
+    graph.close()
+
     # ---- end to end through the public API from pinned host buffers
     res_h = {k: torch.empty_like(out[k], device="cpu").pin_memory() for k in ("d", "goodput_bits", "reward")}
     stream = torch.cuda.current_stream(dev)
@@ -381,6 +397,9 @@ def main():
                              % (w.sym.size * 8 / 1e6, hb["decode"] / 1e6),
                        "parallelism": f"replicas x{world}"},
             "codewords_per_s": world * w.n_cb * args.steps / (ms / 1e3),
+            "graph": {"ms_per_step": ms_graph / args.steps,
+                      "value": world * info_bits * args.steps / (ms_graph / 1e3) / 1e9, "unit": "Gbit/s",
+                      "decoder_launches": len(b.plan())},
             "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "int8": int8,
             "e2e": {"value": e2e_val, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches, "clocks": clocks}

@@ -57,6 +57,12 @@ typedef struct ldpc_batch ldpc_batch;     /* opaque, owned by the library */
 
 typedef enum { LDPC_F32 = 0, LDPC_I8 = 1, LDPC_I16 = 2 } ldpc_mode;
 
+/* Decoder launch plan of a batch (see ldpc_session_set_strategy). */
+#define LDPC_PLAN_MIXED 0 /* one persistent launch over every shape (plus one for global-message shapes) */
+#define LDPC_PLAN_PER_Z 1 /* one persistent launch per lifting size */
+
+typedef struct ldpc_graph ldpc_graph; /* opaque: an instantiated CUDA graph of one batch step */
+
 /*
  * One base matrix.  Edges are listed in row-major (row, col) order; at most
  * one edge per (row, col).  Row k of the Z x Z block at (row, col) with raw
@@ -144,6 +150,18 @@ LDPC_API int ldpc_session_destroy(ldpc_session *s);
 /* Rebind the session to another stream of the same device (NULL = legacy default). */
 LDPC_API int ldpc_session_set_stream(ldpc_session *s, void *cuda_stream);
 
+/* Work-item tile: code blocks of base graph `bg` at lifting size `Z` are decoded
+ * `G` per thread block (G groups of Z threads).  Tiles set here override the
+ * built-in default (256 / Z, at most 15 for Z > 32) for batches created
+ * afterwards; the planner lowers G further when shared memory requires it.
+ * An autotuner chooses them by timing candidates (paper has no counterpart). */
+typedef struct {
+  int32_t bg, Z, G;
+} ldpc_tile;
+LDPC_API int ldpc_session_set_tiles(ldpc_session *s, const ldpc_tile *tiles, int32_t n);
+/* LDPC_PLAN_MIXED (default) or LDPC_PLAN_PER_Z, for batches created afterwards. */
+LDPC_API int ldpc_session_set_strategy(ldpc_session *s, int32_t strategy);
+
 /* Validate host descriptor arrays and plan a batch: per-block geometry, the
  * decoder's work items (codeword groups of one shape), demap tiles and the
  * slot-to-TB lists.  cbs/tbs/slot_N are host arrays; slot_N[s] is N, the
@@ -154,6 +172,13 @@ LDPC_API int ldpc_batch_create(ldpc_session *s, const ldpc_cb_desc *cbs, int32_t
                       const int32_t *slot_N, ldpc_batch **out);
 LDPC_API int ldpc_batch_destroy(ldpc_batch *b);
 LDPC_API int ldpc_batch_info_get(const ldpc_batch *b, ldpc_batch_info *out);
+
+/* One decoder launch of a batch's plan. */
+typedef struct {
+  int32_t block, grid, smem, n_items, global_messages, max_groups;
+} ldpc_launch_info;
+/* Copy up to `cap` launch records into `out`; *n_launches gets the total. */
+LDPC_API int ldpc_batch_plan_get(const ldpc_batch *b, ldpc_launch_info *out, int32_t cap, int32_t *n_launches);
 
 /*
  * Puncture flushing + max-log soft demapping + rate dematching (paper
@@ -201,6 +226,22 @@ LDPC_API int decode_batch(ldpc_session *s, const ldpc_batch *b, const void *llr_
 LDPC_API int tb_crc_goodput(ldpc_session *s, const ldpc_batch *b, const uint32_t *bits_dev,
                    uint8_t *d_dev, uint64_t *goodput_bits_dev, uint32_t *goodput_sc_dev,
                    float *reward_dev);
+
+/*
+ * Capture one whole step of a batch -- puncture_demap, decode_batch and (if
+ * the batch has TBs) tb_crc_goodput on the given buffers -- into a CUDA graph
+ * and instantiate it, so a step is a single ldpc_graph_launch with no
+ * per-kernel launch overhead (the decoder's work-queue reset is a memset node
+ * inside the graph).  The buffers are baked into the graph: relaunching reads
+ * and writes the same addresses.  Capture runs on a private stream; the
+ * session's stream is unchanged afterwards.
+ */
+LDPC_API int ldpc_graph_create(ldpc_session *s, const ldpc_batch *b, const void *sym_dev,
+                               const uint32_t *mask_dev, void *llr_dev, uint32_t *bits_dev,
+                               int32_t *status_dev, uint8_t *d_dev, uint64_t *goodput_bits_dev,
+                               uint32_t *goodput_sc_dev, float *reward_dev, ldpc_graph **out);
+LDPC_API int ldpc_graph_launch(ldpc_graph *g, void *cuda_stream);
+LDPC_API int ldpc_graph_destroy(ldpc_graph *g);
 
 /*
  * Decode n_cb code blocks of one shape WITHOUT ALLOCATING any memory (the

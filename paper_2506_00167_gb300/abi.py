@@ -25,7 +25,10 @@ EXPORTED = [
     "ldpc_batch_create", "ldpc_batch_destroy", "ldpc_batch_info_get",
     "puncture_demap", "decode_batch", "tb_crc_goodput",
     "ldpc_device_errors", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
+    "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
+    "ldpc_graph_create", "ldpc_graph_launch", "ldpc_graph_destroy",
 ]
+PLAN_MIXED, PLAN_PER_Z = 0, 1
 
 
 class BaseGraphC(ctypes.Structure):
@@ -55,6 +58,15 @@ class CbDescC(ctypes.Structure):
 class TbDescC(ctypes.Structure):
     _fields_ = [("first_cb", ctypes.c_int32), ("n_cb", ctypes.c_int32), ("n_sc", ctypes.c_int32),
                 ("slot", ctypes.c_int32), ("payload_bits", ctypes.c_int32)]
+
+
+class TileC(ctypes.Structure):
+    _fields_ = [("bg", ctypes.c_int32), ("Z", ctypes.c_int32), ("G", ctypes.c_int32)]
+
+
+class LaunchInfoC(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("smem", ctypes.c_int32),
+                ("n_items", ctypes.c_int32), ("global_messages", ctypes.c_int32), ("max_groups", ctypes.c_int32)]
 
 
 class BatchInfoC(ctypes.Structure):
@@ -108,6 +120,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ldpc_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     lib.decode_uniform_noalloc.argtypes = [ctypes.POINTER(BaseGraphC), i32, i32, i32, i32, i32, i32,
                                            ctypes.c_float, i32, i32, i32, vp, vp, vp, vp]
+    lib.ldpc_session_set_tiles.argtypes = [vp, ctypes.POINTER(TileC), i32]
+    lib.ldpc_session_set_strategy.argtypes = [vp, i32]
+    lib.ldpc_batch_plan_get.argtypes = [vp, ctypes.POINTER(LaunchInfoC), i32, ctypes.POINTER(i32)]
+    lib.ldpc_graph_create.argtypes = [vp] * 11 + [ctypes.POINTER(vp)]
+    lib.ldpc_graph_launch.argtypes = [vp, vp]
+    lib.ldpc_graph_destroy.argtypes = [vp]
     lib.ldpc_last_error.restype = ctypes.c_char_p
     lib.ldpc_version.restype = ctypes.c_char_p
     for name in EXPORTED:

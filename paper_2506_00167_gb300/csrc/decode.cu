@@ -260,14 +260,11 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
+  int* s_item = reinterpret_cast<int*>(smem + a.hdr_bytes - 8);
   uint8_t* regions = smem + a.hdr_bytes;
 
   const int tid = threadIdx.x;
-  const int Z = a.Z;
-  const int g = tid / Z;
-  const int k = tid - g * Z;
   const int lane = tid & 31;
-  const uint32_t wmask = (Z >= 32) ? 0xFFFFFFFFu : (((1u << Z) - 1u) << (lane & ~(Z - 1)));
 
   if (tid == 0) {
     mbar_init(s_bar, 1);
@@ -276,9 +273,18 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
   __syncthreads();
   uint32_t phase = 0;
 
-  for (int item_i = blockIdx.x; item_i < a.n_items; item_i += gridDim.x) {
+  // items come from the work queue (largest first) or, without one, by stride
+  for (int next = blockIdx.x;; next += gridDim.x) {
+    if (tid == 0) *s_item = a.queue ? static_cast<int>(atomicAdd(a.queue, 1u)) : next;
+    __syncthreads();
+    const int item_i = *s_item;
+    if (item_i >= a.n_items) break;
     const DecodeItem item = a.items[item_i];
     const ShapeDev sh = a.shapes[item.shape];
+    const int Z = item.Z;
+    const int g = tid / Z;
+    const int k = tid - g * Z;
+    const uint32_t wmask = (Z >= 32) ? 0xFFFFFFFFu : (((1u << Z) - 1u) << (lane & ~(Z - 1)));
 
     // ---- stage the shape table and each group's LLRs (bulk copies)
     if (tid == 0) {
@@ -293,26 +299,26 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
       for (int gg = 0; gg < item.count; ++gg) {
         const CbDev cb = a.cbs[a.item_cbs[item.first + gg]];
         const LT* src = static_cast<const LT*>(a.llr) + cb.llr_off;
-        bulk_g2s(regions + gg * a.region_bytes, src, static_cast<uint32_t>(cb.n_eff * Z) * sizeof(LT), s_bar);
+        bulk_g2s(regions + gg * item.region_bytes, src, static_cast<uint32_t>(cb.n_eff * Z) * sizeof(LT), s_bar);
       }
     }
 
     const bool active = g < item.count;
     CbDev cb{};
     int cbi = 0;
-    LT* L = reinterpret_cast<LT*>(regions + g * a.region_bytes);
+    LT* L = reinterpret_cast<LT*>(regions + g * item.region_bytes);
     MT *mag1, *mag2;
     uint32_t* meta;
     if (RGLOBAL) {
       uint8_t* base = a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.G + g) * a.rscratch_group;
       mag1 = reinterpret_cast<MT*>(base);
-      mag2 = mag1 + a.rec_cap;
-      meta = reinterpret_cast<uint32_t*>(base + 2 * ((a.rec_cap * sizeof(MT) + 15) & ~15));
+      mag2 = mag1 + item.rec_cap;
+      meta = reinterpret_cast<uint32_t*>(base + 2 * ((item.rec_cap * sizeof(MT) + 15) & ~15));
     } else {
-      uint8_t* base = regions + g * a.region_bytes + a.L_bytes + a.hb_bytes;
+      uint8_t* base = regions + g * item.region_bytes + item.L_bytes + item.hb_bytes;
       mag1 = reinterpret_cast<MT*>(base);
-      mag2 = mag1 + a.rec_cap;
-      meta = reinterpret_cast<uint32_t*>(base + 2 * ((a.rec_cap * sizeof(MT) + 15) & ~15));
+      mag2 = mag1 + item.rec_cap;
+      meta = reinterpret_cast<uint32_t*>(base + 2 * ((item.rec_cap * sizeof(MT) + 15) & ~15));
     }
     if (active) {
       cbi = a.item_cbs[item.first + g];
@@ -325,9 +331,9 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
         meta[r] = 0u;
       }
       if constexpr (SAT)
-        st_val(L, a.dummy_base + k, a.post_sat);
+        st_val(L, item.dummy_base + k, a.post_sat);
       else
-        L[a.dummy_base + k] = LT(kBigF);
+        L[item.dummy_base + k] = LT(kBigF);
     }
 
     const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
 
     if (active) {
       const uint32_t* rows = s_tab + sh.row_off;
-      uint32_t* hb = reinterpret_cast<uint32_t*>(regions + g * a.region_bytes + a.L_bytes);
+      uint32_t* hb = reinterpret_cast<uint32_t*>(regions + g * item.region_bytes + item.L_bytes);
       const int m = cb.m_eff;
       const bool wide = (Z & 31) == 0;
       if constexpr (!SAT) {
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
         for (int l = 0; l < m; ++l) {
           const uint32_t info = rows[l];
           check_update<LT, MT, SAT>(s_tab + (info & 0xFFFFu), static_cast<int>(info >> 16), k, Z, L, mag1, mag2,
-                                    meta, l * Z + k, a.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
+                                    meta, l * Z + k, item.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {

@@ -41,9 +41,16 @@ struct CbDev {
 };
 
 // One decoder work item: `count` code blocks of one shape, listed from
-// item_cbs[first]; each is decoded by its own group of Z threads.
+// item_cbs[first]; each is decoded by its own group of Z threads.  The item
+// carries its own shared-memory layout, so one launch can mix lifting sizes:
+// group g's region starts at g * region_bytes and holds the posteriors
+// (L_bytes, with Z dummy slots at element dummy_base), the hard-decision
+// bitmap (hb_bytes) and, unless the launch keeps messages in global memory,
+// rec_cap compressed check records.
 struct DecodeItem {
-  int32_t shape, first, count, pad;
+  int32_t shape, first, count, Z;
+  int32_t region_bytes, L_bytes, hb_bytes, rec_cap;
+  int32_t dummy_base, pad0, pad1, pad2;
 };
 
 struct DemapTile {
@@ -61,20 +68,15 @@ struct DecodeArgs {
   const int32_t* item_cbs;
   const DecodeItem* items;
   int32_t n_items;
-  int32_t Z;
+  uint32_t* queue;          // work-queue counter (zeroed before the launch), or null: static stride
   const void* llr;
   uint32_t* bits;
   int32_t* status;
   uint32_t* err;
   uint8_t* rscratch;        // R records in global memory (RGLOBAL variant)
   int64_t rscratch_group;   // bytes per (block, group) slot
-  int32_t G;                // groups per block
-  int32_t hdr_bytes;        // shape table + mbarrier, 16-byte multiple
-  int32_t region_bytes;     // per-group shared region
-  int32_t L_bytes;          // per-group posterior array (padded)
-  int32_t hb_bytes;         // per-group hard-decision bitmap (Z % 32 == 0), padded
-  int32_t rec_cap;          // records per group (max m_eff * Z)
-  int32_t dummy_base;       // element index of the group's dummy posteriors (Z of them)
+  int32_t G;                // group slots per block in rscratch
+  int32_t hdr_bytes;        // edge table + mbarrier + item slot, 16-byte multiple
   int32_t max_iter, early_term;
   float beta, msg_sat, post_sat;
 };

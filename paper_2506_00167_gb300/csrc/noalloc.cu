@@ -45,7 +45,8 @@ static __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
 struct SetupArgs {
   uint32_t tab[kMaxTabWords];
   ShapeDev shape;
-  CbDev proto;   // geometry shared by every code block; offsets filled per block
+  CbDev proto;       // geometry shared by every code block; offsets filled per block
+  DecodeItem proto_item;  // layout shared by every work item; first/count filled per item
   int32_t n_cb, G;
   uint8_t* scratch;
 };
@@ -68,8 +69,7 @@ __global__ void noalloc_setup_kernel(const SetupArgs a) {
     reinterpret_cast<CbDev*>(base + kOffCbs)[i] = d;
     reinterpret_cast<int32_t*>(base + kOffItemCbs)[i] = i;
     if (i % a.G == 0) {
-      DecodeItem it{};
-      it.shape = 0;
+      DecodeItem it = a.proto_item;
       it.first = i;
       it.count = min(a.G, a.n_cb - i);
       reinterpret_cast<DecodeItem*>(base + kOffItems)[i / a.G] = it;
@@ -286,6 +286,15 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     proto.kb = kb;
     sa.shape = sh;
     sa.proto = proto;
+    DecodeItem pit{};
+    pit.shape = 0;
+    pit.Z = Z;
+    pit.region_bytes = region;
+    pit.L_bytes = L_bytes;
+    pit.hb_bytes = hb_bytes;
+    pit.rec_cap = rec_cap;
+    pit.dummy_base = dummy;
+    sa.proto_item = pit;
     sa.n_cb = n_cb;
     sa.G = G;
     sa.scratch = scratch;
@@ -306,7 +315,7 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     a.item_cbs = reinterpret_cast<const int32_t*>(scratch + kOffItemCbs);
     a.items = reinterpret_cast<const DecodeItem*>(scratch + kOffItems);
     a.n_items = n_items;
-    a.Z = Z;
+    a.queue = nullptr;
     a.llr = llr_dev;
     a.bits = bits_dev;
     a.status = status_dev;
@@ -315,11 +324,6 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     a.rscratch_group = rec_bytes;
     a.G = G;
     a.hdr_bytes = hdr_bytes;
-    a.region_bytes = region;
-    a.L_bytes = L_bytes;
-    a.hb_bytes = hb_bytes;
-    a.rec_cap = rec_cap;
-    a.dummy_base = dummy;
     a.max_iter = max_iter;
     a.early_term = early_term ? 1 : 0;
     if (mode == LDPC_F32) {

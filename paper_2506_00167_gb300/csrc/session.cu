@@ -33,6 +33,8 @@ struct ldpc_session {
   std::vector<int> zset;
   std::vector<ldpcgb::ShapeDev> shapes;
   std::map<std::pair<int, int>, int> shape_index;  // (bg, Z) -> shape
+  std::map<std::pair<int, int>, int> tiles;        // (bg, Z) -> code blocks per work item
+  int strategy = LDPC_PLAN_MIXED;
   uint32_t* d_crc_table = nullptr;
   uint32_t* d_err = nullptr;
 };
@@ -40,15 +42,19 @@ struct ldpc_session {
 namespace {
 
 struct Launch {
-  int Z = 0, G = 1, block = 0, smem = 0, grid = 0;
+  int G = 1, block = 0, smem = 0, grid = 0;  // G: most groups any item of the launch uses
   bool rglobal = false;
   int item_begin = 0, item_count = 0;
-  int hdr_bytes = 0, region_bytes = 0, L_bytes = 0, hb_bytes = 0, rec_cap = 0, dummy_base = 0;
+  int hdr_bytes = 0;
   int64_t rscratch_group = 0;
   int64_t rscratch_off = 0;  // into the batch's scratch buffer
 };
 
 }  // namespace
+
+struct ldpc_graph {
+  cudaGraphExec_t exec = nullptr;
+};
 
 struct ldpc_batch {
   ldpc_session* s = nullptr;
@@ -62,6 +68,7 @@ struct ldpc_batch {
   int32_t* d_item_cbs = nullptr;
   uint8_t* d_rscratch = nullptr;
   int64_t rscratch_bytes = 0;
+  uint32_t* d_queues = nullptr;  // one work-queue counter per decoder launch
   ldpcgb::DemapTile* d_tiles = nullptr;
   int n_tiles = 0;
   ldpcgb::TbDev* d_tbs = nullptr;
@@ -171,6 +178,163 @@ void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32
   for (uint32_t ri : row_info) tabs.push_back(ri);
   while ((tabs.size() - sh.tab_off) % 4) tabs.push_back(0u);
   sh.tab_words = static_cast<int32_t>(tabs.size()) - sh.tab_off;
+}
+
+int default_tile(int Z) {
+  int G = std::max(1, 256 / Z);
+  if (Z > 32) G = std::min(G, 15);  // named barriers 1..15, one per group
+  return G;
+}
+
+// Plan the decoder launches of a batch: code blocks of one (base graph, Z)
+// shape are chunked into work items of G blocks (the shape's tile, default or
+// autotuned); each shape gets one shared-memory layout sized for its largest
+// block; items go to one launch (LDPC_PLAN_MIXED: every shape whose state fits
+// shared memory, plus a second launch whose check messages live in global
+// memory) or one launch per lifting size (LDPC_PLAN_PER_Z); within a launch
+// items are ordered largest first and handed out by a work queue.
+int plan_decode(ldpc_session* s, ldpc_batch* b) {
+  const int n_cb = static_cast<int>(b->cbs.size());
+  const int esz = s->mode == LDPC_F32 ? 4 : (s->mode == LDPC_I8 ? 1 : 2);
+  struct SP {
+    int shape = 0, Z = 0, G = 1, max_n = 0, max_m = 0;
+    int L_bytes = 0, hb_bytes = 0, rec_bytes = 0, tab_words = 0;
+    bool rglobal = false;
+    std::vector<int> cbs;
+  };
+  std::map<int, SP> sps;
+  for (int i = 0; i < n_cb; ++i) sps[b->cbs[i].shape].cbs.push_back(i);
+  for (auto& kv : sps) {
+    SP& p = kv.second;
+    p.shape = kv.first;
+    const ShapeDev& sd = s->shapes[p.shape];
+    p.Z = sd.Z;
+    std::stable_sort(p.cbs.begin(), p.cbs.end(), [&](int x, int y) { return b->cbs[x].m_eff > b->cbs[y].m_eff; });
+    for (int i : p.cbs) {
+      p.max_n = std::max(p.max_n, b->cbs[i].n_eff);
+      p.max_m = std::max(p.max_m, b->cbs[i].m_eff);
+    }
+    p.L_bytes = align16((p.max_n + 1) * p.Z * esz);
+    p.hb_bytes = (p.Z % 32 == 0) ? align16(p.max_n * (p.Z / 32) * 4) : 0;
+    const int rec_cap = p.max_m * p.Z;
+    p.rec_bytes = 2 * align16(rec_cap * esz) + align16(rec_cap * 4);
+    std::vector<uint32_t> tmp;
+    ShapeDev d = sd;
+    build_table(s->bgs[sd.bg], p.Z, p.max_n * p.Z, tmp, d);
+    p.tab_words = d.tab_words;
+    auto t = s->tiles.find({sd.bg, p.Z});
+    p.G = t != s->tiles.end() ? t->second : default_tile(p.Z);
+    if (p.Z > 32) p.G = std::min(p.G, 15);
+    if (p.G * p.Z > 512) p.G = std::max(1, 512 / p.Z);
+  }
+  // launch groups
+  std::map<std::pair<int, int>, std::vector<int>> groups;  // (key, rglobal) -> shapes
+  for (auto& kv : sps) {
+    SP& p = kv.second;
+    const int hdr = align16(p.tab_words * 4) + 16;
+    while (p.G > 1 && hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem) --p.G;
+    if (p.Z == 16 && p.G > 1 && (p.G & 1)) --p.G;
+    p.rglobal = hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem;
+    if (p.rglobal && hdr + p.G * (p.L_bytes + p.hb_bytes) > kMaxSmem)
+      return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
+    const int key = s->strategy == LDPC_PLAN_PER_Z ? p.Z : 0;
+    groups[{key, p.rglobal ? 1 : 0}].push_back(kv.first);
+  }
+  std::vector<DecodeItem> items;
+  std::vector<int32_t> item_cbs;
+  std::vector<ShapeDev> lshapes;
+  std::vector<uint32_t> tabs;
+  int64_t scratch_total = 0;
+  for (auto& gkv : groups) {
+    const bool rglobal = gkv.first.second != 0;
+    Launch L;
+    L.rglobal = rglobal;
+    int tw = 0;
+    for (int sh : gkv.second) tw = std::max(tw, sps[sh].tab_words);
+    L.hdr_bytes = align16(tw * 4) + 16;
+    struct Cost {
+      double cost;
+      DecodeItem it;
+      std::vector<int32_t> cbs;
+    };
+    std::vector<Cost> list;
+    int smem = 0, block = 0, gmax = 1;
+    int64_t rec_max = 0;
+    for (int sh : gkv.second) {
+      SP& p = sps[sh];
+      const int region = p.L_bytes + p.hb_bytes + (rglobal ? 0 : p.rec_bytes);
+      while (p.G > 1 && L.hdr_bytes + p.G * region > kMaxSmem) --p.G;
+      if (L.hdr_bytes + p.G * region > kMaxSmem)
+        return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
+      ShapeDev d = s->shapes[sh];
+      build_table(s->bgs[d.bg], p.Z, p.max_n * p.Z, tabs, d);
+      const int local = static_cast<int>(lshapes.size());
+      lshapes.push_back(d);
+      smem = std::max(smem, L.hdr_bytes + p.G * region);
+      block = std::max(block, p.G * p.Z);
+      gmax = std::max(gmax, p.G);
+      rec_max = std::max<int64_t>(rec_max, p.rec_bytes);
+      const auto& g = s->bgs[d.bg];
+      for (size_t q = 0; q < p.cbs.size();) {
+        Cost c;
+        c.it = DecodeItem{};
+        c.it.shape = local;
+        c.it.Z = p.Z;
+        c.it.region_bytes = region;
+        c.it.L_bytes = p.L_bytes;
+        c.it.hb_bytes = p.hb_bytes;
+        c.it.rec_cap = p.max_m * p.Z;
+        c.it.dummy_base = p.max_n * p.Z;
+        const int m0 = b->cbs[p.cbs[q]].m_eff;
+        int cnt = 0;
+        while (q < p.cbs.size() && cnt < p.G) {
+          c.cbs.push_back(p.cbs[q]);
+          ++q;
+          ++cnt;
+        }
+        c.it.count = cnt;
+        const int edges = static_cast<int>(std::count_if(g.row.begin(), g.row.end(), [&](int r) { return r < m0; }));
+        c.cost = static_cast<double>(edges) * p.Z;  // groups run side by side: the largest block sets the time
+        list.push_back(std::move(c));
+      }
+    }
+    std::stable_sort(list.begin(), list.end(), [](const Cost& x, const Cost& y) { return x.cost > y.cost; });
+    L.item_begin = static_cast<int>(items.size());
+    for (auto& c : list) {
+      c.it.first = static_cast<int32_t>(item_cbs.size());
+      for (int i : c.cbs) item_cbs.push_back(i);
+      items.push_back(c.it);
+    }
+    L.item_count = static_cast<int>(items.size()) - L.item_begin;
+    L.G = gmax;
+    L.block = (block + 31) & ~31;
+    L.smem = smem;
+    int per_sm = 0;
+    cudaError_t e = decode_occupancy(s->mode, L.rglobal, L.block, L.smem, &per_sm);
+    if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+    if (per_sm < 1) return fail(LDPC_EINVAL, "decoder launch does not fit an SM");
+    L.grid = std::min(L.item_count, per_sm * s->num_sms);
+    if (L.rglobal) {
+      L.rscratch_group = rec_max;
+      L.rscratch_off = scratch_total;
+      scratch_total += static_cast<int64_t>(L.grid) * L.G * rec_max;
+    }
+    b->launches.push_back(L);
+  }
+  int rc;
+  if ((rc = upload(s, &b->d_items, items, &b->owned, &b->bytes)) ||
+      (rc = upload(s, &b->d_item_cbs, item_cbs, &b->owned, &b->bytes)) ||
+      (rc = upload(s, &b->d_shapes, lshapes, &b->owned, &b->bytes)) ||
+      (rc = upload(s, &b->d_tabs, tabs, &b->owned, &b->bytes)) ||
+      (rc = upload(s, &b->d_queues, std::vector<uint32_t>(std::max<size_t>(1, b->launches.size()), 0u), &b->owned,
+                   &b->bytes)))
+    return rc;
+  if (scratch_total > 0) {
+    if ((rc = dev_alloc(s, &b->d_rscratch, static_cast<size_t>(scratch_total), &b->owned, &b->bytes))) return rc;
+    b->rscratch_bytes = scratch_total;
+  }
+  b->info.n_items = static_cast<int32_t>(items.size());
+  return LDPC_OK;
 }
 
 int session_free(ldpc_session* s) {
@@ -384,98 +548,9 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
     int rc = upload(s, &b->d_cbs, b->cbs, &b->owned, &b->bytes);
     if (rc) return bail(rc, g_err);
 
-    // ---- decoder plan: one launch per Z, items of G same-shape code blocks
-    std::map<int, std::vector<int>> by_z;
-    for (int i = 0; i < n_cb; ++i) by_z[b->cbs[i].Z].push_back(i);
-    std::vector<DecodeItem> items;
-    std::vector<int32_t> item_cbs;
-    std::vector<ShapeDev> lshapes;  // (launch, shape) tables
-    std::vector<uint32_t> tabs;
-    int64_t scratch_total = 0;
-    for (auto& kv : by_z) {
-      const int Z = kv.first;
-      auto& idx = kv.second;
-      // same shape together, larger m_eff first
-      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-        if (b->cbs[x].shape != b->cbs[y].shape) return b->cbs[x].shape < b->cbs[y].shape;
-        return b->cbs[x].m_eff > b->cbs[y].m_eff;
-      });
-      int max_n = 0, max_m = 0, tab_words = 0;
-      for (int i : idx) {
-        max_n = std::max(max_n, b->cbs[i].n_eff);
-        max_m = std::max(max_m, b->cbs[i].m_eff);
-      }
-      // this launch's tables: padding edges point at the dummy slot after L
-      std::map<int, int> local;  // session shape -> batch shape
-      for (int i : idx) {
-        const int sh = b->cbs[i].shape;
-        if (local.count(sh)) continue;
-        ShapeDev d = s->shapes[sh];
-        build_table(s->bgs[d.bg], Z, max_n * Z, tabs, d);
-        tab_words = std::max(tab_words, d.tab_words);
-        local[sh] = static_cast<int>(lshapes.size());
-        lshapes.push_back(d);
-      }
-      const int msz = s->mode == LDPC_F32 ? 4 : (s->mode == LDPC_I8 ? 1 : 2);
-      Launch L;
-      L.Z = Z;
-      L.rec_cap = max_m * Z;
-      L.dummy_base = max_n * Z;
-      L.L_bytes = align16((max_n + 1) * Z * esz);
-      L.hb_bytes = (Z % 32 == 0) ? align16(max_n * (Z / 32) * 4) : 0;
-      const int rec_bytes = 2 * align16(L.rec_cap * msz) + align16(L.rec_cap * 4);
-      L.hdr_bytes = align16(tab_words * 4) + 16;
-      int G = std::max(1, 256 / Z);
-      if (Z > 32) G = std::min(G, 15);
-      L.rglobal = false;
-      const int base_bytes = L.L_bytes + L.hb_bytes;
-      while (G > 1 && L.hdr_bytes + G * (base_bytes + rec_bytes) > kMaxSmem) --G;
-      if (Z == 16 && G > 1 && (G & 1)) --G;
-      if (L.hdr_bytes + G * (base_bytes + rec_bytes) > kMaxSmem) L.rglobal = true;
-      L.region_bytes = L.rglobal ? base_bytes : base_bytes + rec_bytes;
-      if (L.hdr_bytes + G * L.region_bytes > kMaxSmem)
-        return bail(LDPC_EINVAL, "Z=" + std::to_string(Z) + ": code block too large for shared memory");
-      L.G = G;
-      L.block = G * Z;
-      L.smem = L.hdr_bytes + G * L.region_bytes;
-      L.item_begin = static_cast<int>(items.size());
-      for (size_t p = 0; p < idx.size();) {
-        DecodeItem it{};
-        const int sshape = b->cbs[idx[p]].shape;
-        it.shape = local[sshape];
-        it.first = static_cast<int32_t>(item_cbs.size());
-        int cnt = 0;
-        while (p < idx.size() && cnt < G && b->cbs[idx[p]].shape == sshape) {
-          item_cbs.push_back(idx[p]);
-          ++p;
-          ++cnt;
-        }
-        it.count = cnt;
-        items.push_back(it);
-      }
-      L.item_count = static_cast<int>(items.size()) - L.item_begin;
-      int per_sm = 0;
-      cudaError_t e = decode_occupancy(s->mode, L.rglobal, L.block, L.smem, &per_sm);
-      if (e != cudaSuccess) return bail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
-      if (per_sm < 1) return bail(LDPC_EINVAL, "decoder launch does not fit an SM");
-      L.grid = std::min(L.item_count, per_sm * s->num_sms);
-      if (L.rglobal) {
-        L.rscratch_group = rec_bytes;
-        L.rscratch_off = scratch_total;
-        scratch_total += static_cast<int64_t>(L.grid) * G * rec_bytes;
-      }
-      b->launches.push_back(L);
-    }
-    if ((rc = upload(s, &b->d_items, items, &b->owned, &b->bytes)) ||
-        (rc = upload(s, &b->d_item_cbs, item_cbs, &b->owned, &b->bytes)) ||
-        (rc = upload(s, &b->d_shapes, lshapes, &b->owned, &b->bytes)) ||
-        (rc = upload(s, &b->d_tabs, tabs, &b->owned, &b->bytes)))
-      return bail(rc, g_err);
-    if (scratch_total > 0) {
-      if ((rc = dev_alloc(s, &b->d_rscratch, static_cast<size_t>(scratch_total), &b->owned, &b->bytes)))
-        return bail(rc, g_err);
-      b->rscratch_bytes = scratch_total;
-    }
+    // ---- decoder plan
+    rc = plan_decode(s, b);
+    if (rc) return bail(rc, g_err);
 
     // ---- demap tiles
     std::vector<DemapTile> tiles;
@@ -526,7 +601,6 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
     b->info.n_cb = n_cb;
     b->info.n_tb = n_tb;
     b->info.n_slots = n_tb > 0 ? n_slots : 0;
-    b->info.n_items = static_cast<int32_t>(items.size());
     b->info.info_bits = info_bits;
     *out = b;
     return LDPC_OK;
@@ -535,6 +609,91 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
   } catch (...) {
     return fail(LDPC_EINVAL, "unexpected host exception");
   }
+}
+
+int ldpc_session_set_tiles(ldpc_session* s, const ldpc_tile* tiles, int32_t n) {
+  if (!s || n < 0 || (n > 0 && !tiles)) return fail(LDPC_EINVAL, "bad tile arguments");
+  for (int i = 0; i < n; ++i) {
+    const ldpc_tile& t = tiles[i];
+    if (t.bg < 0 || t.bg >= static_cast<int>(s->bgs.size()) || !s->shape_index.count({t.bg, t.Z}) || t.G < 1 ||
+        t.G * t.Z > 512 || (t.Z > 32 && t.G > 15))
+      return fail(LDPC_EINVAL, "tile " + std::to_string(i) + ": unknown (bg, Z) or G out of range");
+  }
+  for (int i = 0; i < n; ++i) s->tiles[{tiles[i].bg, tiles[i].Z}] = tiles[i].G;
+  return LDPC_OK;
+}
+
+int ldpc_session_set_strategy(ldpc_session* s, int32_t strategy) {
+  if (!s || (strategy != LDPC_PLAN_MIXED && strategy != LDPC_PLAN_PER_Z)) return fail(LDPC_EINVAL, "bad strategy");
+  s->strategy = strategy;
+  return LDPC_OK;
+}
+
+int ldpc_batch_plan_get(const ldpc_batch* b, ldpc_launch_info* out, int32_t cap, int32_t* n_launches) {
+  if (!b || !n_launches || cap < 0 || (cap > 0 && !out)) return fail(LDPC_EINVAL, "bad arguments");
+  *n_launches = static_cast<int32_t>(b->launches.size());
+  for (int i = 0; i < std::min<int>(cap, static_cast<int>(b->launches.size())); ++i) {
+    const Launch& L = b->launches[i];
+    out[i] = ldpc_launch_info{L.block, L.grid, L.smem, L.item_count, L.rglobal ? 1 : 0, L.G};
+  }
+  return LDPC_OK;
+}
+
+int ldpc_graph_create(ldpc_session* s, const ldpc_batch* b, const void* sym_dev, const uint32_t* mask_dev,
+                      void* llr_dev, uint32_t* bits_dev, int32_t* status_dev, uint8_t* d_dev,
+                      uint64_t* goodput_bits_dev, uint32_t* goodput_sc_dev, float* reward_dev, ldpc_graph** out) {
+  if (!s || !b || !out || b->s != s) return fail(LDPC_EINVAL, "bad graph arguments");
+  *out = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  cudaStream_t saved = s->stream;
+  s->stream = cap;
+  int rc = LDPC_OK;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "cudaStreamBeginCapture");
+  } else {
+    rc = puncture_demap(s, b, sym_dev, mask_dev, llr_dev);
+    if (!rc) rc = decode_batch(s, b, llr_dev, bits_dev, status_dev);
+    if (!rc && b->info.n_tb) rc = tb_crc_goodput(s, b, bits_dev, d_dev, goodput_bits_dev, goodput_sc_dev, reward_dev);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+  }
+  s->stream = saved;
+  ldpc_graph* g = nullptr;
+  if (!rc) {
+    g = new (std::nothrow) ldpc_graph();
+    if (!g) {
+      rc = fail(LDPC_ENOMEM, "host allocation");
+    } else {
+      e = cudaGraphInstantiate(&g->exec, graph, 0);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "cudaGraphInstantiate");
+        delete g;
+        g = nullptr;
+      }
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (rc) return rc;
+  *out = g;
+  return LDPC_OK;
+}
+
+int ldpc_graph_launch(ldpc_graph* g, void* stream) {
+  if (!g) return fail(LDPC_EINVAL, "null graph");
+  cudaError_t e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int ldpc_graph_destroy(ldpc_graph* g) {
+  if (!g) return LDPC_OK;
+  cudaGraphExecDestroy(g->exec);
+  delete g;
+  return LDPC_OK;
 }
 
 int ldpc_batch_info_get(const ldpc_batch* b, ldpc_batch_info* out) {
@@ -568,7 +727,12 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
   if (b->info.n_cb == 0) return LDPC_OK;
   if (!llr_dev || !bits_dev || !status_dev) return fail(LDPC_EINVAL, "null buffer");
   if (reinterpret_cast<uintptr_t>(llr_dev) % 16) return fail(LDPC_EINVAL, "LLR buffer must be 16-byte aligned");
-  for (const Launch& L : b->launches) {
+  if (!b->launches.empty()) {
+    cudaError_t e = cudaMemsetAsync(b->d_queues, 0, b->launches.size() * sizeof(uint32_t), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decode_batch queue reset");
+  }
+  for (size_t li = 0; li < b->launches.size(); ++li) {
+    const Launch& L = b->launches[li];
     DecodeArgs a{};
     a.shapes = b->d_shapes;
     a.tabs = b->d_tabs;
@@ -576,7 +740,7 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
     a.item_cbs = b->d_item_cbs;
     a.items = b->d_items + L.item_begin;
     a.n_items = L.item_count;
-    a.Z = L.Z;
+    a.queue = b->d_queues + li;
     a.llr = llr_dev;
     a.bits = bits_dev;
     a.status = status_dev;
@@ -585,11 +749,6 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
     a.rscratch_group = L.rscratch_group;
     a.G = L.G;
     a.hdr_bytes = L.hdr_bytes;
-    a.region_bytes = L.region_bytes;
-    a.L_bytes = L.L_bytes;
-    a.hb_bytes = L.hb_bytes;
-    a.dummy_base = L.dummy_base;
-    a.rec_cap = L.rec_cap;
     a.max_iter = s->max_iter;
     a.early_term = s->early_term;
     if (s->mode == LDPC_F32) {

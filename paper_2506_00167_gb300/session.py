@@ -71,6 +71,15 @@ class Batch:
     def info_bits(self) -> int:
         return self.info.info_bits
 
+    def plan(self) -> list:
+        """The decoder launches of this batch: dicts of block, grid, smem, n_items, global_messages, max_groups."""
+        lib = abi.load()
+        n = ctypes.c_int32()
+        abi.check(lib.ldpc_batch_plan_get(self.handle, None, 0, ctypes.byref(n)), "ldpc_batch_plan_get")
+        arr = (abi.LaunchInfoC * max(1, n.value))()
+        abi.check(lib.ldpc_batch_plan_get(self.handle, arr, n.value, ctypes.byref(n)), "ldpc_batch_plan_get")
+        return [{f: getattr(arr[i], f) for f, _ in abi.LaunchInfoC._fields_} for i in range(n.value)]
+
     def alloc_outputs(self, device=None) -> dict:
         dev = torch.device("cuda", self.session.device if device is None else device)
         i = self.info
@@ -181,7 +190,64 @@ class Session:
             self.tb_crc_goodput(b, out["bits"], out["d"], out["goodput_bits"], out["goodput_sc"], out["reward"])
         return out
 
+    # ------------------------------------------------------------------ planning
+    def set_tiles(self, tiles) -> None:
+        """tiles: iterable of (bg index, Z, G) -- code blocks per decoder work item."""
+        tiles = list(tiles)
+        arr = (abi.TileC * max(1, len(tiles)))(*[abi.TileC(int(b), int(z), int(g)) for b, z, g in tiles])
+        abi.check(abi.load().ldpc_session_set_tiles(self.handle, arr, len(tiles)), "ldpc_session_set_tiles")
+
+    def set_strategy(self, strategy: str) -> None:
+        code = {"mixed": abi.PLAN_MIXED, "per_z": abi.PLAN_PER_Z}[strategy]
+        abi.check(abi.load().ldpc_session_set_strategy(self.handle, code), "ldpc_session_set_strategy")
+
+    def load_tiles(self, path: str, base_graphs) -> int:
+        """Apply tiles from an autotuner cache (see autotune.py); returns how many matched."""
+        from .autotune import tiles_from_cache
+        t = tiles_from_cache(path, base_graphs, self.mode)
+        if t:
+            self.set_tiles(t)
+        return len(t)
+
     def device_errors(self) -> int:
         v = ctypes.c_uint32()
         abi.check(abi.load().ldpc_device_errors(self.handle, ctypes.byref(v)), "ldpc_device_errors")
         return int(v.value)
+
+
+class Graph:
+    """One whole batch step (demap, decode, CRC/goodput) captured as a CUDA graph on fixed buffers."""
+
+    def __init__(self, session: Session, b: Batch, sym: torch.Tensor, mask: torch.Tensor, out: dict):
+        i = b.info
+        ptrs = [
+            _check_tensor(sym, torch.complex64, i.sym_elems, "sym", session.device),
+            _check_tensor(mask, torch.int32, i.mask_words, "mask", session.device),
+            _check_tensor(out["llr"], LLR_TORCH[session.mode], i.llr_elems, "llr", session.device),
+            _check_tensor(out["bits"], torch.int32, i.bits_words, "bits", session.device),
+            _check_tensor(out["status"], torch.int32, i.n_cb, "status", session.device),
+            _check_tensor(out["d"], torch.uint8, i.n_tb, "d", session.device),
+            _check_tensor(out["goodput_bits"], torch.int64, i.n_slots, "goodput_bits", session.device),
+            _check_tensor(out["goodput_sc"], torch.int32, i.n_slots, "goodput_sc", session.device),
+            _check_tensor(out["reward"], torch.float32, i.n_slots, "reward", session.device),
+        ]
+        self._keep = (session, b, sym, mask, out)
+        h = ctypes.c_void_p()
+        abi.check(abi.load().ldpc_graph_create(session.handle, b.handle, *ptrs, ctypes.byref(h)), "ldpc_graph_create")
+        self.handle = h.value
+        self.device = session.device
+
+    def launch(self) -> None:
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        abi.check(abi.load().ldpc_graph_launch(self.handle, s), "ldpc_graph_launch")
+
+    def close(self) -> None:
+        if getattr(self, "handle", 0):
+            abi.check(abi.load().ldpc_graph_destroy(self.handle), "ldpc_graph_destroy")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

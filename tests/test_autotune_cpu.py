@@ -1,0 +1,35 @@
+"""Autotuner bookkeeping that needs no GPU: candidate tiles, cache keys, synthetic descriptors."""
+import json
+
+import numpy as np
+
+from paper_2506_00167_gb300 import autotune as at
+from workload import default_bgs
+
+
+def test_candidates_respect_block_and_barrier_limits():
+    for Z in [16, 32, 64, 128, 256, 384]:
+        c = at.candidates(Z)
+        assert c and all(g * Z <= 512 for g in c)
+        if Z > 32:
+            assert max(c) <= 15
+        if Z == 16:
+            assert all(g % 2 == 0 for g in c)
+
+
+def test_synthetic_descriptors_are_valid_shapes():
+    bgs = default_bgs()
+    cbs = at.synthetic_cbs(bgs[0], 0, 384, 8)
+    assert np.all(cbs["E"] == 16896) and np.all(np.diff(cbs["llr_offset"]) == 46 * 384)
+    assert np.all(cbs["llr_offset"] % 16 == 0)
+
+
+def test_cache_round_trip_by_graph_hash(tmp_path):
+    bgs = default_bgs()
+    path = tmp_path / "c.json"
+    data = {"GB300|i8": {"device": "GB300", "mode": "i8", "tiles": [
+        {"bg": at.bg_key(bgs[1]), "Z": 64, "G": 3}, {"bg": "unknown", "Z": 32, "G": 8}]}}
+    path.write_text(json.dumps(data))
+    assert at.tiles_from_cache(str(path), bgs, "i8", device_name="GB300") == [(1, 64, 3)]
+    assert at.tiles_from_cache(str(path), bgs, "f32", device_name="GB300") == []
+    assert at.bg_key(bgs[0]) != at.bg_key(bgs[1])
