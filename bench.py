@@ -179,6 +179,91 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- precision sweep
+def _oracle_errors(args):
+    """Worker: block errors of the float64 oracle on one noisy sub-batch."""
+    w, mi, et = args
+    from oracle import path as opath
+    out = opath.run(w, "f64", mi, et)
+    return int(opath.block_errors(w, out["words"]).sum()), w.n_cb
+
+
+def run_precision_sweep(args):
+    """BLER per Es/N0 point: GPU float32 / INT8 / INT16 against the float64 oracle, 95 % Wilson intervals.
+
+    A pool of noiseless code blocks (the large workload's shape, URLLC masks
+    included) is encoded once; every batch draws fresh seeded AWGN for the
+    whole pool.  The GPU decodes args.sweep_n code blocks per point in all
+    three modes; the oracle decodes the first args.sweep_oracle_n of them.
+    """
+    import torch
+    from oracle.stats import wilson
+    from paper_2506_00167_gb300 import Session
+    from workload import large_fp32
+    from workload.configs import es_n0_sigma2, subset
+    from workload.rng import np_stream
+
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores)
+    torch.cuda.set_device(0)
+    n_pool = args.sweep_pool
+    w0 = large_fp32(n_cw=n_pool, noiseless=True, seed=40)
+    mi, et = w0.meta["max_iter"], bool(w0.meta["early_term"])
+    x = w0.sym.astype(np.complex128)
+    info = torch.from_numpy(w0.info_words.view(np.int32)).cuda().view(n_pool, -1)
+    mask = torch.from_numpy(w0.mask.view(np.int32)).cuda()
+    sess = {m: Session(w0.bgs, w0.z_set, mode=m, max_iter=mi, early_term=et, sat=SAT[m]) for m in ("f32", "i8", "i16")}
+    points = [float(v) for v in np.arange(args.sweep_lo, args.sweep_lo + 0.5 * 10, 0.5)]
+    rows = []
+    t_start = time.perf_counter()
+    for pi, snr in enumerate(points):
+        s2 = float(es_n0_sigma2(snr))
+        cbs = w0.cbs.copy()
+        cbs["inv_sigma2"] = np.float32(1.0 / s2)
+        batches = {m: sess[m].batch(cbs) for m in sess}
+        outs = {m: batches[m].alloc_outputs() for m in sess}
+        err = {m: 0 for m in sess}
+        iters = {m: 0 for m in sess}
+        n_done = 0
+        rng = np_stream(40, 7, pi)
+        oracle_jobs = []
+        while n_done < args.sweep_n:
+            noise = rng.standard_normal((2, x.size))
+            y = (x + np.sqrt(s2 / 2.0) * (noise[0] + 1j * noise[1])).astype(np.complex64)
+            sym = torch.from_numpy(y).cuda()
+            for m in sess:
+                s, b, o = sess[m], batches[m], outs[m]
+                s.puncture_demap(b, sym, mask, o["llr"])
+                s.decode_batch(b, o["llr"], o["bits"], o["status"])
+                err[m] += int((o["bits"].view(n_pool, -1) != info).any(dim=1).sum())
+                iters[m] += int((o["status"] & 0xFFFF).sum())
+            if n_done < args.sweep_oracle_n:
+                wn = subset(w0, range(min(n_pool, args.sweep_oracle_n - n_done)))
+                wn.sym = y[:wn.sym.size].copy()
+                wn.cbs["inv_sigma2"] = np.float32(1.0 / s2)
+                per = max(1, wn.n_tb // cores)
+                oracle_jobs.append(pool.map_async(_oracle_errors, [
+                    (subset(wn, range(i, min(wn.n_tb, i + per))), mi, et) for i in range(0, wn.n_tb, per)]))
+            n_done += n_pool
+        o_err = o_n = 0
+        for job in oracle_jobs:
+            for e_, n_ in job.get():
+                o_err += e_
+                o_n += n_
+        row = {"es_n0_db": snr, "n_gpu": n_done, "n_oracle": o_n}
+        for m in sess:
+            row[m] = {"bler": err[m] / n_done, "ci95": wilson(err[m], n_done), "mean_iters": iters[m] / n_done}
+        row["f64_oracle"] = {"bler": o_err / max(o_n, 1), "ci95": wilson(o_err, o_n)}
+        lo, hi = row["f64_oracle"]["ci95"]
+        row["f32_inside_oracle_ci"] = bool(lo <= row["f32"]["bler"] <= hi)
+        rows.append(row)
+        print(json.dumps({"point": row}), flush=True)
+    pool.close()
+    res = {"sweep": "precision", "workload": "BG1-shaped Z=384 K=8448 R=1/2 16-QAM with URLLC masks",
+           "points": rows, "wall_s": time.perf_counter() - t_start, "oracle_cores": cores}
+    print(json.dumps(res), flush=True)
+
+
 # ----------------------------------------------------------------------------- main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -195,7 +280,15 @@ def main():
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
+    ap.add_argument("--sweep", default=None, choices=["precision"],
+                    help="run a measurement sweep instead of the benchmark line")
+    ap.add_argument("--sweep-n", type=int, default=100000, help="code blocks per SNR point (GPU)")
+    ap.add_argument("--sweep-oracle-n", type=int, default=2048, help="code blocks per SNR point (oracle)")
+    ap.add_argument("--sweep-pool", type=int, default=4096, help="distinct encoded code blocks")
+    ap.add_argument("--sweep-lo", type=float, default=5.5, help="lowest Es/N0 point, dB (10 points, 0.5 dB apart)")
     args = ap.parse_args()
+    if args.sweep == "precision":
+        return run_precision_sweep(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
 
