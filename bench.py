@@ -264,6 +264,92 @@ def run_precision_sweep(args):
     print(json.dumps(res), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+def _pct(x, q):
+    return float(np.percentile(x, q)) if len(x) else None
+
+
+def run_serving(args):
+    """Replay config 5's request stream through the decode service; latency vs the 125 us slot.
+
+    40 UEs, Poisson TB requests per 125 us slot (args.serve_load TBs per UE per
+    slot, 1.0 = the configuration's rate), TBs of 1-16 code blocks of the mixed
+    shapes drawn from a pool of pre-encoded TBs with codebook URLLC puncturing;
+    INT8 service.  Beside it, the FP32 unbatched plain path: one TB at a time
+    through puncture_demap + decode_batch + tb_crc_goodput, synchronised.
+    """
+    import torch
+    from paper_2506_00167_gb300 import Server, Session, abi
+    from workload.configs import subset
+    from workload.serving import SLOT_NS, arrivals, pool_bytes, tb_pool, tb_records
+
+    torch.cuda.set_device(0)
+    t_gen = time.perf_counter()
+    w = tb_pool(args.serve_pool, seed=5)
+    raw, mask_base = pool_bytes(w)
+    host = torch.from_numpy(raw).pin_memory()
+    gen_s = time.perf_counter() - t_gen
+    kbits = np.array([w.bgs[int(w.cbs[int(tb["first_cb"])]["bg"])].kb * int(w.cbs[int(tb["first_cb"])]["Z"])
+                      * int(tb["n_cb"]) for tb in w.tbs], dtype=np.int64)
+    sess = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
+    srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000)
+    base_recs = tb_records(w, mask_base, abi.SERVE_TB_NP)
+    # warm-up
+    warm = base_recs[:64].copy()
+    warm["tag"] = np.arange(warm.size)
+    srv.replay(warm, np.zeros(warm.size, np.int64), timeout_ms=30000)
+    loads = []
+    for load in args.serve_loads:
+        t_arr, pidx = arrivals(args.serve_slots, n_ue=40, tb_per_slot=load, n_pool=w.n_tb, seed=6)
+        recs = base_recs[pidx].copy()
+        recs["tag"] = np.arange(recs.size)
+        t0 = time.perf_counter()
+        done = srv.replay(recs, t_arr, timeout_ms=60000)
+        wall = time.perf_counter() - t0
+        lat_us = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
+        bits = int(kbits[pidx].sum())
+        span_s = max(wall, args.serve_slots * SLOT_NS / 1e9)
+        loads.append({"tb_per_ue_per_slot": load, "requests": int(recs.size), "code_blocks": int(recs["n_cb"].sum()),
+                      "offered_gbps": bits / (args.serve_slots * SLOT_NS / 1e9) / 1e9,
+                      "served_gbps": bits / wall / 1e9, "wall_s": wall,
+                      "p50_us": _pct(lat_us, 50), "p99_us": _pct(lat_us, 99), "p999_us": _pct(lat_us, 99.9),
+                      "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
+                      "tb_crc_ok_frac": float(np.mean(done["d"])), "mean_max_iters": float(np.mean(done["max_iters"]))})
+        print(json.dumps({"serving_point": loads[-1]}), flush=True)
+        del span_s
+    srv.stop()
+    # FP32 unbatched plain path: one TB at a time, synchronised
+    sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
+    n_plain = min(args.serve_plain, w.n_tb)
+    per = []
+    for t in range(n_plain):
+        sub = subset(w, [t])
+        b = sess32.batch(sub.cbs, sub.tbs, sub.slot_N)
+        sym = torch.from_numpy(sub.sym.astype(np.complex64)).cuda()
+        mask = torch.from_numpy(sub.mask.view(np.int32)).cuda()
+        per.append((b, sym, mask, b.alloc_outputs(), int(kbits[t])))
+    for b, sym, mask, out, _ in per[:8]:
+        sess32.run(b, sym, mask, out)
+    torch.cuda.synchronize()
+    lat = []
+    tot_bits = 0
+    t0 = time.perf_counter()
+    for b, sym, mask, out, kb in per:
+        t1 = time.perf_counter()
+        sess32.run(b, sym, mask, out)
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t1) * 1e6)
+        tot_bits += kb
+    wall = time.perf_counter() - t0
+    plain = {"mode": "f32", "tbs": n_plain, "gbps": tot_bits / wall / 1e9, "p50_us": _pct(lat, 50),
+             "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9)}
+    res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
+                                   "mixed shapes, 128-entry URLLC codebook, INT8 service",
+                       "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
+                       "loads": loads, "fp32_unbatched_plain": plain}}
+    print(json.dumps(res), flush=True)
+
+
 # ----------------------------------------------------------------------------- main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -280,6 +366,11 @@ def main():
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
+    ap.add_argument("--serve", action="store_true", help="replay the served request stream instead")
+    ap.add_argument("--serve-slots", type=int, default=8000)
+    ap.add_argument("--serve-pool", type=int, default=1024)
+    ap.add_argument("--serve-plain", type=int, default=400)
+    ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.25, 0.5, 0.75, 1.0])
     ap.add_argument("--sweep", default=None, choices=["precision"],
                     help="run a measurement sweep instead of the benchmark line")
     ap.add_argument("--sweep-n", type=int, default=100000, help="code blocks per SNR point (GPU)")
@@ -287,6 +378,8 @@ def main():
     ap.add_argument("--sweep-pool", type=int, default=4096, help="distinct encoded code blocks")
     ap.add_argument("--sweep-lo", type=float, default=5.5, help="lowest Es/N0 point, dB (10 points, 0.5 dB apart)")
     args = ap.parse_args()
+    if args.serve:
+        return run_serving(args)
     if args.sweep == "precision":
         return run_precision_sweep(args)
     if args.warmup < 3 and args.impl == "ours":

@@ -271,6 +271,73 @@ LDPC_API int decode_uniform_noalloc(const ldpc_base_graph *g, int32_t Z, int32_t
                                     int32_t post_sat, const void *llr_dev, uint32_t *bits_dev,
                                     int32_t *status_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of TB decode requests (the paper's per-TTI receiver
+ * feedback loop, Sec. IV "UE", run as a service).  One persistent device
+ * loop (one thread block per SM) takes work items -- up to G code blocks of
+ * one TB -- from a ring in pinned host memory as soon as the host publishes
+ * them, so requests that arrive while others are decoding start on the next
+ * free SM; no kernel is launched per request.  Each item demaps its blocks'
+ * symbols straight from the caller's pinned host pool into shared memory
+ * (puncture flushing + max-log + quantisation fused into the decoder's
+ * prologue), decodes them, and the last item of a TB runs its CRC-24 check,
+ * copies the decoded bits to the caller's result pool and writes a
+ * completion record to pinned host memory.  Admission: a request is admitted
+ * only if its device-resident state (decoded bits, status words) fits the
+ * arena of arena_bytes and the rings have room; otherwise submit stops and
+ * reports how many were admitted, and the caller retries after completions
+ * free space.  Every device wait is bounded: the loop exits after
+ * idle_timeout_us without work (submit relaunches it) or when stopped.
+ * Shapes whose decoder state does not fit shared memory are rejected
+ * (LDPC_EINVAL); the integer modes fit every shape up to Z = 384.
+ */
+typedef struct ldpc_server ldpc_server;
+
+typedef struct {
+  uint64_t arena_bytes;      /* device-memory budget for admitted requests */
+  int32_t max_inflight;      /* requests admitted at once, 1..65536 */
+  int32_t idle_timeout_us;   /* device loop idles this long before exiting (e.g. 200000) */
+  const void *host_pool;     /* pinned, mapped host memory holding the requests' symbols and masks */
+  uint64_t host_pool_bytes;
+  void *result_pool;         /* pinned, mapped host memory receiving decoded bits (may be NULL) */
+  uint64_t result_pool_bytes;
+} ldpc_serve_desc;
+
+typedef struct {
+  int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16 */
+  int32_t n_sc, payload_bits;   /* n_e; payload_bits = n_cb * kb * Z - 24 */
+  float inv_sigma2;
+  int64_t sym_offset;           /* bytes into host_pool (8-aligned): n_cb * E/Qm float2, block after block */
+  int64_t mask_offset;          /* bytes into host_pool (4-aligned): n_cb * ceil(E/Qm/32) words */
+  int64_t result_offset;        /* bytes into result_pool (4-aligned) for n_cb * kb*Z/32 words, or -1 */
+  uint64_t tag;                 /* echoed in the completion */
+} ldpc_serve_tb;
+
+typedef struct {
+  uint64_t tag;
+  int32_t d;                    /* 1: the TB's CRC-24 check passed */
+  int32_t max_iters;            /* most iterations any of its code blocks ran */
+  int32_t all_syndrome_ok;      /* every code block ended with a zero syndrome */
+  int32_t status;               /* 0, or LDPC_ETIMEOUT if the service stopped before it completed */
+  int64_t t_submit_ns;          /* host steady clock at submission (replay: the scheduled arrival) */
+  int64_t t_complete_ns;        /* host steady clock when the completion was collected */
+} ldpc_serve_done;
+
+/* Allocate the arena and rings and start the device loop on a private stream. */
+LDPC_API int ldpc_serve_start(ldpc_session *s, const ldpc_serve_desc *d, ldpc_server **out);
+/* Admit requests in order until one does not fit; *n_admitted says how many were taken. */
+LDPC_API int ldpc_serve_submit(ldpc_server *srv, const ldpc_serve_tb *tbs, int32_t n, int32_t *n_admitted);
+/* Collect up to cap completions (frees their arena space). */
+LDPC_API int ldpc_serve_poll(ldpc_server *srv, ldpc_serve_done *out, int32_t cap, int32_t *n_out);
+/* Replay an arrival schedule: submit tbs[i] at arrival_ns[i] (ns after the call starts, non-decreasing),
+ * retrying admission as space frees, and collect every completion into out[0..n) in completion order.
+ * Latency = t_complete_ns - t_submit_ns with t_submit_ns the scheduled arrival.  Gives up with
+ * LDPC_ETIMEOUT if nothing completes for timeout_ms. */
+LDPC_API int ldpc_serve_replay(ldpc_server *srv, const ldpc_serve_tb *tbs, const int64_t *arrival_ns, int32_t n,
+                               ldpc_serve_done *out, int32_t timeout_ms);
+/* Stop the device loop (bounded wait) and free the server. */
+LDPC_API int ldpc_serve_stop(ldpc_server *srv);
+
 /* Synchronise the session stream and return (then clear) the device error word. */
 LDPC_API int ldpc_device_errors(ldpc_session *s, uint32_t *flags_out);
 

@@ -6,6 +6,6 @@ behind the C-ABI in ``include/ldpcgb.h`` (``libldpcgb.so``).  This package is
 the ctypes binding; it needs the built library and a CUDA device.
 """
 from .abi import LdpcError, load, CB_NP, TB_NP, MODES  # noqa: F401
-from .session import Session, Batch, Graph  # noqa: F401
+from .session import Session, Batch, Graph, Server  # noqa: F401
 
-__all__ = ["Session", "Batch", "Graph", "LdpcError", "load", "CB_NP", "TB_NP", "MODES"]
+__all__ = ["Session", "Batch", "Graph", "Server", "LdpcError", "load", "CB_NP", "TB_NP", "MODES"]

@@ -27,6 +27,7 @@ EXPORTED = [
     "ldpc_device_errors", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
     "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
     "ldpc_graph_create", "ldpc_graph_launch", "ldpc_graph_destroy",
+    "ldpc_serve_start", "ldpc_serve_submit", "ldpc_serve_poll", "ldpc_serve_replay", "ldpc_serve_stop",
 ]
 PLAN_MIXED, PLAN_PER_Z = 0, 1
 
@@ -69,6 +70,26 @@ class LaunchInfoC(ctypes.Structure):
                 ("n_items", ctypes.c_int32), ("global_messages", ctypes.c_int32), ("max_groups", ctypes.c_int32)]
 
 
+class ServeDescC(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
+                ("idle_timeout_us", ctypes.c_int32), ("host_pool", ctypes.c_void_p),
+                ("host_pool_bytes", ctypes.c_uint64), ("result_pool", ctypes.c_void_p),
+                ("result_pool_bytes", ctypes.c_uint64)]
+
+
+class ServeTbC(ctypes.Structure):
+    _fields_ = [("bg", ctypes.c_int32), ("Z", ctypes.c_int32), ("Qm", ctypes.c_int32), ("E", ctypes.c_int32),
+                ("n_cb", ctypes.c_int32), ("n_sc", ctypes.c_int32), ("payload_bits", ctypes.c_int32),
+                ("inv_sigma2", ctypes.c_float), ("sym_offset", ctypes.c_int64), ("mask_offset", ctypes.c_int64),
+                ("result_offset", ctypes.c_int64), ("tag", ctypes.c_uint64)]
+
+
+class ServeDoneC(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("d", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("all_syndrome_ok", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_complete_ns", ctypes.c_int64)]
+
+
 class BatchInfoC(ctypes.Structure):
     _fields_ = [("sym_elems", ctypes.c_int64), ("mask_words", ctypes.c_int64), ("llr_elems", ctypes.c_int64),
                 ("bits_words", ctypes.c_int64), ("n_cb", ctypes.c_int32), ("n_tb", ctypes.c_int32),
@@ -88,6 +109,17 @@ def _np_dtype(struct) -> np.dtype:
 
 CB_NP = _np_dtype(CbDescC)
 TB_NP = _np_dtype(TbDescC)
+
+
+def _np_dtype_any(struct) -> np.dtype:
+    conv = {ctypes.c_int32: "<i4", ctypes.c_int64: "<i8", ctypes.c_float: "<f4", ctypes.c_uint64: "<u8"}
+    names = [n for n, _ in struct._fields_]
+    return np.dtype({"names": names, "formats": [conv[t] for _, t in struct._fields_],
+                     "offsets": [getattr(struct, n).offset for n in names], "itemsize": ctypes.sizeof(struct)})
+
+
+SERVE_TB_NP = _np_dtype_any(ServeTbC)
+SERVE_DONE_NP = _np_dtype_any(ServeDoneC)
 
 _lib = None
 
@@ -126,6 +158,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ldpc_graph_create.argtypes = [vp] * 11 + [ctypes.POINTER(vp)]
     lib.ldpc_graph_launch.argtypes = [vp, vp]
     lib.ldpc_graph_destroy.argtypes = [vp]
+    lib.ldpc_serve_start.argtypes = [vp, ctypes.POINTER(ServeDescC), ctypes.POINTER(vp)]
+    lib.ldpc_serve_submit.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+    lib.ldpc_serve_poll.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+    lib.ldpc_serve_replay.argtypes = [vp, vp, vp, i32, vp, i32]
+    lib.ldpc_serve_stop.argtypes = [vp]
     lib.ldpc_last_error.restype = ctypes.c_char_p
     lib.ldpc_version.restype = ctypes.c_char_p
     for name in EXPORTED:

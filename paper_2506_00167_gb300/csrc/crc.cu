@@ -13,25 +13,13 @@
 // GF(2) multiply with x^(32 * words after the segment) mod g (a per-batch
 // table) and the warp xor-reduces.  No atomics: the block reduces the slot's
 // sums in shared memory, so results are deterministic.
-#include "internal.cuh"
+#include "crc_core.cuh"
 
 namespace ldpcgb {
 
 namespace {
 
-constexpr uint32_t kPolyFull = 0x1864CFBu;
-
-// a(x) * b(x) mod g(x), deg a, b < 24.
-__device__ __forceinline__ uint32_t gf2_mulmod(uint32_t a, uint32_t b) {
-  uint64_t p = 0;
-#pragma unroll
-  for (int i = 0; i < 24; ++i)
-    if ((b >> i) & 1u) p ^= static_cast<uint64_t>(a) << i;
-#pragma unroll
-  for (int i = 46; i >= 24; --i)
-    if ((p >> i) & 1u) p ^= static_cast<uint64_t>(kPolyFull) << (i - 24);
-  return static_cast<uint32_t>(p);
-}
+using namespace crccore;
 
 __global__ void __launch_bounds__(kCrcBlock) tb_crc_goodput_kernel(const CrcArgs a) {
   __shared__ uint32_t s_tab[256];

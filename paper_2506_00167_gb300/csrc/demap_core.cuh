@@ -1,0 +1,100 @@
+// Device building blocks of the max-log demapper, shared by the batch
+// demapper (demap.cu) and the serving loop's fused prologue (serve.cu).
+#pragma once
+
+#include "internal.cuh"
+
+namespace ldpcgb {
+namespace demapcore {
+
+// Unnormalised recursive Gray PAM amplitude of per-axis label c (q bits, the
+// first label bit is the most significant bit of c).
+constexpr int pam_amp(int c, int q) {
+  int sign = ((c >> (q - 1)) & 1) ? -1 : 1;
+  if (q == 1) return sign;
+  return sign * ((1 << (q - 1)) - pam_amp(c & ((1 << (q - 1)) - 1), q - 1));
+}
+
+struct PamTable {
+  float v[5][16];
+};
+
+constexpr PamTable make_pam() {
+  PamTable t{};
+  const float norm[5] = {0.f, 1.4142135623730951f, 3.1622776601683795f, 6.48074069840786f, 13.038404810405298f};
+  for (int q = 1; q <= 4; ++q)
+    for (int c = 0; c < (1 << q); ++c) t.v[q][c] = static_cast<float>(pam_amp(c, q)) / norm[q];
+  return t;
+}
+
+__constant__ PamTable kPam = make_pam();
+
+// Max-log LLRs of the q bits of one axis, written to out[2t + off].
+template <int q>
+__device__ __forceinline__ void axis_llr(float y, float inv_s2, float* out, int off) {
+  float m0[q], m1[q];
+#pragma unroll
+  for (int t = 0; t < q; ++t) {
+    m0[t] = 3.0e38f;
+    m1[t] = 3.0e38f;
+  }
+#pragma unroll
+  for (int c = 0; c < (1 << q); ++c) {
+    const float d = y - kPam.v[q][c];
+    const float d2 = d * d;
+#pragma unroll
+    for (int t = 0; t < q; ++t) {
+      if ((c >> (q - 1 - t)) & 1)
+        m1[t] = fminf(m1[t], d2);
+      else
+        m0[t] = fminf(m0[t], d2);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < q; ++t) out[2 * t + off] = (m1[t] - m0[t]) * inv_s2;
+}
+
+template <typename LT>
+__device__ __forceinline__ LT to_llr(float lam, float q_scale, float sat) {
+  if constexpr (sizeof(LT) == 4) {
+    return lam;
+  } else {
+    float x = roundf(lam * q_scale);  // round half away from zero
+    x = fminf(fmaxf(x, -sat), sat);
+    return static_cast<LT>(__float2int_rn(x));
+  }
+}
+
+// Resource element r of a code block (symbol y, punctured or not) into its
+// Qm codeword positions, `out` pointing at the block's position t0.
+template <typename LT, int Qm>
+__device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, LT* out, int r, int n_re,
+                                              int interleave, float q_scale, float llr_sat) {
+  float lam[Qm];
+  axis_llr<Qm / 2>(y.x, inv_sigma2, lam, 0);
+  axis_llr<Qm / 2>(y.y, inv_sigma2, lam, 1);
+#pragma unroll
+  for (int i = 0; i < Qm; ++i) {
+    const LT v = punct ? LT(0) : to_llr<LT>(lam[i], q_scale, llr_sat);
+    out[interleave ? i * n_re + r : r * Qm + i] = v;
+  }
+}
+
+template <typename LT, int Qm>
+__device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, int r) {
+  const float2 y = a.sym[cb.re_off + r];
+  const bool punct = (a.mask[cb.mask_off + (r >> 5)] >> (r & 31)) & 1u;
+  float lam[Qm];
+  axis_llr<Qm / 2>(y.x, cb.inv_sigma2, lam, 0);
+  axis_llr<Qm / 2>(y.y, cb.inv_sigma2, lam, 1);
+  LT* out = static_cast<LT*>(a.llr) + cb.llr_off + cb.t0;
+#pragma unroll
+  for (int i = 0; i < Qm; ++i) {
+    const LT v = punct ? LT(0) : to_llr<LT>(lam[i], a.q_scale, a.llr_sat);
+    const int pos = a.interleave ? i * cb.n_re + r : r * Qm + i;
+    out[pos] = v;
+  }
+}
+
+}  // namespace demapcore
+}  // namespace ldpcgb

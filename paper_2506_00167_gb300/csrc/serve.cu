@@ -1,0 +1,883 @@
+// Continuous-batching decode service: a persistent device loop fed through
+// rings in pinned host memory (see the serving section of ldpcgb.h).
+//
+// Host -> device: work items (up to G code blocks of one TB), code-block
+// records and request records live in pinned, mapped host memory; the host
+// writes them with plain stores, then publishes the new ring tail after a
+// release fence.  Each thread block of the device loop claims the next
+// published item with a compare-and-swap on a device head counter (so a
+// block that gives up waiting never strands a claimed item), reads its
+// records with system-scope loads, demaps the blocks' symbols from the host
+// pool directly into shared memory, decodes them, and writes bits and status
+// into the device arena.  The block that finishes a request's last item runs
+// the TB CRC-24, copies the decoded bits to the host result pool and writes a
+// completion record to a host ring, sequence number last after a system
+// fence.  All waits are bounded by %globaltimer.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "crc_core.cuh"
+#include "decode_core.cuh"
+#include "demap_core.cuh"
+
+namespace ldpcgb {
+namespace {
+
+constexpr int kServeBlock = 384;
+constexpr int kMaxTbCb = 16;
+
+struct ServeItem {  // host ring entry
+  int32_t req, cb0, count, n_items;
+};
+
+struct ServeReq {  // host record per request slot
+  uint64_t tag;
+  int32_t n_cb, words, shape, pad;
+  int64_t bits_off;    // arena word offset of the TB's decoded bits (contiguous)
+  int64_t status_off;  // arena word offset of its status words
+  int64_t result_off;  // byte offset into the result pool, -1 for none
+};
+
+struct ServeDone {  // device -> host completion record
+  uint64_t tag;
+  int32_t d, max_iters, all_ok, req;
+  uint32_t seq, pad;
+};
+
+struct HostCtl {  // host-written control words
+  uint32_t tail;
+  uint32_t stop;
+  uint32_t pad[14];
+};
+
+struct DevCtl {  // device counters
+  uint32_t head, done, err, pad;
+};
+
+struct ServeShape {  // one (bg, Z) shape with its shared-memory layout in the loop
+  ShapeDev sh;
+  int32_t G, region_bytes, L_bytes, hb_bytes, rec_cap, dummy_base, feasible, pad;
+};
+
+struct ServeArgs {
+  const ServeShape* shapes;
+  const uint32_t* tabs;
+  const ServeItem* items;
+  uint32_t item_cap;
+  const CbDev* cbs;  // code-block records: re_off/mask_off index the host pool (elements/words),
+                     // bits_off and llr_off (status index) the arena
+  uint32_t cb_cap;
+  const ServeReq* reqs;
+  ServeDone* done;
+  uint32_t done_cap;
+  const HostCtl* hctl;
+  DevCtl* dctl;
+  uint32_t* counts;  // per request slot: items finished
+  uint32_t* arena;
+  const uint8_t* host_pool;
+  uint8_t* result_pool;
+  const uint32_t* crc_table;
+  const uint32_t* xpow32;
+  int32_t hdr_bytes, interleave, max_iter, early_term;
+  float q_scale, llr_sat, beta, msg_sat, post_sat;
+  uint64_t idle_ns;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_sys(const T* p) {
+  return *const_cast<const volatile T*>(p);
+}
+
+__device__ __forceinline__ float2 ld_sys_f2(const float2* p) {
+  float2 v;
+  asm volatile("ld.volatile.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+
+// Claim the next published work item: its index, -1 if stopped, -2 after the idle limit.
+__device__ int64_t claim_item(const ServeArgs& a) {
+  const uint64_t t0 = gtimer();
+  unsigned ns = 32;
+  for (;;) {
+    const uint32_t tail = ld_acquire_sys(&a.hctl->tail);
+    const uint32_t h = atomicAdd(&a.dctl->head, 0u);
+    if (h != tail) {
+      if (atomicCAS(&a.dctl->head, h, h + 1u) == h) return static_cast<int64_t>(h);
+      continue;
+    }
+    if (ld_sys(&a.hctl->stop)) return -1;
+    if (gtimer() - t0 > a.idle_ns) return -2;
+    __nanosleep(ns);
+    ns = ns < 1024 ? ns * 2 : 1024;
+  }
+}
+
+__device__ CbDev load_cb(const CbDev* p) {
+  CbDev c;
+  const volatile int32_t* s = reinterpret_cast<const volatile int32_t*>(p);
+  int32_t* d = reinterpret_cast<int32_t*>(&c);
+#pragma unroll
+  for (int i = 0; i < static_cast<int>(sizeof(CbDev) / 4); ++i) d[i] = s[i];
+  return c;
+}
+
+template <typename LT>
+__device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, LT* L, int k, int Z) {
+  using namespace demapcore;
+  for (int p = k; p < cb.t0; p += Z) L[p] = LT(0);
+  for (int p = cb.t0 + cb.E + k; p < cb.n_eff * Z; p += Z) L[p] = LT(0);
+  const float2* sym = reinterpret_cast<const float2*>(a.host_pool) + cb.re_off;
+  const volatile uint32_t* msk = reinterpret_cast<const volatile uint32_t*>(a.host_pool) + cb.mask_off;
+  LT* out = L + cb.t0;
+  for (int r = k; r < cb.n_re; r += Z) {
+    const float2 y = ld_sys_f2(sym + r);
+    const bool punct = (msk[r >> 5] >> (r & 31)) & 1u;
+    switch (cb.Qm) {
+      case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
+      case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
+      case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
+      default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
+    }
+  }
+}
+
+template <typename LT, typename MT, bool SAT>
+__global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
+  using namespace core;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
+  uint8_t* regions = smem + a.hdr_bytes;
+  __shared__ long long s_claim;
+  __shared__ int s_last;
+  __shared__ uint32_t s_res[3];  // d, most iterations, all syndromes zero
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (;;) {
+    if (tid == 0) {
+      s_claim = claim_item(a);  // -2 (idle): exit quietly, the host relaunches on demand
+    }
+    __syncthreads();
+    const long long idx = s_claim;
+    if (idx < 0) break;
+    const ServeItem* ip = a.items + (static_cast<uint32_t>(idx) % a.item_cap);
+    const int req = ld_sys(&ip->req), cb0 = ld_sys(&ip->cb0), count = ld_sys(&ip->count);
+    const int n_items = ld_sys(&ip->n_items);
+    const int first_cb = static_cast<int>(static_cast<uint32_t>(cb0) % a.cb_cap);
+    const CbDev cb_first = load_cb(a.cbs + first_cb);
+    const ServeShape ssh = a.shapes[cb_first.shape];
+    const ShapeDev& sh = ssh.sh;
+    const int Z = sh.Z;
+    const int g = tid / Z;
+    const int k = tid - g * Z;
+    const uint32_t wmask = (Z >= 32) ? 0xFFFFFFFFu : (((1u << Z) - 1u) << (lane & ~(Z - 1)));
+
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
+      bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
+    }
+    const bool active = g < count;
+    CbDev cb{};
+    LT* L = reinterpret_cast<LT*>(regions + g * ssh.region_bytes);
+    uint8_t* rbase = regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
+    MT* mag1 = reinterpret_cast<MT*>(rbase);
+    MT* mag2 = mag1 + ssh.rec_cap;
+    uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
+    if (active) {
+      cb = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + g) % a.cb_cap));
+      for (int r = k; r < cb.m_eff * Z; r += Z) {
+        mag1[r] = MT(0);
+        mag2[r] = MT(0);
+        meta[r] = 0u;
+      }
+      if constexpr (SAT)
+        st_val(L, ssh.dummy_base + k, a.post_sat);
+      else
+        L[ssh.dummy_base + k] = LT(kBigF);
+      demap_into_smem(a, cb, L, k, Z);  // puncture flushing + max-log, straight into shared memory
+    }
+    const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
+    phase ^= 1u;
+    if (!__syncthreads_and(got)) {
+      if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
+      mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
+      return;
+    }
+
+    if (active) {
+      const uint32_t* rows = s_tab + sh.row_off;
+      uint32_t* hb = reinterpret_cast<uint32_t*>(regions + g * ssh.region_bytes + ssh.L_bytes);
+      const int m = cb.m_eff;
+      const bool wide = (Z & 31) == 0;
+      int it = 1;
+      bool ok = false;
+      for (;; ++it) {
+        for (int l = 0; l < m; ++l) {
+          const uint32_t info = rows[l];
+          check_update<LT, MT, SAT>(s_tab + (info & 0xFFFFu), static_cast<int>(info >> 16), k, Z, L, mag1, mag2,
+                                    meta, l * Z + k, ssh.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
+          group_sync(Z, g, wmask);
+        }
+        if (a.early_term || it == a.max_iter) {
+          bool bad;
+          if (wide) {
+            hard_bitmap(L, hb, cb.n_eff, k, Z);
+            group_sync(Z, g, wmask);
+            bad = syndrome_bitmap(s_tab, rows, hb, m, k, Z);
+          } else {
+            bad = syndrome_direct(s_tab, rows, m, k, Z, L);
+          }
+          ok = !group_any(Z, g, wmask, bad);
+          if (ok && a.early_term) break;
+          if (it == a.max_iter) break;
+        }
+      }
+      uint32_t* out = a.arena + cb.bits_off;
+      if (wide) {
+        const int nw = cb.kb * (Z >> 5);
+        for (int i = k; i < nw; i += Z) out[i] = hb[i];
+      } else {
+        const int sh16 = lane & 16;
+        for (int c = 0; c < cb.kb; c += 2) {
+          const uint32_t b0 = __ballot_sync(wmask, L[c * Z + k] < LT(0)) >> sh16;
+          const uint32_t b1 = __ballot_sync(wmask, L[(c + 1) * Z + k] < LT(0)) >> sh16;
+          if (k == 0) out[c >> 1] = (b0 & 0xFFFFu) | (b1 << 16);
+        }
+      }
+      if (k == 0) a.arena[cb.llr_off] = static_cast<uint32_t>(it | (ok ? (1 << 16) : 0));
+    }
+    // ---- request bookkeeping: the block finishing the last item completes the TB
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t prev = atomicAdd(a.counts + req, 1u);
+      s_last = (prev + 1u == static_cast<uint32_t>(n_items)) ? 1 : 0;
+      if (s_last) {
+        a.counts[req] = 0u;
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_last) {
+      const ServeReq* rq = a.reqs + req;
+      const uint64_t tag = ld_sys(&rq->tag);
+      const int n_cb = ld_sys(&rq->n_cb);
+      const int W = ld_sys(&rq->words);
+      const int64_t bits_off = ld_sys(&rq->bits_off);
+      const int64_t status_off = ld_sys(&rq->status_off);
+      const int64_t result_off = ld_sys(&rq->result_off);
+      const volatile uint32_t* bits = a.arena + bits_off;
+      if (tid < 32) {
+        using namespace crccore;
+        const int per = (W + 31) >> 5;
+        const int w0 = min(W, lane * per);
+        const int w1 = min(W, w0 + per);
+        uint32_t state = 0;
+        for (int w = w0; w < w1; ++w) {
+          const uint32_t v = __brev(bits[w]);
+#pragma unroll
+          for (int bb = 3; bb >= 0; --bb) {
+            const uint32_t byte = (v >> (8 * bb)) & 0xFFu;
+            state = ((state << 8) & 0xFFFFFFu) ^ a.crc_table[((state >> 16) ^ byte) & 0xFFu];
+          }
+        }
+        if (w0 < w1) state = gf2_mulmod(state, a.xpow32[W - w1]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) state ^= __shfl_xor_sync(0xFFFFFFFFu, state, o);
+        uint32_t st = lane < n_cb ? a.arena[status_off + lane] : (1u << 16);
+        uint32_t iters = st & 0xFFFFu;
+        uint32_t okb = (st >> 16) & 1u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          iters = max(iters, __shfl_xor_sync(0xFFFFFFFFu, iters, o));
+          okb &= __shfl_xor_sync(0xFFFFFFFFu, okb, o);
+        }
+        if (lane == 0) {
+          s_res[0] = state == 0u ? 1u : 0u;
+          s_res[1] = iters;
+          s_res[2] = okb;
+        }
+      }
+      if (result_off >= 0) {
+        volatile uint32_t* res = reinterpret_cast<volatile uint32_t*>(a.result_pool + result_off);
+        for (int i = tid; i < W; i += blockDim.x) res[i] = bits[i];
+      }
+      __threadfence_system();
+      __syncthreads();
+      if (tid == 0) {
+        const uint32_t slot = atomicAdd(&a.dctl->done, 1u);
+        volatile ServeDone* rec = a.done + (slot % a.done_cap);
+        rec->tag = tag;
+        rec->d = static_cast<int32_t>(s_res[0]);
+        rec->max_iters = static_cast<int32_t>(s_res[1]);
+        rec->all_ok = static_cast<int32_t>(s_res[2]);
+        rec->req = req;
+        __threadfence_system();
+        rec->seq = slot + 1u;
+        __threadfence_system();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+const void* serve_kernel_ptr(int mode) {
+  switch (mode) {
+    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false>);
+    case LDPC_I8: return reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true>);
+    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true>);
+  }
+}
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+int align16s(int x) { return (x + 15) & ~15; }
+
+// First-fit allocator over arena words with coalescing frees.
+struct Arena {
+  std::map<int64_t, int64_t> free_;  // offset -> length
+  explicit Arena(int64_t words) { free_[0] = words; }
+  int64_t alloc(int64_t n) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        const int64_t off = it->first;
+        const int64_t rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        return off;
+      }
+    }
+    return -1;
+  }
+  void release(int64_t off, int64_t n) {
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+}  // namespace
+}  // namespace ldpcgb
+
+using namespace ldpcgb;
+
+struct ldpc_server {
+  ldpc_session* s = nullptr;
+  int mode = LDPC_I8;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  bool running = false;
+  // host-mapped rings
+  HostCtl* hctl = nullptr;
+  ServeItem* items = nullptr;
+  CbDev* cbs = nullptr;
+  ServeReq* reqs = nullptr;
+  ServeDone* done = nullptr;
+  uint32_t item_cap = 0, cb_cap = 0, done_cap = 0;
+  int32_t max_inflight = 0;
+  // device
+  DevCtl* dctl = nullptr;
+  uint32_t* counts = nullptr;
+  uint32_t* arena = nullptr;
+  ServeShape* shapes = nullptr;
+  uint32_t* tabs = nullptr;
+  uint32_t* xpow32 = nullptr;
+  uint32_t* crc_table = nullptr;
+  std::vector<ServeShape> hshapes;
+  ServeArgs args{};
+  int smem = 0, grid = 0;
+  const uint8_t* host_pool = nullptr;
+  uint64_t host_pool_bytes = 0;
+  uint8_t* result_pool = nullptr;
+  uint64_t result_pool_bytes = 0;
+  // host bookkeeping
+  Arena* alloc = nullptr;
+  std::vector<int32_t> free_slots;
+  struct Slot {
+    int64_t arena_off = 0, arena_words = 0;
+    int32_t n_items = 0, n_cb = 0;
+    int64_t t_submit = 0;
+  };
+  std::vector<Slot> slot_info;
+  uint32_t tail = 0, cb_tail = 0;
+  uint64_t items_inflight = 0, cbs_inflight = 0;
+  uint32_t rd = 0;
+};
+
+namespace {
+
+int srv_fail(int code, const std::string& m) {
+  set_error(m);
+  return code;
+}
+
+void free_server(ldpc_server* v) {
+  if (!v) return;
+  cudaFreeHost(v->hctl);
+  cudaFreeHost(v->items);
+  cudaFreeHost(v->cbs);
+  cudaFreeHost(v->reqs);
+  cudaFreeHost(v->done);
+  cudaFree(v->dctl);
+  cudaFree(v->counts);
+  cudaFree(v->arena);
+  cudaFree(v->shapes);
+  cudaFree(v->tabs);
+  cudaFree(v->xpow32);
+  cudaFree(v->crc_table);
+  if (v->done_ev) cudaEventDestroy(v->done_ev);
+  if (v->stream) cudaStreamDestroy(v->stream);
+  delete v->alloc;
+  delete v;
+}
+
+int launch_loop(ldpc_server* v) {
+  void* kargs[] = {&v->args};
+  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode), dim3(v->grid), dim3(kServeBlock), kargs,
+                                   static_cast<size_t>(v->smem), v->stream);
+  if (e != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop launch: ") + cudaGetErrorString(e));
+  e = cudaEventRecord(v->done_ev, v->stream);
+  if (e != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+  v->running = true;
+  return LDPC_OK;
+}
+
+// Relaunch the device loop if it has exited (idle limit reached).
+int ensure_running(ldpc_server* v) {
+  if (v->running) {
+    const cudaError_t q = cudaEventQuery(v->done_ev);
+    if (q == cudaErrorNotReady) return LDPC_OK;
+    if (q != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop: ") + cudaGetErrorString(q));
+    v->running = false;
+  }
+  return launch_loop(v);
+}
+
+template <typename T>
+int host_alloc(T** p, size_t n) {
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(p), bytes, cudaHostAllocMapped);
+  if (e != cudaSuccess) return srv_fail(LDPC_ENOMEM, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+  std::memset(*p, 0, bytes);
+  return LDPC_OK;
+}
+
+template <typename T>
+T* dev_ptr(T* host) {
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, host, 0) != cudaSuccess) return nullptr;
+  return static_cast<T*>(d);
+}
+
+}  // namespace
+
+// Accessors into the session (defined in session.cu).
+namespace ldpcgb {
+int session_serve_info(ldpc_session* s, int* mode, int* interleave, int* max_iter, int* early_term, float* q_scale,
+                       float* llr_sat, float* beta, float* msg_sat, float* post_sat, int* num_sms);
+int session_shape_count(ldpc_session* s);
+int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh);
+int session_shape_lookup(ldpc_session* s, int bg, int Z);
+const uint32_t* session_crc_table(ldpc_session* s);
+}  // namespace ldpcgb
+
+extern "C" {
+
+int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** out) {
+  try {
+    if (!s || !d || !out || !d->host_pool || d->max_inflight < 1 || d->max_inflight > 65536 ||
+        d->arena_bytes < 1024 || d->idle_timeout_us < 1)
+      return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
+    *out = nullptr;
+    auto* v = new (std::nothrow) ldpc_server();
+    if (!v) return srv_fail(LDPC_ENOMEM, "host allocation");
+    v->s = s;
+    int interleave = 1, max_iter = 10, et = 1, sms = 0;
+    float q_scale = 4, llr_sat = 63, beta = 1, msg_sat = 63, post_sat = 127;
+    session_serve_info(s, &v->mode, &interleave, &max_iter, &et, &q_scale, &llr_sat, &beta, &msg_sat, &post_sat,
+                       &sms);
+    cudaGetDevice(&v->device);
+    const int esz = v->mode == LDPC_F32 ? 4 : (v->mode == LDPC_I8 ? 1 : 2);
+    // ---- per-shape tables and layouts, sized for the largest block of the shape
+    std::vector<uint32_t> tabs;
+    int tw = 0;
+    const int n_sh = session_shape_count(s);
+    for (int i = 0; i < n_sh; ++i) {
+      ServeShape ss{};
+      ShapeDev sd{};
+      std::vector<uint32_t> tmp;
+      session_shape_table(s, i, 0, tmp, sd);  // geometry only
+      const int Z = sd.Z;
+      ss.dummy_base = sd.nb * Z;
+      session_shape_table(s, i, ss.dummy_base, tabs, sd);
+      ss.sh = sd;
+      tw = std::max(tw, sd.tab_words);
+      ss.rec_cap = sd.mb * Z;
+      ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
+      ss.hb_bytes = (Z % 32 == 0) ? align16s(sd.nb * (Z / 32) * 4) : 0;
+      const int rec_bytes = 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
+      ss.region_bytes = ss.L_bytes + ss.hb_bytes + rec_bytes;
+      ss.G = std::max(1, kServeBlock / Z);
+      if (Z > 32) ss.G = std::min(ss.G, 15);
+      v->hshapes.push_back(ss);
+    }
+    const int hdr = align16s(tw * 4) + 16;
+    int smem = hdr;
+    for (auto& ss : v->hshapes) {
+      while (ss.G > 1 && hdr + ss.G * ss.region_bytes > kMaxSmem) --ss.G;
+      if (ss.sh.Z == 16 && ss.G > 1 && (ss.G & 1)) --ss.G;
+      ss.feasible = hdr + ss.G * ss.region_bytes <= kMaxSmem;
+      if (ss.feasible) smem = std::max(smem, hdr + ss.G * ss.region_bytes);
+    }
+    v->smem = smem;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode));
+    if (e == cudaSuccess && smem + static_cast<int>(fa.sharedSizeBytes) > kMaxSmem) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode), kServeBlock, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+      free_server(v);
+      return srv_fail(LDPC_ECUDA, std::string("serve loop does not fit an SM (") + std::to_string(smem) +
+                                      " B shared, " + std::to_string(fa.numRegs) + " registers): " +
+                                      cudaGetErrorString(e));
+    }
+    v->grid = per_sm * sms;
+    // ---- rings and arena
+    v->max_inflight = d->max_inflight;
+    v->item_cap = static_cast<uint32_t>(d->max_inflight) * kMaxTbCb;
+    v->cb_cap = static_cast<uint32_t>(d->max_inflight) * kMaxTbCb;
+    v->done_cap = static_cast<uint32_t>(d->max_inflight);
+    int rc;
+    const int64_t arena_words = static_cast<int64_t>(d->arena_bytes / 4);
+    if ((rc = host_alloc(&v->hctl, 1)) || (rc = host_alloc(&v->items, v->item_cap)) ||
+        (rc = host_alloc(&v->cbs, v->cb_cap)) || (rc = host_alloc(&v->reqs, d->max_inflight)) ||
+        (rc = host_alloc(&v->done, v->done_cap))) {
+      free_server(v);
+      return rc;
+    }
+    std::vector<uint32_t> xp(kMaxTbCb * 8448 / 32 * 2 + 1);
+    {
+      uint32_t cur = 1;
+      for (size_t m = 0; m < xp.size(); ++m) {
+        xp[m] = cur;
+        for (int i = 0; i < 32; ++i) {
+          cur <<= 1;
+          if (cur & 0x1000000u) cur ^= 0x1864CFBu;
+        }
+      }
+    }
+    auto up = [&](auto** p, const auto& vec) -> int {
+      using T = std::remove_reference_t<decltype(vec[0])>;
+      cudaError_t ee = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(vec.size(), 1) * sizeof(T));
+      if (ee == cudaSuccess && !vec.empty())
+        ee = cudaMemcpy(*p, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
+      return ee == cudaSuccess ? LDPC_OK : srv_fail(LDPC_ENOMEM, std::string("serve: ") + cudaGetErrorString(ee));
+    };
+    std::vector<uint32_t> zeros4(4, 0u), zcount(d->max_inflight, 0u);
+    if ((rc = up(&v->shapes, v->hshapes)) || (rc = up(&v->tabs, tabs)) || (rc = up(&v->xpow32, xp)) ||
+        (rc = up(&v->dctl, zeros4)) || (rc = up(&v->counts, zcount))) {
+      free_server(v);
+      return rc;
+    }
+    e = cudaMalloc(&v->arena, static_cast<size_t>(arena_words) * 4);
+    if (e != cudaSuccess) {
+      free_server(v);
+      return srv_fail(LDPC_ENOMEM, std::string("serve arena: ") + cudaGetErrorString(e));
+    }
+    v->alloc = new Arena(arena_words);
+    for (int i = d->max_inflight - 1; i >= 0; --i) v->free_slots.push_back(i);
+    v->slot_info.resize(d->max_inflight);
+    v->host_pool = static_cast<const uint8_t*>(d->host_pool);
+    v->host_pool_bytes = d->host_pool_bytes;
+    v->result_pool = static_cast<uint8_t*>(d->result_pool);
+    v->result_pool_bytes = d->result_pool_bytes;
+    const uint8_t* pool_dev = dev_ptr(const_cast<uint8_t*>(v->host_pool));
+    uint8_t* res_dev = v->result_pool ? dev_ptr(v->result_pool) : nullptr;
+    if (!pool_dev || (v->result_pool && !res_dev)) {
+      free_server(v);
+      return srv_fail(LDPC_EINVAL, "host_pool / result_pool must be pinned, mapped host memory");
+    }
+    e = cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->done_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      free_server(v);
+      return srv_fail(LDPC_ECUDA, std::string("serve stream: ") + cudaGetErrorString(e));
+    }
+    ServeArgs& a = v->args;
+    a.shapes = v->shapes;
+    a.tabs = v->tabs;
+    a.items = dev_ptr(v->items);
+    a.item_cap = v->item_cap;
+    a.cbs = dev_ptr(v->cbs);
+    a.cb_cap = v->cb_cap;
+    a.reqs = dev_ptr(v->reqs);
+    a.done = dev_ptr(v->done);
+    a.done_cap = v->done_cap;
+    a.hctl = dev_ptr(v->hctl);
+    a.dctl = v->dctl;
+    a.counts = v->counts;
+    a.arena = v->arena;
+    a.host_pool = pool_dev;
+    a.result_pool = res_dev;
+    a.crc_table = session_crc_table(s);
+    a.xpow32 = v->xpow32;
+    a.hdr_bytes = hdr;
+    a.interleave = interleave;
+    a.max_iter = max_iter;
+    a.early_term = et;
+    a.q_scale = q_scale;
+    a.llr_sat = llr_sat;
+    a.beta = beta;
+    a.msg_sat = msg_sat;
+    a.post_sat = post_sat;
+    a.idle_ns = static_cast<uint64_t>(d->idle_timeout_us) * 1000ull;
+    if (!a.items || !a.cbs || !a.reqs || !a.done || !a.hctl) {
+      free_server(v);
+      return srv_fail(LDPC_ECUDA, "mapped host rings unavailable");
+    }
+    if ((rc = launch_loop(v))) {
+      free_server(v);
+      return rc;
+    }
+    *out = v;
+    return LDPC_OK;
+  } catch (...) {
+    return srv_fail(LDPC_EINVAL, "unexpected host exception");
+  }
+}
+
+int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32_t* n_admitted) {
+  if (!v || (n > 0 && !tbs) || !n_admitted || n < 0) return srv_fail(LDPC_EINVAL, "bad submit arguments");
+  *n_admitted = 0;
+  // ---- validate every request before admitting any
+  for (int i = 0; i < n; ++i) {
+    const ldpc_serve_tb& tb = tbs[i];
+    const std::string at = "serve request " + std::to_string(i) + ": ";
+    const int shape = session_shape_lookup(v->s, tb.bg, tb.Z);
+    if (shape < 0) return srv_fail(LDPC_EINVAL, at + "unknown (bg, Z)");
+    const ServeShape& ss = v->hshapes[shape];
+    if (!ss.feasible) return srv_fail(LDPC_EINVAL, at + "shape does not fit the serving loop's shared memory");
+    const ShapeDev& sd = ss.sh;
+    const int t0 = sd.npc * tb.Z;
+    if (tb.n_cb < 1 || tb.n_cb > kMaxTbCb || (tb.Qm != 2 && tb.Qm != 4 && tb.Qm != 6 && tb.Qm != 8) || tb.E <= 0 ||
+        tb.E % tb.Qm || t0 + tb.E > sd.nb * tb.Z)
+      return srv_fail(LDPC_EINVAL, at + "bad n_cb, Qm or E");
+    const int K = sd.kb * tb.Z;
+    if (K % 32 || tb.payload_bits != tb.n_cb * K - 24) return srv_fail(LDPC_EINVAL, at + "payload_bits");
+    const int n_re = tb.E / tb.Qm;
+    const int mw = (n_re + 31) / 32;
+    if (tb.sym_offset < 0 || tb.sym_offset % 8 || tb.mask_offset < 0 || tb.mask_offset % 4 ||
+        static_cast<uint64_t>(tb.sym_offset) + static_cast<uint64_t>(tb.n_cb) * n_re * 8 > v->host_pool_bytes ||
+        static_cast<uint64_t>(tb.mask_offset) + static_cast<uint64_t>(tb.n_cb) * mw * 4 > v->host_pool_bytes)
+      return srv_fail(LDPC_EINVAL, at + "symbols/masks outside the host pool or misaligned");
+    if (tb.result_offset >= 0 &&
+        (!v->result_pool || tb.result_offset % 4 ||
+         static_cast<uint64_t>(tb.result_offset) + static_cast<uint64_t>(tb.n_cb) * K / 8 > v->result_pool_bytes))
+      return srv_fail(LDPC_EINVAL, at + "result outside the result pool or misaligned");
+    if (!(tb.inv_sigma2 >= 0.f)) return srv_fail(LDPC_EINVAL, at + "inv_sigma2");
+  }
+  // ---- admit in order while the request slots, rings and arena have room
+  const int64_t t = now_ns();
+  int taken = 0;
+  for (; taken < n; ++taken) {
+    const ldpc_serve_tb& tb = tbs[taken];
+    const int shape = session_shape_lookup(v->s, tb.bg, tb.Z);
+    const ServeShape& ss = v->hshapes[shape];
+    const ShapeDev& sd = ss.sh;
+    const int t0 = sd.npc * tb.Z;
+    const int K = sd.kb * tb.Z;
+    const int n_re = tb.E / tb.Qm;
+    const int mw = (n_re + 31) / 32;
+    const int cols = (tb.E + t0 + tb.Z - 1) / tb.Z;
+    const int m_eff = std::min(sd.mb, std::max(sd.mc, cols - sd.kb));
+    const int G = std::max(1, std::min(ss.G, tb.n_cb));
+    const int n_items = (tb.n_cb + G - 1) / G;
+    if (v->free_slots.empty() || v->items_inflight + n_items > v->item_cap || v->cbs_inflight + tb.n_cb > v->cb_cap)
+      break;
+    const int64_t words = static_cast<int64_t>(tb.n_cb) * (K / 32) + tb.n_cb;
+    const int64_t off = v->alloc->alloc(words);
+    if (off < 0) break;
+    const int slot = v->free_slots.back();
+    v->free_slots.pop_back();
+    auto& si = v->slot_info[slot];
+    si.arena_off = off;
+    si.arena_words = words;
+    si.n_items = n_items;
+    si.n_cb = tb.n_cb;
+    si.t_submit = t;
+    ServeReq& rq = v->reqs[slot];
+    rq.tag = tb.tag;
+    rq.n_cb = tb.n_cb;
+    rq.words = tb.n_cb * (K / 32);
+    rq.shape = shape;
+    rq.bits_off = off;
+    rq.status_off = off + static_cast<int64_t>(tb.n_cb) * (K / 32);
+    rq.result_off = tb.result_offset;
+    const uint32_t cb_first = v->cb_tail;
+    for (int j = 0; j < tb.n_cb; ++j) {
+      CbDev c{};
+      c.shape = shape;
+      c.Z = tb.Z;
+      c.Qm = tb.Qm;
+      c.E = tb.E;
+      c.t0 = t0;
+      c.m_eff = m_eff;
+      c.n_eff = sd.kb + m_eff;
+      c.n_re = n_re;
+      c.kb = sd.kb;
+      c.re_off = tb.sym_offset / 8 + static_cast<int64_t>(j) * n_re;
+      c.mask_off = tb.mask_offset / 4 + static_cast<int64_t>(j) * mw;
+      c.llr_off = rq.status_off + j;  // status word index in the arena
+      c.bits_off = off + static_cast<int64_t>(j) * (K / 32);
+      c.inv_sigma2 = tb.inv_sigma2;
+      v->cbs[(cb_first + j) % v->cb_cap] = c;
+    }
+    v->cb_tail += tb.n_cb;
+    for (int it = 0; it < n_items; ++it) {
+      ServeItem& item = v->items[v->tail % v->item_cap];
+      item.req = slot;
+      item.cb0 = static_cast<int32_t>(cb_first + it * G);
+      item.count = std::min(G, tb.n_cb - it * G);
+      item.n_items = n_items;
+      ++v->tail;
+    }
+    v->items_inflight += n_items;
+    v->cbs_inflight += tb.n_cb;
+  }
+  if (taken > 0) {
+    std::atomic_thread_fence(std::memory_order_release);
+    reinterpret_cast<volatile uint32_t*>(&v->hctl->tail)[0] = v->tail;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    const int rc = ensure_running(v);
+    if (rc) return rc;
+  }
+  *n_admitted = taken;
+  return LDPC_OK;
+}
+
+int ldpc_serve_poll(ldpc_server* v, ldpc_serve_done* out, int32_t cap, int32_t* n_out) {
+  if (!v || !n_out || cap < 0 || (cap > 0 && !out)) return srv_fail(LDPC_EINVAL, "bad poll arguments");
+  int n = 0;
+  while (n < cap) {
+    volatile ServeDone* rec = v->done + (v->rd % v->done_cap);
+    if (rec->seq != v->rd + 1u) break;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const int slot = rec->req;
+    auto& si = v->slot_info[slot];
+    ldpc_serve_done o{};
+    o.tag = rec->tag;
+    o.d = rec->d;
+    o.max_iters = rec->max_iters;
+    o.all_syndrome_ok = rec->all_ok;
+    o.status = 0;
+    o.t_submit_ns = si.t_submit;
+    o.t_complete_ns = now_ns();
+    out[n++] = o;
+    v->alloc->release(si.arena_off, si.arena_words);
+    v->items_inflight -= si.n_items;
+    v->cbs_inflight -= si.n_cb;
+    v->free_slots.push_back(slot);
+    ++v->rd;
+  }
+  *n_out = n;
+  if (v->items_inflight > 0) return ensure_running(v);  // a loop that idled out while items were pending
+  return LDPC_OK;
+}
+
+int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* arrival_ns, int32_t n,
+                      ldpc_serve_done* out, int32_t timeout_ms) {
+  if (!v || n < 0 || (n > 0 && (!tbs || !arrival_ns || !out)) || timeout_ms < 1)
+    return srv_fail(LDPC_EINVAL, "bad replay arguments");
+  std::vector<int64_t> sched(n);
+  std::map<uint64_t, int> by_tag;
+  for (int i = 0; i < n; ++i) by_tag[tbs[i].tag] = i;
+  if (static_cast<int>(by_tag.size()) != n) return srv_fail(LDPC_EINVAL, "replay: tags must be unique");
+  const int64_t t0 = now_ns();
+  for (int i = 0; i < n; ++i) sched[i] = t0 + arrival_ns[i];
+  int next = 0, got = 0;
+  int64_t last_progress = t0;
+  std::vector<ldpc_serve_done> buf(1024);
+  while (got < n) {
+    const int64_t now = now_ns();
+    int due = next;
+    while (due < n && sched[due] <= now) ++due;
+    if (due > next) {
+      int32_t adm = 0;
+      const int rc = ldpc_serve_submit(v, tbs + next, due - next, &adm);
+      if (rc) return rc;
+      next += adm;
+    }
+    int32_t k = 0;
+    const int rc = ldpc_serve_poll(v, buf.data(), static_cast<int32_t>(buf.size()), &k);
+    if (rc) return rc;
+    for (int i = 0; i < k; ++i) {
+      ldpc_serve_done o = buf[i];
+      auto f = by_tag.find(o.tag);
+      if (f != by_tag.end()) o.t_submit_ns = sched[f->second];
+      out[got++] = o;
+    }
+    if (k > 0 || due > next) last_progress = now_ns();
+    if (now_ns() - last_progress > static_cast<int64_t>(timeout_ms) * 1000000ll)
+      return srv_fail(LDPC_ETIMEOUT, "replay: no completion within the timeout");
+  }
+  return LDPC_OK;
+}
+
+int ldpc_serve_stop(ldpc_server* v) {
+  if (!v) return LDPC_OK;
+  reinterpret_cast<volatile uint32_t*>(&v->hctl->stop)[0] = 1u;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  int rc = LDPC_OK;
+  if (v->running) {
+    const cudaError_t e = cudaStreamSynchronize(v->stream);  // the loop sees the stop flag within ~1 us
+    if (e != cudaSuccess) rc = srv_fail(LDPC_ECUDA, std::string("serve stop: ") + cudaGetErrorString(e));
+  }
+  free_server(v);
+  return rc;
+}
+
+}  // extern "C"

@@ -348,6 +348,47 @@ int session_free(ldpc_session* s) {
 
 }  // namespace
 
+namespace ldpcgb {
+
+int session_serve_info(ldpc_session* s, int* mode, int* interleave, int* max_iter, int* early_term, float* q_scale,
+                       float* llr_sat, float* beta, float* msg_sat, float* post_sat, int* num_sms) {
+  *mode = s->mode;
+  *interleave = s->interleave;
+  *max_iter = s->max_iter;
+  *early_term = s->early_term;
+  *q_scale = s->q_scale;
+  if (s->mode == LDPC_F32) {
+    *llr_sat = 3.0e38f;
+    *beta = s->beta_f32;
+    *msg_sat = 3.0e38f;
+    *post_sat = 3.0e38f;
+  } else {
+    *llr_sat = static_cast<float>(s->llr_sat);
+    *beta = static_cast<float>(s->offset_lsb);
+    *msg_sat = static_cast<float>(s->msg_sat);
+    *post_sat = static_cast<float>(s->post_sat);
+  }
+  *num_sms = s->num_sms;
+  return LDPC_OK;
+}
+
+int session_shape_count(ldpc_session* s) { return static_cast<int>(s->shapes.size()); }
+
+int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh) {
+  sh = s->shapes[shape];
+  build_table(s->bgs[sh.bg], sh.Z, dummy, tabs, sh);
+  return LDPC_OK;
+}
+
+int session_shape_lookup(ldpc_session* s, int bg, int Z) {
+  auto it = s->shape_index.find({bg, Z});
+  return it == s->shape_index.end() ? -1 : it->second;
+}
+
+const uint32_t* session_crc_table(ldpc_session* s) { return s->d_crc_table; }
+
+}  // namespace ldpcgb
+
 extern "C" {
 
 const char* ldpc_last_error(void) { return g_err.c_str(); }

@@ -251,3 +251,58 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching decode service on a session (see the serving section of ldpcgb.h).
+
+    host_pool / result_pool: pinned CPU tensors (``pin_memory()``) holding the
+    requests' symbols and masks, and receiving decoded bits.  Requests are
+    numpy arrays of ``abi.SERVE_TB_NP``.
+    """
+
+    def __init__(self, session: Session, host_pool: torch.Tensor, result_pool: torch.Tensor | None = None,
+                 arena_bytes: int = 8 << 30, max_inflight: int = 4096, idle_timeout_us: int = 200000):
+        for t, name in ((host_pool, "host_pool"), (result_pool, "result_pool")):
+            if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous pinned CPU tensor")
+        self._keep = (session, host_pool, result_pool)
+        d = abi.ServeDescC(int(arena_bytes), int(max_inflight), int(idle_timeout_us), host_pool.data_ptr(),
+                           host_pool.numel() * host_pool.element_size(),
+                           result_pool.data_ptr() if result_pool is not None else None,
+                           result_pool.numel() * result_pool.element_size() if result_pool is not None else 0)
+        h = ctypes.c_void_p()
+        abi.check(abi.load().ldpc_serve_start(session.handle, ctypes.byref(d), ctypes.byref(h)), "ldpc_serve_start")
+        self.handle = h.value
+
+    def submit(self, tbs: np.ndarray) -> int:
+        a = np.ascontiguousarray(tbs, dtype=abi.SERVE_TB_NP)
+        n = ctypes.c_int32()
+        abi.check(abi.load().ldpc_serve_submit(self.handle, a.ctypes.data, a.size, ctypes.byref(n)),
+                  "ldpc_serve_submit")
+        return n.value
+
+    def poll(self, cap: int = 4096) -> np.ndarray:
+        out = np.zeros(cap, dtype=abi.SERVE_DONE_NP)
+        n = ctypes.c_int32()
+        abi.check(abi.load().ldpc_serve_poll(self.handle, out.ctypes.data, cap, ctypes.byref(n)), "ldpc_serve_poll")
+        return out[:n.value]
+
+    def replay(self, tbs: np.ndarray, arrival_ns: np.ndarray, timeout_ms: int = 10000) -> np.ndarray:
+        a = np.ascontiguousarray(tbs, dtype=abi.SERVE_TB_NP)
+        t = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        out = np.zeros(a.size, dtype=abi.SERVE_DONE_NP)
+        abi.check(abi.load().ldpc_serve_replay(self.handle, a.ctypes.data, t.ctypes.data, a.size, out.ctypes.data,
+                                               int(timeout_ms)), "ldpc_serve_replay")
+        return out
+
+    def stop(self) -> None:
+        if getattr(self, "handle", 0):
+            abi.check(abi.load().ldpc_serve_stop(self.handle), "ldpc_serve_stop")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

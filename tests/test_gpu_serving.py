@@ -1,0 +1,128 @@
+"""Continuous-batching decode service (GPU): same result alone and in the mix, admission, idle relaunch."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2506_00167_gb300 import LdpcError, Server, abi
+from workload.configs import subset
+from workload.serving import pool_bytes, tb_pool, tb_records
+
+from gpu_helpers import device_inputs, session_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pool():
+    w = tb_pool(40, seed=7)
+    raw, mask_base = pool_bytes(w)
+    host = torch.from_numpy(raw).pin_memory()
+    return w, host, mask_base
+
+
+def _tb_words(w, t):
+    tb = w.tbs[t]
+    c = w.cbs[int(tb["first_cb"])]
+    return int(tb["n_cb"]) * w.bgs[int(c["bg"])].kb * int(c["Z"]) // 32
+
+
+def _wait(srv, n, timeout=20.0):
+    got = []
+    t0 = time.time()
+    while sum(g.size for g in got) < n:
+        got.append(srv.poll())
+        assert time.time() - t0 < timeout, "service did not complete in time"
+    return np.concatenate(got)
+
+
+def _batch_reference(w, idx):
+    """The same TBs through the batch path (puncture_demap + decode_batch + tb_crc_goodput)."""
+    sub = subset(w, idx)
+    s = session_for(sub, "i8")
+    b = s.batch(sub.cbs, sub.tbs, sub.slot_N)
+    sym, mask = device_inputs(sub)
+    out = s.run(b, sym, mask, b.alloc_outputs())
+    torch.cuda.synchronize()
+    bits = out["bits"].cpu().numpy().view(np.uint32)
+    per_tb = []
+    for t in range(sub.n_tb):
+        c = sub.cbs[int(sub.tbs[t]["first_cb"])]
+        o = int(c["bits_word_offset"])
+        per_tb.append(bits[o:o + _tb_words(sub, t)].copy())
+    return out["d"].cpu().numpy()[:sub.n_tb], per_tb
+
+
+def test_result_is_the_same_alone_and_in_the_mix(pool):
+    w, host, mask_base = pool
+    n = w.n_tb
+    words = [_tb_words(w, t) for t in range(n)]
+    offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
+    res = torch.zeros(2 * int(offs[-1]), dtype=torch.int32).pin_memory()
+    s = session_for(w, "i8")
+    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=256)
+    alone = [0, 3, 7, 11]
+    # alone: one request at a time on an idle service
+    d_alone = {}
+    for t in alone:
+        rec = tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=[t], tags=[t], result_offsets=[4 * offs[t]])
+        assert srv.submit(rec) == 1
+        done = _wait(srv, 1)
+        assert int(done["tag"][0]) == t
+        d_alone[t] = int(done["d"][0])
+    bits_alone = {t: res[offs[t]:offs[t + 1]].numpy().view(np.uint32).copy() for t in alone}
+    # in the mix: every TB arrives together (results into the second half of the result pool)
+    base = int(offs[-1])
+    recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * (base + offs[:-1]))
+    done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
+    assert sorted(done["tag"].tolist()) == list(range(n))
+    d_mix = {int(r["tag"]): int(r["d"]) for r in done}
+    for t in alone:
+        assert d_mix[t] == d_alone[t]
+        assert np.array_equal(res[base + offs[t]:base + offs[t + 1]].numpy().view(np.uint32), bits_alone[t])
+    # and both equal the batch path bit for bit
+    d_ref, bits_ref = _batch_reference(w, range(n))
+    for t in range(n):
+        assert d_mix[t] == int(d_ref[t]), t
+        assert np.array_equal(res[base + offs[t]:base + offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
+    assert 0 < sum(d_mix.values()) <= n
+    lat = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
+    assert np.all(lat > 0)
+    srv.stop()
+
+
+def test_admission_waits_for_memory(pool):
+    w, host, mask_base = pool
+    s = session_for(w, "i8")
+    need = [_tb_words(w, t) + int(w.tbs[t]["n_cb"]) for t in range(3)]
+    srv = Server(s, host, None, arena_bytes=4 * (need[0] + need[1]), max_inflight=64)
+    recs = tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=[0, 1, 2], tags=[0, 1, 2])
+    assert srv.submit(recs) == 2          # the third does not fit the arena yet
+    done = _wait(srv, 2)
+    assert sorted(done["tag"].tolist()) == [0, 1]
+    assert srv.submit(recs[2:]) == 1      # admitted once the first two freed their space
+    assert _wait(srv, 1)["tag"][0] == 2
+    srv.stop()
+
+
+def test_idle_loop_is_relaunched_and_bad_requests_rejected(pool):
+    w, host, mask_base = pool
+    s = session_for(w, "i8")
+    srv = Server(s, host, None, arena_bytes=1 << 24, max_inflight=16, idle_timeout_us=2000)
+    rec = tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=[5], tags=[1])
+    assert srv.submit(rec) == 1
+    _wait(srv, 1)
+    time.sleep(0.05)                      # the device loop idles out meanwhile
+    rec["tag"] = 2
+    assert srv.submit(rec) == 1
+    assert _wait(srv, 1)["tag"][0] == 2
+    bad = rec.copy()
+    bad["Z"] = 48
+    with pytest.raises(LdpcError, match="EINVAL"):
+        srv.submit(bad)
+    bad = rec.copy()
+    bad["sym_offset"] = host.numel()
+    with pytest.raises(LdpcError, match="host pool"):
+        srv.submit(bad)
+    srv.stop()
