@@ -140,6 +140,21 @@ def peak_alu_gops(num_sms: int, mhz: float) -> float:
     return num_sms * ALU_LANES_PER_SM * mhz * 1e6 / 1e9
 
 
+def decoder_traffic(mode: str, n_cb: int, config: str):
+    """DRAM bytes per decode launch from the committed ncu capture, or None if the decoder changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "decode_traffic.json")
+    if config != "large" or not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = b"".join(open(os.path.join(ROOT, "paper_2506_00167_gb300", "csrc", f), "rb").read()
+                   for f in ("decode.cu", "decode_core.cuh", "internal.cuh"))
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("decoder_source_sha256_16"):
+        return None
+    m = rec["modes"].get(mode)
+    return None if m is None else m["bytes_per_launch_full"] * n_cb / m["scaled_to"]
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -536,7 +551,8 @@ def main():
     achieved_g = ALU_OPS_PER_EDGE * eu / (k_ms["decode"] / 1e3) / 1e9
     hb = hbm_bytes(w, mode)
     roof = {"bound": "alu", "achieved": achieved_g, "peak": peak_g, "unit": "Glaneop/s",
-            "frac": achieved_g / peak_g, "traffic": None,
+            "frac": achieved_g / peak_g, "traffic": decoder_traffic(mode, w.n_cb, args.config),
+            "traffic_source": "profiles/decode_traffic.json (ncu dram bytes, 2048-block capture scaled to the launch)",
             "kernel": "oms_decode_kernel", "launch_ms": k_ms["decode"],
             "edge_updates_per_launch": eu, "alu_ops_per_edge_update": ALU_OPS_PER_EDGE,
             "peak_basis": f"ALU pipe: {num_sms} SMs x {ALU_LANES_PER_SM} lanes x {mhz:.0f} MHz "

@@ -190,6 +190,145 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
   }
 }
 
+// INT8, two code blocks per thread group (see decode_core.cuh): items list
+// up to 2G code blocks of one shape, largest first, paired in order, so the
+// first block of a pair has at least as many decoded rows as the second.  A
+// pair runs the first block's rows; for the second block the extra rows only
+// touch its never-sent parity columns (LLR 0) and leave every other variable
+// unchanged, and its syndrome covers its own rows only.
+__global__ void __launch_bounds__(512) oms_decode_i8x2_kernel(const DecodeArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
+  int* s_item = reinterpret_cast<int*>(smem + a.hdr_bytes - 8);
+  uint8_t* regions = smem + a.hdr_bytes;
+  const int tid = threadIdx.x;
+  const int beta = static_cast<int>(a.beta);
+  const __half2 msg = __float2half2_rn(a.msg_sat);
+  const __half2 post = __float2half2_rn(a.post_sat);
+
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (int next = blockIdx.x;; next += gridDim.x) {
+    if (tid == 0) *s_item = a.queue ? static_cast<int>(atomicAdd(a.queue, 1u)) : next;
+    __syncthreads();
+    const int item_i = *s_item;
+    if (item_i >= a.n_items) break;
+    const DecodeItem item = a.items[item_i];
+    const ShapeDev sh = a.shapes[item.shape];
+    const int Z = item.Z;
+    const int g = tid / Z;
+    const int k = tid - g * Z;
+    const int pairs = (item.count + 1) >> 1;
+    uint8_t* reg = regions + g * item.region_bytes;
+    uint32_t* L = reinterpret_cast<uint32_t*>(reg);
+    uint32_t* hbA = reinterpret_cast<uint32_t*>(reg + item.L_bytes);
+    uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + item.L_bytes + item.hb_bytes);
+    uint8_t* recs = reg + item.L_bytes + 2 * item.hb_bytes;
+    uint32_t* mags = reinterpret_cast<uint32_t*>(recs);
+    uint32_t* sg1 = mags + item.rec_cap;
+    uint32_t* sg2 = sg1 + item.rec_cap;
+
+    // ---- stage the table and each pair's int8 LLRs (into its message area)
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      uint32_t bytes = static_cast<uint32_t>(sh.tab_words) * 4u;
+      for (int c = 0; c < item.count; ++c) bytes += static_cast<uint32_t>(a.cbs[a.item_cbs[item.first + c]].n_eff * Z);
+      mbar_arrive_expect_tx(s_bar, bytes);
+      bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
+      for (int pp = 0; pp < pairs; ++pp) {
+        uint8_t* st = regions + pp * item.region_bytes + item.L_bytes + 2 * item.hb_bytes;
+        const CbDev ca = a.cbs[a.item_cbs[item.first + 2 * pp]];
+        const uint32_t na = static_cast<uint32_t>(ca.n_eff * Z);
+        bulk_g2s(st, static_cast<const int8_t*>(a.llr) + ca.llr_off, na, s_bar);
+        if (2 * pp + 1 < item.count) {
+          const CbDev cbb = a.cbs[a.item_cbs[item.first + 2 * pp + 1]];
+          bulk_g2s(st + ((na + 15u) & ~15u), static_cast<const int8_t*>(a.llr) + cbb.llr_off,
+                   static_cast<uint32_t>(cbb.n_eff * Z), s_bar);
+        }
+      }
+    }
+    const bool active = g < pairs;
+    const bool hasB = 2 * g + 1 < item.count;
+    CbDev A{}, Bc{};
+    int ia = 0, ib = 0;
+    if (active) {
+      ia = a.item_cbs[item.first + 2 * g];
+      A = a.cbs[ia];
+      if (hasB) {
+        ib = a.item_cbs[item.first + 2 * g + 1];
+        Bc = a.cbs[ib];
+      }
+    }
+    const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
+    phase ^= 1u;
+    if (!__syncthreads_and(got)) {
+      if (tid == 0) atomicOr(a.err, LDPC_DEVERR_TMA_TIMEOUT);
+      mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
+      return;
+    }
+    if (active) {
+      const int8_t* stA = reinterpret_cast<const int8_t*>(recs);
+      const int8_t* stB = stA + ((A.n_eff * Z + 15) & ~15);
+      const int nA = A.n_eff * Z, nB = hasB ? Bc.n_eff * Z : 0;
+      const __half2 h1536 = __float2half2_rn(1536.0f);
+      for (int p = k; p < nA; p += Z) {
+        const uint32_t va = static_cast<uint32_t>(0x6600 + stA[p]) & 0xFFFFu;
+        const uint32_t vb = static_cast<uint32_t>(0x6600 + (p < nB ? stB[p] : 0)) & 0xFFFFu;
+        L[p] = as_u32(__hsub2(as_h2(va | (vb << 16)), h1536));
+      }
+      group_sync(Z, g, 0xFFFFFFFFu);
+      for (int r = k; r < A.m_eff * Z; r += Z) {
+        mags[r] = 0u;
+        sg1[r] = 0u;
+        sg2[r] = 0u;
+      }
+      group_sync(Z, g, 0xFFFFFFFFu);
+
+      const uint32_t* rows = s_tab + sh.row_off;
+      const int mA = A.m_eff, mB = hasB ? Bc.m_eff : 0;
+      bool doneA = false, doneB = !hasB;
+      for (int it = 1;; ++it) {
+        for (int l = 0; l < mA; ++l) {
+          const uint32_t info = rows[l];
+          check_update_x2(s_tab + (info & 0xFFFFu), static_cast<int>(info >> 16), k, Z, L, mags, sg1, sg2, l * Z + k,
+                          item.dummy_base + k, beta, msg, post);
+          group_sync(Z, g, 0xFFFFFFFFu);
+        }
+        if (a.early_term || it == a.max_iter) {
+          hard_bitmap_x2(L, hbA, hbB, A.n_eff, k, Z);
+          group_sync(Z, g, 0xFFFFFFFFu);
+          const bool badA = !doneA && syndrome_bitmap(s_tab, rows, hbA, mA, k, Z);
+          const bool badB = !doneB && syndrome_bitmap(s_tab, rows, hbB, mB, k, Z);
+          const bool okA = !group_any(Z, g, 0xFFFFFFFFu, badA);
+          const bool okB = !group_any(Z, g, 0xFFFFFFFFu, badB);
+          const bool last = it == a.max_iter;
+          const int nw = A.kb * (Z >> 5);
+          if (!doneA && ((okA && a.early_term) || last)) {
+            uint32_t* out = a.bits + A.bits_off;
+            for (int i = k; i < nw; i += Z) out[i] = hbA[i];
+            if (k == 0) a.status[ia] = it | (okA ? (1 << 16) : 0);
+            doneA = true;
+          }
+          if (!doneB && ((okB && a.early_term) || last)) {
+            uint32_t* out = a.bits + Bc.bits_off;
+            for (int i = k; i < nw; i += Z) out[i] = hbB[i];
+            if (k == 0) a.status[ib] = it | (okB ? (1 << 16) : 0);
+            doneB = true;
+          }
+          if (doneA && doneB) break;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <bool RG>
 const void* decode_kernel_ptr(int mode) {
   switch (mode) {
@@ -205,23 +344,29 @@ const void* kernel_for(int mode, bool rglobal) {
 
 }  // namespace
 
+const void* kernel_kind(int mode, int kind) {
+  return kind == kKindPairI8 ? reinterpret_cast<const void*>(&oms_decode_i8x2_kernel)
+                             : kernel_for(mode, kind == kKindGlobal);
+}
+
 cudaError_t decode_prepare(int mode) {
-  for (int rg = 0; rg < 2; ++rg) {
-    cudaError_t e = cudaFuncSetAttribute(kernel_for(mode, rg != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  for (int kind = 0; kind < 3; ++kind) {
+    if (kind == kKindPairI8 && mode != LDPC_I8) continue;
+    cudaError_t e = cudaFuncSetAttribute(kernel_kind(mode, kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSmem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t decode_occupancy(int mode, bool rglobal, int block, int smem, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_for(mode, rglobal), block, smem);
+cudaError_t decode_occupancy(int mode, int kind, int block, int smem, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_kind(mode, kind), block, smem);
 }
 
-cudaError_t launch_decode(int mode, bool rglobal, dim3 grid, dim3 block, int smem, cudaStream_t st,
+cudaError_t launch_decode(int mode, int kind, dim3 grid, dim3 block, int smem, cudaStream_t st,
                           const DecodeArgs& a) {
   void* args[] = {const_cast<DecodeArgs*>(&a)};
-  return cudaLaunchKernel(kernel_for(mode, rglobal), grid, block, args, static_cast<size_t>(smem), st);
+  return cudaLaunchKernel(kernel_kind(mode, kind), grid, block, args, static_cast<size_t>(smem), st);
 }
 
 }  // namespace ldpcgb

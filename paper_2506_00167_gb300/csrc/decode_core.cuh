@@ -221,3 +221,141 @@ __device__ __forceinline__ bool syndrome_direct(const uint32_t* __restrict__ tab
 
 }  // namespace core
 }  // namespace ldpcgb
+
+// ============================================================================
+// INT8, two code blocks per thread.  Every INT8 intermediate is an integer of
+// magnitude < 2048 (|Q| <= 190, keys |Q|*32 + j <= 2043), which fp16
+// represents exactly, and half2 min/max/add/fma on such values are exact; so
+// the pair (block A in the low half, block B in the high half) is decoded
+// bit-identically to two separate INT8 decodes with one instruction stream.
+// Per check the state is three words: magnitudes (m1A, m1B, m2A, m2B bytes),
+// sign history of edges 0..15 (A: bit 15-j, B: bit 31-j) and of edges 16..26
+// (A: bits 15..5, B: bits 31..21) with the argmins in bits 0..4 and 16..20.
+#include <cuda_fp16.h>
+
+namespace ldpcgb {
+namespace core {
+
+__device__ __forceinline__ __half2 as_h2(uint32_t u) {
+  __half2 h;
+  memcpy(&h, &u, 4);
+  return h;
+}
+
+__device__ __forceinline__ uint32_t as_u32(__half2 h) {
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+// half2 (1024 + a, 1024 + b) - 1024 for 0 <= a, b < 1024
+__device__ __forceinline__ __half2 small_pair(uint32_t a, uint32_t b) {
+  return __hsub2(as_h2((0x6400u + a) | ((0x6400u + b) << 16)), __float2half2_rn(1024.0f));
+}
+
+// one pair check (l, k); `dummy` is this thread's dummy slot
+__device__ __forceinline__ void check_update_x2(const uint32_t* __restrict__ tab, int deg, int k, int Z,
+                                                uint32_t* __restrict__ L, uint32_t* __restrict__ mags,
+                                                uint32_t* __restrict__ sg1, uint32_t* __restrict__ sg2, int rec,
+                                                int dummy, int beta, __half2 msg, __half2 post) {
+  L[dummy] = as_u32(post);
+  const uint32_t mg = mags[rec];
+  const uint32_t s1 = sg1[rec];
+  const uint32_t s2 = sg2[rec];
+  const __half2 h1024 = __float2half2_rn(1024.0f);
+  const __half2 M1 = __hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5140)), h1024);
+  const __half2 M2 = __hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5342)), h1024);
+  const __half2 I = __hsub2(as_h2((s2 & 0x001F001Fu) | 0x64006400u), h1024);
+  const __half2 h32 = __float2half2_rn(32.0f);
+  const __half2 npost = __hneg2(post);
+  const int nch = (deg + 3) >> 2;
+
+  uint32_t q[kMaxChunks * 4];
+  int addr[kMaxChunks * 4];
+  __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
+  uint32_t par = 0;
+  uint32_t sgn = s1;
+#pragma unroll
+  for (int c = 0; c < kMaxChunks; ++c) {
+    if (c >= nch) break;
+    const uint4 B = *reinterpret_cast<const uint4*>(tab + 8 * c);
+    const uint4 S = *reinterpret_cast<const uint4*>(tab + 8 * c + 4);
+    addr[4 * c + 0] = static_cast<int>(B.x) + rot(k, S.x, Z);
+    addr[4 * c + 1] = static_cast<int>(B.y) + rot(k, S.y, Z);
+    addr[4 * c + 2] = static_cast<int>(B.z) + rot(k, S.z, Z);
+    addr[4 * c + 3] = static_cast<int>(B.w) + rot(k, S.w, Z);
+    uint32_t lv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lv[i] = L[addr[4 * c + i]];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * c + i;
+      if (j == 16) sgn = s2;
+      const __half2 J = __float2half2_rn(static_cast<float>(j));
+      const uint32_t eq = __heq2_mask(I, J);
+      const uint32_t rb = ((as_u32(M2) & eq) | (as_u32(M1) & ~eq)) | (sgn & 0x80008000u);
+      sgn <<= 1;
+      __half2 Q = __hsub2(as_h2(lv[i]), as_h2(rb));
+      Q = __hmin2(__hmax2(Q, npost), post);
+      q[j] = as_u32(Q);
+      par ^= q[j];
+      const __half2 key = __hfma2(__hmin2(__habs2(Q), msg), h32, J);
+      min2 = __hmin2(min2, __hmax2(min1, key));
+      min1 = __hmin2(min1, key);
+    }
+  }
+  const float2 f1 = __half22float2(min1), f2 = __half22float2(min2);
+  const int kA1 = f2i_exact(f1.x), kB1 = f2i_exact(f1.y), kA2 = f2i_exact(f2.x), kB2 = f2i_exact(f2.y);
+  const uint32_t idxA = kA1 & 31, idxB = kB1 & 31;
+  const uint32_t nA1 = max((kA1 >> 5) - beta, 0), nB1 = max((kB1 >> 5) - beta, 0);
+  const uint32_t nA2 = max((kA2 >> 5) - beta, 0), nB2 = max((kB2 >> 5) - beta, 0);
+  const __half2 N1 = small_pair(nA1, nB1), N2 = small_pair(nA2, nB2), In = small_pair(idxA, idxB);
+  const uint32_t pm = par & 0x80008000u;
+  uint32_t acc1 = 0, acc2 = 0;
+#pragma unroll
+  for (int c = 0; c < kMaxChunks; ++c) {
+    if (c >= nch) break;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * c + i;
+      const uint32_t eq = __heq2_mask(In, __float2half2_rn(static_cast<float>(j)));
+      const uint32_t rb = ((as_u32(N2) & eq) | (as_u32(N1) & ~eq)) | ((q[j] ^ pm) & 0x80008000u);
+      __half2 v = __hadd2(as_h2(q[j]), as_h2(rb));
+      v = __hmin2(__hmax2(v, npost), post);
+      L[addr[j]] = as_u32(v);  // padding edges write the dummy slot
+      const uint32_t bit = (rb >> 15) & 0x00010001u;
+      if (j < 16)
+        acc1 = ((acc1 << 1) & 0xFFFEFFFEu) | bit;
+      else
+        acc2 = ((acc2 << 1) & 0xFFFEFFFEu) | bit;
+    }
+  }
+  const int n_all = 4 * nch;
+  const int n1 = n_all < 16 ? n_all : 16;
+  acc1 <<= (16 - n1);
+  const int n2 = n_all - 16;
+  acc2 = n2 > 0 ? ((acc2 << (16 - n2)) & 0xFFE0FFE0u) : 0u;
+  mags[rec] = nA1 | (nB1 << 8) | (nA2 << 16) | (nB2 << 24);
+  sg1[rec] = acc1;
+  sg2[rec] = acc2 | idxA | (idxB << 16);
+}
+
+// hard decisions of both blocks of a pair into their bitmaps
+__device__ __forceinline__ void hard_bitmap_x2(const uint32_t* __restrict__ L, uint32_t* __restrict__ hbA,
+                                               uint32_t* __restrict__ hbB, int n_eff, int k, int Z) {
+  const int W = Z >> 5;
+  const int w = k >> 5;
+  const bool lane0 = (k & 31) == 0;
+  for (int c = 0; c < n_eff; ++c) {
+    const uint32_t v = L[c * Z + k];
+    const uint32_t a = __ballot_sync(0xFFFFFFFFu, (v & 0x8000u) != 0u);
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (v & 0x80000000u) != 0u);
+    if (lane0) {
+      hbA[c * W + w] = a;
+      hbB[c * W + w] = b;
+    }
+  }
+}
+
+}  // namespace core
+}  // namespace ldpcgb

@@ -110,9 +110,14 @@ struct CrcArgs {
 void set_error(const std::string& msg);
 
 // Kernel launchers (defined next to their kernels).
-cudaError_t launch_decode(int mode, bool rglobal, dim3 grid, dim3 block, int smem, cudaStream_t st,
+// Decoder kernel kinds: messages in shared memory, in global memory, or the
+// INT8 kernel that decodes two code blocks per thread group.
+constexpr int kKindShared = 0;
+constexpr int kKindGlobal = 1;
+constexpr int kKindPairI8 = 2;
+cudaError_t launch_decode(int mode, int kind, dim3 grid, dim3 block, int smem, cudaStream_t st,
                           const DecodeArgs& a);
-cudaError_t decode_occupancy(int mode, bool rglobal, int block, int smem, int* blocks_per_sm);
+cudaError_t decode_occupancy(int mode, int kind, int block, int smem, int* blocks_per_sm);
 cudaError_t decode_prepare(int mode);  // raise the dynamic shared-memory limit
 cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
 cudaError_t launch_crc(int n_slots, cudaStream_t st, const CrcArgs& a);

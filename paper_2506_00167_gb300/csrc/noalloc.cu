@@ -265,7 +265,7 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int block = G * Z;
     const int smem = hdr_bytes + G * region;
-    cudaError_t e = decode_occupancy(mode, true, block, smem, &per_sm);
+    cudaError_t e = decode_occupancy(mode, kKindGlobal, block, smem, &per_sm);
     if (e != cudaSuccess || per_sm < 1) {
       set_error("decode_uniform_noalloc: occupancy query failed");
       return LDPC_ECUDA;
@@ -335,7 +335,7 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
       a.msg_sat = static_cast<float>(msg_sat);
       a.post_sat = static_cast<float>(post_sat);
     }
-    e = launch_decode(mode, true, dim3(grid), dim3(block), smem, st, a);
+    e = launch_decode(mode, kKindGlobal, dim3(grid), dim3(block), smem, st, a);
     if (e != cudaSuccess) {
       set_error(std::string("decode_uniform_noalloc: decode launch: ") + cudaGetErrorString(e));
       return LDPC_ECUDA;

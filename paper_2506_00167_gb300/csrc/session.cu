@@ -44,6 +44,7 @@ namespace {
 struct Launch {
   int G = 1, block = 0, smem = 0, grid = 0;  // G: most groups any item of the launch uses
   bool rglobal = false;
+  int kind = ldpcgb::kKindShared;
   int item_begin = 0, item_count = 0;
   int hdr_bytes = 0;
   int64_t rscratch_group = 0;
@@ -200,6 +201,8 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     int shape = 0, Z = 0, G = 1, max_n = 0, max_m = 0;
     int L_bytes = 0, hb_bytes = 0, rec_bytes = 0, tab_words = 0;
     bool rglobal = false;
+    int kind = kKindShared;
+    int pair_region = 0, pair_L = 0;  // paired INT8 layout
     std::vector<int> cbs;
   };
   std::map<int, SP> sps;
@@ -228,17 +231,34 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     if (p.G * p.Z > 512) p.G = std::max(1, 512 / p.Z);
   }
   // launch groups
-  std::map<std::pair<int, int>, std::vector<int>> groups;  // (key, rglobal) -> shapes
+  const bool pair_ok = s->mode == LDPC_I8 && s->post_sat >= 2 * s->msg_sat;
+  std::map<std::pair<int, int>, std::vector<int>> groups;  // (key, kind) -> shapes
   for (auto& kv : sps) {
     SP& p = kv.second;
     const int hdr = align16(p.tab_words * 4) + 16;
-    while (p.G > 1 && hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem) --p.G;
-    if (p.Z == 16 && p.G > 1 && (p.G & 1)) --p.G;
-    p.rglobal = hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem;
-    if (p.rglobal && hdr + p.G * (p.L_bytes + p.hb_bytes) > kMaxSmem)
-      return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
+    if (pair_ok && p.Z % 32 == 0) {
+      // two code blocks per group: posteriors as half2 pairs, two bitmaps, 3 message words per check
+      // (the message area first holds both blocks' int8 LLRs)
+      p.pair_L = align16((p.max_n + 1) * p.Z * 4);
+      const int recs = std::max(align16(3 * p.max_m * p.Z * 4), 2 * align16(p.max_n * p.Z));
+      p.pair_region = p.pair_L + 2 * p.hb_bytes + recs;
+      int G = p.G;
+      while (G > 1 && hdr + G * p.pair_region > kMaxSmem) --G;
+      if (hdr + G * p.pair_region <= kMaxSmem) {
+        p.kind = kKindPairI8;
+        p.G = G;
+      }
+    }
+    if (p.kind != kKindPairI8) {
+      while (p.G > 1 && hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem) --p.G;
+      if (p.Z == 16 && p.G > 1 && (p.G & 1)) --p.G;
+      p.rglobal = hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem;
+      if (p.rglobal && hdr + p.G * (p.L_bytes + p.hb_bytes) > kMaxSmem)
+        return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
+      p.kind = p.rglobal ? kKindGlobal : kKindShared;
+    }
     const int key = s->strategy == LDPC_PLAN_PER_Z ? p.Z : 0;
-    groups[{key, p.rglobal ? 1 : 0}].push_back(kv.first);
+    groups[{key, p.kind}].push_back(kv.first);
   }
   std::vector<DecodeItem> items;
   std::vector<int32_t> item_cbs;
@@ -246,9 +266,12 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
   std::vector<uint32_t> tabs;
   int64_t scratch_total = 0;
   for (auto& gkv : groups) {
-    const bool rglobal = gkv.first.second != 0;
+    const int kind = gkv.first.second;
+    const bool rglobal = kind == kKindGlobal;
+    const bool pair = kind == kKindPairI8;
     Launch L;
     L.rglobal = rglobal;
+    L.kind = kind;
     int tw = 0;
     for (int sh : gkv.second) tw = std::max(tw, sps[sh].tab_words);
     L.hdr_bytes = align16(tw * 4) + 16;
@@ -262,7 +285,7 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     int64_t rec_max = 0;
     for (int sh : gkv.second) {
       SP& p = sps[sh];
-      const int region = p.L_bytes + p.hb_bytes + (rglobal ? 0 : p.rec_bytes);
+      const int region = pair ? p.pair_region : p.L_bytes + p.hb_bytes + (rglobal ? 0 : p.rec_bytes);
       while (p.G > 1 && L.hdr_bytes + p.G * region > kMaxSmem) --p.G;
       if (L.hdr_bytes + p.G * region > kMaxSmem)
         return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
@@ -281,13 +304,14 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
         c.it.shape = local;
         c.it.Z = p.Z;
         c.it.region_bytes = region;
-        c.it.L_bytes = p.L_bytes;
+        c.it.L_bytes = pair ? p.pair_L : p.L_bytes;
         c.it.hb_bytes = p.hb_bytes;
         c.it.rec_cap = p.max_m * p.Z;
         c.it.dummy_base = p.max_n * p.Z;
         const int m0 = b->cbs[p.cbs[q]].m_eff;
         int cnt = 0;
-        while (q < p.cbs.size() && cnt < p.G) {
+        const int per_item = pair ? 2 * p.G : p.G;
+        while (q < p.cbs.size() && cnt < per_item) {
           c.cbs.push_back(p.cbs[q]);
           ++q;
           ++cnt;
@@ -310,7 +334,7 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     L.block = (block + 31) & ~31;
     L.smem = smem;
     int per_sm = 0;
-    cudaError_t e = decode_occupancy(s->mode, L.rglobal, L.block, L.smem, &per_sm);
+    cudaError_t e = decode_occupancy(s->mode, L.kind, L.block, L.smem, &per_sm);
     if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
     if (per_sm < 1) return fail(LDPC_EINVAL, "decoder launch does not fit an SM");
     L.grid = std::min(L.item_count, per_sm * s->num_sms);
@@ -801,7 +825,7 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
       a.msg_sat = static_cast<float>(s->msg_sat);
       a.post_sat = static_cast<float>(s->post_sat);
     }
-    cudaError_t e = launch_decode(s->mode, L.rglobal, dim3(L.grid), dim3(L.block), L.smem, s->stream, a);
+    cudaError_t e = launch_decode(s->mode, L.kind, dim3(L.grid), dim3(L.block), L.smem, s->stream, a);
     if (e != cudaSuccess) return cuda_fail(e, "decode_batch launch");
   }
   return LDPC_OK;
