@@ -116,11 +116,7 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
       cb = a.cbs[cbi];
       // R = 0 before the first iteration, and this thread's dummy slot (both
       // overlap the copies in flight: neither region is a copy target)
-      for (int r = k; r < cb.m_eff * Z; r += Z) {
-        mag1[r] = MT(0);
-        mag2[r] = MT(0);
-        meta[r] = 0u;
-      }
+      zero_records(mag1, mag2, meta, cb.m_eff * Z, k, Z);
       if constexpr (SAT)
         st_val(L, item.dummy_base + k, a.post_sat);
       else

@@ -70,13 +70,21 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
   // |Q| saturates at msg_sat and (edge index larger) never beats a real edge;
   // float: 1e30 absorbs every update and needs no reset
   if constexpr (SAT) st_val(L, dummy, post_sat);
-  const float r1 = ld_val(mag1, rec);
-  const float r2 = ld_val(mag2, rec);
+  float r1, r2;
+  if constexpr (sizeof(MT) == 4) {  // float: both magnitudes in one 8-byte record
+    const float2 rr = reinterpret_cast<const float2*>(mag1)[rec];
+    r1 = rr.x;
+    r2 = rr.y;
+  } else {
+    r1 = ld_val(mag1, rec);
+    r2 = ld_val(mag2, rec);
+  }
   const uint32_t mo = meta[rec];
   const int idx_o = static_cast<int>(mo >> 27);
-  // edge 0's sign at bit 31; positions past deg read as negative, so padding
-  // edges see Q = dummy + |R| (large and positive)
-  uint32_t sgn = (mo << (32 - deg)) | ((1u << (32 - deg)) - 1u);
+  // edge 0's sign at bit 31; in the integer modes positions past deg read as
+  // negative, so padding edges see Q = dummy + |R| (large and positive); the
+  // float dummy (1e30) is large whatever the sign
+  uint32_t sgn = SAT ? ((mo << (32 - deg)) | ((1u << (32 - deg)) - 1u)) : (mo << (32 - deg));
   const int nch = (deg + 3) >> 2;
 
   float q[kMaxChunks * 4];
@@ -122,7 +130,11 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
     n1 = fmaxf(min1 - beta, 0.0f);
     n2 = fmaxf(min2 - beta, 0.0f);
   }
+  // magnitudes carrying the parity in their sign bit: the sign of R'_j is
+  // parity ^ sign(Q_j), one xor with Q_j's sign bit
   const uint32_t pm = par & 0x80000000u;
+  const float n1s = __uint_as_float(__float_as_uint(n1) | pm);
+  const float n2s = __uint_as_float(__float_as_uint(n2) | pm);
   uint32_t rs = 0;
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
@@ -137,9 +149,8 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
         is_min = (fabsf(q[j]) == min1);
         idx = is_min ? j : idx;
       }
-      const float m = is_min ? n2 : n1;
-      // sign of R'_j = parity of the other edges' signs = parity ^ sign(Q_j)
-      const uint32_t rb = __float_as_uint(m) | ((__float_as_uint(q[j]) ^ pm) & 0x80000000u);
+      const float m = is_min ? n2s : n1s;
+      const uint32_t rb = __float_as_uint(m) ^ (__float_as_uint(q[j]) & 0x80000000u);
       float v = q[j] + __uint_as_float(rb);
       if (SAT) v = fminf(fmaxf(v, -post_sat), post_sat);
       st_val(L, addr[j], v);  // padding edges write the dummy slot
@@ -147,9 +158,28 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
     }
   }
   rs >>= 4 * nch - deg;  // drop the padding edges' bits
-  st_val(mag1, rec, n1);
-  st_val(mag2, rec, n2);
+  if constexpr (sizeof(MT) == 4) {
+    reinterpret_cast<float2*>(mag1)[rec] = make_float2(n1, n2);
+  } else {
+    st_val(mag1, rec, n1);
+    st_val(mag2, rec, n2);
+  }
   meta[rec] = rs | (static_cast<uint32_t>(idx) << 27);
+}
+
+// R = 0 for the first n check records (float: the magnitudes are one float2
+// array spanning the mag1 and mag2 areas).
+template <typename MT>
+__device__ __forceinline__ void zero_records(MT* mag1, MT* mag2, uint32_t* meta, int n, int k, int Z) {
+  for (int r = k; r < n; r += Z) {
+    if constexpr (sizeof(MT) == 4) {
+      reinterpret_cast<float2*>(mag1)[r] = make_float2(0.0f, 0.0f);
+    } else {
+      mag1[r] = MT(0);
+      mag2[r] = MT(0);
+    }
+    meta[r] = 0u;
+  }
 }
 
 // Edge e of a row whose chunks start at `tab`: (column base, shift).

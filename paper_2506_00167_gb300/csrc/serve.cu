@@ -212,11 +212,7 @@ __global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
     uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
     if (active) {
       cb = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + g) % a.cb_cap));
-      for (int r = k; r < cb.m_eff * Z; r += Z) {
-        mag1[r] = MT(0);
-        mag2[r] = MT(0);
-        meta[r] = 0u;
-      }
+      zero_records(mag1, mag2, meta, cb.m_eff * Z, k, Z);
       if constexpr (SAT)
         st_val(L, ssh.dummy_base + k, a.post_sat);
       else

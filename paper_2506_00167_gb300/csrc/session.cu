@@ -212,7 +212,13 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     p.shape = kv.first;
     const ShapeDev& sd = s->shapes[p.shape];
     p.Z = sd.Z;
-    std::stable_sort(p.cbs.begin(), p.cbs.end(), [&](int x, int y) { return b->cbs[x].m_eff > b->cbs[y].m_eff; });
+    // larger blocks first; among equal sizes, by noise level, so the blocks
+    // that share a work item (and, paired, a thread group) need similar
+    // iteration counts and finish together
+    std::stable_sort(p.cbs.begin(), p.cbs.end(), [&](int x, int y) {
+      if (b->cbs[x].m_eff != b->cbs[y].m_eff) return b->cbs[x].m_eff > b->cbs[y].m_eff;
+      return b->cbs[x].inv_sigma2 < b->cbs[y].inv_sigma2;
+    });
     for (int i : p.cbs) {
       p.max_n = std::max(p.max_n, b->cbs[i].n_eff);
       p.max_m = std::max(p.max_m, b->cbs[i].m_eff);
