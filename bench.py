@@ -55,6 +55,19 @@ def make_workload(name: str, rank: int = 0, n: int | None = None):
     raise ValueError(name)
 
 
+def reduce_over_ranks(ms: float, units: int, world: int, device=None):
+    """(slowest rank's time, all ranks' units): the timing contract across replicas."""
+    if world == 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t_ms = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_u = torch.tensor([int(units)], dtype=torch.int64, device=device)
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_u, op=dist.ReduceOp.SUM)
+    return float(t_ms.item()), int(t_u.item())
+
+
 def oracle_sample(w, n_tb: int, n_chunks: int):
     from workload.configs import subset
     idx = np.arange(min(n_tb, w.n_tb))
@@ -487,13 +500,10 @@ def main():
     s, b, out, ms, k_ms, status = timed(mode)
     clocks = clk.stop()
 
-    # max over ranks
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    # slowest rank, all ranks' decoded bits
     info_bits = w.info_bits_total()
-    value = world * info_bits * args.steps / (ms / 1e3) / 1e9
+    ms, all_bits = reduce_over_ranks(ms, info_bits * args.steps, world, dev)
+    value = all_bits / (ms / 1e3) / 1e9
     ms_step = ms / args.steps
 
     # ---- the same step as one captured CUDA graph per step
@@ -535,12 +545,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
-    e2e_val = world * info_bits * args.steps / (ms_e2e / 1e3) / 1e9
+    ms_e2e, e2e_bits = reduce_over_ranks(e0.elapsed_time(e1), info_bits * args.steps, world, dev)
+    e2e_val = e2e_bits / (ms_e2e / 1e3) / 1e9
     h2d = sym_h.numel() * 8 + mask_h.numel() * 4
     d2h = sum(t.numel() * t.element_size() for t in res_h.values())
 

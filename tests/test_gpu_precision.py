@@ -1,0 +1,32 @@
+"""Precision on the GPU against the float64 oracle: BLER inside the oracle's 95 % Wilson interval."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import path as opath
+from oracle.stats import wilson
+from workload import large_fp32
+
+from gpu_helpers import batch_for, device_inputs, session_for
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fp32_and_int16_bler_inside_oracle_interval():
+    # 7.5 dB Es/N0 sits in the waterfall of this code (BLER ~ 0.4), where a
+    # precision loss would show first
+    w = large_fp32(n_cw=192, snr_points=(7.5,), seed=71)
+    ref = opath.run(w, "f64", 10, True)
+    err_ref = opath.block_errors(w, ref["words"])
+    lo, hi = wilson(int(err_ref.sum()), w.n_cb)
+    assert 0.05 < err_ref.mean() < 0.95
+    sym, mask = device_inputs(w)
+    for mode in ["f32", "i16"]:
+        s = session_for(w, mode)
+        b = batch_for(s, w)
+        out = s.run(b, sym, mask, b.alloc_outputs())
+        torch.cuda.synchronize()
+        err = opath.block_errors(w, out["bits"].cpu().numpy().view(np.uint32))
+        assert lo <= err.mean() <= hi, (mode, err.mean(), lo, hi)
+        # and block by block the outcomes agree with the oracle's almost always
+        assert np.mean(err == err_ref) >= 0.97, mode
