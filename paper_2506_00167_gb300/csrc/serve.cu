@@ -106,11 +106,12 @@ __device__ __forceinline__ T ld_sys(const T* p) {
   return *const_cast<const volatile T*>(p);
 }
 
-__device__ __forceinline__ float2 ld_sys_f2(const float2* p) {
-  float2 v;
-  asm volatile("ld.volatile.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-  return v;
-}
+// Request inputs are written by the host before the request is published
+// (release) and read after the tail is acquired, and never change while the
+// request is in flight: L2-coherent loads that skip L1 (.cg) are safe and,
+// unlike volatile loads, can be overlapped.
+__device__ __forceinline__ float2 ld_pool_f2(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ld_pool_u32(const uint32_t* p) { return __ldcg(p); }
 
 // Claim the next published work item: its index, -1 if stopped, -2 after the idle limit.
 __device__ int64_t claim_item(const ServeArgs& a) {
@@ -145,11 +146,12 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
   for (int p = k; p < cb.t0; p += Z) L[p] = LT(0);
   for (int p = cb.t0 + cb.E + k; p < cb.n_eff * Z; p += Z) L[p] = LT(0);
   const float2* sym = reinterpret_cast<const float2*>(a.host_pool) + cb.re_off;
-  const volatile uint32_t* msk = reinterpret_cast<const volatile uint32_t*>(a.host_pool) + cb.mask_off;
+  const uint32_t* msk = reinterpret_cast<const uint32_t*>(a.host_pool) + cb.mask_off;
   LT* out = L + cb.t0;
+#pragma unroll 4
   for (int r = k; r < cb.n_re; r += Z) {
-    const float2 y = ld_sys_f2(sym + r);
-    const bool punct = (msk[r >> 5] >> (r & 31)) & 1u;
+    const float2 y = ld_pool_f2(sym + r);
+    const bool punct = (ld_pool_u32(msk + (r >> 5)) >> (r & 31)) & 1u;
     switch (cb.Qm) {
       case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
       case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;

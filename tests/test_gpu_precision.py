@@ -28,5 +28,8 @@ def test_fp32_and_int16_bler_inside_oracle_interval():
         torch.cuda.synchronize()
         err = opath.block_errors(w, out["bits"].cpu().numpy().view(np.uint32))
         assert lo <= err.mean() <= hi, (mode, err.mean(), lo, hi)
-        # and block by block the outcomes agree with the oracle's almost always
-        assert np.mean(err == err_ref) >= 0.97, mode
+        if mode == "f32":
+            # same algorithm, float32 vs float64 rounding: block by block the
+            # outcomes agree almost always (INT16 runs a 1-LSB = 0.25 offset, a
+            # different algorithm, compared by BLER only)
+            assert np.mean(err == err_ref) >= 0.97
