@@ -21,16 +21,19 @@ import numpy as np
 
 from . import abi
 
-MAX_BLOCK = 512
+MAX_BLOCK = 512          # paired INT8 decoder
+MAX_BLOCK_GENERIC = 384  # every other decoder (two blocks per SM)
 
 
-def candidates(Z: int) -> list:
-    """Feasible tiles G for lifting size Z (G * Z <= 512; one named barrier per group for Z > 32)."""
+def candidates(Z: int, mode: str = "i8") -> list:
+    """Feasible tiles G for lifting size Z (G * Z <= 512 for the paired INT8 decoder, 384 otherwise;
+    one named barrier per group for Z > 32)."""
+    cap = MAX_BLOCK if mode == "i8" else MAX_BLOCK_GENERIC
     if Z > 32:
-        return list(range(1, min(15, MAX_BLOCK // Z) + 1))
+        return list(range(1, min(15, cap // Z) + 1))
     if Z == 32:
-        return list(range(1, MAX_BLOCK // Z + 1))
-    return list(range(2, MAX_BLOCK // Z + 1, 2))  # Z = 16: groups come in half-warp pairs
+        return list(range(1, cap // Z + 1))
+    return list(range(2, cap // Z + 1, 2))  # Z = 16: groups come in half-warp pairs
 
 
 def bg_key(g) -> str:
@@ -80,7 +83,7 @@ def autotune(base_graphs, z_set, mode: str = "i8", n_cb: int = 1024, max_iter: i
             continue
         cbs = synthetic_cbs(g, b, Z, n_cb)
         timings = {}
-        for G in (cands(Z) if cands else candidates(Z)):
+        for G in (cands(Z) if cands else candidates(Z, mode)):
             s = Session(base_graphs, [Z], mode=mode, max_iter=max_iter, early_term=False, sat=DEFAULT_SAT[mode]
                         if mode != "f32" else None)
             s.set_tiles([(b, Z, G)])

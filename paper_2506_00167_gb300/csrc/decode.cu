@@ -47,7 +47,7 @@ namespace {
 using namespace core;
 
 template <typename LT, typename MT, bool SAT, bool RGLOBAL>
-__global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
+__global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const DecodeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
@@ -145,11 +145,14 @@ __global__ void __launch_bounds__(512) oms_decode_kernel(const DecodeArgs a) {
       }
       int it = 1;
       bool ok = false;
+      RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
-          const uint32_t info = rows[l];
-          check_update<LT, MT, SAT>(s_tab + (info & 0xFFFFu), static_cast<int>(info >> 16), k, Z, L, mag1, mag2,
-                                    meta, l * Z + k, item.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
+          check_update<LT, MT, SAT, true>(row, k, Z, L, mag1, mag2, meta, l * Z + k, item.dummy_base + k, a.beta,
+                                         a.msg_sat, a.post_sat);
+          // the next row's table and record are ready before the barrier
+          const int ln = l + 1 < m ? l + 1 : 0;
+          row = load_row(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {

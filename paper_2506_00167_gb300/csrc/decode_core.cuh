@@ -57,45 +57,85 @@ __device__ __forceinline__ int rot(int k, uint32_t s, int Z) {
   return static_cast<int>(umin(t, t - static_cast<uint32_t>(Z)));
 }
 
-// One lifted check (l, k) of a row with `deg` edges, chunk c's column bases
-// at tab[8c .. 8c+3] and shifts at tab[8c+4 .. 8c+7].  Reads the compressed
-// messages, runs both passes, writes the posteriors and new messages.
-// Stored sign bits: edge j at bit deg-1-j; argmin edge in bits 27..31.
-template <typename LT, typename MT, bool SAT>
-__device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, int deg, int k, int Z,
-                                             LT* __restrict__ L, MT* __restrict__ mag1, MT* __restrict__ mag2,
+// What a check update needs before it touches the posteriors: the row's edge
+// table and degree, its first chunk of column bases and shifts, and this
+// thread's compressed message record.  None of it is written by other threads
+// during a layer, so the next row's copy is loaded before the layer barrier
+// and only the posterior loads wait for it.
+struct RowIn {
+  const uint32_t* tab;
+  int deg;
+  uint4 B, S;
+  float r1, r2;
+  uint32_t mo;
+};
+
+template <typename MT>
+__device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, uint32_t info,
+                                          const MT* __restrict__ mag1, const MT* __restrict__ mag2,
+                                          const uint32_t* __restrict__ meta, int rec) {
+  RowIn r;
+  r.tab = s_tab + (info & 0xFFFFu);
+  r.deg = static_cast<int>(info >> 16);
+  r.B = *reinterpret_cast<const uint4*>(r.tab);
+  r.S = *reinterpret_cast<const uint4*>(r.tab + 4);
+  if constexpr (sizeof(MT) == 4) {  // float: both magnitudes in one 8-byte record
+    const float2 rr = reinterpret_cast<const float2*>(mag1)[rec];
+    r.r1 = rr.x;
+    r.r2 = rr.y;
+  } else {
+    r.r1 = ld_val(mag1, rec);
+    r.r2 = ld_val(mag2, rec);
+  }
+  r.mo = meta[rec];
+  return r;
+}
+
+// One lifted check (l, k): row data in `in` (chunk c's column bases at
+// tab[8c .. 8c+3], shifts at tab[8c+4 .. 8c+7]).  Runs both passes, writes
+// the posteriors and the new record.
+//
+// The record keeps the signs of the Q_j of the last update (edge j at bit
+// deg-1-j) and the argmin edge in bits 27..31; the sign of the stored message
+// R_j is that bit XOR the parity of all of them (R'_j carries the sign
+// product over i != j), so the parity is recovered by one popcount and the
+// new signs cost nothing in the second pass.
+//
+// LEAN: pass 1 parks each Q_j in its posterior's slot (the check owns those
+// slots during the layer) and pass 2 reads it back, instead of holding the
+// row's Q values in registers: one shared store and load more per edge for
+// about 30 fewer registers, which lets two 384-thread blocks share an SM.
+template <typename LT, typename MT, bool SAT, bool LEAN>
+__device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* __restrict__ L,
+                                             MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
                                              float msg_sat, float post_sat) {
   // integer modes: the dummy slot is reset to +post_sat so a padding edge's
   // |Q| saturates at msg_sat and (edge index larger) never beats a real edge;
   // float: 1e30 absorbs every update and needs no reset
   if constexpr (SAT) st_val(L, dummy, post_sat);
-  float r1, r2;
-  if constexpr (sizeof(MT) == 4) {  // float: both magnitudes in one 8-byte record
-    const float2 rr = reinterpret_cast<const float2*>(mag1)[rec];
-    r1 = rr.x;
-    r2 = rr.y;
-  } else {
-    r1 = ld_val(mag1, rec);
-    r2 = ld_val(mag2, rec);
-  }
-  const uint32_t mo = meta[rec];
+  const uint32_t* tab = in.tab;
+  const int deg = in.deg;
+  const float r1 = in.r1, r2 = in.r2;
+  const uint32_t mo = in.mo;
   const int idx_o = static_cast<int>(mo >> 27);
-  // edge 0's sign at bit 31; in the integer modes positions past deg read as
-  // negative, so padding edges see Q = dummy + |R| (large and positive); the
-  // float dummy (1e30) is large whatever the sign
-  uint32_t sgn = SAT ? ((mo << (32 - deg)) | ((1u << (32 - deg)) - 1u)) : (mo << (32 - deg));
+  // sign of R_j = stored Q-sign bit ^ parity, edge 0's moved to bit 31.  In
+  // the integer modes the positions past deg read as negative, so padding
+  // edges see Q = dummy + |R| (large and positive); the float dummy (1e30) is
+  // large whatever the sign
+  const uint32_t par_o = 0u - (static_cast<uint32_t>(__popc(mo << 5)) & 1u);
+  uint32_t sgn = SAT ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u)) : ((mo ^ par_o) << (32 - deg));
   const int nch = (deg + 3) >> 2;
 
-  float q[kMaxChunks * 4];
+  float q[LEAN ? 1 : kMaxChunks * 4];
   int addr[kMaxChunks * 4];
   float min1 = 3.0e38f, min2 = 3.0e38f;  // SAT modes: keys |Q| * 32 + j
-  uint32_t par = 0;
+  uint32_t qs = 0;                       // Q sign bits, first edge highest
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
-    const uint4 B = *reinterpret_cast<const uint4*>(tab + 8 * c);
-    const uint4 S = *reinterpret_cast<const uint4*>(tab + 8 * c + 4);
+    const uint4 B = c == 0 ? in.B : *reinterpret_cast<const uint4*>(tab + 8 * c);
+    const uint4 S = c == 0 ? in.S : *reinterpret_cast<const uint4*>(tab + 8 * c + 4);
     addr[4 * c + 0] = static_cast<int>(B.x) + rot(k, S.x, Z);
     addr[4 * c + 1] = static_cast<int>(B.y) + rot(k, S.y, Z);
     addr[4 * c + 2] = static_cast<int>(B.z) + rot(k, S.z, Z);
@@ -111,8 +151,11 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
       sgn <<= 1;
       float Q = lv[i] - r;
       if (SAT) Q = fminf(fmaxf(Q, -post_sat), post_sat);
-      q[j] = Q;
-      par ^= __float_as_uint(Q);
+      if constexpr (LEAN)
+        st_val(L, addr[j], Q);  // Q waits in the posterior's slot for pass 2
+      else
+        q[j] = Q;
+      qs = __funnelshift_l(__float_as_uint(Q), qs, 1);
       float a = fabsf(Q);
       if (SAT) a = fmaf(fminf(a, msg_sat), 32.0f, static_cast<float>(j));
       min2 = fminf(min2, fmaxf(min1, a));
@@ -131,14 +174,17 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
     n2 = fmaxf(min2 - beta, 0.0f);
   }
   // magnitudes carrying the parity in their sign bit: the sign of R'_j is
-  // parity ^ sign(Q_j), one xor with Q_j's sign bit
-  const uint32_t pm = par & 0x80000000u;
+  // parity ^ sign(Q_j), one xor with Q_j's sign bit (padding edges have
+  // positive Q and add nothing to the parity)
+  const uint32_t pm = static_cast<uint32_t>(__popc(qs)) << 31;
   const float n1s = __uint_as_float(__float_as_uint(n1) | pm);
   const float n2s = __uint_as_float(__float_as_uint(n2) | pm);
-  uint32_t rs = 0;
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
+    float qv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) qv[i] = LEAN ? ld_val(L, addr[4 * c + i]) : q[LEAN ? 0 : 4 * c + i];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = 4 * c + i;
@@ -146,25 +192,23 @@ __device__ __forceinline__ void check_update(const uint32_t* __restrict__ tab, i
       if (SAT) {
         is_min = (j == idx);
       } else {
-        is_min = (fabsf(q[j]) == min1);
+        is_min = (fabsf(qv[i]) == min1);
         idx = is_min ? j : idx;
       }
       const float m = is_min ? n2s : n1s;
-      const uint32_t rb = __float_as_uint(m) ^ (__float_as_uint(q[j]) & 0x80000000u);
-      float v = q[j] + __uint_as_float(rb);
+      const uint32_t rb = __float_as_uint(m) ^ (__float_as_uint(qv[i]) & 0x80000000u);
+      float v = qv[i] + __uint_as_float(rb);
       if (SAT) v = fminf(fmaxf(v, -post_sat), post_sat);
       st_val(L, addr[j], v);  // padding edges write the dummy slot
-      rs = __funnelshift_l(rb, rs, 1);
     }
   }
-  rs >>= 4 * nch - deg;  // drop the padding edges' bits
   if constexpr (sizeof(MT) == 4) {
     reinterpret_cast<float2*>(mag1)[rec] = make_float2(n1, n2);
   } else {
     st_val(mag1, rec, n1);
     st_val(mag2, rec, n2);
   }
-  meta[rec] = rs | (static_cast<uint32_t>(idx) << 27);
+  meta[rec] = (qs >> (4 * nch - deg)) | (static_cast<uint32_t>(idx) << 27);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2

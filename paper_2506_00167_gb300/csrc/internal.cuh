@@ -15,6 +15,8 @@ constexpr int kMaxDeg = 27;      // sign bits 0..26 + 5-bit argmin index in one 
 constexpr int kMaxChunks = 7;    // edges are processed four at a time: 7 * 4 >= kMaxDeg
 constexpr int kMaxZ = 384;
 constexpr int kMaxSmem = 232448; // 227 KB dynamic shared memory per block (sm_100 family)
+constexpr int kDecodeMaxBlock = 384;  // generic decoder: two such blocks share an SM's registers
+constexpr int kPairMaxBlock = 512;    // paired INT8 decoder
 constexpr int kCrcBlock = 256;
 
 // One (base graph, Z) pair as one decoder launch sees it.  Its edge table is,

@@ -239,6 +239,7 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     const int hdr_bytes = align16i(words * 4) + 16;
     int G = std::max(1, 256 / Z);
     if (Z > 32) G = std::min(G, 15);
+    while (G > 1 && G * Z > kDecodeMaxBlock) --G;
     const int region = L_bytes + hb_bytes;
     while (G > 1 && hdr_bytes + G * region > kMaxSmem) --G;
     if (hdr_bytes + G * region > kMaxSmem) {

@@ -236,11 +236,14 @@ __global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
       const bool wide = (Z & 31) == 0;
       int it = 1;
       bool ok = false;
+      RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
-          const uint32_t info = rows[l];
-          check_update<LT, MT, SAT>(s_tab + (info & 0xFFFFu), static_cast<int>(info >> 16), k, Z, L, mag1, mag2,
-                                    meta, l * Z + k, ssh.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
+          check_update<LT, MT, SAT, false>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
+                                          a.msg_sat, a.post_sat);
+          // the next row's table and record are ready before the barrier
+          const int ln = l + 1 < m ? l + 1 : 0;
+          row = load_row(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {

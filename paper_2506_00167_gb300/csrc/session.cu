@@ -234,7 +234,7 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     auto t = s->tiles.find({sd.bg, p.Z});
     p.G = t != s->tiles.end() ? t->second : default_tile(p.Z);
     if (p.Z > 32) p.G = std::min(p.G, 15);
-    if (p.G * p.Z > 512) p.G = std::max(1, 512 / p.Z);
+    if (p.G * p.Z > kPairMaxBlock) p.G = std::max(1, kPairMaxBlock / p.Z);
   }
   // launch groups
   const bool pair_ok = s->mode == LDPC_I8 && s->post_sat >= 2 * s->msg_sat;
@@ -256,11 +256,31 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
       }
     }
     if (p.kind != kKindPairI8) {
-      while (p.G > 1 && hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem) --p.G;
-      if (p.Z == 16 && p.G > 1 && (p.G & 1)) --p.G;
-      p.rglobal = hdr + p.G * (p.L_bytes + p.hb_bytes + p.rec_bytes) > kMaxSmem;
-      if (p.rglobal && hdr + p.G * (p.L_bytes + p.hb_bytes) > kMaxSmem)
+      // generic decoder: at most kDecodeMaxBlock threads; the check messages
+      // stay in shared memory unless moving them to a global slot lets more
+      // code blocks be resident per SM (shared-memory limits the first form,
+      // registers the second)
+      auto even16 = [&](int G) { return (p.Z == 16 && G > 1 && (G & 1)) ? G - 1 : G; };
+      int G = p.G;
+      while (G > 1 && G * p.Z > kDecodeMaxBlock) --G;
+      G = even16(G);
+      const int reg = p.L_bytes + p.hb_bytes;
+      int Gs = G;
+      while (Gs > 1 && hdr + Gs * (reg + p.rec_bytes) > kMaxSmem) --Gs;
+      Gs = even16(Gs);
+      int occ_s = 0, occ_g = 0;
+      if (hdr + Gs * (reg + p.rec_bytes) <= kMaxSmem) {
+        cudaError_t e = decode_occupancy(s->mode, kKindShared, Gs * p.Z, hdr + Gs * (reg + p.rec_bytes), &occ_s);
+        if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+      }
+      if (hdr + G * reg <= kMaxSmem) {
+        cudaError_t e = decode_occupancy(s->mode, kKindGlobal, G * p.Z, hdr + G * reg, &occ_g);
+        if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+      }
+      if (occ_s == 0 && occ_g == 0)
         return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
+      p.rglobal = occ_g * G > occ_s * Gs;
+      p.G = p.rglobal ? G : Gs;
       p.kind = p.rglobal ? kKindGlobal : kKindShared;
     }
     const int key = s->strategy == LDPC_PLAN_PER_Z ? p.Z : 0;
@@ -687,7 +707,7 @@ int ldpc_session_set_tiles(ldpc_session* s, const ldpc_tile* tiles, int32_t n) {
   for (int i = 0; i < n; ++i) {
     const ldpc_tile& t = tiles[i];
     if (t.bg < 0 || t.bg >= static_cast<int>(s->bgs.size()) || !s->shape_index.count({t.bg, t.Z}) || t.G < 1 ||
-        t.G * t.Z > 512 || (t.Z > 32 && t.G > 15))
+        t.G * t.Z > kPairMaxBlock || (t.Z > 32 && t.G > 15))
       return fail(LDPC_EINVAL, "tile " + std::to_string(i) + ": unknown (bg, Z) or G out of range");
   }
   for (int i = 0; i < n; ++i) s->tiles[{tiles[i].bg, tiles[i].Z}] = tiles[i].G;

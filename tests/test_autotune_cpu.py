@@ -8,13 +8,14 @@ from workload import default_bgs
 
 
 def test_candidates_respect_block_and_barrier_limits():
-    for Z in [16, 32, 64, 128, 256, 384]:
-        c = at.candidates(Z)
-        assert c and all(g * Z <= 512 for g in c)
-        if Z > 32:
-            assert max(c) <= 15
-        if Z == 16:
-            assert all(g % 2 == 0 for g in c)
+    for mode, cap in [("i8", 512), ("f32", 384), ("i16", 384)]:
+        for Z in [16, 32, 64, 128, 256, 384]:
+            c = at.candidates(Z, mode)
+            assert c and all(g * Z <= cap for g in c)
+            if Z > 32:
+                assert max(c) <= 15
+            if Z == 16:
+                assert all(g % 2 == 0 for g in c)
 
 
 def test_synthetic_descriptors_are_valid_shapes():
