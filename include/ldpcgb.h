@@ -153,8 +153,8 @@ LDPC_API int ldpc_session_set_stream(ldpc_session *s, void *cuda_stream);
 /* Work-item tile: code blocks of base graph `bg` at lifting size `Z` are decoded
  * `G` per thread block (G groups of Z threads).  Tiles set here override the
  * built-in default (256 / Z, at most 15 for Z > 32) for batches created
- * afterwards; G * Z <= 512.  The planner lowers G further when shared memory
- * requires it, and to G * Z <= 384 for every decoder but the paired INT8 one.
+ * afterwards; G * Z <= 512.  The planner lowers G to G * Z <= 384 (two decoder
+ * blocks share an SM) and further when shared memory requires it.
  * An autotuner chooses them by timing candidates (paper has no counterpart). */
 typedef struct {
   int32_t bg, Z, G;

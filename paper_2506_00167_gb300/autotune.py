@@ -21,19 +21,18 @@ import numpy as np
 
 from . import abi
 
-MAX_BLOCK = 512          # paired INT8 decoder
-MAX_BLOCK_GENERIC = 384  # every other decoder (two blocks per SM)
+MAX_BLOCK = 384  # two decoder blocks share an SM's registers
 
 
 def candidates(Z: int, mode: str = "i8") -> list:
-    """Feasible tiles G for lifting size Z (G * Z <= 512 for the paired INT8 decoder, 384 otherwise;
-    one named barrier per group for Z > 32)."""
-    cap = MAX_BLOCK if mode == "i8" else MAX_BLOCK_GENERIC
+    """Feasible tiles G for lifting size Z (G * Z <= 384; one named barrier per group for Z > 32).
+    The bound is the same for every mode; `mode` is accepted for symmetry with the tuner."""
+    del mode
     if Z > 32:
-        return list(range(1, min(15, cap // Z) + 1))
+        return list(range(1, min(15, MAX_BLOCK // Z) + 1))
     if Z == 32:
-        return list(range(1, cap // Z + 1))
-    return list(range(2, cap // Z + 1, 2))  # Z = 16: groups come in half-warp pairs
+        return list(range(1, MAX_BLOCK // Z + 1))
+    return list(range(2, MAX_BLOCK // Z + 1, 2))  # Z = 16: groups come in half-warp pairs
 
 
 def bg_key(g) -> str:

@@ -195,7 +195,12 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
 // pair runs the first block's rows; for the second block the extra rows only
 // touch its never-sent parity columns (LLR 0) and leave every other variable
 // unchanged, and its syndrome covers its own rows only.
-__global__ void __launch_bounds__(512) oms_decode_i8x2_kernel(const DecodeArgs a) {
+//
+// RGLOBAL: the three message words per check live in a global scratch slot
+// per resident group, and the int8 LLRs are read straight from global memory
+// (one 32-bit load per four variables of each block) instead of being staged.
+template <bool RGLOBAL>
+__global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(const DecodeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
@@ -229,18 +234,22 @@ __global__ void __launch_bounds__(512) oms_decode_i8x2_kernel(const DecodeArgs a
     uint32_t* hbA = reinterpret_cast<uint32_t*>(reg + item.L_bytes);
     uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + item.L_bytes + item.hb_bytes);
     uint8_t* recs = reg + item.L_bytes + 2 * item.hb_bytes;
+    if (RGLOBAL) recs = a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.G + g) * a.rscratch_group;
     uint32_t* mags = reinterpret_cast<uint32_t*>(recs);
     uint32_t* sg1 = mags + item.rec_cap;
     uint32_t* sg2 = sg1 + item.rec_cap;
 
-    // ---- stage the table and each pair's int8 LLRs (into its message area)
+    // ---- stage the table and (shared-message form) each pair's int8 LLRs
+    // into its message area
     if (tid == 0) {
       fence_proxy_async_smem();
       uint32_t bytes = static_cast<uint32_t>(sh.tab_words) * 4u;
-      for (int c = 0; c < item.count; ++c) bytes += static_cast<uint32_t>(a.cbs[a.item_cbs[item.first + c]].n_eff * Z);
+      if (!RGLOBAL)
+        for (int c = 0; c < item.count; ++c)
+          bytes += static_cast<uint32_t>(a.cbs[a.item_cbs[item.first + c]].n_eff * Z);
       mbar_arrive_expect_tx(s_bar, bytes);
       bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
-      for (int pp = 0; pp < pairs; ++pp) {
+      for (int pp = 0; pp < (RGLOBAL ? 0 : pairs); ++pp) {
         uint8_t* st = regions + pp * item.region_bytes + item.L_bytes + 2 * item.hb_bytes;
         const CbDev ca = a.cbs[a.item_cbs[item.first + 2 * pp]];
         const uint32_t na = static_cast<uint32_t>(ca.n_eff * Z);
@@ -272,14 +281,33 @@ __global__ void __launch_bounds__(512) oms_decode_i8x2_kernel(const DecodeArgs a
       return;
     }
     if (active) {
-      const int8_t* stA = reinterpret_cast<const int8_t*>(recs);
-      const int8_t* stB = stA + ((A.n_eff * Z + 15) & ~15);
       const int nA = A.n_eff * Z, nB = hasB ? Bc.n_eff * Z : 0;
       const __half2 h1536 = __float2half2_rn(1536.0f);
-      for (int p = k; p < nA; p += Z) {
-        const uint32_t va = static_cast<uint32_t>(0x6600 + stA[p]) & 0xFFFFu;
-        const uint32_t vb = static_cast<uint32_t>(0x6600 + (p < nB ? stB[p] : 0)) & 0xFFFFu;
-        L[p] = as_u32(__hsub2(as_h2(va | (vb << 16)), h1536));
+      if (RGLOBAL) {
+        // n_eff * Z is a multiple of 32 and the LLR offsets of 16: four
+        // variables per 32-bit load, written as one 16-byte store
+        const uint32_t* gA = reinterpret_cast<const uint32_t*>(static_cast<const int8_t*>(a.llr) + A.llr_off);
+        const uint32_t* gB = reinterpret_cast<const uint32_t*>(static_cast<const int8_t*>(a.llr) + Bc.llr_off);
+        for (int p4 = k; p4 < (nA >> 2); p4 += Z) {
+          const uint32_t wa = __ldg(gA + p4);
+          const uint32_t wb = 4 * p4 < nB ? __ldg(gB + p4) : 0u;
+          uint32_t o[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t va = (0x6600u + static_cast<uint32_t>(static_cast<int8_t>(wa >> (8 * i)))) & 0xFFFFu;
+            const uint32_t vb = (0x6600u + static_cast<uint32_t>(static_cast<int8_t>(wb >> (8 * i)))) & 0xFFFFu;
+            o[i] = as_u32(__hsub2(as_h2(va | (vb << 16)), h1536));
+          }
+          reinterpret_cast<uint4*>(L)[p4] = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+      } else {
+        const int8_t* stA = reinterpret_cast<const int8_t*>(recs);
+        const int8_t* stB = stA + ((nA + 15) & ~15);
+        for (int p = k; p < nA; p += Z) {
+          const uint32_t va = static_cast<uint32_t>(0x6600 + stA[p]) & 0xFFFFu;
+          const uint32_t vb = static_cast<uint32_t>(0x6600 + (p < nB ? stB[p] : 0)) & 0xFFFFu;
+          L[p] = as_u32(__hsub2(as_h2(va | (vb << 16)), h1536));
+        }
       }
       group_sync(Z, g, 0xFFFFFFFFu);
       for (int r = k; r < A.m_eff * Z; r += Z) {
@@ -344,13 +372,14 @@ const void* kernel_for(int mode, bool rglobal) {
 }  // namespace
 
 const void* kernel_kind(int mode, int kind) {
-  return kind == kKindPairI8 ? reinterpret_cast<const void*>(&oms_decode_i8x2_kernel)
-                             : kernel_for(mode, kind == kKindGlobal);
+  if (kind == kKindPairI8) return reinterpret_cast<const void*>(&oms_decode_i8x2_kernel<false>);
+  if (kind == kKindPairI8Global) return reinterpret_cast<const void*>(&oms_decode_i8x2_kernel<true>);
+  return kernel_for(mode, kind == kKindGlobal);
 }
 
 cudaError_t decode_prepare(int mode) {
-  for (int kind = 0; kind < 3; ++kind) {
-    if (kind == kKindPairI8 && mode != LDPC_I8) continue;
+  for (int kind = 0; kind < kKinds; ++kind) {
+    if (kind_is_pair(kind) && mode != LDPC_I8) continue;
     cudaError_t e = cudaFuncSetAttribute(kernel_kind(mode, kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSmem);
     if (e != cudaSuccess) return e;

@@ -327,7 +327,10 @@ __device__ __forceinline__ __half2 small_pair(uint32_t a, uint32_t b) {
   return __hsub2(as_h2((0x6400u + a) | ((0x6400u + b) << 16)), __float2half2_rn(1024.0f));
 }
 
-// one pair check (l, k); `dummy` is this thread's dummy slot
+// one pair check (l, k); `dummy` is this thread's dummy slot.  Pass 1 parks
+// each Q_j pair in its posterior's slot and pass 2 reads it back (the check
+// owns those slots during the layer), which keeps the row's Q values out of
+// registers.
 __device__ __forceinline__ void check_update_x2(const uint32_t* __restrict__ tab, int deg, int k, int Z,
                                                 uint32_t* __restrict__ L, uint32_t* __restrict__ mags,
                                                 uint32_t* __restrict__ sg1, uint32_t* __restrict__ sg2, int rec,
@@ -344,7 +347,6 @@ __device__ __forceinline__ void check_update_x2(const uint32_t* __restrict__ tab
   const __half2 npost = __hneg2(post);
   const int nch = (deg + 3) >> 2;
 
-  uint32_t q[kMaxChunks * 4];
   int addr[kMaxChunks * 4];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
   uint32_t par = 0;
@@ -371,8 +373,8 @@ __device__ __forceinline__ void check_update_x2(const uint32_t* __restrict__ tab
       sgn <<= 1;
       __half2 Q = __hsub2(as_h2(lv[i]), as_h2(rb));
       Q = __hmin2(__hmax2(Q, npost), post);
-      q[j] = as_u32(Q);
-      par ^= q[j];
+      L[addr[j]] = as_u32(Q);
+      par ^= as_u32(Q);
       const __half2 key = __hfma2(__hmin2(__habs2(Q), msg), h32, J);
       min2 = __hmin2(min2, __hmax2(min1, key));
       min1 = __hmin2(min1, key);
@@ -389,12 +391,15 @@ __device__ __forceinline__ void check_update_x2(const uint32_t* __restrict__ tab
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
+    uint32_t qv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) qv[i] = L[addr[4 * c + i]];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = 4 * c + i;
       const uint32_t eq = __heq2_mask(In, __float2half2_rn(static_cast<float>(j)));
-      const uint32_t rb = ((as_u32(N2) & eq) | (as_u32(N1) & ~eq)) | ((q[j] ^ pm) & 0x80008000u);
-      __half2 v = __hadd2(as_h2(q[j]), as_h2(rb));
+      const uint32_t rb = ((as_u32(N2) & eq) | (as_u32(N1) & ~eq)) | ((qv[i] ^ pm) & 0x80008000u);
+      __half2 v = __hadd2(as_h2(qv[i]), as_h2(rb));
       v = __hmin2(__hmax2(v, npost), post);
       L[addr[j]] = as_u32(v);  // padding edges write the dummy slot
       const uint32_t bit = (rb >> 15) & 0x00010001u;

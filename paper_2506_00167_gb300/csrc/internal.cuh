@@ -15,8 +15,8 @@ constexpr int kMaxDeg = 27;      // sign bits 0..26 + 5-bit argmin index in one 
 constexpr int kMaxChunks = 7;    // edges are processed four at a time: 7 * 4 >= kMaxDeg
 constexpr int kMaxZ = 384;
 constexpr int kMaxSmem = 232448; // 227 KB dynamic shared memory per block (sm_100 family)
-constexpr int kDecodeMaxBlock = 384;  // generic decoder: two such blocks share an SM's registers
-constexpr int kPairMaxBlock = 512;    // paired INT8 decoder
+constexpr int kDecodeMaxBlock = 384;  // decoder blocks: two of them share an SM's registers
+constexpr int kTileMaxBlock = 512;    // largest G * Z a tile may request
 constexpr int kCrcBlock = 256;
 
 // One (base graph, Z) pair as one decoder launch sees it.  Its edge table is,
@@ -113,10 +113,15 @@ void set_error(const std::string& msg);
 
 // Kernel launchers (defined next to their kernels).
 // Decoder kernel kinds: messages in shared memory, in global memory, or the
-// INT8 kernel that decodes two code blocks per thread group.
+// INT8 kernel that decodes two code blocks per thread group (messages in
+// shared or in global memory).
 constexpr int kKindShared = 0;
 constexpr int kKindGlobal = 1;
 constexpr int kKindPairI8 = 2;
+constexpr int kKindPairI8Global = 3;
+constexpr int kKinds = 4;
+constexpr bool kind_is_pair(int kind) { return kind == kKindPairI8 || kind == kKindPairI8Global; }
+constexpr bool kind_is_global(int kind) { return kind == kKindGlobal || kind == kKindPairI8Global; }
 cudaError_t launch_decode(int mode, int kind, dim3 grid, dim3 block, int smem, cudaStream_t st,
                           const DecodeArgs& a);
 cudaError_t decode_occupancy(int mode, int kind, int block, int smem, int* blocks_per_sm);

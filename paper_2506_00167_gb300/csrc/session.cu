@@ -234,56 +234,73 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
     auto t = s->tiles.find({sd.bg, p.Z});
     p.G = t != s->tiles.end() ? t->second : default_tile(p.Z);
     if (p.Z > 32) p.G = std::min(p.G, 15);
-    if (p.G * p.Z > kPairMaxBlock) p.G = std::max(1, kPairMaxBlock / p.Z);
+    if (p.G * p.Z > kDecodeMaxBlock) p.G = std::max(1, kDecodeMaxBlock / p.Z);
   }
-  // launch groups
+  // launch groups.  Per shape, both record placements are sized: messages in
+  // shared memory (G lowered until the region fits) or in a global slot per
+  // resident group; the global form is preferred when it lets more code
+  // blocks be resident per SM (shared memory limits the first form, registers
+  // the second).  Shapes that share a launch share the placement: global if
+  // any of them prefers it, so a mixed batch stays one persistent launch.
   const bool pair_ok = s->mode == LDPC_I8 && s->post_sat >= 2 * s->msg_sat;
+  struct Opt {
+    bool pair = false, pref_global = false;
+    int Gs = 0, Gg = 0, reg = 0, recs = 0;
+  };
+  std::map<int, Opt> opts;
+  std::map<std::pair<int, bool>, bool> key_global;  // (launch key, pair family) -> global placement
+  for (auto& kv : sps) {
+    SP& p = kv.second;
+    Opt o;
+    const int hdr = align16(p.tab_words * 4) + 16;
+    o.pair = pair_ok && p.Z % 32 == 0;
+    if (o.pair) {
+      // two code blocks per group: posteriors as half2 pairs, two bitmaps, 3 message words per check
+      // (in shared memory the message area first holds both blocks' int8 LLRs)
+      p.pair_L = align16((p.max_n + 1) * p.Z * 4);
+      o.recs = std::max(align16(3 * p.max_m * p.Z * 4), 2 * align16(p.max_n * p.Z));
+      o.reg = p.pair_L + 2 * p.hb_bytes;
+      p.rec_bytes = 3 * align16(p.max_m * p.Z * 4);
+    } else {
+      o.recs = p.rec_bytes;
+      o.reg = p.L_bytes + p.hb_bytes;
+    }
+    auto even16 = [&](int G) { return (p.Z == 16 && G > 1 && (G & 1)) ? G - 1 : G; };
+    int G = p.G;
+    while (G > 1 && G * p.Z > kDecodeMaxBlock) --G;
+    G = even16(G);
+    int Gs = G;
+    while (Gs > 1 && hdr + Gs * (o.reg + o.recs) > kMaxSmem) --Gs;
+    Gs = even16(Gs);
+    const int kind_s = o.pair ? kKindPairI8 : kKindShared, kind_g = o.pair ? kKindPairI8Global : kKindGlobal;
+    int occ_s = 0, occ_g = 0;
+    if (hdr + Gs * (o.reg + o.recs) <= kMaxSmem) {
+      cudaError_t e = decode_occupancy(s->mode, kind_s, Gs * p.Z, hdr + Gs * (o.reg + o.recs), &occ_s);
+      if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+    }
+    if (hdr + G * o.reg <= kMaxSmem) {
+      cudaError_t e = decode_occupancy(s->mode, kind_g, G * p.Z, hdr + G * o.reg, &occ_g);
+      if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+    }
+    if (occ_g == 0)
+      return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
+    o.Gs = occ_s > 0 ? Gs : 0;
+    o.Gg = G;
+    o.pref_global = occ_g * G > occ_s * Gs;
+    const int key = s->strategy == LDPC_PLAN_PER_Z ? p.Z : 0;
+    key_global[{key, o.pair}] = key_global[{key, o.pair}] || o.pref_global;
+    opts[kv.first] = o;
+  }
   std::map<std::pair<int, int>, std::vector<int>> groups;  // (key, kind) -> shapes
   for (auto& kv : sps) {
     SP& p = kv.second;
-    const int hdr = align16(p.tab_words * 4) + 16;
-    if (pair_ok && p.Z % 32 == 0) {
-      // two code blocks per group: posteriors as half2 pairs, two bitmaps, 3 message words per check
-      // (the message area first holds both blocks' int8 LLRs)
-      p.pair_L = align16((p.max_n + 1) * p.Z * 4);
-      const int recs = std::max(align16(3 * p.max_m * p.Z * 4), 2 * align16(p.max_n * p.Z));
-      p.pair_region = p.pair_L + 2 * p.hb_bytes + recs;
-      int G = p.G;
-      while (G > 1 && hdr + G * p.pair_region > kMaxSmem) --G;
-      if (hdr + G * p.pair_region <= kMaxSmem) {
-        p.kind = kKindPairI8;
-        p.G = G;
-      }
-    }
-    if (p.kind != kKindPairI8) {
-      // generic decoder: at most kDecodeMaxBlock threads; the check messages
-      // stay in shared memory unless moving them to a global slot lets more
-      // code blocks be resident per SM (shared-memory limits the first form,
-      // registers the second)
-      auto even16 = [&](int G) { return (p.Z == 16 && G > 1 && (G & 1)) ? G - 1 : G; };
-      int G = p.G;
-      while (G > 1 && G * p.Z > kDecodeMaxBlock) --G;
-      G = even16(G);
-      const int reg = p.L_bytes + p.hb_bytes;
-      int Gs = G;
-      while (Gs > 1 && hdr + Gs * (reg + p.rec_bytes) > kMaxSmem) --Gs;
-      Gs = even16(Gs);
-      int occ_s = 0, occ_g = 0;
-      if (hdr + Gs * (reg + p.rec_bytes) <= kMaxSmem) {
-        cudaError_t e = decode_occupancy(s->mode, kKindShared, Gs * p.Z, hdr + Gs * (reg + p.rec_bytes), &occ_s);
-        if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
-      }
-      if (hdr + G * reg <= kMaxSmem) {
-        cudaError_t e = decode_occupancy(s->mode, kKindGlobal, G * p.Z, hdr + G * reg, &occ_g);
-        if (e != cudaSuccess) return fail(LDPC_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
-      }
-      if (occ_s == 0 && occ_g == 0)
-        return fail(LDPC_EINVAL, "Z=" + std::to_string(p.Z) + ": code block too large for shared memory");
-      p.rglobal = occ_g * G > occ_s * Gs;
-      p.G = p.rglobal ? G : Gs;
-      p.kind = p.rglobal ? kKindGlobal : kKindShared;
-    }
+    const Opt& o = opts[kv.first];
     const int key = s->strategy == LDPC_PLAN_PER_Z ? p.Z : 0;
+    const bool glob = key_global[{key, o.pair}];
+    p.G = glob ? o.Gg : o.Gs;
+    p.rglobal = glob;
+    p.kind = o.pair ? (glob ? kKindPairI8Global : kKindPairI8) : (glob ? kKindGlobal : kKindShared);
+    if (o.pair) p.pair_region = glob ? o.reg : o.reg + o.recs;
     groups[{key, p.kind}].push_back(kv.first);
   }
   std::vector<DecodeItem> items;
@@ -293,8 +310,8 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
   int64_t scratch_total = 0;
   for (auto& gkv : groups) {
     const int kind = gkv.first.second;
-    const bool rglobal = kind == kKindGlobal;
-    const bool pair = kind == kKindPairI8;
+    const bool rglobal = kind_is_global(kind);
+    const bool pair = kind_is_pair(kind);
     Launch L;
     L.rglobal = rglobal;
     L.kind = kind;
@@ -707,7 +724,7 @@ int ldpc_session_set_tiles(ldpc_session* s, const ldpc_tile* tiles, int32_t n) {
   for (int i = 0; i < n; ++i) {
     const ldpc_tile& t = tiles[i];
     if (t.bg < 0 || t.bg >= static_cast<int>(s->bgs.size()) || !s->shape_index.count({t.bg, t.Z}) || t.G < 1 ||
-        t.G * t.Z > kPairMaxBlock || (t.Z > 32 && t.G > 15))
+        t.G * t.Z > kTileMaxBlock || (t.Z > 32 && t.G > 15))
       return fail(LDPC_EINVAL, "tile " + std::to_string(i) + ": unknown (bg, Z) or G out of range");
   }
   for (int i = 0; i < n; ++i) s->tiles[{tiles[i].bg, tiles[i].Z}] = tiles[i].G;

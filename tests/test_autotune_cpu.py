@@ -8,7 +8,7 @@ from workload import default_bgs
 
 
 def test_candidates_respect_block_and_barrier_limits():
-    for mode, cap in [("i8", 512), ("f32", 384), ("i16", 384)]:
+    for mode, cap in [("i8", 384), ("f32", 384), ("i16", 384)]:
         for Z in [16, 32, 64, 128, 256, 384]:
             c = at.candidates(Z, mode)
             assert c and all(g * Z <= cap for g in c)
