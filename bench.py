@@ -168,6 +168,30 @@ def decoder_traffic(mode: str, n_cb: int, config: str):
     return None if m is None else m["bytes_per_launch_full"] * n_cb / m["scaled_to"]
 
 
+TILE_CACHE = os.path.join(ROOT, "results", "autotune_tiles.json")
+
+
+def apply_tiles(s, w, mode: str, how: str, world: int = 1):
+    """Work-item tiles for the session: 'auto' = the autotuner's cache for this GPU and mode (tuned now, on
+    the workload's shapes, when the cache has no entry and the run has one rank), 'default' = built-in
+    tiles, else a cache path."""
+    if how == "default":
+        return {"source": "built-in default"}
+    path = TILE_CACHE if how == "auto" else how
+    tag = w.meta.get("name")
+    n = s.load_tiles(path, w.bgs, tag=tag)
+    tuned_now = False
+    if n == 0 and how == "auto" and world == 1:
+        from paper_2506_00167_gb300.autotune import autotune_batch
+        autotune_batch(w.bgs, w.z_set, w.cbs, mode=mode, max_iter=3, reps=3, cache_path=path, tag=tag)
+        n = s.load_tiles(path, w.bgs, tag=tag)
+        tuned_now = True
+    if n == 0:
+        return {"source": "built-in default (no autotuner entry for this GPU)"}
+    return {"source": "autotuner cache " + os.path.relpath(path, ROOT) + (" (tuned in this run)" if tuned_now else ""),
+            "shapes": n}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -389,6 +413,8 @@ def main():
     ap.add_argument("--mode", default=None, choices=["f32", "i8", "i16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-int8", action="store_true")
+    ap.add_argument("--tiles", default="auto",
+                    help="decoder tiles: auto (autotuner cache for this GPU, tuned if absent), default, or a path")
     ap.add_argument("--cpu-tb", type=int, default=1536, help="TBs in the timed CPU-oracle sample")
     ap.add_argument("--n", type=int, default=None, help="workload size (code blocks / slots); default full")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
@@ -450,8 +476,11 @@ def main():
         if world > 1:
             dist.barrier()
 
+    tiles_used = {}
+
     def timed(mode_):
         s = Session(w.bgs, w.z_set, mode=mode_, max_iter=mi, early_term=et, sat=SAT[mode_])
+        tiles_used[mode_] = apply_tiles(s, w, mode_, args.tiles, world)
         b = s.batch(w.cbs, w.tbs, w.slot_N)
         out = b.alloc_outputs(local)
         stream = torch.cuda.current_stream(dev)
@@ -590,7 +619,7 @@ def main():
                "sample": f"first {min(args.cpu_tb, w.n_tb)} TBs of the workload, float64 oracle "
                          f"(demap + decode + CRC), {cores} spawned processes, {dt:.1f} s wall"}
 
-    gpu_launches = args.steps * (2 + len(set(int(z) for z in w.cbs["Z"])))
+    gpu_launches = args.steps * (2 + len(b.plan()))  # demap + decoder launches + CRC/goodput per step
     line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"f32": "f32", "i8": "i8", "i16": "i16"}[mode],
@@ -603,7 +632,7 @@ def main():
                        "mean_iters": float(np.mean(status & 0xFFFF)),
                        "l2": "inputs larger than L2 (symbols %.0f MB + LLRs %.0f MB per step)"
                              % (w.sym.size * 8 / 1e6, hb["decode"] / 1e6),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tiles": tiles_used.get(mode)},
             "codewords_per_s": world * w.n_cb * args.steps / (ms / 1e3),
             "graph": {"ms_per_step": ms_graph / args.steps,
                       "value": world * info_bits * args.steps / (ms_graph / 1e3) / 1e9, "unit": "Gbit/s",

@@ -4,12 +4,21 @@ A tile is G: how many code blocks of one (base graph, Z) shape a thread block
 decodes side by side (G groups of Z threads).  Larger G means more warps per
 block and fewer block-level hand-offs; smaller G means less shared memory per
 block and therefore more resident blocks.  The best G depends on the shape,
-the mode and the GPU, so it is measured: for each shape the tuner times
-``decode_batch`` on a synthetic batch for every feasible G (fixed iteration
-count, early termination off, random LLRs on the device -- the per-iteration
-cost does not depend on the values) and keeps the fastest.  Results are cached
-as JSON keyed by the GPU name, the mode and a hash of the base graph, and
-applied to a session with ``Session.load_tiles``.
+the mode, the GPU and -- because a mixed batch is one persistent launch whose
+block size is the largest G * Z of its shapes -- on the other shapes in the
+batch.  So it is measured:
+
+* ``autotune`` times each shape alone, on a synthetic batch large enough to
+  fill the GPU, for every feasible G and keeps the fastest;
+* ``autotune_batch`` tunes the tiles of every shape of a given batch
+  together, by coordinate descent on the decode time of the whole batch,
+  starting from the built-in tiles and keeping a change only when it gains.
+
+Both time ``decode_batch`` with a fixed iteration count and early termination
+off on random LLRs (the per-iteration cost does not depend on the values).
+Results are cached as JSON keyed by the GPU name, the mode and an optional
+workload tag, with each tile keyed by a hash of its base graph, and applied to
+a session with ``Session.load_tiles``.
 """
 from __future__ import annotations
 
@@ -66,9 +75,126 @@ def synthetic_cbs(g, bg_index: int, Z: int, n_cb: int, rate: float = 0.5, Qm: in
     return cbs
 
 
-def autotune(base_graphs, z_set, mode: str = "i8", n_cb: int = 1024, max_iter: int = 3, reps: int = 5,
-             cache_path: str | None = None, shapes=None, cands=None) -> dict:
-    """Time every feasible tile for each (base graph, Z); returns (and optionally caches) the results."""
+def default_tile(Z: int) -> int:
+    """The library's built-in tile (as the planner applies it: G * Z <= 384, even G for Z = 16)."""
+    G = max(1, 256 // Z)
+    if Z > 32:
+        G = min(G, 15)
+    G = min(G, max(1, MAX_BLOCK // Z))
+    if Z == 16 and G > 1 and G % 2:
+        G -= 1
+    return G
+
+
+def _random_llr(n: int, mode: str):
+    import torch
+
+    from .session import DEFAULT_SAT, LLR_TORCH
+    if mode == "f32":
+        return torch.randn(n, device="cuda", dtype=torch.float32) * 4.0
+    lim = DEFAULT_SAT[mode][0]
+    return torch.randint(-lim, lim + 1, (n,), device="cuda", dtype=torch.int32).to(LLR_TORCH[mode])
+
+
+def _time_decode(base_graphs, z_set, mode, max_iter, tiles, cbs, reps, llr_cache):
+    """Mean decode_batch time (ms) of the batch `cbs` under the given tiles, or None if it does not plan."""
+    import torch
+
+    from .session import DEFAULT_SAT, Session
+    s = Session(base_graphs, z_set, mode=mode, max_iter=max_iter, early_term=False,
+                sat=DEFAULT_SAT[mode] if mode != "f32" else None)
+    try:
+        s.set_tiles(tiles)
+        bt = s.batch(cbs)
+    except abi.LdpcError:
+        s.close()
+        return None
+    n = bt.info.llr_elems
+    if llr_cache.get("n") != n:
+        llr_cache["n"], llr_cache["llr"] = n, _random_llr(n, mode)
+    llr = llr_cache["llr"]
+    bits = torch.empty(bt.info.bits_words, dtype=torch.int32, device="cuda")
+    status = torch.empty(bt.n_cb, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        s.decode_batch(bt, llr, bits, status)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        s.decode_batch(bt, llr, bits, status)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del bt
+    s.close()
+    return ms
+
+
+def _write_cache(cache_path, key, entry):
+    merged = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            merged = json.load(f)
+    prev = {(t["bg"], t["Z"]): t for t in merged.get(key, {}).get("tiles", [])}
+    for t in entry["tiles"]:
+        prev[(t["bg"], t["Z"])] = t
+    merged[key] = dict(entry, tiles=list(prev.values()))
+    with open(cache_path, "w") as f:
+        json.dump(merged, f, indent=1, sort_keys=True)
+
+
+def cache_key(device: str, mode: str, tag: str | None = None) -> str:
+    return f"{device}|{mode}" + (f"|{tag}" if tag else "")
+
+
+def autotune_batch(base_graphs, z_set, cbs, mode: str = "i8", max_iter: int = 3, reps: int = 3,
+                   sweeps: int = 2, min_gain: float = 0.01, cache_path: str | None = None,
+                   tag: str | None = None, cands=None) -> dict:
+    """Tiles for every shape of the batch `cbs`, tuned together on the batch's decode time."""
+    import torch
+
+    dev_name = torch.cuda.get_device_name()
+    shapes = sorted({(int(c["bg"]), int(c["Z"])) for c in cbs})
+    tiles = {sh: default_tile(sh[1]) for sh in shapes}
+    llr_cache = {}
+
+    def measure(t):
+        return _time_decode(base_graphs, z_set, mode, max_iter, [(b, z, g) for (b, z), g in t.items()], cbs, reps,
+                            llr_cache)
+
+    base_ms = best = measure(tiles)
+    if best is None:
+        raise RuntimeError("the batch does not plan with the built-in tiles")
+    trials = 1
+    for _ in range(sweeps):
+        improved = False
+        for sh in shapes:
+            for G in (cands(sh[1]) if cands else candidates(sh[1], mode)):
+                if G == tiles[sh]:
+                    continue
+                trial = dict(tiles)
+                trial[sh] = G
+                ms = measure(trial)
+                trials += 1
+                if ms is not None and ms < best * (1.0 - min_gain):
+                    best, tiles, improved = ms, trial, True
+        if not improved:
+            break
+    entry = {"device": dev_name, "mode": mode, "objective": "whole-batch decode time", "tag": tag,
+             "default_ms": base_ms, "tuned_ms": best, "trials": trials,
+             "tiles": [{"bg": bg_key(base_graphs[b]), "bg_shape": [base_graphs[b].mb, base_graphs[b].nb,
+                                                                 base_graphs[b].kb], "Z": z, "G": g}
+                       for (b, z), g in tiles.items()]}
+    if cache_path:
+        _write_cache(cache_path, cache_key(dev_name, mode, tag), entry)
+    return entry
+
+
+def autotune(base_graphs, z_set, mode: str = "i8", n_cb: int | None = None, max_iter: int = 3, reps: int = 5,
+             cache_path: str | None = None, shapes=None, cands=None, tag: str | None = None) -> dict:
+    """Time every feasible tile for each (base graph, Z) alone; returns (and optionally caches) the results.
+    Each shape's synthetic batch holds n_cb code blocks, by default as many lifted variables as 2048
+    blocks at Z = 384, so every tile fills the GPU."""
     import torch
 
     from .session import DEFAULT_SAT, LLR_TORCH, Session
@@ -80,7 +206,8 @@ def autotune(base_graphs, z_set, mode: str = "i8", n_cb: int = 1024, max_iter: i
         g = base_graphs[b]
         if (g.kb * Z) % 32:
             continue
-        cbs = synthetic_cbs(g, b, Z, n_cb)
+        nb = n_cb if n_cb else max(64, 2048 * 384 // Z)
+        cbs = synthetic_cbs(g, b, Z, nb)
         timings = {}
         for G in (cands(Z) if cands else candidates(Z, mode)):
             s = Session(base_graphs, [Z], mode=mode, max_iter=max_iter, early_term=False, sat=DEFAULT_SAT[mode]
@@ -110,7 +237,7 @@ def autotune(base_graphs, z_set, mode: str = "i8", n_cb: int = 1024, max_iter: i
                 s.decode_batch(bt, llr, bits, status)
             e1.record()
             torch.cuda.synchronize()
-            timings[G] = e0.elapsed_time(e1) * 1e3 / reps / n_cb
+            timings[G] = e0.elapsed_time(e1) * 1e3 / reps / nb
             del bt, s
         if not timings:
             continue
@@ -118,22 +245,13 @@ def autotune(base_graphs, z_set, mode: str = "i8", n_cb: int = 1024, max_iter: i
         result["tiles"].append({"bg": bg_key(g), "bg_shape": [g.mb, g.nb, g.kb], "Z": Z, "G": best,
                                 "us_per_cb": timings[best], "all_us_per_cb": {str(k): v for k, v in timings.items()}})
     if cache_path:
-        merged = {}
-        if os.path.exists(cache_path):
-            with open(cache_path) as f:
-                merged = json.load(f)
-        key = f"{dev_name}|{mode}"
-        prev = {(t["bg"], t["Z"]): t for t in merged.get(key, {}).get("tiles", [])}
-        for t in result["tiles"]:
-            prev[(t["bg"], t["Z"])] = t
-        merged[key] = {"device": dev_name, "mode": mode, "tiles": list(prev.values())}
-        with open(cache_path, "w") as f:
-            json.dump(merged, f, indent=1, sort_keys=True)
+        _write_cache(cache_path, cache_key(dev_name, mode, tag), dict(result, objective="per-shape time"))
     return result
 
 
-def tiles_from_cache(path: str, base_graphs, mode: str, device_name: str | None = None) -> list:
-    """(bg index, Z, G) triples from a cache file for this GPU and mode (empty if none match)."""
+def tiles_from_cache(path: str, base_graphs, mode: str, device_name: str | None = None,
+                     tag: str | None = None) -> list:
+    """(bg index, Z, G) triples from a cache file for this GPU, mode and workload tag (empty if none)."""
     if not os.path.exists(path):
         return []
     with open(path) as f:
@@ -141,7 +259,7 @@ def tiles_from_cache(path: str, base_graphs, mode: str, device_name: str | None 
     if device_name is None:
         import torch
         device_name = torch.cuda.get_device_name() if torch.cuda.is_available() else ""
-    entry = data.get(f"{device_name}|{mode}")
+    entry = data.get(cache_key(device_name, mode, tag))
     if not entry:
         return []
     keys = {bg_key(g): i for i, g in enumerate(base_graphs)}

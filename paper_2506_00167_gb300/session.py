@@ -105,6 +105,8 @@ class Session:
         lib = abi.load()
         self.mode = mode
         self.device = torch.cuda.current_device()
+        self.n_bg = len(base_graphs)
+        self.z_set = [int(z) for z in z_set]
         llr_sat, msg_sat, post_sat = DEFAULT_SAT[mode] if sat is None else sat
         self._keep = []
         bgs = (abi.BaseGraphC * len(base_graphs))()
@@ -201,10 +203,12 @@ class Session:
         code = {"mixed": abi.PLAN_MIXED, "per_z": abi.PLAN_PER_Z}[strategy]
         abi.check(abi.load().ldpc_session_set_strategy(self.handle, code), "ldpc_session_set_strategy")
 
-    def load_tiles(self, path: str, base_graphs) -> int:
-        """Apply tiles from an autotuner cache (see autotune.py); returns how many matched."""
+    def load_tiles(self, path: str, base_graphs, tag: str | None = None) -> int:
+        """Apply the tiles of an autotuner cache entry (see autotune.py) that name this session's shapes;
+        returns how many were applied."""
         from .autotune import tiles_from_cache
-        t = tiles_from_cache(path, base_graphs, self.mode)
+        t = [x for x in tiles_from_cache(path, base_graphs, self.mode, tag=tag)
+             if x[0] < self.n_bg and x[1] in self.z_set]
         if t:
             self.set_tiles(t)
         return len(t)

@@ -34,3 +34,20 @@ def test_cache_round_trip_by_graph_hash(tmp_path):
     assert at.tiles_from_cache(str(path), bgs, "i8", device_name="GB300") == [(1, 64, 3)]
     assert at.tiles_from_cache(str(path), bgs, "f32", device_name="GB300") == []
     assert at.bg_key(bgs[0]) != at.bg_key(bgs[1])
+
+
+def test_default_tile_matches_the_planner_caps():
+    for Z, G in [(16, 16), (32, 8), (64, 4), (128, 2), (256, 1), (384, 1)]:
+        assert at.default_tile(Z) == G
+        assert at.default_tile(Z) * Z <= at.MAX_BLOCK
+
+
+def test_tagged_cache_entries_are_separate(tmp_path):
+    bgs = default_bgs()
+    path = tmp_path / "c.json"
+    data = {at.cache_key("GB300", "i8", "mixed"): {"tiles": [{"bg": at.bg_key(bgs[0]), "Z": 32, "G": 6}]},
+            at.cache_key("GB300", "i8"): {"tiles": [{"bg": at.bg_key(bgs[0]), "Z": 32, "G": 2}]}}
+    path.write_text(json.dumps(data))
+    assert at.tiles_from_cache(str(path), bgs, "i8", device_name="GB300", tag="mixed") == [(0, 32, 6)]
+    assert at.tiles_from_cache(str(path), bgs, "i8", device_name="GB300") == [(0, 32, 2)]
+    assert at.tiles_from_cache(str(path), bgs, "i8", device_name="GB300", tag="large") == []

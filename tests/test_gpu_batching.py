@@ -8,7 +8,7 @@ import torch
 from oracle import decoder as odec
 from oracle import demap as odemap
 from paper_2506_00167_gb300 import Graph
-from paper_2506_00167_gb300.autotune import autotune, tiles_from_cache
+from paper_2506_00167_gb300.autotune import autotune, autotune_batch, tiles_from_cache
 from workload import mixed
 
 from gpu_helpers import device_inputs, session_for, to_np_u32
@@ -72,7 +72,7 @@ def test_graph_replay_matches_direct_calls(wmix):
 def test_autotune_picks_a_feasible_tile_and_round_trips(tmp_path, wmix):
     w = wmix
     cache = tmp_path / "tiles.json"
-    res = autotune(w.bgs, [32, 64], mode="i8", n_cb=64, max_iter=2, reps=2, cache_path=str(cache),
+    res = autotune(w.bgs, [32, 64], mode="i8", n_cb=256, max_iter=2, reps=2, cache_path=str(cache),
                    shapes=[(1, 32), (1, 64)], cands=lambda Z: [1, 2] if Z > 32 else [2, 4])
     assert len(res["tiles"]) == 2
     for t in res["tiles"]:
@@ -83,3 +83,21 @@ def test_autotune_picks_a_feasible_tile_and_round_trips(tmp_path, wmix):
     assert sorted((z for _, z, _ in tiles)) == [32, 64]
     s = session_for(w, "i8")
     assert s.load_tiles(str(cache), w.bgs) == 2
+
+
+def test_batch_autotuner_never_loses_to_default_and_keeps_results(tmp_path, wmix):
+    """Coordinate descent on the whole batch: the tuned time is no worse than the built-in tiles', the tiles
+    apply to a session, and decoding under them gives the oracle's bits."""
+    w = wmix
+    cache = tmp_path / "tiles.json"
+    ent = autotune_batch(w.bgs, w.z_set, w.cbs, mode="i8", max_iter=2, reps=2, sweeps=1, cache_path=str(cache),
+                         tag="mix", cands=lambda Z: [1, 2])
+    assert ent["tuned_ms"] <= ent["default_ms"] and ent["trials"] >= 1
+    assert tiles_from_cache(str(cache), w.bgs, "i8") == []          # tagged entry only
+    s = session_for(w, "i8")
+    assert s.load_tiles(str(cache), w.bgs, tag="mix") == len({(int(c["bg"]), int(c["Z"])) for c in w.cbs})
+    llr_np = odemap.quantise(odemap.demap_workload(w), 4.0, 63)
+    want_bits, want_status = odec.decode_workload(w, llr_np, 10, True, odec.INT8)
+    bits, status, plan = _decode(s, w, llr_np, np.int8)
+    assert len(plan) == 1
+    assert np.array_equal(bits, want_bits) and np.array_equal(status, want_status)

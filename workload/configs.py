@@ -260,7 +260,7 @@ def tiny_fp32(n_per_point: int = 1000, ebn0_points=(0, 1, 2, 3, 4), seed: int = 
             widths.append(width)
             snrs.append(eb)
     w = build("tiny_fp32", bgs, specs, widths, punct, seed, snr_db=snrs, noiseless=noiseless)
-    w.meta.update(dict(max_iter=8, early_term=0, mode="f32", offset=0.5))
+    w.meta.update(dict(name="tiny", max_iter=8, early_term=0, mode="f32", offset=0.5))
     return w
 
 
@@ -304,7 +304,7 @@ def large_fp32(n_cw: int = 4096, snr_points=(6, 7, 8, 9, 10, 11, 12), seed: int 
             snrs.append(snr)
     w = build("large_fp32", bgs, specs, [width_slot] * n_slots, punct, seed, snr_db=snrs,
               noiseless=noiseless)
-    w.meta.update(dict(max_iter=10, early_term=1, mode="f32", offset=0.5))
+    w.meta.update(dict(name="large", max_iter=10, early_term=1, mode="f32", offset=0.5))
     return w
 
 
@@ -381,7 +381,7 @@ def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int 
         punct.append(P)
     w = build("mixed", bgs, specs, widths, punct, seed, snr_db=snrs, z_set=list(MIX_Z),
               noiseless=noiseless)
-    w.meta.update(dict(max_iter=10, early_term=1, mode="i8", offset=0.5))
+    w.meta.update(dict(name="mixed", max_iter=10, early_term=1, mode="i8", offset=0.5))
     return w
 
 
