@@ -320,11 +320,13 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
       const uint32_t* rows = s_tab + sh.row_off;
       const int mA = A.m_eff, mB = hasB ? Bc.m_eff : 0;
       bool doneA = false, doneB = !hasB;
+      PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
       for (int it = 1;; ++it) {
         for (int l = 0; l < mA; ++l) {
-          const uint32_t info = rows[l];
-          check_update_x2(s_tab + (info & 0xFFFFu), static_cast<int>(info >> 16), k, Z, L, mags, sg1, sg2, l * Z + k,
-                          item.dummy_base + k, beta, msg, post);
+          check_update_x2(prow, k, Z, L, mags, sg1, sg2, l * Z + k, item.dummy_base + k, beta, msg, post);
+          // the next row's table entry and message words are loaded before the barrier
+          const int ln = l + 1 < mA ? l + 1 : 0;
+          prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
           group_sync(Z, g, 0xFFFFFFFFu);
         }
         if (a.early_term || it == a.max_iter) {

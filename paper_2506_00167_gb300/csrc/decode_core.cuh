@@ -331,14 +331,35 @@ __device__ __forceinline__ __half2 small_pair(uint32_t a, uint32_t b) {
 // each Q_j pair in its posterior's slot and pass 2 reads it back (the check
 // owns those slots during the layer), which keeps the row's Q values out of
 // registers.
-__device__ __forceinline__ void check_update_x2(const uint32_t* __restrict__ tab, int deg, int k, int Z,
-                                                uint32_t* __restrict__ L, uint32_t* __restrict__ mags,
-                                                uint32_t* __restrict__ sg1, uint32_t* __restrict__ sg2, int rec,
-                                                int dummy, int beta, __half2 msg, __half2 post) {
+// The row's table and degree and this check's three message words (mg, s1,
+// s2) come from the caller, which loads the next row's before the layer
+// barrier.
+struct PairIn {
+  const uint32_t* tab;
+  int deg;
+  uint32_t mg, s1, s2;
+};
+
+__device__ __forceinline__ PairIn load_pair_row(const uint32_t* __restrict__ s_tab, uint32_t info,
+                                                const uint32_t* __restrict__ mags, const uint32_t* __restrict__ sg1,
+                                                const uint32_t* __restrict__ sg2, int rec) {
+  PairIn r;
+  r.tab = s_tab + (info & 0xFFFFu);
+  r.deg = static_cast<int>(info >> 16);
+  r.mg = mags[rec];
+  r.s1 = sg1[rec];
+  r.s2 = sg2[rec];
+  return r;
+}
+
+__device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
+                                                uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
+                                                uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
+                                                __half2 msg, __half2 post) {
   L[dummy] = as_u32(post);
-  const uint32_t mg = mags[rec];
-  const uint32_t s1 = sg1[rec];
-  const uint32_t s2 = sg2[rec];
+  const uint32_t* tab = in.tab;
+  const int deg = in.deg;
+  const uint32_t mg = in.mg, s1 = in.s1, s2 = in.s2;
   const __half2 h1024 = __float2half2_rn(1024.0f);
   const __half2 M1 = __hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5140)), h1024);
   const __half2 M2 = __hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5342)), h1024);
