@@ -302,9 +302,8 @@ __device__ __forceinline__ bool syndrome_direct(const uint32_t* __restrict__ tab
 // represents exactly, and half2 min/max/add/fma on such values are exact; so
 // the pair (block A in the low half, block B in the high half) is decoded
 // bit-identically to two separate INT8 decodes with one instruction stream.
-// Per check the state is three words: magnitudes (m1A, m1B, m2A, m2B bytes),
-// sign history of edges 0..15 (A: bit 15-j, B: bit 31-j) and of edges 16..26
-// (A: bits 15..5, B: bits 31..21) with the argmins in bits 0..4 and 16..20.
+// Per check the state is three words: magnitudes (m1A, m1B, m2A, m2B bytes)
+// and two words of sign history and argmins (layout at check_update_x2).
 #include <cuda_fp16.h>
 
 namespace ldpcgb {
@@ -352,6 +351,21 @@ __device__ __forceinline__ PairIn load_pair_row(const uint32_t* __restrict__ s_t
   return r;
 }
 
+// Address of edge e of a row (tab = the row's chunks) for check k.
+__device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int Z) {
+  const uint32_t* t = tab + 8 * (e >> 2) + (e & 3);
+  return static_cast<int>(t[0]) + rot(k, t[4], Z);
+}
+
+// Stored form (v2): magnitudes as above; Q-sign history of the last update,
+// edge j < 16 at bit j (A) and 16 + j (B) of s1, edges 16..26 at bits
+// 5 + (j-16) (A) and 21 + (j-16) (B) of s2, argmins in s2 bits 0..4 / 16..20.
+// The sign of the stored message R_j is that bit XOR the parity of the
+// block's Q signs (R'_j carries the sign product over i != j).
+//
+// Pass 2 writes every edge with the smaller magnitude; the argmin edge of
+// each block, whose message takes the second magnitude instead, is then
+// rewritten from its Q, read before pass 2 (the check owns the slot).
 __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
                                                 uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
                                                 uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
@@ -361,8 +375,12 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const int deg = in.deg;
   const uint32_t mg = in.mg, s1 = in.s1, s2 = in.s2;
   const __half2 h1024 = __float2half2_rn(1024.0f);
-  const __half2 M1 = __hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5140)), h1024);
-  const __half2 M2 = __hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5342)), h1024);
+  // parity of each block's stored Q signs, as the two sign bits of a half2
+  const uint32_t xs = s1 ^ (s2 & 0xFFE0FFE0u);
+  const uint32_t pm_o = ((static_cast<uint32_t>(__popc(xs & 0xFFFFu)) & 1u) << 15) |
+                        ((static_cast<uint32_t>(__popc(xs >> 16)) & 1u) << 31);
+  const uint32_t M1s = as_u32(__hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5140)), h1024)) | pm_o;
+  const uint32_t M2s = as_u32(__hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5342)), h1024)) | pm_o;
   const __half2 I = __hsub2(as_h2((s2 & 0x001F001Fu) | 0x64006400u), h1024);
   const __half2 h32 = __float2half2_rn(32.0f);
   const __half2 npost = __hneg2(post);
@@ -370,8 +388,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
 
   int addr[kMaxChunks * 4];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
-  uint32_t par = 0;
-  uint32_t sgn = s1;
+  uint32_t acc1 = 0, acc2 = 0;  // Q signs: each new edge enters at bits 15 / 31
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
@@ -387,15 +404,18 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = 4 * c + i;
-      if (j == 16) sgn = s2;
       const __half2 J = __float2half2_rn(static_cast<float>(j));
       const uint32_t eq = __heq2_mask(I, J);
-      const uint32_t rb = ((as_u32(M2) & eq) | (as_u32(M1) & ~eq)) | (sgn & 0x80008000u);
-      sgn <<= 1;
+      // (edge 27 can only be padding, whose sign does not matter)
+      const uint32_t sw = j < 16 ? (s1 << (15 - j)) : (j <= 26 ? (s2 << (26 - j)) : 0u);
+      const uint32_t rb = ((M2s & eq) | (M1s & ~eq)) ^ (sw & 0x80008000u);
       __half2 Q = __hsub2(as_h2(lv[i]), as_h2(rb));
       Q = __hmin2(__hmax2(Q, npost), post);
       L[addr[j]] = as_u32(Q);
-      par ^= as_u32(Q);
+      if (j < 16)
+        acc1 = ((acc1 >> 1) & 0x7FFF7FFFu) | (as_u32(Q) & 0x80008000u);
+      else
+        acc2 = ((acc2 >> 1) & 0x7FFF7FFFu) | (as_u32(Q) & 0x80008000u);
       const __half2 key = __hfma2(__hmin2(__habs2(Q), msg), h32, J);
       min2 = __hmin2(min2, __hmax2(min1, key));
       min1 = __hmin2(min1, key);
@@ -406,9 +426,15 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const uint32_t idxA = kA1 & 31, idxB = kB1 & 31;
   const uint32_t nA1 = max((kA1 >> 5) - beta, 0), nB1 = max((kB1 >> 5) - beta, 0);
   const uint32_t nA2 = max((kA2 >> 5) - beta, 0), nB2 = max((kB2 >> 5) - beta, 0);
-  const __half2 N1 = small_pair(nA1, nB1), N2 = small_pair(nA2, nB2), In = small_pair(idxA, idxB);
-  const uint32_t pm = par & 0x80008000u;
-  uint32_t acc1 = 0, acc2 = 0;
+  const uint32_t xa = acc1 ^ acc2;  // every processed edge's sign once (padding edges are positive)
+  const uint32_t pm = ((static_cast<uint32_t>(__popc(xa & 0xFFFFu)) & 1u) << 15) |
+                      ((static_cast<uint32_t>(__popc(xa >> 16)) & 1u) << 31);
+  const uint32_t N1s = as_u32(small_pair(nA1, nB1)) | pm;
+  const uint32_t N2s = as_u32(small_pair(nA2, nB2)) | pm;
+  // the two argmin edges and their Q values, before pass 2 overwrites them
+  const int aA = edge_addr(tab, static_cast<int>(idxA), k, Z);
+  const int aB = edge_addr(tab, static_cast<int>(idxB), k, Z);
+  const uint32_t qsel = (L[aA] & 0x0000FFFFu) | (L[aB] & 0xFFFF0000u);
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
@@ -417,27 +443,25 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     for (int i = 0; i < 4; ++i) qv[i] = L[addr[4 * c + i]];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = 4 * c + i;
-      const uint32_t eq = __heq2_mask(In, __float2half2_rn(static_cast<float>(j)));
-      const uint32_t rb = ((as_u32(N2) & eq) | (as_u32(N1) & ~eq)) | ((qv[i] ^ pm) & 0x80008000u);
+      const uint32_t rb = N1s ^ (qv[i] & 0x80008000u);
       __half2 v = __hadd2(as_h2(qv[i]), as_h2(rb));
       v = __hmin2(__hmax2(v, npost), post);
-      L[addr[j]] = as_u32(v);  // padding edges write the dummy slot
-      const uint32_t bit = (rb >> 15) & 0x00010001u;
-      if (j < 16)
-        acc1 = ((acc1 << 1) & 0xFFFEFFFEu) | bit;
-      else
-        acc2 = ((acc2 << 1) & 0xFFFEFFFEu) | bit;
+      L[addr[4 * c + i]] = as_u32(v);  // padding edges write the dummy slot
     }
+  }
+  {
+    const uint32_t rb = N2s ^ (qsel & 0x80008000u);
+    const uint32_t v = as_u32(__hmin2(__hmax2(__hadd2(as_h2(qsel), as_h2(rb)), npost), post));
+    L[aA] = (L[aA] & 0xFFFF0000u) | (v & 0x0000FFFFu);
+    L[aB] = (L[aB] & 0x0000FFFFu) | (v & 0xFFFF0000u);
   }
   const int n_all = 4 * nch;
   const int n1 = n_all < 16 ? n_all : 16;
-  acc1 <<= (16 - n1);
   const int n2 = n_all - 16;
-  acc2 = n2 > 0 ? ((acc2 << (16 - n2)) & 0xFFE0FFE0u) : 0u;
   mags[rec] = nA1 | (nB1 << 8) | (nA2 << 16) | (nB2 << 24);
-  sg1[rec] = acc1;
-  sg2[rec] = acc2 | idxA | (idxB << 16);
+  sg1[rec] = acc1 >> (16 - n1);
+  const uint32_t a2 = n2 <= 0 ? 0u : (n2 <= 11 ? acc2 >> (11 - n2) : acc2 << (n2 - 11));
+  sg2[rec] = (a2 & 0xFFE0FFE0u) | idxA | (idxB << 16);
 }
 
 // hard decisions of both blocks of a pair into their bitmaps
