@@ -70,7 +70,7 @@ typedef struct ldpc_graph ldpc_graph; /* opaque: an instantiated CUDA graph of o
  * information, the next mc columns core parity (rows [0, mc) are the core
  * rows), the rest extension parity, one per extension row.  The first
  * n_punct_cols information columns are never transmitted.  The paper gives
- * no code parameters (Sec. III-B, Sec. IV "Tx Signal Processing"); callers
+ * no code parameters (Sec. III-B, Sec. VI-A "Tx Signal Processing"); callers
  * supply seeded matrices.  Host pointers, copied at ldpc_session_create.
  */
 typedef struct {
@@ -183,7 +183,7 @@ LDPC_API int ldpc_batch_plan_get(const ldpc_batch *b, ldpc_launch_info *out, int
 
 /*
  * Puncture flushing + max-log soft demapping + rate dematching (paper
- * Sec. IV "UE": the LLRs of bits on punctured resource elements are set to 0
+ * Sec. VI-D "UE": the LLRs of bits on punctured resource elements are set to 0
  * after the soft demodulator; the demapper algorithm is not stated there,
  * this library uses max-log).  For each resource element r of each block:
  * if its mask bit is set all Qm LLRs are 0, otherwise
@@ -208,7 +208,7 @@ LDPC_API int puncture_demap(ldpc_session *s, const ldpc_batch *b, const void *sy
  * [L < 0] is checked against the m_eff rows; with early termination a block
  * stops at the first zero syndrome.  Writes each block's kb*Z information bits
  * to bits_dev and status_dev[cb] = iterations | (syndrome_zero << 16).
- * The paper's decoder is a toolbox function (Sec. IV "UE"); this is the
+ * The paper's decoder is a toolbox function (Sec. VI-D "UE"); this is the
  * algorithm this library fixes in its place.
  */
 LDPC_API int decode_batch(ldpc_session *s, const ldpc_batch *b, const void *llr_dev,
@@ -218,7 +218,7 @@ LDPC_API int decode_batch(ldpc_session *s, const ldpc_batch *b, const void *llr_
  * Transport-block CRC-24 check and per-slot goodput and reward.  d_e = 1 iff
  * the TB's (payload_bits + 24) decoded bits are a multiple of
  * g(x) = 0x1864CFB (register from 0, first bit highest degree) -- the same
- * test as comparing received and recomputed CRC bits (Sec. IV "UE Feedback").
+ * test as comparing received and recomputed CRC bits (Sec. VI-D "UE Feedback").
  * Per slot t:  goodput_bits[t] = sum_e d_e * payload_bits_e;
  *              goodput_sc[t]   = sum_e d_e * n_e               (eq. 1)
  *              reward[t]       = (1/N_t) * sum_e (d_e - 1) n_e  (eq. 2)
@@ -274,7 +274,7 @@ LDPC_API int decode_uniform_noalloc(const ldpc_base_graph *g, int32_t Z, int32_t
 
 /* ------------------------------------------------------------------ serving
  * Continuous batching of TB decode requests (the paper's per-TTI receiver
- * feedback loop, Sec. IV "UE", run as a service).  One persistent device
+ * feedback loop, Sec. VI-D "UE", run as a service).  One persistent device
  * loop (one thread block per SM) takes work items -- up to G code blocks of
  * one TB -- from a ring in pinned host memory as soon as the host publishes
  * them, so requests that arrive while others are decoding start on the next

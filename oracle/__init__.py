@@ -6,7 +6,7 @@ product path (the C-ABI library and its Python binding) never does and fails
 loudly without its CUDA extension.
 
 The oracle restates, step by step and in plain NumPy, what the receive path
-computes (paper Sec. III-B eq. 1, Sec. V-A eq. 2, Sec. IV "UE"): puncture
+computes (paper Sec. III-B eq. 1, Sec. V-A eq. 2, Sec. VI-D "UE"): puncture
 flushing (LLR := 0), max-log soft demapping by brute force over the whole
 constellation, layered offset-min-sum decoding in float64 and in exact
 integer (INT8/INT16 saturating) arithmetic, the transport-block CRC-24 check,

@@ -1,7 +1,7 @@
 """CRC-24 over a transport block (oracle; test infrastructure only).
 
 The paper sets d_e from a bitwise comparison of the CRC bits recovered after
-decoding with those attached at the transmitter (Sec. IV "UE Feedback";
+decoding with those attached at the transmitter (Sec. VI-D "UE Feedback";
 Sec. III-B defines d_e).  It names no polynomial; this build uses generator
 g(x) = x^24 + x^23 + x^18 + x^17 + x^14 + x^11 + x^10 + x^7 + x^6 + x^5 + x^4
 + x^3 + x + 1 (0x864CFB), register starting at 0, first bit = highest-degree

@@ -1,7 +1,7 @@
 """Layered offset-min-sum decoding of a QC-LDPC code (oracle; test infrastructure only).
 
 The paper's receiver LDPC-decodes the flushed LLRs with a toolbox decoder
-(Sec. IV "UE") and states neither algorithm nor parameters; this build fixes
+(Sec. VI-D "UE") and states neither algorithm nor parameters; this build fixes
 layered offset min-sum.  Notation: the lifted check (l, k) of base row l
 connects, through base edge (l, j) with column c_j and shift s_j = V mod Z,
 to variable v_j(k) = c_j * Z + (k + s_j) mod Z.  With posterior L (initially

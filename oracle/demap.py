@@ -2,7 +2,7 @@
 
 Test infrastructure only.  The receiver soft-demodulates, then sets the
 confidence of every bit carried by a resource element that URLLC punctured
-to "NULL", i.e. LLR 0, so the decoder treats it as an erasure (Sec. IV "UE",
+to "NULL", i.e. LLR 0, so the decoder treats it as an erasure (Sec. VI-D "UE",
 "Rx Signal Processing").  The paper's demodulator is a toolbox function whose
 algorithm it does not state; this build uses max-log:
 

@@ -1,6 +1,6 @@
 """Systematic QC-LDPC encoder and parity check (oracle; test infrastructure only).
 
-The paper encodes with a toolbox LDPC encoder (Sec. IV "Tx Signal
+The paper encodes with a toolbox LDPC encoder (Sec. VI-A "Tx Signal
 Processing") and gives no parameters.  For the seeded dual-diagonal base
 matrices of this build the encoder is a closed form: with the core-row
 partial sums lambda_r = sum_j P^{s_rj} u_j over the information columns,

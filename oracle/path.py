@@ -2,7 +2,7 @@
 
 puncture flushing + max-log demap (``demap``) -> layered offset min-sum
 (``decoder``) -> TB CRC-24, goodput and reward (``goodput``), in the order of
-Sec. IV "UE".  Used by the parity tests and by the benchmark's timed CPU
+Sec. VI-D "UE".  Used by the parity tests and by the benchmark's timed CPU
 baseline.
 """
 from __future__ import annotations

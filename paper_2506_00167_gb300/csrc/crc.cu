@@ -2,7 +2,7 @@
 //
 // d_e = 1 iff the TB's decoded (A + 24) bits are a multiple of g(x) (register
 // from 0, first bit = highest degree): the same test as comparing the CRC
-// recomputed from the received payload with the received CRC (paper Sec. IV
+// recomputed from the received payload with the received CRC (paper Sec. VI-D
 // "UE Feedback").  Per slot: goodput_sc = sum_e d_e n_e (Sec. III-B, eq. 1),
 // reward = (1/N) sum_e (d_e - 1) n_e (Sec. V-A, eq. 2), and the delivered
 // payload bits.

@@ -1,7 +1,7 @@
 // Layered offset-min-sum decoding of QC-LDPC code blocks on sm_103a.
 //
 // Algorithm (the paper's receiver decodes with a toolbox LDPC decoder and
-// states no algorithm, Sec. IV "UE"; this library fixes layered offset min-sum):
+// states no algorithm, Sec. VI-D "UE"; this library fixes layered offset min-sum):
 // every iteration runs base rows l = 0 .. m_eff-1 in order.  Lifted check
 // (l, k) reaches, through base edge j (column c_j, shift s_j = V mod Z),
 // variable v_j = c_j * Z + (k + s_j) mod Z, and updates

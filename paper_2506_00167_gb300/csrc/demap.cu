@@ -1,7 +1,7 @@
 // Puncture flushing + max-log soft demapping + rate dematching on sm_103a.
 //
 // The receiver sets the LLRs of bits carried by URLLC-punctured resource
-// elements to 0 after soft demodulation (paper Sec. IV "UE"); the
+// elements to 0 after soft demodulation (paper Sec. VI-D "UE"); the
 // demodulator itself is unstated there and this library uses max-log over
 // NR-style Gray QAM.  Max-log is separable per axis for this constellation:
 // the Q part of |y - s|^2 cancels in the difference for an I bit, so each

@@ -1,7 +1,7 @@
 """Seeded NR-style quasi-cyclic base matrices.
 
 Input generation only.  The paper runs LDPC coding through a toolbox and
-publishes no code parameters (Sec. III-B; Sec. IV "Tx Signal Processing"), so
+publishes no code parameters (Sec. III-B; Sec. VI-A "Tx Signal Processing"), so
 the base matrices are generated from a seed rather than taken from any
 standard table.  Construction (one ``BaseGraph`` per shape):
 

@@ -5,7 +5,7 @@ mini-slots of two OFDM symbols; eMBB user ``e`` holds ``n_e`` subcarriers for
 the slot; URLLC packets of ``L`` subcarriers preempt eMBB resource elements
 in a mini-slot; the puncturing vector ``y(t, tau)`` counts how many of each
 user's subcarriers are taken.  The receiver is told which resource elements
-were punctured (Sec. IV, "SC Puncturing Mapping").
+were punctured (Sec. VI-A, "SC Puncturing Mapping").
 
 A ``Workload`` holds everything one batch of the receive path consumes, laid
 out exactly as the C-ABI wants it:

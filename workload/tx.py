@@ -2,7 +2,7 @@
 
 The paper's transmitter appends CRC bits to random eMBB data, LDPC-encodes,
 rate-matches, punctures the resource elements taken by URLLC, and modulates
-(Sec. IV, "eMBB Traffic Generator" and "Tx Signal Processing").  This module
+(Sec. VI-A, "eMBB Traffic Generator" and "Tx Signal Processing").  This module
 produces those transmitted symbols for the tests and the benchmark.  It holds
 none of the receiver's arithmetic: no demapping, no decoding, no CRC check.
 
