@@ -7,11 +7,14 @@
 // the Q part of |y - s|^2 cancels in the difference for an I bit, so each
 // LLR is a minimum over the 2^(Qm/2) PAM levels of one axis.
 //
-// One thread per resource element: one 8-byte symbol load, Qm LLRs, each
-// written to its interleaved codeword position t0 + i * (E/Qm) + r -- for a
-// fixed bit plane i consecutive threads write consecutive positions, so every
-// store is coalesced.  The first tile of each block also zero-fills the
-// positions never transmitted.
+// A block covers a tile of kDemapTile resource elements of one code block,
+// each thread kDemapPerThread of them, kDemapBlock apart: all of a thread's
+// symbol and mask-word loads are issued before any arithmetic, so enough
+// bytes are in flight per SM to keep HBM busy.  Each resource element gives
+// Qm LLRs, written to its interleaved codeword position t0 + i * (E/Qm) + r --
+// for a fixed bit plane i consecutive threads write consecutive positions, so
+// every store is coalesced.  The first tile of each code block also
+// zero-fills the positions never transmitted.
 #include "demap_core.cuh"
 
 namespace ldpcgb {
@@ -24,13 +27,26 @@ template <typename LT>
 __global__ void __launch_bounds__(kDemapBlock) demap_kernel(const DemapArgs a) {
   const DemapTile tile = a.tiles[blockIdx.x];
   const CbDev cb = a.cbs[tile.cb];
-  const int r = tile.re_start + threadIdx.x;
-  if (r < cb.n_re) {
-    switch (cb.Qm) {
-      case 2: demap_re<LT, 2>(a, cb, r); break;
-      case 4: demap_re<LT, 4>(a, cb, r); break;
-      case 6: demap_re<LT, 6>(a, cb, r); break;
-      default: demap_re<LT, 8>(a, cb, r); break;
+  float2 y[kDemapPerThread];
+  uint32_t mw[kDemapPerThread];
+#pragma unroll
+  for (int u = 0; u < kDemapPerThread; ++u) {
+    const int r = tile.re_start + u * kDemapBlock + static_cast<int>(threadIdx.x);
+    if (r < cb.n_re) {
+      y[u] = __ldcs(a.sym + cb.re_off + r);  // read once: streaming
+      mw[u] = __ldg(a.mask + cb.mask_off + (r >> 5));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kDemapPerThread; ++u) {
+    const int r = tile.re_start + u * kDemapBlock + static_cast<int>(threadIdx.x);
+    if (r < cb.n_re) {
+      switch (cb.Qm) {
+        case 2: demap_re<LT, 2>(a, cb, r, y[u], mw[u]); break;
+        case 4: demap_re<LT, 4>(a, cb, r, y[u], mw[u]); break;
+        case 6: demap_re<LT, 6>(a, cb, r, y[u], mw[u]); break;
+        default: demap_re<LT, 8>(a, cb, r, y[u], mw[u]); break;
+      }
     }
   }
   if (tile.re_start == 0) {  // positions never transmitted hold LLR 0

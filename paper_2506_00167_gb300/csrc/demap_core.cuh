@@ -81,9 +81,8 @@ __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_si
 }
 
 template <typename LT, int Qm>
-__device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, int r) {
-  const float2 y = a.sym[cb.re_off + r];
-  const bool punct = (a.mask[cb.mask_off + (r >> 5)] >> (r & 31)) & 1u;
+__device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, int r, float2 y, uint32_t mask_word) {
+  const bool punct = (mask_word >> (r & 31)) & 1u;
   float lam[Qm];
   axis_llr<Qm / 2>(y.x, cb.inv_sigma2, lam, 0);
   axis_llr<Qm / 2>(y.y, cb.inv_sigma2, lam, 1);

@@ -130,6 +130,8 @@ cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs
 cudaError_t launch_crc(int n_slots, cudaStream_t st, const CrcArgs& a);
 
 constexpr int kDemapBlock = 256;
+constexpr int kDemapPerThread = 4;                        // resource elements per thread
+constexpr int kDemapTile = kDemapBlock * kDemapPerThread;  // resource elements per block
 
 }  // namespace ldpcgb
 

@@ -663,7 +663,7 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
     // ---- demap tiles
     std::vector<DemapTile> tiles;
     for (int i = 0; i < n_cb; ++i)
-      for (int r = 0; r < std::max(1, b->cbs[i].n_re); r += kDemapBlock) tiles.push_back({i, r});
+      for (int r = 0; r < std::max(1, b->cbs[i].n_re); r += kDemapTile) tiles.push_back({i, r});
     b->n_tiles = static_cast<int>(tiles.size());
     if ((rc = upload(s, &b->d_tiles, tiles, &b->owned, &b->bytes))) return bail(rc, g_err);
 
