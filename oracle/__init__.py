@@ -29,5 +29,11 @@ Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
   max-log ML on a tree code (float and exact integer), dropped-rows identity.
 * ``goodput``: pinned -- closed-form eq. 1 and eq. 2 values and bounds.
 * ``stats``: pinned -- Wilson interval against its textbook closed form.
+* ``policy`` (URLLC puncturing allocations: RP, SeF, the KL-projection
+  feasibility enforcer, SC masks): pinned -- RP and SeF reproduce the paper's
+  Table VI columns (except one printed RP column, documented there);
+  Huntington-Hill rounding is the brute-force minimum of its objective; the
+  KL projection matches its closed form without caps, its KKT form, and a
+  convex solver; feasible integer vectors are fixed points of the enforcer.
 """
-from . import crc, demap, decoder, encoder, goodput, stats, path  # noqa: F401
+from . import crc, demap, decoder, encoder, goodput, stats, path, policy  # noqa: F401

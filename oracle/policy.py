@@ -1,0 +1,166 @@
+"""URLLC puncturing allocations: the two benchmark policies and the feasibility enforcer.
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+Per mini-slot, a URLLC demand of D subcarriers is taken from the eMBB users'
+allocations n_e (the eMBB schedule s(t), Sec. III-A):
+
+* RP, "Resource Proportion" (Sec. VII-A): users lose SCs in proportion to
+  n_e.  The quotas q_e = D n_e / sum(n) are made integers summing to D by
+  Huntington-Hill rounding (below).
+* SeF, "Smallest eMBB First" (Sec. VII-A): users in ascending order of n_e
+  (ties: lower index first) lose all their SCs until D is met; the last one
+  loses the remainder.
+* Feasibility enforcer (Sec. V-B): a real puncturing vector m that may
+  exceed the allocations is replaced by the integer vector nearest to it:
+  first the projection m^ onto {0 <= m^_e <= n_e, sum m^_e = jL} minimising
+  the KL divergence sum_e m_e log(m_e / m^_e) (eq. 6, eq. 7), solved by
+  water-filling, then Huntington-Hill rounding of m^ to integers summing to
+  jL.
+
+Readings where the paper is silent (each fixed here and in the CUDA path):
+
+* Huntington-Hill rounding keeps every value between its floor and its
+  ceiling (the paper: each value is rounded up or down): start from the
+  floors and hand the remaining units out one at a time to the largest
+  priority q_e / sqrt(a_e (a_e + 1)) (a_e the current value; a_e = 0 gives
+  infinite priority), among values still below their ceiling and their cap
+  n_e; equal priorities go to the lower index.  Priorities are computed and
+  compared in float64.
+* KL projection: users with m_e > 0 take m^_e = min(n_e, c m_e) with one
+  scale c >= 0 (the KKT conditions of eq. 7); users with m_e = 0 take 0 unless
+  the others' allocations cannot hold jL, in which case the remainder is
+  spread over them in proportion to n_e (their terms of eq. 6 are zero for any
+  value, so any split is optimal; this one is the water-filling continuation).
+* Subcarriers: user e's band is the n_e subcarriers after those of users
+  1 .. e-1 (SC 0 first); the punctured SCs of a mini-slot are the lowest-index
+  m_e SCs of the band, in both OFDM symbols of the mini-slot.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_MINISLOT = 7
+SYM_PER_MINISLOT = 2
+
+
+def hh_round(quota, total: int, cap=None) -> np.ndarray:
+    """Integers a with sum(a) == total, floor(q) <= a <= ceil(q), a <= cap (Huntington-Hill order)."""
+    q = np.asarray(quota, dtype=np.float64)
+    n = q.size
+    cap = np.full(n, np.iinfo(np.int64).max, dtype=np.int64) if cap is None else np.asarray(cap, dtype=np.int64)
+    a = np.minimum(np.floor(q).astype(np.int64), cap)
+    hi = np.minimum(np.ceil(q).astype(np.int64), cap)
+    left = int(total) - int(a.sum())
+    if left < 0 or left > int((hi - a).sum()):
+        raise ValueError("no rounding of these quotas sums to the total")
+    for _ in range(left):
+        best, best_p = -1, -1.0
+        for e in range(n):
+            if a[e] >= hi[e]:
+                continue
+            p = math.inf if a[e] == 0 else q[e] / math.sqrt(float(a[e]) * float(a[e] + 1))
+            if p > best_p:  # strict: the lower index keeps a tie
+                best, best_p = e, p
+        a[best] += 1
+    return a
+
+
+def rp(n, demand: int) -> np.ndarray:
+    """Resource Proportion: SCs taken from each user for a demand of `demand` SCs."""
+    n = np.asarray(n, dtype=np.int64)
+    q = float(demand) * n.astype(np.float64) / float(n.sum())
+    return hh_round(q, demand, n)
+
+
+def sef(n, demand: int) -> np.ndarray:
+    """Smallest eMBB First: whole allocations, smallest first (lower index on ties)."""
+    n = np.asarray(n, dtype=np.int64)
+    out = np.zeros_like(n)
+    left = int(demand)
+    for e in sorted(range(n.size), key=lambda i: (int(n[i]), i)):
+        take = min(left, int(n[e]))
+        out[e] = take
+        left -= take
+    if left:
+        raise ValueError("demand exceeds the allocations")
+    return out
+
+
+def kl_project(m, n, total: float) -> np.ndarray:
+    """argmin sum_e m_e log(m_e / x_e)  s.t.  0 <= x <= n, sum x = total  (eq. 6, eq. 7).
+
+    Sums run in index order (capped users in breakpoint order), one float64
+    operation at a time, so that another implementation following the same
+    order reproduces the result bit for bit.
+    """
+    m = [float(v) for v in m]
+    n = [float(v) for v in n]
+    E = len(m)
+    pos = [e for e in range(E) if m[e] > 0]
+    zero = [e for e in range(E) if not m[e] > 0]
+    cap_all = 0.0
+    for e in range(E):
+        cap_all += n[e]
+    if total > cap_all:
+        raise ValueError("total exceeds the allocations")
+    x = np.zeros(E, dtype=np.float64)
+    cap_pos = 0.0
+    for e in pos:
+        cap_pos += n[e]
+    if cap_pos <= total:
+        # every user with m_e > 0 is capped; the rest goes to the others by capacity
+        for e in pos:
+            x[e] = n[e]
+        rest = total - cap_pos
+        cap0 = 0.0
+        for e in zero:
+            cap0 += n[e]
+        if rest > 0 and cap0 > 0:
+            for e in zero:
+                x[e] = rest * n[e] / cap0
+        return x
+    # water-filling on the scale c: users reach their cap in order of n_e / m_e
+    order = sorted(pos, key=lambda e: (n[e] / m[e], e))
+    free_m = 0.0
+    for e in pos:
+        free_m += m[e]
+    capped = 0.0
+    c = 0.0
+    for e in order:
+        c = (total - capped) / free_m
+        if c * m[e] <= n[e]:
+            break
+        capped += n[e]
+        free_m -= m[e]
+    for e in pos:
+        x[e] = min(n[e], c * m[e])
+    return x
+
+
+def enforce(m, n, j: int, L: int) -> np.ndarray:
+    """Feasible integer puncturing vector for branch j (demand j*L SCs)."""
+    x = kl_project(m, n, float(j * L))
+    return hh_round(x, j * L, np.asarray(n, dtype=np.int64))
+
+
+def sc_mask(n, m_per_minislot) -> np.ndarray:
+    """(14, sum(n)) bool: punctured subcarriers per OFDM symbol (lowest-index SCs of each band)."""
+    n = np.asarray(n, dtype=np.int64)
+    m = np.asarray(m_per_minislot, dtype=np.int64).reshape(N_MINISLOT, n.size)
+    start = np.concatenate([[0], np.cumsum(n)[:-1]])
+    out = np.zeros((N_MINISLOT * SYM_PER_MINISLOT, int(n.sum())), dtype=bool)
+    for ms in range(N_MINISLOT):
+        for e in range(n.size):
+            k = int(m[ms, e])
+            if k:
+                out[ms * SYM_PER_MINISLOT:(ms + 1) * SYM_PER_MINISLOT, start[e]:start[e] + k] = True
+    return out
+
+
+def allocate(n, demand_per_minislot, policy: str) -> np.ndarray:
+    """(7, E) SCs punctured per mini-slot and user under `policy` ('rp' or 'sef')."""
+    fn = {"rp": rp, "sef": sef}[policy]
+    return np.stack([fn(n, int(d)) if d else np.zeros(len(n), dtype=np.int64) for d in demand_per_minislot])

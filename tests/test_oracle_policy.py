@@ -1,0 +1,162 @@
+"""The puncturing-allocation oracle (RP, SeF, feasibility enforcer) against the paper and the mathematics."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import policy as P
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "table6_rp_sef.txt")
+
+
+def _table6():
+    rows = {}
+    for ln in open(GOLD):
+        ln = ln.strip()
+        if ln and not ln.startswith("#"):
+            k, *v = ln.split()
+            rows[k] = np.array([int(x) for x in v])
+    return rows
+
+
+def test_rp_and_sef_reproduce_table6():
+    t = _table6()
+    s = t["s"]
+    assert s.sum() == 780
+    assert np.array_equal(P.rp(s, 300), t["rp_300"])
+    assert np.array_equal(P.sef(s, 300), t["sef_300"])
+    assert np.array_equal(P.sef(s, 600), t["sef_600"])
+
+
+def test_rp_600_differs_from_the_printed_column_by_one_sc_between_two_users():
+    # The printed RP column for 600 SCs gives user 1 47 SCs (quota 46.15) and user 3 55 (quota 55.38):
+    # no rounding of the proportional quotas that keeps the sum (Huntington-Hill, largest remainder,
+    # per-packet) gives that; the reading keeps Huntington-Hill, one SC away from the print.
+    t = _table6()
+    ours = P.rp(t["s"], 600)
+    assert ours.sum() == 600 == t["rp_600"].sum()
+    d = ours - t["rp_600"]
+    assert np.abs(d).sum() == 2 and d[0] == -1 and d[2] == 1
+
+
+def _hh_cost(a, q):
+    # Huntington-Hill minimises sum q_e^2 / a_e (equivalently sum (a_e - q_e)^2 / a_e)
+    c = 0.0
+    for ae, qe in zip(a, q):
+        if qe > 0:
+            if ae == 0:
+                return math.inf
+            c += qe * qe / ae
+    return c
+
+
+def test_hh_round_is_the_minimum_of_its_objective_by_brute_force():
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        E = int(rng.integers(2, 6))
+        q = rng.uniform(0, 9, E) * (rng.random(E) < 0.85)
+        T = int(round(q.sum()))
+        lo, hi = np.floor(q).astype(int), np.ceil(q).astype(int)
+        if not lo.sum() <= T <= hi.sum():
+            continue
+        a = P.hh_round(q, T)
+        assert a.sum() == T and np.all(a >= lo) and np.all(a <= hi)
+        best = min(_hh_cost(c, q) for c in itertools.product(*[range(l, h + 1) for l, h in zip(lo, hi)])
+                   if sum(c) == T)
+        assert math.isclose(_hh_cost(a, q), best, rel_tol=1e-12) or (best == math.inf)
+
+
+def test_hh_round_special_cases():
+    assert np.array_equal(P.hh_round([3.0, 5.0, 2.0], 10), [3, 5, 2])        # integer quotas stay
+    assert np.array_equal(P.hh_round([1.5, 1.5], 3), [2, 1])                 # tie: lower index first
+    assert np.array_equal(P.hh_round([0.2, 0.2, 0.6], 1), [1, 0, 0])         # a zero seat has top priority
+    assert np.array_equal(P.hh_round([2.5, 2.5], 5, cap=[2, 9]), [2, 3])     # caps bind
+    with pytest.raises(ValueError):
+        P.hh_round([1.2, 1.2], 5)
+
+
+def test_rp_is_proportional_within_one_sc_and_respects_allocations():
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        n = rng.integers(12, 200, size=int(rng.integers(2, 12)))
+        D = int(rng.integers(1, n.sum() + 1))
+        a = P.rp(n, D)
+        q = D * n / n.sum()
+        assert a.sum() == D and np.all(a <= n) and np.all(np.abs(a - q) < 1)
+
+
+def test_sef_closed_form():
+    n = np.array([30, 10, 20, 10])
+    assert np.array_equal(P.sef(n, 15), [0, 10, 0, 5])      # ties: lower index first
+    assert np.array_equal(P.sef(n, 45), [5, 10, 20, 10])
+    assert np.array_equal(P.sef(n, 70), n)
+    with pytest.raises(ValueError):
+        P.sef(n, 71)
+
+
+def test_kl_projection_closed_form_without_caps():
+    m = np.array([3.0, 1.0, 0.0, 4.0])
+    n = np.array([100.0, 100.0, 100.0, 100.0])
+    x = P.kl_project(m, n, 40.0)
+    assert np.allclose(x, 40.0 * m / m.sum(), rtol=0, atol=1e-12)
+
+
+def test_kl_projection_against_a_convex_solver():
+    opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        E = int(rng.integers(2, 8))
+        n = rng.integers(10, 120, E).astype(float)
+        m = rng.uniform(0, 150, E)
+        T = float(rng.integers(1, int(n.sum())))
+        x = P.kl_project(m, n, T)
+        assert math.isclose(x.sum(), T, rel_tol=1e-12) and np.all(x >= 0) and np.all(x <= n + 1e-9)
+
+        def f(v):
+            v = np.maximum(v, 1e-12)
+            return float(np.sum(m * np.log(m / v)))
+        res = opt.minimize(f, np.full(E, T / E).clip(0, n), method="SLSQP", bounds=list(zip([1e-9] * E, n)),
+                           constraints=[{"type": "eq", "fun": lambda v: v.sum() - T}],
+                           options={"ftol": 1e-12, "maxiter": 500})
+        assert f(x) <= res.fun + 1e-6 * max(1.0, abs(res.fun))
+
+
+def test_kl_projection_kkt_form_and_zero_users():
+    m = np.array([50.0, 0.0, 200.0, 10.0])
+    n = np.array([60.0, 30.0, 40.0, 70.0])
+    x = P.kl_project(m, n, 90.0)
+    # capped user 3 at 40; the others share the rest in proportion to m: c = 50 / 60
+    assert np.allclose(x, [50 * 50 / 60, 0.0, 40.0, 10 * 50 / 60], atol=1e-12)
+    x = P.kl_project(m, n, 190.0)  # positive users all capped (170); the remaining 20 goes to user 2
+    assert np.allclose(x, [60.0, 20.0, 40.0, 70.0], atol=1e-12)
+
+
+def test_enforcer_returns_a_feasible_integer_vector_and_keeps_feasible_ones():
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        E = int(rng.integers(2, 12))
+        n = rng.integers(12, 150, E)
+        L = int(rng.integers(20, 120))
+        j = int(rng.integers(1, max(2, n.sum() // L) + 1))
+        if j * L > n.sum():
+            continue
+        m = rng.uniform(0, 1.5, E) * n
+        a = P.enforce(m, n, j, L)
+        assert a.dtype.kind == "i" and a.sum() == j * L and np.all(a >= 0) and np.all(a <= n)
+        # an integer vector that is already feasible is its own projection and rounding
+        f = P.rp(n, j * L)
+        assert np.array_equal(P.enforce(f.astype(float), n, j, L), f)
+
+
+def test_sc_mask_counts_and_bands():
+    n = np.array([60, 108, 72])
+    m = np.zeros((7, 3), dtype=int)
+    m[1] = [10, 0, 72]
+    m[6] = [60, 5, 1]
+    msk = P.sc_mask(n, m)
+    assert msk.shape == (14, 240)
+    assert np.array_equal(msk.sum(axis=1), np.repeat(m.sum(axis=1), 2))
+    assert msk[2, :10].all() and not msk[2, 10:60].any() and msk[2, 168:240].all()
+    assert msk[12, 60:65].all() and not msk[12, 65:168].any() and msk[13, 168]
