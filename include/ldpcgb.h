@@ -339,6 +339,54 @@ LDPC_API int ldpc_serve_replay(ldpc_server *srv, const ldpc_serve_tb *tbs, const
 /* Stop the device loop (bounded wait) and free the server. */
 LDPC_API int ldpc_serve_stop(ldpc_server *srv);
 
+/* ---------------------------------------------------------------- puncturing allocations
+ *
+ * Which subcarriers URLLC takes from the eMBB users.  The paper compares its
+ * learned policy with two fixed ones (Sec. VII-A) and repairs its policy's
+ * output with a feasibility enforcer (Sec. V-B); these calls compute the
+ * fixed policies, the enforcer and the per-subcarrier masks they imply,
+ * batched, on the device.  They need no session; every pointer is a device
+ * pointer owned by the caller, every call enqueues on `cuda_stream` (NULL =
+ * legacy default stream) and returns LDPC_OK or LDPC_EINVAL (bad sizes, null
+ * buffer) / LDPC_ECUDA (launch failure) without waiting for the kernel.
+ * Per-problem failures are reported in status_dev (0 = ok) and leave that
+ * problem's output zero.
+ *
+ * Integer rounding everywhere is Huntington-Hill: every value goes to its
+ * floor or its ceiling (never above its cap), the units left after the
+ * floors go one at a time to the largest q_e / sqrt(a_e (a_e + 1)) (infinite
+ * for a_e = 0), equal priorities to the lower index; priorities in float64. */
+#define LDPC_POLICY_RP 0  /* "Resource Proportion": in proportion to the allocations */
+#define LDPC_POLICY_SEF 1 /* "Smallest eMBB First": smallest allocations taken whole first (lower index on ties) */
+
+/* SCs taken from each user, per (TTI, mini-slot).  alloc_dev: int32 [n_tti][n_users] SCs scheduled per
+ * user (the eMBB schedule s(t)); demand_dev: int32 [n_tti][7] URLLC SCs per mini-slot; punct_dev (out):
+ * int32 [n_tti][7][n_users]; status_dev (out): int32 [n_tti][7], 1 = demand above the TTI's total
+ * allocation.  1 <= n_users <= 32. */
+LDPC_API int ldpc_puncture_alloc(int32_t policy, int32_t n_tti, int32_t n_users, const int32_t *alloc_dev,
+                                 const int32_t *demand_dev, int32_t *punct_dev, int32_t *status_dev,
+                                 void *cuda_stream);
+
+/* Feasibility enforcer (Sec. V-B): for each problem, the integer vector nearest a real puncturing vector
+ * that may exceed the allocations.  First the projection x of m onto {0 <= x_e <= n_e, sum x = total}
+ * minimising sum_e m_e log(m_e / x_e) (eq. 6, eq. 7; users with m_e > 0 get min(n_e, c m_e) with one scale
+ * c, users with m_e <= 0 get 0 unless the others cannot hold the total, then the rest in proportion to
+ * n_e), then Huntington-Hill rounding to integers summing to total.  punct_real_dev: float64
+ * [n_prob][n_users]; alloc_dev: int32 [n_prob][n_users]; total_dev: int32 [n_prob] (j * L for branch j);
+ * punct_dev (out): int32 [n_prob][n_users]; status_dev (out): int32 [n_prob], 1 = total above the
+ * allocations, 2 = no rounding sums to the total. */
+LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const double *punct_real_dev,
+                                      const int32_t *alloc_dev, const int32_t *total_dev, int32_t *punct_dev,
+                                      int32_t *status_dev, void *cuda_stream);
+
+/* Puncture bitmap per (TTI, OFDM symbol): user e's band is the alloc SCs after users 0..e-1 (SC 0
+ * first) and the lowest punct SCs of the band are punctured in both symbols of the mini-slot (a reading:
+ * the paper does not say which SCs).  punct_dev as written by ldpc_puncture_alloc (each value at most its
+ * allocation); mask_dev (out): uint32 [n_tti][14][words_per_symbol], bit b of word w = SC 32w + b; SCs
+ * beyond 32 * words_per_symbol are dropped. */
+LDPC_API int ldpc_sc_mask(int32_t n_tti, int32_t n_users, const int32_t *alloc_dev, const int32_t *punct_dev,
+                          int32_t words_per_symbol, uint32_t *mask_dev, void *cuda_stream);
+
 /* Synchronise the session stream and return (then clear) the device error word. */
 LDPC_API int ldpc_device_errors(ldpc_session *s, uint32_t *flags_out);
 

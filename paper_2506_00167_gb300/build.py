@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libldpcgb.so")
 
-SOURCES = ["session.cu", "decode.cu", "demap.cu", "crc.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["session.cu", "decode.cu", "demap.cu", "crc.cu", "noalloc.cu", "serve.cu", "policy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
