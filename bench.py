@@ -406,6 +406,104 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- main arm
+def run_policy(args):
+    """Puncturing allocations for the paper's case-study setting (N = 780 SCs, 10 eMBB users, 300-SC
+    URLLC packets): RP and SeF per mini-slot and the per-symbol SC masks for args.policy_tti TTIs, the
+    feasibility enforcer over the floor(N/L) = 2 branches of every TTI, the enforcer's latency for one TTI
+    (the RT O-DU step, one launch) and its throughput on a large batch; beside them the oracle on a
+    bounded sample on the host cores."""
+    import torch
+    from oracle import policy as OP
+    from paper_2506_00167_gb300 import policy as GP
+    from workload.policy import branch_samples, schedules
+
+    torch.cuda.set_device(0)
+    T = args.policy_tti
+    alloc_np, demand_np = schedules(T)
+    m_np, n_np, tot_np = branch_samples(alloc_np)
+    alloc = torch.from_numpy(alloc_np.astype(np.int32)).cuda()
+    demand = torch.from_numpy(demand_np.astype(np.int32)).cuda()
+    m, n, tot = (torch.from_numpy(m_np.astype(np.float32)).cuda(), torch.from_numpy(n_np.astype(np.int32)).cuda(),
+                 torch.from_numpy(tot_np.astype(np.int32)).cuda())
+    words = (780 + 31) // 32
+
+    def dev_ms(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"workload": f"{T} TTIs: N = 780 SCs (65 PRBs), 10 eMBB users, 7 mini-slots, 300-SC URLLC packets "
+                       "from 12 users with Bernoulli(0.08) arrivals per mini-slot (at most 2 per mini-slot)"}
+    for pol in ["rp", "sef"]:
+        pm, _ = GP.puncture_alloc(alloc, demand, pol)
+        ms_alloc = dev_ms(lambda: GP.puncture_alloc(alloc, demand, pol), args.steps)
+        ms_mask = dev_ms(lambda: GP.sc_mask(alloc, pm, words), args.steps)
+        out[pol] = {"alloc_ms": ms_alloc, "mask_ms": ms_mask, "tti_per_s": T / ((ms_alloc + ms_mask) / 1e3),
+                    "mask_gbs": T * 14 * words * 4 / (ms_mask / 1e3) / 1e9}
+    ms_enf = dev_ms(lambda: GP.enforce(m, n, tot), args.steps)
+    out["enforcer"] = {"problems": int(tot_np.size), "batch_ms": ms_enf}
+    # one TTI (2 branches) per launch: the RT O-DU step's latency
+    m1, n1, t1 = m[:2].contiguous(), n[:2].contiguous(), tot[:2].contiguous()
+    lat = []
+    for _ in range(200):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        GP.enforce(m1, n1, t1)
+        e1.record()
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1) * 1e3)
+    host = []
+    for _ in range(200):
+        t0 = time.perf_counter()
+        GP.enforce(m1, n1, t1)
+        torch.cuda.synchronize()
+        host.append((time.perf_counter() - t0) * 1e6)
+    out["enforcer"]["one_tti_events_around_call_us_p50"] = float(np.percentile(lat[20:], 50))
+    out["enforcer"]["one_tti_host_roundtrip_us_p50"] = float(np.percentile(host[20:], 50))
+    # the kernel alone: 100 one-TTI calls captured in a CUDA graph and replayed back to back
+    # (device time per call, inter-kernel gaps included; the binding's host overhead excluded)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            GP.enforce(m1, n1, t1)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(100):
+            GP.enforce(m1, n1, t1)
+    out["enforcer"]["one_tti_kernel_us"] = dev_ms(lambda: g.replay(), 20) * 1e3 / 100
+    # throughput on a large batch
+    big = 1 << 20
+    reps = -(-big // tot_np.size)
+    mb, nb, tb = (m.repeat(reps, 1)[:big].contiguous(), n.repeat(reps, 1)[:big].contiguous(),
+                  tot.repeat(reps)[:big].contiguous())
+    ms_big = dev_ms(lambda: GP.enforce(mb, nb, tb), 5)
+    out["enforcer"]["large_batch"] = {"problems": big, "ms": ms_big, "problems_per_s": big / (ms_big / 1e3)}
+    # oracle, bounded sample
+    k = min(2000, tot_np.size)
+    t0 = time.perf_counter()
+    for p in range(k):
+        OP.enforce(m_np[p].astype(np.float32), n_np[p], int(tot_np[p]) // 300, 300)
+    cpu_enf = (time.perf_counter() - t0) / k
+    t0 = time.perf_counter()
+    for t in range(min(1000, T)):
+        OP.allocate(alloc_np[t], demand_np[t], "rp")
+    cpu_rp = (time.perf_counter() - t0) / min(1000, T)
+    out["cpu_oracle"] = {"enforcer_us_per_problem": cpu_enf * 1e6, "rp_us_per_tti": cpu_rp * 1e6, "cores": 1,
+                         "sample": f"first {k} enforcer problems, first {min(1000, T)} TTIs (RP), one process"}
+    out["paper_context"] = "the paper reports 10-30 us for its enforcer on a V100 (Sec. V-B): context only"
+    print(json.dumps({"policy": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,6 +522,8 @@ def main():
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
     ap.add_argument("--serve", action="store_true", help="replay the served request stream instead")
+    ap.add_argument("--policy", action="store_true", help="time the puncturing allocations (RP, SeF, enforcer)")
+    ap.add_argument("--policy-tti", type=int, default=5000)
     ap.add_argument("--serve-slots", type=int, default=8000)
     ap.add_argument("--serve-pool", type=int, default=1024)
     ap.add_argument("--serve-plain", type=int, default=400)
@@ -437,6 +537,8 @@ def main():
     args = ap.parse_args()
     if args.serve:
         return run_serving(args)
+    if args.policy:
+        return run_policy(args)
     if args.sweep == "precision":
         return run_precision_sweep(args)
     if args.warmup < 3 and args.impl == "ours":

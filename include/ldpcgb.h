@@ -355,7 +355,9 @@ LDPC_API int ldpc_serve_stop(ldpc_server *srv);
  * Integer rounding everywhere is Huntington-Hill: every value goes to its
  * floor or its ceiling (never above its cap), the units left after the
  * floors go one at a time to the largest q_e / sqrt(a_e (a_e + 1)) (infinite
- * for a_e = 0), equal priorities to the lower index; priorities in float64. */
+ * for a_e = 0), equal priorities to the lower index.  Quotas, priorities and
+ * the KL projection are float32, each operation rounded once in a fixed
+ * order, so results are reproducible bit for bit. */
 #define LDPC_POLICY_RP 0  /* "Resource Proportion": in proportion to the allocations */
 #define LDPC_POLICY_SEF 1 /* "Smallest eMBB First": smallest allocations taken whole first (lower index on ties) */
 
@@ -371,11 +373,11 @@ LDPC_API int ldpc_puncture_alloc(int32_t policy, int32_t n_tti, int32_t n_users,
  * that may exceed the allocations.  First the projection x of m onto {0 <= x_e <= n_e, sum x = total}
  * minimising sum_e m_e log(m_e / x_e) (eq. 6, eq. 7; users with m_e > 0 get min(n_e, c m_e) with one scale
  * c, users with m_e <= 0 get 0 unless the others cannot hold the total, then the rest in proportion to
- * n_e), then Huntington-Hill rounding to integers summing to total.  punct_real_dev: float64
+ * n_e), then Huntington-Hill rounding to integers summing to total.  punct_real_dev: float32
  * [n_prob][n_users]; alloc_dev: int32 [n_prob][n_users]; total_dev: int32 [n_prob] (j * L for branch j);
  * punct_dev (out): int32 [n_prob][n_users]; status_dev (out): int32 [n_prob], 1 = total above the
  * allocations, 2 = no rounding sums to the total. */
-LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const double *punct_real_dev,
+LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const float *punct_real_dev,
                                       const int32_t *alloc_dev, const int32_t *total_dev, int32_t *punct_dev,
                                       int32_t *status_dev, void *cuda_stream);
 

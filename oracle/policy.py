@@ -25,8 +25,10 @@ Readings where the paper is silent (each fixed here and in the CUDA path):
   floors and hand the remaining units out one at a time to the largest
   priority q_e / sqrt(a_e (a_e + 1)) (a_e the current value; a_e = 0 gives
   infinite priority), among values still below their ceiling and their cap
-  n_e; equal priorities go to the lower index.  Priorities are computed and
-  compared in float64.
+  n_e; equal priorities go to the lower index.
+* Precision: the paper does not fix one; quotas, priorities and the KL
+  projection are float32 (the policy network's output type), every operation
+  rounded once and taken in a fixed order.
 * KL projection: users with m_e > 0 take m^_e = min(n_e, c m_e) with one
   scale c >= 0 (the KKT conditions of eq. 7); users with m_e = 0 take 0 unless
   the others' allocations cannot hold jL, in which case the remainder is
@@ -38,17 +40,18 @@ Readings where the paper is silent (each fixed here and in the CUDA path):
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 N_MINISLOT = 7
 SYM_PER_MINISLOT = 2
 
 
+F32 = np.float32
+
+
 def hh_round(quota, total: int, cap=None) -> np.ndarray:
     """Integers a with sum(a) == total, floor(q) <= a <= ceil(q), a <= cap (Huntington-Hill order)."""
-    q = np.asarray(quota, dtype=np.float64)
+    q = np.asarray(quota, dtype=np.float32)
     n = q.size
     cap = np.full(n, np.iinfo(np.int64).max, dtype=np.int64) if cap is None else np.asarray(cap, dtype=np.int64)
     a = np.minimum(np.floor(q).astype(np.int64), cap)
@@ -57,11 +60,11 @@ def hh_round(quota, total: int, cap=None) -> np.ndarray:
     if left < 0 or left > int((hi - a).sum()):
         raise ValueError("no rounding of these quotas sums to the total")
     for _ in range(left):
-        best, best_p = -1, -1.0
+        best, best_p = -1, F32(-1.0)
         for e in range(n):
             if a[e] >= hi[e]:
                 continue
-            p = math.inf if a[e] == 0 else q[e] / math.sqrt(float(a[e]) * float(a[e] + 1))
+            p = F32(np.inf) if a[e] == 0 else q[e] / np.sqrt(F32(a[e]) * F32(a[e] + 1))
             if p > best_p:  # strict: the lower index keeps a tie
                 best, best_p = e, p
         a[best] += 1
@@ -71,7 +74,7 @@ def hh_round(quota, total: int, cap=None) -> np.ndarray:
 def rp(n, demand: int) -> np.ndarray:
     """Resource Proportion: SCs taken from each user for a demand of `demand` SCs."""
     n = np.asarray(n, dtype=np.int64)
-    q = float(demand) * n.astype(np.float64) / float(n.sum())
+    q = F32(demand) * n.astype(np.float32) / F32(n.sum())
     return hh_round(q, demand, n)
 
 
@@ -89,52 +92,50 @@ def sef(n, demand: int) -> np.ndarray:
     return out
 
 
-def kl_project(m, n, total: float) -> np.ndarray:
-    """argmin sum_e m_e log(m_e / x_e)  s.t.  0 <= x <= n, sum x = total  (eq. 6, eq. 7).
+def kl_project(m, n, total) -> np.ndarray:
+    """argmin sum_e m_e log(m_e / x_e)  s.t.  0 <= x <= n, sum x = total  (eq. 6, eq. 7), in float32.
 
-    Sums run in index order (capped users in breakpoint order), one float64
-    operation at a time, so that another implementation following the same
-    order reproduces the result bit for bit.
+    Sums of allocations are integers (exact in any order); sums of m run in
+    index order, one float32 operation at a time, so that another
+    implementation following the same order reproduces the result bit for
+    bit.
     """
-    m = [float(v) for v in m]
-    n = [float(v) for v in n]
-    E = len(m)
+    m = np.asarray(m, dtype=np.float32)
+    n = np.asarray(n, dtype=np.float32)
+    total = F32(total)
+    E = m.size
     pos = [e for e in range(E) if m[e] > 0]
     zero = [e for e in range(E) if not m[e] > 0]
-    cap_all = 0.0
-    for e in range(E):
-        cap_all += n[e]
-    if total > cap_all:
+    if total > F32(n.astype(np.int64).sum()):
         raise ValueError("total exceeds the allocations")
-    x = np.zeros(E, dtype=np.float64)
-    cap_pos = 0.0
-    for e in pos:
-        cap_pos += n[e]
+    x = np.zeros(E, dtype=np.float32)
+    cap_pos = F32(sum(int(n[e]) for e in pos))
     if cap_pos <= total:
         # every user with m_e > 0 is capped; the rest goes to the others by capacity
         for e in pos:
             x[e] = n[e]
         rest = total - cap_pos
-        cap0 = 0.0
-        for e in zero:
-            cap0 += n[e]
+        cap0 = F32(sum(int(n[e]) for e in zero))
         if rest > 0 and cap0 > 0:
             for e in zero:
                 x[e] = rest * n[e] / cap0
         return x
-    # water-filling on the scale c: users reach their cap in order of n_e / m_e
+    # water-filling on the scale c: users reach their cap in order of n_e / m_e.
+    # With the first k users of that order capped, c_k = (total - their n) /
+    # (sum of the other users' m, added in index order); c is the first c_k
+    # that leaves the k-th user of the order below its cap.
     order = sorted(pos, key=lambda e: (n[e] / m[e], e))
-    free_m = 0.0
-    for e in pos:
-        free_m += m[e]
-    capped = 0.0
-    c = 0.0
-    for e in order:
+    rank = {e: k for k, e in enumerate(order)}
+    c = F32(0.0)
+    for k, e in enumerate(order):
+        capped = F32(sum(int(n[f]) for f in pos if rank[f] < k))
+        free_m = F32(0.0)
+        for f in pos:
+            if rank[f] >= k:
+                free_m = free_m + m[f]
         c = (total - capped) / free_m
         if c * m[e] <= n[e]:
             break
-        capped += n[e]
-        free_m -= m[e]
     for e in pos:
         x[e] = min(n[e], c * m[e])
     return x
@@ -142,7 +143,7 @@ def kl_project(m, n, total: float) -> np.ndarray:
 
 def enforce(m, n, j: int, L: int) -> np.ndarray:
     """Feasible integer puncturing vector for branch j (demand j*L SCs)."""
-    x = kl_project(m, n, float(j * L))
+    x = kl_project(m, n, j * L)
     return hh_round(x, j * L, np.asarray(n, dtype=np.int64))
 
 

@@ -1,17 +1,21 @@
 // URLLC puncturing allocations on sm_103a: the two benchmark policies of the
 // paper's evaluation (Sec. VII-A), the feasibility enforcer of its RT O-DU
 // (Sec. V-B, eq. 6 and eq. 7) and the per-subcarrier puncture masks they
-// imply.  Each problem is a handful of users (at most 32), so one thread
-// solves one problem serially and a batch is many problems side by side.
+// imply.  A problem is a handful of users (at most 32): one warp solves one
+// problem with one lane per user, so a single problem (the RT O-DU's
+// per-TTI step) takes a few dependent operations per lane rather than a
+// serial loop, and a batch is many warps side by side.
 //
-// Rounding ("Huntington-Hill"): start from the floors of the real quotas and
-// hand the remaining units out one at a time to the largest priority
-// q_e / sqrt(a_e (a_e + 1)) (infinite for a_e = 0) among values below their
-// ceiling and their cap; equal priorities go to the lower index.  Every
-// floating-point step is an explicitly rounded float64 operation taken in a
-// fixed order (no contraction into fused multiply-adds), so a CPU
-// implementation taking the same steps agrees bit for bit and the integer
-// decisions match.
+// Rounding ("Huntington-Hill"): every value starts at its floor and may go
+// to its ceiling (never above its cap); the units left go to the values of
+// largest priority q_e / sqrt(a_e (a_e + 1)) (a_e the floor; infinite for
+// a_e = 0), equal priorities to the lower index.  A value can take at most
+// one unit, so handing units out one at a time by priority is the same as
+// giving them to the `left` highest-ranked values.  Arithmetic is float32 (the
+// paper fixes no precision; the policy network's output is float32), every
+// step an explicitly rounded operation in a fixed order (no fused
+// multiply-adds), so a CPU implementation taking the same steps agrees bit
+// for bit and the integer decisions match.
 #include <cmath>
 #include <string>
 
@@ -22,160 +26,145 @@ namespace ldpcgb {
 namespace {
 
 constexpr int kMaxUsers = 32;
-constexpr int kMiniSlots = 7;  // mini-slots per slot, two OFDM symbols each
-constexpr int kPolicyBlock = 128;
+constexpr int kMiniSlots = 7;     // mini-slots per slot, two OFDM symbols each
+constexpr int kPolicyBlock = 128;  // four problems per block
+constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Huntington-Hill rounding of q[0..E) to integers summing to `total`, each
-// within [floor(q), min(ceil(q), cap)].  Returns false if impossible.
-__device__ bool hh_round(const double* q, const int* cap, int E, int total, int* a) {
-  int hi[kMaxUsers];
-  int sum = 0, room = 0;
-  for (int e = 0; e < E; ++e) {
-    const int f = static_cast<int>(floor(q[e]));
-    const int c = static_cast<int>(ceil(q[e]));
-    a[e] = min(f, cap[e]);
-    hi[e] = min(c, cap[e]);
-    sum += a[e];
-    room += hi[e] - a[e];
-  }
-  int left = total - sum;
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Huntington-Hill rounding of lane e's quota q (lanes >= E pass active = false)
+// to an integer; the lane values sum to `total`.  Returns false (on every
+// lane) if no rounding within [floor, min(ceil, cap)] sums to the total.
+__device__ bool hh_round_warp(float q, int cap, bool active, int total, int lane, int E, int* out) {
+  int a = active ? min(static_cast<int>(floorf(q)), cap) : 0;
+  const int hi = active ? min(static_cast<int>(ceilf(q)), cap) : 0;
+  const int left = total - warp_sum(a);
+  const int room = warp_sum(hi - a);
   if (left < 0 || left > room) return false;
-  for (; left > 0; --left) {
-    int best = -1;
-    double best_p = -1.0;
-    for (int e = 0; e < E; ++e) {
-      if (a[e] >= hi[e]) continue;
-      const double p =
-          a[e] == 0 ? INFINITY
-                    : __ddiv_rn(q[e], __dsqrt_rn(__dmul_rn(static_cast<double>(a[e]), static_cast<double>(a[e] + 1))));
-      if (p > best_p) {
-        best = e;
-        best_p = p;
-      }
-    }
-    ++a[best];
+  const bool elig = hi > a;
+  const float p = !elig ? -1.0f
+                  : a == 0 ? INFINITY
+                           : __fdiv_rn(q, __fsqrt_rn(__fmul_rn(static_cast<float>(a), static_cast<float>(a + 1))));
+  // rank among eligible lanes: higher priority first, lower index on ties
+  int rank = 0;
+  for (int f = 0; f < E; ++f) {  // E is the same on every lane
+    const float pf = __shfl_sync(kFull, p, f);
+    const bool ef = __shfl_sync(kFull, elig, f);
+    if (ef && (pf > p || (pf == p && f < lane))) ++rank;
   }
+  if (elig && rank < left) ++a;
+  *out = a;
   return true;
 }
 
-// One thread per (TTI, mini-slot): SCs taken from each user for that
+// One warp per (TTI, mini-slot): SCs taken from each user for that
 // mini-slot's demand.  status: 0 ok, 1 demand exceeds the allocations.
 __global__ void __launch_bounds__(kPolicyBlock) alloc_kernel(int policy, int n_prob, int E, const int32_t* n,
                                                             const int32_t* demand, int32_t* m, int32_t* status) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_prob) return;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= n_prob) return;  // whole warps leave together
   const int t = p / kMiniSlots;
-  const int32_t* nt = n + static_cast<int64_t>(t) * E;
-  int32_t* out = m + static_cast<int64_t>(p) * E;
+  const bool active = lane < E;
+  const int cap = active ? n[static_cast<int64_t>(t) * E + lane] : 0;
+  const int S = warp_sum(cap);
   const int D = demand[p];
-  int cap[kMaxUsers];
-  int S = 0;
-  for (int e = 0; e < E; ++e) {
-    cap[e] = nt[e];
-    S += cap[e];
-  }
-  int a[kMaxUsers];
   bool ok = D <= S;
-  if (ok && D == 0) {
-    for (int e = 0; e < E; ++e) a[e] = 0;
-  } else if (ok && policy == LDPC_POLICY_RP) {
-    double q[kMaxUsers];
-    for (int e = 0; e < E; ++e)
-      q[e] = __ddiv_rn(__dmul_rn(static_cast<double>(D), static_cast<double>(cap[e])), static_cast<double>(S));
-    ok = hh_round(q, cap, E, D, a);
-  } else if (ok) {  // smallest allocation first, lower index on ties
-    bool used[kMaxUsers];
-    for (int e = 0; e < E; ++e) {
-      used[e] = false;
-      a[e] = 0;
-    }
-    int left = D;
-    for (int k = 0; k < E && left > 0; ++k) {
-      int pick = -1;
-      for (int e = 0; e < E; ++e)
-        if (!used[e] && (pick < 0 || cap[e] < cap[pick])) pick = e;
-      used[pick] = true;
-      a[pick] = min(left, cap[pick]);
-      left -= a[pick];
+  int a = 0;
+  if (ok && D > 0) {
+    if (policy == LDPC_POLICY_RP) {
+      const float q = __fdiv_rn(__fmul_rn(static_cast<float>(D), static_cast<float>(cap)), static_cast<float>(S));
+      ok = hh_round_warp(q, cap, active, D, lane, E, &a);
+    } else {  // smallest allocation first, lower index on ties: SCs of the users ranked before this one
+      int before = 0;
+      for (int f = 0; f < E; ++f) {  // E is the same on every lane
+        const int cf = __shfl_sync(kFull, cap, f);
+        if (cf < cap || (cf == cap && f < lane)) before += cf;
+      }
+      a = active ? max(0, min(cap, D - before)) : 0;
     }
   }
-  for (int e = 0; e < E; ++e) out[e] = ok ? a[e] : 0;
-  status[p] = ok ? 0 : 1;
+  if (active) m[static_cast<int64_t>(p) * E + lane] = ok ? a : 0;
+  if (lane == 0) status[p] = ok ? 0 : 1;
 }
 
-// One thread per problem: KL projection (eq. 7) by water-filling, then
+// One warp per problem: KL projection (eq. 7) by water-filling, then
 // Huntington-Hill rounding.  status: 0 ok, 1 total exceeds the allocations,
 // 2 no rounding sums to the total.
-__global__ void __launch_bounds__(kPolicyBlock) enforce_kernel(int n_prob, int E, const double* m_in,
+__global__ void __launch_bounds__(kPolicyBlock) enforce_kernel(int n_prob, int E, const float* m_in,
                                                               const int32_t* n_in, const int32_t* total_in,
                                                               int32_t* out, int32_t* status) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (p >= n_prob) return;
-  const double* m = m_in + static_cast<int64_t>(p) * E;
-  const int32_t* nn = n_in + static_cast<int64_t>(p) * E;
-  int32_t* o = out + static_cast<int64_t>(p) * E;
+  const bool active = lane < E;
+  const int64_t off = static_cast<int64_t>(p) * E + lane;
+  const float me = active ? m_in[off] : 0.0f;
+  const int cap = active ? n_in[off] : 0;
+  const float ne = static_cast<float>(cap);
+  const bool pos = active && me > 0.0f;
   const int T = total_in[p];
-  const double total = static_cast<double>(T);
-  double n[kMaxUsers], x[kMaxUsers];
-  int cap[kMaxUsers];
-  double cap_all = 0.0, cap_pos = 0.0;
-  for (int e = 0; e < E; ++e) {
-    cap[e] = nn[e];
-    n[e] = static_cast<double>(cap[e]);
-    x[e] = 0.0;
-    cap_all = __dadd_rn(cap_all, n[e]);
-    if (m[e] > 0.0) cap_pos = __dadd_rn(cap_pos, n[e]);
-  }
+  const float total = static_cast<float>(T);
+  // allocations are integers: their sums are exact in any order
+  const int cap_all = warp_sum(cap);
+  const int cap_pos = warp_sum(pos ? cap : 0);
   int st = 0;
-  if (total > cap_all) {
+  float x = 0.0f;
+  if (T > cap_all) {
     st = 1;
-  } else if (cap_pos <= total) {
+  } else if (cap_pos <= T) {
     // every user with m_e > 0 is capped; the rest goes to the others by capacity
-    double cap0 = 0.0;
-    for (int e = 0; e < E; ++e) {
-      if (m[e] > 0.0)
-        x[e] = n[e];
-      else
-        cap0 = __dadd_rn(cap0, n[e]);
-    }
-    const double rest = __dsub_rn(total, cap_pos);
-    if (rest > 0.0 && cap0 > 0.0)
-      for (int e = 0; e < E; ++e)
-        if (!(m[e] > 0.0)) x[e] = __ddiv_rn(__dmul_rn(rest, n[e]), cap0);
+    const int cap0 = cap_all - cap_pos;
+    const float rest = static_cast<float>(T - cap_pos);
+    if (pos)
+      x = ne;
+    else if (active && rest > 0.0f && cap0 > 0)
+      x = __fdiv_rn(__fmul_rn(rest, ne), static_cast<float>(cap0));
   } else {
     // water-filling: users reach their cap in order of n_e / m_e (lower index on ties)
-    int order[kMaxUsers];
-    double brk[kMaxUsers];
-    int k = 0;
-    double free_m = 0.0;
-    for (int e = 0; e < E; ++e) {
-      if (!(m[e] > 0.0)) continue;
-      free_m = __dadd_rn(free_m, m[e]);
-      const double b = __ddiv_rn(n[e], m[e]);
-      int i = k++;
-      while (i > 0 && brk[i - 1] > b) {  // stable insertion: equal breakpoints keep index order
-        brk[i] = brk[i - 1];
-        order[i] = order[i - 1];
-        --i;
+    const float b = pos ? __fdiv_rn(ne, me) : 0.0f;
+    int rank = 0;
+    for (int f = 0; f < E; ++f) {  // E is the same on every lane
+      const float bf = __shfl_sync(kFull, b, f);
+      const bool pf = __shfl_sync(kFull, pos, f);
+      if (pf && (bf < b || (bf == b && f < lane))) ++rank;
+    }
+    // lane k evaluates "the first k users of the order capped": c_k and whether
+    // the k-th user stays below its cap
+    const int npos = __popc(__ballot_sync(kFull, pos));
+    const int k = lane;
+    int capped = 0;
+    float free_m = 0.0f, mk = 0.0f, nk = 0.0f;
+    for (int f = 0; f < E; ++f) {
+      const float mf = __shfl_sync(kFull, me, f);
+      const int cf = __shfl_sync(kFull, cap, f);
+      const bool pf = __shfl_sync(kFull, pos, f);
+      const int rf = __shfl_sync(kFull, pos ? rank : -1, f);
+      if (!pf) continue;
+      if (rf < k)
+        capped += cf;
+      else
+        free_m = __fadd_rn(free_m, mf);  // index order, as in the definition
+      if (rf == k) {
+        mk = mf;
+        nk = static_cast<float>(cf);
       }
-      brk[i] = b;
-      order[i] = e;
     }
-    double capped = 0.0, c = 0.0;
-    for (int i = 0; i < k; ++i) {
-      const int e = order[i];
-      c = __ddiv_rn(__dsub_rn(total, capped), free_m);
-      if (__dmul_rn(c, m[e]) <= n[e]) break;
-      capped = __dadd_rn(capped, n[e]);
-      free_m = __dsub_rn(free_m, m[e]);
-    }
-    for (int e = 0; e < E; ++e)
-      if (m[e] > 0.0) x[e] = fmin(n[e], __dmul_rn(c, m[e]));
+    const float ck = k < npos ? __fdiv_rn(__fsub_rn(total, static_cast<float>(capped)), free_m) : 0.0f;
+    const bool stop = k < npos && __fmul_rn(ck, mk) <= nk;
+    const unsigned hit = __ballot_sync(kFull, stop);
+    const int kstar = hit ? __ffs(hit) - 1 : npos - 1;
+    const float c = __shfl_sync(kFull, ck, kstar);
+    if (pos) x = fminf(ne, __fmul_rn(c, me));
   }
-  int a[kMaxUsers];
-  if (st == 0 && !hh_round(x, cap, E, T, a)) st = 2;
-  for (int e = 0; e < E; ++e) o[e] = st == 0 ? a[e] : 0;
-  status[p] = st;
+  int a = 0;
+  if (st == 0 && !hh_round_warp(x, cap, active, T, lane, E, &a)) st = 2;
+  if (active) out[off] = st == 0 ? a : 0;
+  if (lane == 0) status[p] = st;
 }
 
 // One thread per (TTI, OFDM symbol, 32-SC word): bit b of word w is SC
@@ -238,19 +227,21 @@ LDPC_API int ldpc_puncture_alloc(int32_t policy, int32_t n_tti, int32_t n_users,
   if (n_tti == 0) return LDPC_OK;
   if (!alloc_dev || !demand_dev || !punct_dev || !status_dev) return policy_fail(LDPC_EINVAL, "null buffer");
   const int n_prob = n_tti * kMiniSlots;
-  alloc_kernel<<<grid_for(n_prob), kPolicyBlock, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+  alloc_kernel<<<grid_for(static_cast<int64_t>(n_prob) * 32), kPolicyBlock, 0,
+                 static_cast<cudaStream_t>(cuda_stream)>>>(
       policy, n_prob, n_users, alloc_dev, demand_dev, punct_dev, status_dev);
   return launch_status(cudaGetLastError());
 }
 
-LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const double* punct_real_dev,
+LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const float* punct_real_dev,
                                       const int32_t* alloc_dev, const int32_t* total_dev, int32_t* punct_dev,
                                       int32_t* status_dev, void* cuda_stream) {
   if (n_prob < 0 || n_users < 1 || n_users > kMaxUsers) return policy_fail(LDPC_EINVAL, "n_users must be 1..32");
   if (n_prob == 0) return LDPC_OK;
   if (!punct_real_dev || !alloc_dev || !total_dev || !punct_dev || !status_dev)
     return policy_fail(LDPC_EINVAL, "null buffer");
-  enforce_kernel<<<grid_for(n_prob), kPolicyBlock, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+  enforce_kernel<<<grid_for(static_cast<int64_t>(n_prob) * 32), kPolicyBlock, 0,
+                  static_cast<cudaStream_t>(cuda_stream)>>>(
       n_prob, n_users, punct_real_dev, alloc_dev, total_dev, punct_dev, status_dev);
   return launch_status(cudaGetLastError());
 }

@@ -44,9 +44,9 @@ def puncture_alloc(alloc: torch.Tensor, demand: torch.Tensor, policy: str):
 
 
 def enforce(punct_real: torch.Tensor, alloc: torch.Tensor, total: torch.Tensor):
-    """punct_real float64 [P, E], alloc int32 [P, E], total int32 [P] -> (punct int32 [P, E], status int32 [P])."""
+    """punct_real float32 [P, E], alloc int32 [P, E], total int32 [P] -> (punct int32 [P, E], status int32 [P])."""
     P, E = punct_real.shape
-    _need(punct_real, torch.float64, (P, E), "punct_real")
+    _need(punct_real, torch.float32, (P, E), "punct_real")
     _need(alloc, torch.int32, (P, E), "alloc")
     _need(total, torch.int32, (P,), "total")
     punct = torch.empty((P, E), dtype=torch.int32, device=alloc.device)

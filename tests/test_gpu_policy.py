@@ -61,7 +61,7 @@ def _oracle_enforce(mr, n, total):
     st = np.zeros(len(total), dtype=np.int64)
     for p in range(len(total)):
         try:
-            x = P.kl_project(mr[p], n[p], float(total[p]))
+            x = P.kl_project(mr[p], n[p], int(total[p]))
         except ValueError:
             st[p] = 1
             continue
@@ -77,7 +77,7 @@ def test_enforcer_matches_oracle(E):
     rng = np.random.default_rng(200 + E)
     Pn = 3000
     n = rng.integers(12, 150, size=(Pn, E))
-    mr = rng.uniform(0, 1.6, size=(Pn, E)) * n
+    mr = (rng.uniform(0, 1.6, size=(Pn, E)) * n).astype(np.float32)
     mr[rng.random((Pn, E)) < 0.2] = 0.0              # users the policy leaves alone
     mr[::5] = np.round(mr[::5])                       # integer-valued inputs, ties among breakpoints
     mr[::13, : max(1, E // 2)] = -1.0                 # negative entries count as zero

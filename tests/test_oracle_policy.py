@@ -100,7 +100,7 @@ def test_kl_projection_closed_form_without_caps():
     m = np.array([3.0, 1.0, 0.0, 4.0])
     n = np.array([100.0, 100.0, 100.0, 100.0])
     x = P.kl_project(m, n, 40.0)
-    assert np.allclose(x, 40.0 * m / m.sum(), rtol=0, atol=1e-12)
+    assert np.allclose(x, 40.0 * m / m.sum(), rtol=1e-6, atol=0)
 
 
 def test_kl_projection_against_a_convex_solver():
@@ -112,15 +112,16 @@ def test_kl_projection_against_a_convex_solver():
         m = rng.uniform(0, 150, E)
         T = float(rng.integers(1, int(n.sum())))
         x = P.kl_project(m, n, T)
-        assert math.isclose(x.sum(), T, rel_tol=1e-12) and np.all(x >= 0) and np.all(x <= n + 1e-9)
+        # float32 arithmetic: the sum holds to float32 rounding
+        assert math.isclose(float(x.astype(np.float64).sum()), T, rel_tol=1e-5) and np.all(x >= 0) and np.all(x <= n)
 
         def f(v):
-            v = np.maximum(v, 1e-12)
+            v = np.maximum(np.asarray(v, dtype=np.float64), 1e-12)
             return float(np.sum(m * np.log(m / v)))
         res = opt.minimize(f, np.full(E, T / E).clip(0, n), method="SLSQP", bounds=list(zip([1e-9] * E, n)),
                            constraints=[{"type": "eq", "fun": lambda v: v.sum() - T}],
                            options={"ftol": 1e-12, "maxiter": 500})
-        assert f(x) <= res.fun + 1e-6 * max(1.0, abs(res.fun))
+        assert f(x) <= res.fun + 1e-4 * max(1.0, abs(res.fun))
 
 
 def test_kl_projection_kkt_form_and_zero_users():
@@ -128,9 +129,9 @@ def test_kl_projection_kkt_form_and_zero_users():
     n = np.array([60.0, 30.0, 40.0, 70.0])
     x = P.kl_project(m, n, 90.0)
     # capped user 3 at 40; the others share the rest in proportion to m: c = 50 / 60
-    assert np.allclose(x, [50 * 50 / 60, 0.0, 40.0, 10 * 50 / 60], atol=1e-12)
+    assert np.allclose(x, [50 * 50 / 60, 0.0, 40.0, 10 * 50 / 60], rtol=1e-6, atol=0)
     x = P.kl_project(m, n, 190.0)  # positive users all capped (170); the remaining 20 goes to user 2
-    assert np.allclose(x, [60.0, 20.0, 40.0, 70.0], atol=1e-12)
+    assert np.allclose(x, [60.0, 20.0, 40.0, 70.0], rtol=1e-6, atol=0)
 
 
 def test_enforcer_returns_a_feasible_integer_vector_and_keeps_feasible_ones():
