@@ -49,3 +49,55 @@ def branch_samples(alloc: np.ndarray, seed: int = 8):
     raw = rng.uniform(0.0, 1.5, size=a.shape) * a
     m = raw * (total / raw.sum(axis=1))[:, None]
     return m, np.repeat(alloc, J, axis=0), total.astype(np.int64)
+
+
+# ---------------------------------------------------------------------------- link-level case study
+QM_CASE = 4      # 16-QAM
+R_CASE = 0.5     # BG2-shaped codes at rate 1/2: 5 Z resource elements per code block
+CASE_Z = (32, 64, 128, 256, 384)
+MAX_CB_CASE = 8
+
+
+def tb_shape_for_band(width: int):
+    """(Z, n_cb) of the TB a user's band carries: BG2-shaped, rate 1/2, 16-QAM, the (Z, n_cb <= 8)
+    that fills the most of the band's 14 x width resource elements (ties: fewer, larger code blocks)."""
+    avail = 14 * width
+    best = None
+    for Z in CASE_Z:
+        per_cb = 5 * Z
+        n = min(MAX_CB_CASE, avail // per_cb)
+        if n >= 1 and (best is None or n * per_cb > best[0] or (n * per_cb == best[0] and Z > best[1])):
+            best = (n * per_cb, Z, n)
+    if best is None:
+        raise ValueError("band too narrow for the smallest code block")
+    return best[1], best[2]
+
+
+def case_study(alloc: np.ndarray, masks: list, seed: int = 9, spread_db=(0.0, 3.0)):
+    """Link-level TTIs of the paper's case-study setting under given puncture masks.
+
+    alloc: [T, 10] SCs per user (``schedules``); masks[t]: (14, 780) bool punctured REs of TTI t (from a
+    puncturing policy).  Each user's band (its SCs after those of the users before it) carries one TB of
+    BG2-shaped rate-1/2 16-QAM code blocks (``tb_shape_for_band``) at Es/N0 ~ U[op + lo, op + hi] with
+    op the operating point of that rate and modulation; slot width N = 780 SCs.
+    """
+    from .configs import (N_SYM, TBSpec, build, default_bgs, es_n0_sigma2, operating_point_db)
+    bgs = default_bgs()
+    rng = np_stream(seed, 23, alloc.shape[0])
+    specs, widths, snrs = [], [], []
+    E = int(QM_CASE * 5 * 1)  # per Z unit; E = QM * 5Z
+    for t in range(alloc.shape[0]):
+        sc0 = 0
+        for e in range(alloc.shape[1]):
+            w = int(alloc[t, e])
+            Z, n_cb = tb_shape_for_band(w)
+            snr = operating_point_db(R_CASE, QM_CASE) + float(rng.uniform(*spread_db))
+            specs.append(TBSpec(t, 1, Z, QM_CASE, E * Z, n_cb, float(es_n0_sigma2(snr)), sc0, w))
+            snrs.append(snr)
+            sc0 += w
+        widths.append(sc0)
+    if any(m.shape != (N_SYM, N_SC) for m in masks):
+        raise ValueError("masks must be (14, 780)")
+    w = build("case_study", bgs, specs, widths, list(masks), seed, snr_db=snrs)
+    w.meta.update(dict(name="case_study", max_iter=10, early_term=1, mode="f32", offset=0.5))
+    return w
