@@ -165,3 +165,56 @@ def allocate(n, demand_per_minislot, policy: str) -> np.ndarray:
     """(7, E) SCs punctured per mini-slot and user under `policy` ('rp' or 'sef')."""
     fn = {"rp": rp, "sef": sef}[policy]
     return np.stack([fn(n, int(d)) if d else np.zeros(len(n), dtype=np.int64) for d in demand_per_minislot])
+
+
+# ---------------------------------------------------------------------------- RT O-DU actor (timing form)
+def softplus32(x):
+    """log(1 + e^x) in float32 (numerically safe form)."""
+    x = np.asarray(x, dtype=np.float32)
+    return (np.maximum(x, F32(0)) + np.log1p(np.exp(-np.abs(x)))).astype(np.float32)
+
+
+def actor_forward(x, w1, b1, w2, b2, noise):
+    """Policy network f_a on one branch input (Sec. VI-B, Sec. VII-B setting): one dense hidden layer,
+    ReLU; outputs [mu_1..mu_E, s_1..s_E]; sigma = softplus(s); z = mu + sigma * noise (the
+    reparameterisation); action = (tanh(z) + 1) / 2 in [0, 1].  float32; every sum starts at the bias
+    and adds the products in index order, each product and sum rounded once.
+    Returns (action[E], mu[E], sigma[E])."""
+    x = np.asarray(x, dtype=np.float32)
+    H = w1.shape[0]
+    h = np.zeros(H, dtype=np.float32)
+    for k in range(H):
+        acc = F32(b1[k])
+        for i in range(x.size):
+            acc = acc + F32(w1[k, i]) * x[i]
+        h[k] = max(acc, F32(0))
+    E = w2.shape[0] // 2
+    o = np.zeros(2 * E, dtype=np.float32)
+    for r in range(2 * E):
+        acc = F32(b2[r])
+        for k in range(H):
+            acc = acc + F32(w2[r, k]) * h[k]
+        o[r] = acc
+    mu, s = o[:E], o[E:]
+    sigma = softplus32(s)
+    z = (mu + sigma * np.asarray(noise, dtype=np.float32)).astype(np.float32)
+    action = ((np.tanh(z) + F32(1)) / F32(2)).astype(np.float32)
+    return action, mu, sigma
+
+
+def rt_odu_codebook(alloc, w1, b1, w2, b2, noise, L: int):
+    """Codebook B*(t) of one TTI (Alg. 2): for branches j = 1 .. J the actor's action on input
+    [s(t) / N, j / J], read as the fraction of each user's allocation to puncture, then the
+    feasibility enforcer with total j L.  Returns (codebook [J, E] int64, actions [J, E] float32)."""
+    alloc = np.asarray(alloc, dtype=np.int64)
+    N = int(alloc.sum())
+    J = noise.shape[0]
+    book = np.zeros((J, alloc.size), dtype=np.int64)
+    acts = np.zeros((J, alloc.size), dtype=np.float32)
+    for j in range(1, J + 1):
+        x = np.concatenate([alloc.astype(np.float32) / F32(N), [F32(j) / F32(J)]]).astype(np.float32)
+        a, _, _ = actor_forward(x, w1, b1, w2, b2, noise[j - 1])
+        acts[j - 1] = a
+        m = (a * alloc.astype(np.float32)).astype(np.float32)
+        book[j - 1] = enforce(m, alloc, j, L)
+    return book, acts

@@ -161,3 +161,41 @@ def test_sc_mask_counts_and_bands():
     assert np.array_equal(msk.sum(axis=1), np.repeat(m.sum(axis=1), 2))
     assert msk[2, :10].all() and not msk[2, 10:60].any() and msk[2, 168:240].all()
     assert msk[12, 60:65].all() and not msk[12, 65:168].any() and msk[13, 168]
+
+
+def test_softplus_closed_forms():
+    v = P.softplus32(np.array([0.0, 30.0, -30.0, 1.0], dtype=np.float32))
+    assert np.allclose(v, [math.log(2.0), 30.0, math.exp(-30.0), math.log1p(math.e)], rtol=1e-6, atol=0)
+
+
+def test_actor_forward_by_hand():
+    # x = (0.5, 1); hidden: relu(0 + 0.5 - 1) = 0 and relu(-1 + 0.25 + 2) = 1.25;
+    # mu = 0.5 + 1*0 + 2*1.25 = 3; raw sigma 0 -> softplus(0) = ln 2
+    w1 = np.array([[1.0, -1.0], [0.5, 2.0]], np.float32)
+    b1 = np.array([0.0, -1.0], np.float32)
+    w2 = np.array([[1.0, 2.0], [0.0, 0.0]], np.float32)
+    b2 = np.array([0.5, 0.0], np.float32)
+    a, mu, sg = P.actor_forward([0.5, 1.0], w1, b1, w2, b2, [0.0])
+    assert mu[0] == 3.0 and math.isclose(sg[0], math.log(2.0), rel_tol=1e-7)
+    assert math.isclose(a[0], (math.tanh(3.0) + 1) / 2, rel_tol=1e-7)      # 0.99752738
+    a, _, _ = P.actor_forward([0.5, 1.0], w1, b1, w2, b2, [1.0])          # z = 3 + ln 2
+    assert math.isclose(a[0], (math.tanh(3.0 + math.log(2.0)) + 1) / 2, rel_tol=1e-6)
+
+
+def test_codebook_is_feasible_and_uniform_actions_give_rp():
+    s = _table6()["s"]
+    E, H = 10, 128
+    rng = np.random.default_rng(9)
+    w1 = rng.normal(0, 0.3, (H, E + 1)).astype(np.float32)
+    b1 = rng.normal(0, 0.1, H).astype(np.float32)
+    w2 = rng.normal(0, 0.1, (2 * E, H)).astype(np.float32)
+    b2 = rng.normal(0, 0.1, 2 * E).astype(np.float32)
+    book, acts = P.rt_odu_codebook(s, w1, b1, w2, b2, rng.normal(size=(2, E)).astype(np.float32), 300)
+    assert np.all((acts >= 0) & (acts <= 1))
+    assert book[0].sum() == 300 and book[1].sum() == 600 and np.all(book >= 0) and np.all(book <= s)
+    # a policy that asks every user for the same fraction of its allocation is RP
+    z = np.zeros_like
+    b2u = z(b2)
+    b2u[:E] = 0.3
+    book, _ = P.rt_odu_codebook(s, z(w1), z(b1), z(w2), b2u, np.zeros((2, E), np.float32), 300)
+    assert np.array_equal(book[0], P.rp(s, 300)) and np.array_equal(book[1], P.rp(s, 600))
