@@ -381,6 +381,23 @@ LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const flo
                                       const int32_t *alloc_dev, const int32_t *total_dev, int32_t *punct_dev,
                                       int32_t *status_dev, void *cuda_stream);
 
+/* RT O-DU codebook B*(t) (Alg. 2), one TTI per thread block: for each branch j = 1 .. n_branch the
+ * policy network's forward pass on input [s(t) / N, j / n_branch] (N = the TTI's total allocation): one
+ * dense hidden layer of `hidden` ReLU units, outputs [mu_1..mu_E, s_1..s_E], sigma = softplus(s), the
+ * reparameterised sample z = mu + sigma * noise, action (tanh(z) + 1) / 2 in [0, 1] read as the fraction
+ * of each user's allocation to puncture; then the feasibility enforcer on each branch with total j * L.
+ * The paper's network has trained weights (Sec. VII-B: one hidden layer of 128); none exist here, so the
+ * caller supplies any weights (this is the timing form).  Layouts (row-major, float32): w1_dev
+ * [hidden][n_users + 1], b1_dev [hidden], w2_dev [2 n_users][hidden], b2_dev [2 n_users]; noise_dev
+ * [n_tti][n_branch][n_users] standard-normal draws (random numbers come from the caller).  alloc_dev:
+ * int32 [n_tti][n_users]; outputs: codebook_dev int32 and action_dev float32 [n_tti][n_branch][n_users],
+ * status_dev int32 [n_tti][n_branch] (enforcer status).  1 <= n_users <= 32, hidden <= 1024,
+ * n_branch <= 32.  Sums start at the bias and add products in index order, each rounded once. */
+LDPC_API int ldpc_rt_odu_codebook(int32_t n_tti, int32_t n_users, int32_t hidden, int32_t n_branch, int32_t L,
+                                  const int32_t *alloc_dev, const float *w1_dev, const float *b1_dev,
+                                  const float *w2_dev, const float *b2_dev, const float *noise_dev,
+                                  int32_t *codebook_dev, float *action_dev, int32_t *status_dev, void *cuda_stream);
+
 /* Puncture bitmap per (TTI, OFDM symbol): user e's band is the alloc SCs after users 0..e-1 (SC 0
  * first) and the lowest punct SCs of the band are punctured in both symbols of the mini-slot (a reading:
  * the paper does not say which SCs).  punct_dev as written by ldpc_puncture_alloc (each value at most its

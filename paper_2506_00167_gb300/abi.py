@@ -28,7 +28,7 @@ EXPORTED = [
     "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
     "ldpc_graph_create", "ldpc_graph_launch", "ldpc_graph_destroy",
     "ldpc_serve_start", "ldpc_serve_submit", "ldpc_serve_poll", "ldpc_serve_replay", "ldpc_serve_stop",
-    "ldpc_puncture_alloc", "ldpc_feasibility_enforce", "ldpc_sc_mask",
+    "ldpc_puncture_alloc", "ldpc_feasibility_enforce", "ldpc_sc_mask", "ldpc_rt_odu_codebook",
 ]
 POLICY_RP, POLICY_SEF = 0, 1
 PLAN_MIXED, PLAN_PER_Z = 0, 1

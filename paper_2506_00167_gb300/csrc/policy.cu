@@ -16,6 +16,7 @@
 // step an explicitly rounded operation in a fixed order (no fused
 // multiply-adds), so a CPU implementation taking the same steps agrees bit
 // for bit and the integer decisions match.
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -92,22 +93,13 @@ __global__ void __launch_bounds__(kPolicyBlock) alloc_kernel(int policy, int n_p
   if (lane == 0) status[p] = ok ? 0 : 1;
 }
 
-// One warp per problem: KL projection (eq. 7) by water-filling, then
-// Huntington-Hill rounding.  status: 0 ok, 1 total exceeds the allocations,
-// 2 no rounding sums to the total.
-__global__ void __launch_bounds__(kPolicyBlock) enforce_kernel(int n_prob, int E, const float* m_in,
-                                                              const int32_t* n_in, const int32_t* total_in,
-                                                              int32_t* out, int32_t* status) {
-  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (p >= n_prob) return;
-  const bool active = lane < E;
-  const int64_t off = static_cast<int64_t>(p) * E + lane;
-  const float me = active ? m_in[off] : 0.0f;
-  const int cap = active ? n_in[off] : 0;
+// KL projection (eq. 7) by water-filling, then Huntington-Hill rounding, on
+// one warp: lane e holds user e's real puncturing value `me` and allocation
+// `cap`; writes lane e's integer result and the problem's status (0 ok, 1
+// total exceeds the allocations, 2 no rounding sums to the total).
+__device__ void enforce_warp(float me, int cap, bool active, int T, int lane, int E, int* a_out, int* st_out) {
   const float ne = static_cast<float>(cap);
   const bool pos = active && me > 0.0f;
-  const int T = total_in[p];
   const float total = static_cast<float>(T);
   // allocations are integers: their sums are exact in any order
   const int cap_all = warp_sum(cap);
@@ -163,8 +155,92 @@ __global__ void __launch_bounds__(kPolicyBlock) enforce_kernel(int n_prob, int E
   }
   int a = 0;
   if (st == 0 && !hh_round_warp(x, cap, active, T, lane, E, &a)) st = 2;
-  if (active) out[off] = st == 0 ? a : 0;
+  *a_out = st == 0 ? a : 0;
+  *st_out = st;
+}
+
+// One warp per problem.
+__global__ void __launch_bounds__(kPolicyBlock) enforce_kernel(int n_prob, int E, const float* m_in,
+                                                              const int32_t* n_in, const int32_t* total_in,
+                                                              int32_t* out, int32_t* status) {
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= n_prob) return;
+  const bool active = lane < E;
+  const int64_t off = static_cast<int64_t>(p) * E + lane;
+  int a, st;
+  enforce_warp(active ? m_in[off] : 0.0f, active ? n_in[off] : 0, active, total_in[p], lane, E, &a, &st);
+  if (active) out[off] = a;
   if (lane == 0) status[p] = st;
+}
+
+// RT O-DU step for one TTI per block (Alg. 2): the policy network's forward
+// pass for every branch j = 1 .. J on input [s(t)/N, j/J] (one ReLU hidden
+// layer, outputs means and raw deviations, sigma = softplus, the
+// reparameterised sample z = mu + sigma * noise, action (tanh(z) + 1) / 2 read
+// as the fraction of each user's allocation), then the enforcer per branch on
+// warp j-1 with total j L.  Sums start at the bias and add products in index
+// order, each rounded once (no fused multiply-adds).
+__global__ void rt_odu_kernel(int E, int H, int J, int L, const int32_t* alloc, const float* w1, const float* b1,
+                              const float* w2, const float* b2, const float* noise, int32_t* book, float* act,
+                              int32_t* status) {
+  extern __shared__ float sm[];
+  float* x = sm;                   // [J][E+1]
+  float* h = x + J * (E + 1);      // [J][H]
+  float* o = h + J * H;            // [J][2E]
+  float* m = o + J * 2 * E;        // [J][E]
+  __shared__ int s_alloc[kMaxUsers];
+  __shared__ int s_N;
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid < E) s_alloc[tid] = alloc[static_cast<int64_t>(t) * E + tid];
+  __syncthreads();
+  if (tid == 0) {
+    int N = 0;
+    for (int e = 0; e < E; ++e) N += s_alloc[e];
+    s_N = N;
+  }
+  __syncthreads();
+  const float Nf = static_cast<float>(s_N);
+  for (int i = tid; i < J * (E + 1); i += blockDim.x) {
+    const int j = i / (E + 1), e = i - j * (E + 1);
+    x[i] = e < E ? __fdiv_rn(static_cast<float>(s_alloc[e]), Nf)
+                 : __fdiv_rn(static_cast<float>(j + 1), static_cast<float>(J));
+  }
+  __syncthreads();
+  for (int i = tid; i < J * H; i += blockDim.x) {
+    const int j = i / H, k = i - j * H;
+    float acc = b1[k];
+    for (int e = 0; e <= E; ++e) acc = __fadd_rn(acc, __fmul_rn(w1[k * (E + 1) + e], x[j * (E + 1) + e]));
+    h[i] = acc < 0.0f ? 0.0f : acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < J * 2 * E; i += blockDim.x) {
+    const int j = i / (2 * E), r = i - j * 2 * E;
+    float acc = b2[r];
+    for (int k = 0; k < H; ++k) acc = __fadd_rn(acc, __fmul_rn(w2[r * H + k], h[j * H + k]));
+    o[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < J * E; i += blockDim.x) {
+    const int j = i / E, e = i - j * E;
+    const float mu = o[j * 2 * E + e], s = o[j * 2 * E + E + e];
+    const float sigma = __fadd_rn(fmaxf(s, 0.0f), log1pf(expf(-fabsf(s))));
+    const float z = __fadd_rn(mu, __fmul_rn(sigma, noise[(static_cast<int64_t>(t) * J + j) * E + e]));
+    const float a = __fdiv_rn(__fadd_rn(tanhf(z), 1.0f), 2.0f);
+    act[(static_cast<int64_t>(t) * J + j) * E + e] = a;
+    m[i] = __fmul_rn(a, static_cast<float>(s_alloc[e]));
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp < J) {
+    const bool active = lane < E;
+    int a, st;
+    enforce_warp(active ? m[warp * E + lane] : 0.0f, active ? s_alloc[lane] : 0, active, (warp + 1) * L, lane, E,
+                 &a, &st);
+    if (active) book[(static_cast<int64_t>(t) * J + warp) * E + lane] = a;
+    if (lane == 0) status[static_cast<int64_t>(t) * J + warp] = st;
+  }
 }
 
 // One thread per (TTI, OFDM symbol, 32-SC word): bit b of word w is SC
@@ -243,6 +319,32 @@ LDPC_API int ldpc_feasibility_enforce(int32_t n_prob, int32_t n_users, const flo
   enforce_kernel<<<grid_for(static_cast<int64_t>(n_prob) * 32), kPolicyBlock, 0,
                   static_cast<cudaStream_t>(cuda_stream)>>>(
       n_prob, n_users, punct_real_dev, alloc_dev, total_dev, punct_dev, status_dev);
+  return launch_status(cudaGetLastError());
+}
+
+LDPC_API int ldpc_rt_odu_codebook(int32_t n_tti, int32_t n_users, int32_t hidden, int32_t n_branch, int32_t L,
+                                  const int32_t* alloc_dev, const float* w1_dev, const float* b1_dev,
+                                  const float* w2_dev, const float* b2_dev, const float* noise_dev,
+                                  int32_t* codebook_dev, float* action_dev, int32_t* status_dev, void* cuda_stream) {
+  if (n_tti < 0 || n_users < 1 || n_users > kMaxUsers || hidden < 1 || hidden > 1024 || n_branch < 1 ||
+      n_branch > 32 || L < 1)
+    return policy_fail(LDPC_EINVAL, "bad sizes (users 1..32, hidden 1..1024, branches 1..32)");
+  if (n_tti == 0) return LDPC_OK;
+  if (!alloc_dev || !w1_dev || !b1_dev || !w2_dev || !b2_dev || !noise_dev || !codebook_dev || !action_dev ||
+      !status_dev)
+    return policy_fail(LDPC_EINVAL, "null buffer");
+  const int threads = ((std::max(std::max(hidden, 32 * n_branch), 2 * n_users) + 31) / 32) * 32;
+  if (threads > 1024) return policy_fail(LDPC_EINVAL, "too many threads for one block");
+  const size_t smem = sizeof(float) * static_cast<size_t>(n_branch) *
+                      static_cast<size_t>((n_users + 1) + hidden + 2 * n_users + n_users);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&rt_odu_kernel),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return launch_status(e);
+  }
+  rt_odu_kernel<<<n_tti, threads, smem, static_cast<cudaStream_t>(cuda_stream)>>>(
+      n_users, hidden, n_branch, L, alloc_dev, w1_dev, b1_dev, w2_dev, b2_dev, noise_dev, codebook_dev, action_dev,
+      status_dev);
   return launch_status(cudaGetLastError());
 }
 

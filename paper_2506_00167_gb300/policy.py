@@ -1,7 +1,9 @@
-"""Puncturing allocations on the device: the RP and SeF policies, the feasibility enforcer, SC masks.
+"""Puncturing allocations on the device: the RP and SeF policies, the feasibility enforcer, SC masks,
+and the RT O-DU codebook (policy forward pass + enforcer).
 
-Thin wrappers over ``ldpc_puncture_alloc``, ``ldpc_feasibility_enforce`` and
-``ldpc_sc_mask`` (see ``include/ldpcgb.h``): they check shapes and dtypes,
+Thin wrappers over ``ldpc_puncture_alloc``, ``ldpc_feasibility_enforce``,
+``ldpc_sc_mask`` and ``ldpc_rt_odu_codebook`` (see ``include/ldpcgb.h``):
+they check shapes and dtypes,
 allocate the outputs as torch tensors on the inputs' device and enqueue on the
 current stream.  Every step runs in the library's kernels.
 """
@@ -67,3 +69,25 @@ def sc_mask(alloc: torch.Tensor, punct: torch.Tensor, words_per_symbol: int | No
     abi.check(abi.load().ldpc_sc_mask(T, E, _ptr(alloc), _ptr(punct), int(words_per_symbol), _ptr(mask),
                                       _stream()), "ldpc_sc_mask")
     return mask
+
+
+def rt_odu_codebook(alloc: torch.Tensor, w1: torch.Tensor, b1: torch.Tensor, w2: torch.Tensor, b2: torch.Tensor,
+                    noise: torch.Tensor, L: int):
+    """alloc int32 [T, E]; weights float32 w1 [H, E+1], b1 [H], w2 [2E, H], b2 [2E]; noise float32 [T, J, E]
+    -> (codebook int32 [T, J, E], actions float32 [T, J, E], status int32 [T, J])."""
+    T, E = alloc.shape
+    H = w1.shape[0]
+    J = noise.shape[1]
+    _need(alloc, torch.int32, (T, E), "alloc")
+    _need(w1, torch.float32, (H, E + 1), "w1")
+    _need(b1, torch.float32, (H,), "b1")
+    _need(w2, torch.float32, (2 * E, H), "w2")
+    _need(b2, torch.float32, (2 * E,), "b2")
+    _need(noise, torch.float32, (T, J, E), "noise")
+    book = torch.empty((T, J, E), dtype=torch.int32, device=alloc.device)
+    act = torch.empty((T, J, E), dtype=torch.float32, device=alloc.device)
+    status = torch.empty((T, J), dtype=torch.int32, device=alloc.device)
+    abi.check(abi.load().ldpc_rt_odu_codebook(T, E, H, J, int(L), _ptr(alloc), _ptr(w1), _ptr(b1), _ptr(w2),
+                                              _ptr(b2), _ptr(noise), _ptr(book), _ptr(act), _ptr(status),
+                                              _stream()), "ldpc_rt_odu_codebook")
+    return book, act, status

@@ -110,3 +110,36 @@ def test_sc_mask_matches_oracle():
         bits = np.unpackbits(mask[t].astype("<u4").view(np.uint8), bitorder="little").reshape(14, words * 32)
         assert np.array_equal(bits[:, : want.shape[1]].astype(bool), want)
         assert not bits[:, want.shape[1]:].any()
+
+
+def test_rt_odu_codebook_matches_oracle():
+    from workload.policy import actor_noise, actor_weights, schedules
+    T = 300
+    alloc, _ = schedules(T, seed=41)
+    w1, b1, w2, b2 = actor_weights(seed=42)
+    noise = actor_noise(T, seed=43)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    book, act, st = G.rt_odu_codebook(_cuda_i32(alloc), cu(w1), cu(b1), cu(w2), cu(b2), cu(noise), 300)
+    book, act, st = book.cpu().numpy(), act.cpu().numpy(), st.cpu().numpy()
+    assert not st.any()
+    same = 0
+    for t in range(T):
+        wb, wa = P.rt_odu_codebook(alloc[t], w1, b1, w2, b2, noise[t], 300)
+        # tanh/exp/log1p of the GPU and of NumPy may differ in the last bit: actions agree to float32
+        # rounding, codebooks exactly unless a Huntington-Hill priority falls on such a difference
+        assert np.allclose(act[t], wa, rtol=2e-6, atol=1e-7)
+        same += int(np.array_equal(book[t], wb))
+        for j in range(book.shape[1]):
+            assert book[t, j].sum() == 300 * (j + 1) and np.all(book[t, j] <= alloc[t]) and np.all(book[t, j] >= 0)
+    assert same >= 0.99 * T
+
+
+def test_rt_odu_uniform_policy_is_rp_bit_exact():
+    s = np.array([[60, 108, 72, 72, 72, 48, 72, 48, 96, 132]])
+    E, H = 10, 128
+    z = lambda *sh: torch.zeros(sh, dtype=torch.float32, device="cuda")
+    b2 = z(2 * E)
+    b2[:E] = 0.3
+    book, _, st = G.rt_odu_codebook(_cuda_i32(s), z(H, E + 1), z(H), z(2 * E, H), b2, z(1, 2, E), 300)
+    assert not st.any()
+    assert book[0, 0].tolist() == P.rp(s[0], 300).tolist() and book[0, 1].tolist() == P.rp(s[0], 600).tolist()

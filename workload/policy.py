@@ -101,3 +101,22 @@ def case_study(alloc: np.ndarray, masks: list, seed: int = 9, spread_db=(0.0, 3.
     w = build("case_study", bgs, specs, widths, list(masks), seed, snr_db=snrs)
     w.meta.update(dict(name="case_study", max_iter=10, early_term=1, mode="f32", offset=0.5))
     return w
+
+
+def actor_weights(E: int = N_UE, H: int = 128, seed: int = 10):
+    """Random weights of the policy network's shape (no trained weights exist): Glorot-uniform w1 [H, E+1]
+    and w2 [2E, H], zero biases except a small negative bias on the raw deviations; float32."""
+    rng = np_stream(seed, 24)
+    lim1 = np.sqrt(6.0 / (E + 1 + H))
+    lim2 = np.sqrt(6.0 / (H + 2 * E))
+    w1 = rng.uniform(-lim1, lim1, (H, E + 1)).astype(np.float32)
+    w2 = rng.uniform(-lim2, lim2, (2 * E, H)).astype(np.float32)
+    b1 = np.zeros(H, np.float32)
+    b2 = np.zeros(2 * E, np.float32)
+    b2[E:] = -1.0
+    return w1, b1, w2, b2
+
+
+def actor_noise(n_tti: int, J: int = N_SC // L_URLLC, E: int = N_UE, seed: int = 11):
+    """Standard-normal draws of the reparameterised samples, [T, J, E] float32."""
+    return np_stream(seed, 25, n_tti).standard_normal((n_tti, J, E)).astype(np.float32)
