@@ -14,9 +14,12 @@ recursive Gray QAM: bits b0, b2, .. drive I, b1, b3, .. drive Q; per-axis
 amplitude A(c0, c1, ..) = (1 - 2 c0)(2^(q-1) - A(c1, ..)), A(c) = 1 - 2c;
 unit average energy.
 
-Rate dematching: the Qm bits of resource element r are codeword positions
-t0 + i * (E / Qm) + r (i < Qm) with the row-column interleaver, or
-t0 + r * Qm + i without it; positions never transmitted hold LLR 0.
+Rate dematching: the Qm bits of resource element r are rate-matched bits
+e = i * (E / Qm) + r (i < Qm) with the row-column interleaver, or
+e = r * Qm + i without it; bit e is codeword position t0 + (e mod Ncb), a
+circular buffer of Ncb = nb * Z - t0 positions (redundancy version 0; E > Ncb
+repeats it), and the LLRs of all bits that land on one position are added
+(LLR combining); positions never transmitted hold LLR 0.
 The decoded length is n_eff * Z with n_eff = kb + m_eff and
 m_eff = min(mb, max(mc, ceil((E + t0) / Z) - kb)), t0 = n_punct_cols * Z.
 
@@ -86,10 +89,11 @@ def demap_cb(y, mask_bits, bg, Z, Qm, E, inv_sigma2, interleave=True) -> np.ndar
     lam = maxlog_llr(y[:n_re], Qm, inv_sigma2)          # (n_re, Qm)
     lam[np.asarray(mask_bits[:n_re], dtype=bool)] = 0.0  # puncture flushing
     out = np.zeros(n_eff * Z, dtype=np.float64)
+    ncb = bg.nb * Z - t0
     r = np.arange(n_re)
     for i in range(Qm):
-        pos = t0 + (i * n_re + r if interleave else r * Qm + i)
-        out[pos] = lam[:, i]
+        e = i * n_re + r if interleave else r * Qm + i
+        np.add.at(out, t0 + e % ncb, lam[:, i])
     return out
 
 

@@ -155,3 +155,48 @@ def test_geometry_large_code():
     # same geometry from the workload's helpers (two independent formulas)
     assert (bg.t0(384), bg.m_eff(384, 16896), bg.n_eff(384, 16896)) == (768, 24, 46)
     assert tree_base_graph().n_edges == 9
+
+
+def test_rate_matching_wraps_the_circular_buffer():
+    from workload import tx as TX
+    from workload import default_bgs
+    bgs = default_bgs()
+    bg, Z = bgs[0], 64
+    rng = np.random.default_rng(3)
+    info = rng.integers(0, 2, size=(2, bg.kb * Z), dtype=np.uint8)
+    cw = TX.encode(bg, Z, info, n_cols=bg.nb)
+    ncb = bg.nb * Z - bg.t0(Z)
+    E = ncb + 500
+    e = TX.rate_match(bg, Z, cw, E)
+    assert np.array_equal(e[:, :ncb], cw[:, bg.t0(Z):]) and np.array_equal(e[:, ncb:], e[:, :500])
+
+
+def test_repeated_positions_add_their_llrs():
+    # noiseless QPSK at unit 1/sigma^2: every bit's max-log LLR is +-2 (2 sqrt2 * 1/sqrt2); a position sent
+    # twice carries the sum, +-4, with the sign of its bit
+    from workload import tx as TX
+    from workload import default_bgs
+    bgs = default_bgs()
+    bg, Z, Qm = bgs[1], 32, 2
+    ncb = bg.nb * Z - bg.t0(Z)
+    E = ncb + 2 * 150
+    rng = np.random.default_rng(4)
+    info = rng.integers(0, 2, size=(1, bg.kb * Z), dtype=np.uint8)
+    cw = TX.encode(bg, Z, info, n_cols=bg.nb)
+    y = TX.qam_map(TX.interleave(TX.rate_match(bg, Z, cw, E), Qm, True))[0]
+    llr = demap.demap_cb(y, np.zeros(E // Qm, dtype=bool), bg, Z, Qm, E, 1.0, True)
+    t0 = bg.t0(Z)
+    sign = 1.0 - 2.0 * cw[0, t0:].astype(np.float64)
+    assert np.allclose(llr[t0:t0 + 300], 4.0 * sign[:300], atol=1e-9)
+    assert np.allclose(llr[t0 + 300:t0 + ncb], 2.0 * sign[300:ncb], atol=1e-9)
+    assert np.all(llr[:t0] == 0)
+
+
+def test_noiseless_repetition_decodes_exactly():
+    from oracle import path as opath
+    from workload.configs import repetition
+    w = repetition(3, noiseless=True)
+    assert np.all(w.cbs["E"] > np.array([w.bgs[int(c["bg"])].nb * int(c["Z"]) - w.bgs[int(c["bg"])].t0(int(c["Z"]))
+                                         for c in w.cbs]))
+    r = opath.run(w, "f64", 10, True)
+    assert opath.block_errors(w, r["words"]).sum() == 0 and np.all(r["d"] == 1)

@@ -187,7 +187,7 @@ def build(name: str, bgs: list, specs: list, slot_widths: list, punct: list, see
     for (b, Z, E, Qm), idx in sorted(groups.items()):
         bg = bgs[b]
         info = np.stack([cb_info[i] for i in idx])
-        n_cols = -(-(E + bg.t0(Z)) // Z)
+        n_cols = min(bg.nb, -(-(E + bg.t0(Z)) // Z))  # E beyond the circular buffer repeats it
         cw = tx.encode(bg, Z, info, n_cols=n_cols)
         e = tx.rate_match(bg, Z, cw, E)
         re_bits = tx.interleave(e, Qm, interleave)
@@ -382,6 +382,39 @@ def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int 
     w = build("mixed", bgs, specs, widths, punct, seed, snr_db=snrs, z_set=list(MIX_Z),
               noiseless=noiseless)
     w.meta.update(dict(name="mixed", max_iter=10, early_term=1, mode="i8", offset=0.5))
+    return w
+
+
+def repetition(n_per_shape: int = 24, seed: int = 12, noiseless: bool = False) -> Workload:
+    """Code blocks whose rate matching wraps the circular buffer (E > Ncb = nb*Z - t0): BG1-shaped Z=64 at
+    R = 0.3 and BG2-shaped Z=32 at R = 0.15, 16-QAM, one code block per TB and slot, Es/N0 around the
+    operating point, 1-2 URLLC mini-slot runs per slot."""
+    bgs = default_bgs()
+    rng = np_stream(seed, 4)
+    specs, widths, punct, snrs = [], [], [], []
+    for b, Z, R in [(0, 64, 0.3), (1, 32, 0.15)]:
+        bg = bgs[b]
+        Qm = 4
+        K = bg.kb * Z
+        E = Qm * int(round(K / (R * Qm)))
+        assert bg.nb * Z - bg.t0(Z) < E <= 2 * (bg.nb * Z - bg.t0(Z))
+        n_re = E // Qm
+        width = 12 * -(-n_re // (12 * N_SYM))
+        for _ in range(n_per_shape):
+            slot = len(specs)
+            snr = operating_point_db(R, Qm) + float(rng.uniform(-1.0, 2.0))
+            specs.append(TBSpec(slot, b, Z, Qm, E, 1, float(es_n0_sigma2(snr)), 0, width))
+            snrs.append(snr)
+            P = np.zeros((N_SYM, width), dtype=bool)
+            for _ in range(1 + int(rng.integers(0, 2))):
+                m = int(rng.integers(0, N_MINISLOT))
+                ln = min(12 * (1 + int(rng.integers(0, 3))), width)
+                st = int(rng.integers(0, width - ln + 1))
+                P[2 * m:2 * m + 2, st:st + ln] = True
+            punct.append(P)
+            widths.append(width)
+    w = build("repetition", bgs, specs, widths, punct, seed, snr_db=snrs, noiseless=noiseless)
+    w.meta.update(dict(name="repetition", max_iter=10, early_term=1, mode="f32", offset=0.5))
     return w
 
 

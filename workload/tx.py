@@ -14,8 +14,10 @@ Conventions fixed here (and restated by the receiver side):
   bits fill its code blocks in order, ``K = kb * Z`` bits each, with no filler.
 * Systematic encoding: ``c[0:K] = info``; core parity by the dual-diagonal
   closed form; extension parity is the sum of its row's other blocks.
-* Rate matching: the ``E`` transmitted bits are codeword positions
-  ``[t0, t0 + E)`` with ``t0 = n_punct_cols * Z``.
+* Rate matching (redundancy version 0): bit ``e`` of the ``E`` transmitted
+  bits is codeword position ``t0 + (e mod Ncb)`` with ``t0 = n_punct_cols * Z``
+  and ``Ncb = nb * Z - t0``: positions ``[t0, t0 + E)`` when ``E <= Ncb``, a
+  second pass over the buffer from its start otherwise (``E <= 2 Ncb``).
 * Interleaver (flag, default on): the E bits are written row-wise into ``Qm``
   rows of ``E / Qm`` and read column-wise, so resource element ``r`` carries
   bits ``e[i * (E / Qm) + r]`` for ``i < Qm``.
@@ -114,10 +116,18 @@ def encode(bg: BaseGraph, Z: int, info: np.ndarray, n_cols: int | None = None) -
 
 # --------------------------------------------------------------------------- rate match + QAM
 def rate_match(bg: BaseGraph, Z: int, cw: np.ndarray, E: int) -> np.ndarray:
+    """Redundancy version 0 from a circular buffer of the codeword positions [t0, nb*Z): bit e is
+    position t0 + (e mod Ncb), Ncb = nb*Z - t0, so E > Ncb repeats the buffer from its start (at most
+    once: E <= 2 Ncb)."""
     t0 = bg.t0(Z)
-    if t0 + E > cw.shape[1]:
-        raise ValueError("E exceeds the produced codeword (no repetition in this build)")
-    return cw[:, t0:t0 + E]
+    ncb = bg.nb * Z - t0
+    if E > 2 * ncb:
+        raise ValueError("E exceeds two passes over the circular buffer")
+    if t0 + E <= cw.shape[1]:
+        return cw[:, t0:t0 + E]
+    if cw.shape[1] < bg.nb * Z:
+        raise ValueError("repetition needs the whole codeword")
+    return cw[:, t0 + np.arange(E) % ncb]
 
 
 def interleave(e: np.ndarray, Qm: int, enabled: bool = True) -> np.ndarray:
