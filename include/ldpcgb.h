@@ -102,8 +102,10 @@ typedef struct {
 } ldpc_session_desc;
 
 /*
- * One code block.  Transmitted bits are codeword positions [t0, t0 + E) with
- * t0 = n_punct_cols * Z; the decoder works on n_eff = kb + m_eff columns with
+ * One code block.  Transmitted bit e is codeword position t0 + (e mod Ncb),
+ * t0 = n_punct_cols * Z, Ncb = nb * Z - t0 (a circular buffer read from its
+ * start; E > Ncb repeats it and the receiver adds the LLRs of a position;
+ * E <= 2 Ncb); the decoder works on n_eff = kb + m_eff columns with
  * m_eff = min(mb, max(mc, ceil((E + t0) / Z) - kb)) rows.
  *   re_offset        first complex symbol (float2) of the block, E / Qm of them
  *   mask_word_offset first uint32 of its puncture mask: bit r % 32 of word

@@ -14,7 +14,10 @@
 // Qm LLRs, written to its interleaved codeword position t0 + i * (E/Qm) + r --
 // for a fixed bit plane i consecutive threads write consecutive positions, so
 // every store is coalesced.  The first tile of each code block also
-// zero-fills the positions never transmitted.
+// zero-fills the positions never transmitted.  When rate matching wraps the
+// circular buffer (E > Ncb), this kernel writes the first pass and
+// demap_repeat_kernel then rewrites the repeated positions with the sum of
+// their two LLRs.
 #include "demap_core.cuh"
 
 namespace ldpcgb {
@@ -52,13 +55,50 @@ __global__ void __launch_bounds__(kDemapBlock) demap_kernel(const DemapArgs a) {
   if (tile.re_start == 0) {  // positions never transmitted hold LLR 0
     LT* out = static_cast<LT*>(a.llr) + cb.llr_off;
     for (int p = threadIdx.x; p < cb.t0; p += blockDim.x) out[p] = LT(0);
-    const int tail0 = cb.t0 + cb.E;
+    const int tail0 = cb.t0 + min(cb.E, cb.n_eff * cb.Z - cb.t0);
     const int n = cb.n_eff * cb.Z;
     for (int p = tail0 + threadIdx.x; p < n; p += blockDim.x) out[p] = LT(0);
   }
 }
 
+// Repeated bits e2 in [Ncb, E) of a block whose rate matching wraps: position
+// e2 - Ncb gets lambda(e2 - Ncb) + lambda(e2), one thread per repeated bit,
+// after demap_kernel has written the first pass.
+template <typename LT>
+__global__ void __launch_bounds__(kDemapBlock) demap_repeat_kernel(const DemapArgs a) {
+  const DemapTile tile = a.tiles[blockIdx.x];
+  const CbDev cb = a.cbs[tile.cb];
+  const int e2 = tile.re_start + static_cast<int>(threadIdx.x);
+  if (e2 >= cb.E) return;
+  const int ncb = cb.n_eff * cb.Z - cb.t0;
+  const float2* sym = a.sym + cb.re_off;
+  const uint32_t* msk = a.mask + cb.mask_off;
+  auto ls = [&](int i) { return __ldg(sym + i); };
+  auto lm = [&](int w) { return __ldg(msk + w); };
+  float v;
+  switch (cb.Qm) {
+    case 2: v = bit_llr<2>(e2 - ncb, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm) +
+                bit_llr<2>(e2, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm); break;
+    case 4: v = bit_llr<4>(e2 - ncb, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm) +
+                bit_llr<4>(e2, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm); break;
+    case 6: v = bit_llr<6>(e2 - ncb, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm) +
+                bit_llr<6>(e2, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm); break;
+    default: v = bit_llr<8>(e2 - ncb, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm) +
+                 bit_llr<8>(e2, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm); break;
+  }
+  static_cast<LT*>(a.llr)[cb.llr_off + cb.t0 + e2 - ncb] = to_llr<LT>(v, a.q_scale, a.llr_sat);
+}
+
 }  // namespace
+
+cudaError_t launch_demap_repeat(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a) {
+  if (n_tiles == 0) return cudaSuccess;
+  void* args[] = {const_cast<DemapArgs*>(&a)};
+  const void* fn = mode == LDPC_F32  ? reinterpret_cast<const void*>(&demap_repeat_kernel<float>)
+                   : mode == LDPC_I8 ? reinterpret_cast<const void*>(&demap_repeat_kernel<int8_t>)
+                                     : reinterpret_cast<const void*>(&demap_repeat_kernel<int16_t>);
+  return cudaLaunchKernel(fn, dim3(n_tiles), dim3(kDemapBlock), args, 0, st);
+}
 
 cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a) {
   if (n_tiles == 0) return cudaSuccess;

@@ -65,21 +65,56 @@ __device__ __forceinline__ LT to_llr(float lam, float q_scale, float sat) {
   }
 }
 
+// Rate matching reads a circular buffer of the Ncb = n_eff * Z - t0 codeword
+// positions from t0 (redundancy version 0): rate-matched bit e lands on
+// position t0 + (e mod Ncb), so when E > Ncb the buffer repeats and the two
+// LLRs of a position are added (LLR combining; E <= 2 Ncb).  The thread that
+// owns bit e < Ncb writes the position, adding the LLR of bit e + Ncb when it
+// was sent; it demaps that bit's resource element itself, so each position is
+// written once and the sum is always taken in the same order.
+
+// Max-log LLR of rate-matched bit e (0 for a punctured resource element);
+// sym/msk point at the code block's symbols and mask words.
+template <int Qm, typename LoadSym, typename LoadMask>
+__device__ __noinline__ float bit_llr(int e, int n_re, int interleave, float inv_sigma2, LoadSym ld_sym,
+                                     LoadMask ld_msk) {
+  const int r = interleave ? e % n_re : e / Qm;
+  const int i = interleave ? e / n_re : e % Qm;
+  if ((ld_msk(r >> 5) >> (r & 31)) & 1u) return 0.0f;
+  const float2 y = ld_sym(r);
+  float lam[Qm];
+  axis_llr<Qm / 2>(y.x, inv_sigma2, lam, 0);
+  axis_llr<Qm / 2>(y.y, inv_sigma2, lam, 1);
+  float v = lam[0];
+#pragma unroll
+  for (int t = 1; t < Qm; ++t)
+    if (t == i) v = lam[t];
+  return v;
+}
+
 // Resource element r of a code block (symbol y, punctured or not) into its
-// Qm codeword positions, `out` pointing at the block's position t0.
-template <typename LT, int Qm>
+// codeword positions, `out` pointing at the block's position t0.
+template <typename LT, int Qm, typename LoadSym, typename LoadMask>
 __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, LT* out, int r, int n_re,
-                                              int interleave, float q_scale, float llr_sat) {
+                                              int E, int ncb, int interleave, float q_scale, float llr_sat,
+                                              LoadSym ld_sym, LoadMask ld_msk) {
   float lam[Qm];
   axis_llr<Qm / 2>(y.x, inv_sigma2, lam, 0);
   axis_llr<Qm / 2>(y.y, inv_sigma2, lam, 1);
 #pragma unroll
   for (int i = 0; i < Qm; ++i) {
-    const LT v = punct ? LT(0) : to_llr<LT>(lam[i], q_scale, llr_sat);
-    out[interleave ? i * n_re + r : r * Qm + i] = v;
+    const int e = interleave ? i * n_re + r : r * Qm + i;
+    if (e >= ncb) continue;  // a repetition: added by the owner of e - ncb
+    float v = punct ? 0.0f : lam[i];
+    if (e + ncb < E) v += bit_llr<Qm>(e + ncb, n_re, interleave, inv_sigma2, ld_sym, ld_msk);
+    out[e] = to_llr<LT>(v, q_scale, llr_sat);
   }
 }
 
+// Batch form: writes the first pass over the circular buffer only; the
+// positions that also received a repetition are rewritten with the combined
+// LLR by a second kernel (demap.cu), so this hot loop carries no repetition
+// work.
 template <typename LT, int Qm>
 __device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, int r, float2 y, uint32_t mask_word) {
   const bool punct = (mask_word >> (r & 31)) & 1u;
@@ -87,11 +122,11 @@ __device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, in
   axis_llr<Qm / 2>(y.x, cb.inv_sigma2, lam, 0);
   axis_llr<Qm / 2>(y.y, cb.inv_sigma2, lam, 1);
   LT* out = static_cast<LT*>(a.llr) + cb.llr_off + cb.t0;
+  const int ncb = cb.n_eff * cb.Z - cb.t0;
 #pragma unroll
   for (int i = 0; i < Qm; ++i) {
-    const LT v = punct ? LT(0) : to_llr<LT>(lam[i], a.q_scale, a.llr_sat);
-    const int pos = a.interleave ? i * cb.n_re + r : r * Qm + i;
-    out[pos] = v;
+    const int e = a.interleave ? i * cb.n_re + r : r * Qm + i;
+    if (e < ncb) out[e] = punct ? LT(0) : to_llr<LT>(lam[i], a.q_scale, a.llr_sat);
   }
 }
 

@@ -127,6 +127,7 @@ cudaError_t launch_decode(int mode, int kind, dim3 grid, dim3 block, int smem, c
 cudaError_t decode_occupancy(int mode, int kind, int block, int smem, int* blocks_per_sm);
 cudaError_t decode_prepare(int mode);  // raise the dynamic shared-memory limit
 cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
+cudaError_t launch_demap_repeat(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
 cudaError_t launch_crc(int n_slots, cudaStream_t st, const CrcArgs& a);
 
 constexpr int kDemapBlock = 256;

@@ -161,8 +161,8 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
       return LDPC_EINVAL;
     }
     const int t0 = npc * Z;
-    if (E <= 0 || t0 + E > nb * Z) {
-      set_error("decode_uniform_noalloc: need 0 < E and t0 + E <= nb * Z");
+    if (E <= 0 || E > 2 * (nb * Z - t0)) {  // the rate-matching circular buffer may wrap once
+      set_error("decode_uniform_noalloc: need 0 < E <= 2 (nb * Z - t0)");
       return LDPC_EINVAL;
     }
     const int m_eff = std::min(mb, std::max(mc, (E + t0 + Z - 1) / Z - kb));

@@ -143,8 +143,9 @@ __device__ CbDev load_cb(const CbDev* p) {
 template <typename LT>
 __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, LT* L, int k, int Z) {
   using namespace demapcore;
+  const int ncb = cb.n_eff * Z - cb.t0;  // circular buffer: E > ncb repeats it
   for (int p = k; p < cb.t0; p += Z) L[p] = LT(0);
-  for (int p = cb.t0 + cb.E + k; p < cb.n_eff * Z; p += Z) L[p] = LT(0);
+  for (int p = cb.t0 + min(cb.E, ncb) + k; p < cb.n_eff * Z; p += Z) L[p] = LT(0);
   const float2* sym = reinterpret_cast<const float2*>(a.host_pool) + cb.re_off;
   const uint32_t* msk = reinterpret_cast<const uint32_t*>(a.host_pool) + cb.mask_off;
   LT* out = L + cb.t0;
@@ -152,11 +153,13 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
   for (int r = k; r < cb.n_re; r += Z) {
     const float2 y = ld_pool_f2(sym + r);
     const bool punct = (ld_pool_u32(msk + (r >> 5)) >> (r & 31)) & 1u;
+    auto ls = [&](int i) { return ld_pool_f2(sym + i); };
+    auto lm = [&](int w) { return ld_pool_u32(msk + w); };
     switch (cb.Qm) {
-      case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
-      case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
-      case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
-      default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, a.interleave, a.q_scale, a.llr_sat); break;
+      case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
     }
   }
 }
@@ -705,7 +708,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const ShapeDev& sd = ss.sh;
     const int t0 = sd.npc * tb.Z;
     if (tb.n_cb < 1 || tb.n_cb > kMaxTbCb || (tb.Qm != 2 && tb.Qm != 4 && tb.Qm != 6 && tb.Qm != 8) || tb.E <= 0 ||
-        tb.E % tb.Qm || t0 + tb.E > sd.nb * tb.Z)
+        tb.E % tb.Qm || tb.E > 2 * (sd.nb * tb.Z - t0))  // the circular buffer may wrap once
       return srv_fail(LDPC_EINVAL, at + "bad n_cb, Qm or E");
     const int K = sd.kb * tb.Z;
     if (K % 32 || tb.payload_bits != tb.n_cb * K - 24) return srv_fail(LDPC_EINVAL, at + "payload_bits");

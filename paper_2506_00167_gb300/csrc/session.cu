@@ -72,6 +72,8 @@ struct ldpc_batch {
   uint32_t* d_queues = nullptr;  // one work-queue counter per decoder launch
   ldpcgb::DemapTile* d_tiles = nullptr;
   int n_tiles = 0;
+  ldpcgb::DemapTile* d_rep_tiles = nullptr;  // repeated bits of blocks whose rate matching wraps
+  int n_rep_tiles = 0;
   ldpcgb::TbDev* d_tbs = nullptr;
   int32_t* d_slot_start = nullptr;
   int32_t* d_slot_tbs = nullptr;
@@ -620,8 +622,9 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       if (c.Qm != 2 && c.Qm != 4 && c.Qm != 6 && c.Qm != 8) return bail(LDPC_EINVAL, at + "Qm must be 2/4/6/8");
       const auto& g = s->bgs[c.bg];
       const int t0 = g.npc * c.Z;
-      if (c.E <= 0 || c.E % c.Qm || t0 + c.E > g.nb * c.Z)
-        return bail(LDPC_EINVAL, at + "E must be a positive multiple of Qm with t0 + E <= nb*Z");
+      // rate matching reads a circular buffer of the nb*Z - t0 positions from t0; it may wrap once
+      if (c.E <= 0 || c.E % c.Qm || c.E > 2 * (g.nb * c.Z - t0))
+        return bail(LDPC_EINVAL, at + "E must be a positive multiple of Qm with E <= 2 (nb*Z - t0)");
       if (c.re_offset < 0 || c.mask_word_offset < 0 || c.llr_offset < 0 || c.bits_word_offset < 0 || c.reserved)
         return bail(LDPC_EINVAL, at + "negative offset or nonzero reserved field");
       if ((c.llr_offset * esz) % 16) return bail(LDPC_EINVAL, at + "llr_offset must be 16-byte aligned");
@@ -666,6 +669,15 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       for (int r = 0; r < std::max(1, b->cbs[i].n_re); r += kDemapTile) tiles.push_back({i, r});
     b->n_tiles = static_cast<int>(tiles.size());
     if ((rc = upload(s, &b->d_tiles, tiles, &b->owned, &b->bytes))) return bail(rc, g_err);
+    // blocks whose rate matching wraps the circular buffer: their repeated bits, kDemapBlock per tile
+    std::vector<DemapTile> rep;
+    for (int i = 0; i < n_cb; ++i) {
+      const CbDev& c = b->cbs[i];
+      const int ncb = c.n_eff * c.Z - c.t0;
+      for (int e = ncb; e < c.E; e += kDemapBlock) rep.push_back({i, e});
+    }
+    b->n_rep_tiles = static_cast<int>(rep.size());
+    if (!rep.empty() && (rc = upload(s, &b->d_rep_tiles, rep, &b->owned, &b->bytes))) return bail(rc, g_err);
 
     // ---- transport blocks and slots
     if (n_tb > 0) {
@@ -826,6 +838,10 @@ int puncture_demap(ldpc_session* s, const ldpc_batch* b, const void* sym_dev, co
   a.q_scale = s->q_scale;
   a.llr_sat = static_cast<float>(s->llr_sat);
   cudaError_t e = launch_demap(s->mode, b->n_tiles, s->stream, a);
+  if (e == cudaSuccess && b->n_rep_tiles > 0) {  // LLR combining of repeated bits, after the main pass
+    a.tiles = b->d_rep_tiles;
+    e = launch_demap_repeat(s->mode, b->n_rep_tiles, s->stream, a);
+  }
   return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "puncture_demap launch");
 }
 

@@ -16,6 +16,7 @@ from oracle import demap as odemap
 from oracle import goodput as ogood
 from oracle import path as opath
 from workload import large_fp32, mixed, tiny_fp32
+from workload.configs import repetition
 from workload.basegraph import tree_base_graph
 
 from gpu_helpers import LLR_NP, batch_for, device_inputs, session_for, to_np_u32
@@ -31,6 +32,7 @@ def _workloads():
         "tiny": tiny_fp32(n_per_point=24, ebn0_points=(1, 3)),
         "large": large_fp32(n_cw=10, snr_points=(6, 8, 10, 12)),
         "mixed": mixed(n_slots=3, ues_per_slot=4, max_cb=3),
+        "repetition": repetition(n_per_shape=8),   # rate matching wraps the circular buffer
     }
 
 
@@ -52,7 +54,7 @@ def _params(w):
 
 
 # ------------------------------------------------------------------ demap
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition"])
 def test_demap_f32_matches_oracle(wls, name):
     w = wls[name]
     s = session_for(w, "f32")
@@ -70,7 +72,7 @@ def test_demap_f32_matches_oracle(wls, name):
 
 
 @pytest.mark.parametrize("mode", ["i8", "i16"])
-@pytest.mark.parametrize("name", ["large", "mixed"])
+@pytest.mark.parametrize("name", ["large", "mixed", "repetition"])
 def test_demap_quantised_within_one_lsb(wls, name, mode):
     w = wls[name]
     s = session_for(w, mode)
@@ -91,7 +93,7 @@ def test_demap_quantised_within_one_lsb(wls, name, mode):
 
 # ------------------------------------------------------------------ decode
 @pytest.mark.parametrize("mode", ["i8", "i16"])
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition"])
 def test_decode_integer_bit_exact(wls, name, mode):
     w = wls[name]
     mi, et = _params(w)
@@ -108,7 +110,7 @@ def test_decode_integer_bit_exact(wls, name, mode):
     assert s.device_errors() == 0
 
 
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition"])
 def test_decode_f32_bit_exact_vs_oracle_float32(wls, name):
     w = wls[name]
     mi, et = _params(w)
