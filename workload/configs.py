@@ -323,25 +323,22 @@ def operating_point_db(R: float, Qm: int) -> float:
 
 
 def draw_tb_shape(rng, bgs):
-    """One TB's (bg, Z, R, Qm, E) for the mixed workload; rates below kb/(nb-2) are redrawn."""
+    """One TB's (bg, Z, R, Qm, E) for the mixed workload.  Rates below kb/(nb-2) (BG1-shaped: 1/3)
+    send more bits than the circular buffer holds, so their rate matching wraps it (repetition)."""
     b = int(rng.integers(0, 2))
     bg = bgs[b]
     Z = int(MIX_Z[int(rng.integers(0, len(MIX_Z)))])
     Qm = int(MIX_QM[int(rng.integers(0, len(MIX_QM)))])
-    while True:
-        R = float(rng.uniform(0.3, 0.9))
-        if R >= bg.kb / (bg.nb - 2):
-            break
+    R = float(rng.uniform(0.3, 0.9))
     K = bg.kb * Z
     E = Qm * int(round(K / (R * Qm)))
-    while E + bg.t0(Z) > bg.nb * Z:   # rounding can push one symbol over
-        E -= Qm
     return b, Z, R, Qm, E
 
 
 def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int = 3,
           spread_db: float = 3.0, noiseless: bool = False) -> Workload:
-    """Uneven batch: per TB, BG in {bg1, bg2}, Z in {32..384}, R ~ U[0.3, 0.9], Qm in {2,4,6,8}.
+    """Uneven batch: per TB, BG in {bg1, bg2}, Z in {32..384}, R ~ U[0.3, 0.9] (BG1-shaped below 1/3
+    repeats the circular buffer), Qm in {2,4,6,8}.
 
     Each UE has one TB of U{1..max_cb} code blocks per slot, with a contiguous
     PRB band of ceil(RE_tb / 168) PRBs; the slot grid is the concatenation of
