@@ -347,32 +347,36 @@ def run_serving(args):
     kbits = np.array([w.bgs[int(w.cbs[int(tb["first_cb"])]["bg"])].kb * int(w.cbs[int(tb["first_cb"])]["Z"])
                       * int(tb["n_cb"]) for tb in w.tbs], dtype=np.int64)
     sess = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
-    srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000)
     base_recs = tb_records(w, mask_base, abi.SERVE_TB_NP)
-    # warm-up
-    warm = base_recs[:64].copy()
-    warm["tag"] = np.arange(warm.size)
-    srv.replay(warm, np.zeros(warm.size, np.int64), timeout_ms=30000)
-    loads = []
-    for load in args.serve_loads:
-        t_arr, pidx = arrivals(args.serve_slots, n_ue=40, tb_per_slot=load, n_pool=w.n_tb, seed=6)
-        recs = base_recs[pidx].copy()
-        recs["tag"] = np.arange(recs.size)
-        t0 = time.perf_counter()
-        done = srv.replay(recs, t_arr, timeout_ms=60000)
-        wall = time.perf_counter() - t0
-        lat_us = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
-        bits = int(kbits[pidx].sum())
-        span_s = max(wall, args.serve_slots * SLOT_NS / 1e9)
-        loads.append({"tb_per_ue_per_slot": load, "requests": int(recs.size), "code_blocks": int(recs["n_cb"].sum()),
-                      "offered_gbps": bits / (args.serve_slots * SLOT_NS / 1e9) / 1e9,
-                      "served_gbps": bits / wall / 1e9, "wall_s": wall,
-                      "p50_us": _pct(lat_us, 50), "p99_us": _pct(lat_us, 99), "p999_us": _pct(lat_us, 99.9),
-                      "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
-                      "tb_crc_ok_frac": float(np.mean(done["d"])), "mean_max_iters": float(np.mean(done["max_iters"]))})
-        print(json.dumps({"serving_point": loads[-1]}), flush=True)
-        del span_s
-    srv.stop()
+    curves = {}
+    for loops in args.serve_loops:
+        srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000,
+                     loops_per_sm=loops)
+        # warm-up
+        warm = base_recs[:64].copy()
+        warm["tag"] = np.arange(warm.size)
+        srv.replay(warm, np.zeros(warm.size, np.int64), timeout_ms=30000)
+        loads = []
+        for load in args.serve_loads:
+            t_arr, pidx = arrivals(args.serve_slots, n_ue=40, tb_per_slot=load, n_pool=w.n_tb, seed=6)
+            recs = base_recs[pidx].copy()
+            recs["tag"] = np.arange(recs.size)
+            t0 = time.perf_counter()
+            done = srv.replay(recs, t_arr, timeout_ms=60000)
+            wall = time.perf_counter() - t0
+            lat_us = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
+            bits = int(kbits[pidx].sum())
+            loads.append({"loops_per_sm": loops, "tb_per_ue_per_slot": load, "requests": int(recs.size),
+                          "code_blocks": int(recs["n_cb"].sum()),
+                          "offered_gbps": bits / (args.serve_slots * SLOT_NS / 1e9) / 1e9,
+                          "served_gbps": bits / wall / 1e9, "wall_s": wall,
+                          "p50_us": _pct(lat_us, 50), "p99_us": _pct(lat_us, 99), "p999_us": _pct(lat_us, 99.9),
+                          "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
+                          "tb_crc_ok_frac": float(np.mean(done["d"])),
+                          "mean_max_iters": float(np.mean(done["max_iters"]))})
+            print(json.dumps({"serving_point": loads[-1]}), flush=True)
+        srv.stop()
+        curves[f"{loops}_loops_per_sm"] = loads
     # FP32 unbatched plain path: one TB at a time, synchronised
     sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
     n_plain = min(args.serve_plain, w.n_tb)
@@ -401,7 +405,7 @@ def run_serving(args):
     res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
                                    "mixed shapes, 128-entry URLLC codebook, INT8 service",
                        "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
-                       "loads": loads, "fp32_unbatched_plain": plain}}
+                       "loads": curves, "fp32_unbatched_plain": plain}}
     print(json.dumps(res), flush=True)
 
 
@@ -610,6 +614,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=1024)
     ap.add_argument("--serve-plain", type=int, default=400)
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.25, 0.5, 0.75, 1.0])
+    ap.add_argument("--serve-loops", type=int, nargs="+", default=[2, 1],
+                    help="device loops per SM of the service: 2 (capacity, default) and/or 1 (latency)")
     ap.add_argument("--sweep", default=None, choices=["precision"],
                     help="run a measurement sweep instead of the benchmark line")
     ap.add_argument("--sweep-n", type=int, default=100000, help="code blocks per SNR point (GPU)")

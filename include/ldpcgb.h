@@ -304,6 +304,10 @@ typedef struct {
   uint64_t host_pool_bytes;
   void *result_pool;         /* pinned, mapped host memory receiving decoded bits (may be NULL) */
   uint64_t result_pool_bytes;
+  int32_t loops_per_sm;      /* 1: one device loop per SM, check messages in shared memory (lowest
+                              * latency per code block); 2 (or 0, the default): two loops per SM, messages in
+                              * device memory (twice the code blocks in flight, ~8 % slower each) */
+  int32_t reserved;          /* must be 0 */
 } ldpc_serve_desc;
 
 typedef struct {

@@ -76,7 +76,8 @@ class ServeDescC(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
                 ("idle_timeout_us", ctypes.c_int32), ("host_pool", ctypes.c_void_p),
                 ("host_pool_bytes", ctypes.c_uint64), ("result_pool", ctypes.c_void_p),
-                ("result_pool_bytes", ctypes.c_uint64)]
+                ("result_pool_bytes", ctypes.c_uint64), ("loops_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServeTbC(ctypes.Structure):

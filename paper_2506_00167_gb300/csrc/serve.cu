@@ -87,6 +87,9 @@ struct ServeArgs {
   int32_t hdr_bytes, interleave, max_iter, early_term;
   float q_scale, llr_sat, beta, msg_sat, post_sat;
   uint64_t idle_ns;
+  uint8_t* rscratch;       // message records: one slot per (resident block, group)
+  int64_t rscratch_group;  // bytes per group slot
+  int32_t groups;          // group slots per block
 };
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -164,8 +167,12 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
   }
 }
 
-template <typename LT, typename MT, bool SAT>
-__global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
+// TWO: two loops per SM.  The check messages live in a global slot per
+// (block, group) and each check parks its Q values in the posterior slots
+// between its passes, so the loop fits 80 registers and two 384-thread blocks
+// share an SM: twice the code blocks in flight at a modest cost per block.
+template <typename LT, typename MT, bool SAT, bool TWO>
+__global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const ServeArgs a) {
   using namespace core;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
@@ -211,7 +218,8 @@ __global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
     const bool active = g < count;
     CbDev cb{};
     LT* L = reinterpret_cast<LT*>(regions + g * ssh.region_bytes);
-    uint8_t* rbase = regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
+    uint8_t* rbase = TWO ? a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) * a.rscratch_group
+                               : regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
     MT* mag1 = reinterpret_cast<MT*>(rbase);
     MT* mag2 = mag1 + ssh.rec_cap;
     uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
       RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
-          check_update<LT, MT, SAT, false>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
+          check_update<LT, MT, SAT, TWO>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
                                           a.msg_sat, a.post_sat);
           // the next row's table and record are ready before the barrier
           const int ln = l + 1 < m ? l + 1 : 0;
@@ -352,13 +360,16 @@ __global__ void __launch_bounds__(kServeBlock) serve_kernel(const ServeArgs a) {
   }
 }
 
-const void* serve_kernel_ptr(int mode) {
+template <bool TWO>
+const void* serve_kernel_for(int mode) {
   switch (mode) {
-    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false>);
-    case LDPC_I8: return reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true>);
-    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true>);
+    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false, TWO>);
+    case LDPC_I8: return reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, TWO>);
+    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true, TWO>);
   }
 }
+
+const void* serve_kernel_ptr(int mode, bool two) { return two ? serve_kernel_for<true>(mode) : serve_kernel_for<false>(mode); }
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -428,6 +439,8 @@ struct ldpc_server {
   uint32_t* tabs = nullptr;
   uint32_t* xpow32 = nullptr;
   uint32_t* crc_table = nullptr;
+  uint8_t* rscratch = nullptr;
+  bool two = true;  // two loops per SM (messages in device memory)
   std::vector<ServeShape> hshapes;
   ServeArgs args{};
   int smem = 0, grid = 0;
@@ -470,6 +483,7 @@ void free_server(ldpc_server* v) {
   cudaFree(v->tabs);
   cudaFree(v->xpow32);
   cudaFree(v->crc_table);
+  cudaFree(v->rscratch);
   if (v->done_ev) cudaEventDestroy(v->done_ev);
   if (v->stream) cudaStreamDestroy(v->stream);
   delete v->alloc;
@@ -478,7 +492,7 @@ void free_server(ldpc_server* v) {
 
 int launch_loop(ldpc_server* v) {
   void* kargs[] = {&v->args};
-  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode), dim3(v->grid), dim3(kServeBlock), kargs,
+  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two), dim3(v->grid), dim3(kServeBlock), kargs,
                                    static_cast<size_t>(v->smem), v->stream);
   if (e != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop launch: ") + cudaGetErrorString(e));
   e = cudaEventRecord(v->done_ev, v->stream);
@@ -531,12 +545,14 @@ extern "C" {
 int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** out) {
   try {
     if (!s || !d || !out || !d->host_pool || d->max_inflight < 1 || d->max_inflight > 65536 ||
-        d->arena_bytes < 1024 || d->idle_timeout_us < 1)
+        d->arena_bytes < 1024 || d->idle_timeout_us < 1 || d->loops_per_sm < 0 || d->loops_per_sm > 2 ||
+        d->reserved != 0)
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
     *out = nullptr;
     auto* v = new (std::nothrow) ldpc_server();
     if (!v) return srv_fail(LDPC_ENOMEM, "host allocation");
     v->s = s;
+    v->two = d->loops_per_sm != 1;
     int interleave = 1, max_iter = 10, et = 1, sms = 0;
     float q_scale = 4, llr_sat = 63, beta = 1, msg_sat = 63, post_sat = 127;
     session_serve_info(s, &v->mode, &interleave, &max_iter, &et, &q_scale, &llr_sat, &beta, &msg_sat, &post_sat,
@@ -546,6 +562,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     // ---- per-shape tables and layouts, sized for the largest block of the shape
     std::vector<uint32_t> tabs;
     int tw = 0;
+    int64_t rec_group = 0;
     const int n_sh = session_shape_count(s);
     for (int i = 0; i < n_sh; ++i) {
       ServeShape ss{};
@@ -561,7 +578,8 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
       ss.hb_bytes = (Z % 32 == 0) ? align16s(sd.nb * (Z / 32) * 4) : 0;
       const int rec_bytes = 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
-      ss.region_bytes = ss.L_bytes + ss.hb_bytes + rec_bytes;
+      ss.region_bytes = ss.L_bytes + ss.hb_bytes + (v->two ? 0 : rec_bytes);
+      rec_group = std::max<int64_t>(rec_group, rec_bytes);
       ss.G = std::max(1, kServeBlock / Z);
       if (Z > 32) ss.G = std::min(ss.G, 15);
       v->hshapes.push_back(ss);
@@ -576,13 +594,13 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     }
     v->smem = smem;
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode));
+    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode, v->two));
     if (e == cudaSuccess && smem + static_cast<int>(fa.sharedSizeBytes) > kMaxSmem) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode, v->two), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode), kServeBlock, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode, v->two), kServeBlock, smem);
     if (e != cudaSuccess || per_sm < 1) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, std::string("serve loop does not fit an SM (") + std::to_string(smem) +
@@ -590,6 +608,16 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
                                       cudaGetErrorString(e));
     }
     v->grid = per_sm * sms;
+    int gmax = 1;
+    for (auto& ss : v->hshapes)
+      if (ss.feasible) gmax = std::max(gmax, ss.G);
+    if (v->two) {
+      e = cudaMalloc(&v->rscratch, static_cast<size_t>(v->grid) * gmax * rec_group);
+      if (e != cudaSuccess) {
+        free_server(v);
+        return srv_fail(LDPC_ENOMEM, std::string("serve message slots: ") + cudaGetErrorString(e));
+      }
+    }
     // ---- rings and arena
     v->max_inflight = d->max_inflight;
     v->item_cap = static_cast<uint32_t>(d->max_inflight) * kMaxTbCb;
@@ -679,6 +707,9 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     a.msg_sat = msg_sat;
     a.post_sat = post_sat;
     a.idle_ns = static_cast<uint64_t>(d->idle_timeout_us) * 1000ull;
+    a.rscratch = v->rscratch;
+    a.rscratch_group = rec_group;
+    a.groups = gmax;
     if (!a.items || !a.cbs || !a.reqs || !a.done || !a.hctl) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, "mapped host rings unavailable");

@@ -128,9 +128,10 @@ def test_idle_loop_is_relaunched_and_bad_requests_rejected(pool):
     srv.stop()
 
 
-def test_repetition_blocks_through_the_service_match_the_batch_path():
+@pytest.mark.parametrize("loops", [1, 2])
+def test_repetition_blocks_through_the_service_match_the_batch_path(loops):
     """Code blocks whose rate matching wraps the circular buffer: the service's fused demap combines the
-    repeated LLRs like the batch demapper, bit for bit."""
+    repeated LLRs like the batch demapper, bit for bit, with one or two device loops per SM."""
     from workload.configs import repetition
     w = repetition(n_per_shape=4, seed=13)
     raw, mask_base = pool_bytes(w)
@@ -140,11 +141,31 @@ def test_repetition_blocks_through_the_service_match_the_batch_path():
     offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
     res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
     s = session_for(w, "i8")
-    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64)
+    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, loops_per_sm=loops)
     try:
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
+        d_ref, bits_ref = _batch_reference(w, range(n))
+        for r in done:
+            t = int(r["tag"])
+            assert int(r["d"]) == int(d_ref[t]), t
+            assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
+    finally:
+        srv.stop()
+
+
+def test_one_loop_per_sm_matches_the_batch_path(pool):
+    w, host, mask_base = pool
+    n = w.n_tb
+    words = [_tb_words(w, t) for t in range(n)]
+    offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
+    res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
+    s = session_for(w, "i8")
+    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=256, loops_per_sm=1)
+    try:
+        recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
+        done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         d_ref, bits_ref = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
