@@ -16,9 +16,14 @@ iteration runs the rows l = 0 .. m_eff-1 in order and, for all k at once:
 
 After every full iteration (never before the first) the hard decision
 c_v = [L_v < 0] is tested against the m_eff decoded rows; with early
-termination on, a code block whose syndrome is zero stops there.  Output: the
-K = kb * Z information bits (columns 0 .. kb-1), the iterations run, and
-whether the final syndrome was zero.
+termination on, a code block whose syndrome is zero stops there.  A code
+block that carries its own CRC (the last 24 of its K information bits, see
+``crc``) also stops when its K hard-decided information bits pass that CRC
+(CRC-aided early termination, the usual exit of NR receivers; the paper's
+toolbox decoder is not described further, Sec. VI-D "UE").  Output: the
+K = kb * Z information bits (columns 0 .. kb-1), the iterations run, whether
+the final syndrome was zero and, for a block with a CRC, whether its final
+information bits pass it.
 
 Integer modes (exact int64 arithmetic, then saturation):
 INT8  Q = sat127(L - R); |Q| clamped to 63 before the minimum; offset 1;
@@ -31,6 +36,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import crc
 from .demap import bg_geometry
 
 
@@ -99,11 +105,14 @@ def _syndrome_ok(L, rows):
     return ok
 
 
-def layered_oms(llr, bg, Z, m_eff, max_iter, early_term, arith=F64, return_L=False):
+def layered_oms(llr, bg, Z, m_eff, max_iter, early_term, arith=F64, return_L=False, cb_crc=None,
+                with_crc=False):
     """Decode a batch of code blocks of one shape.
 
-    llr: (B, n_eff*Z) channel LLRs (int for IntArith).  Returns
-    (bits uint8 (B, kb*Z), iters int (B,), ok bool (B,)[, L final (B, n_eff*Z)]).
+    llr: (B, n_eff*Z) channel LLRs (int for IntArith); ``cb_crc``: bool (B,),
+    True for a block whose information bits end in a CRC-24 (0x800063).
+    Returns (bits uint8 (B, kb*Z), iters int (B,), ok bool (B,)[, crc_ok bool
+    (B,) with ``with_crc``][, L final (B, n_eff*Z)]).
     """
     kb = bg.kb
     n_eff = kb + m_eff
@@ -122,6 +131,8 @@ def layered_oms(llr, bg, Z, m_eff, max_iter, early_term, arith=F64, return_L=Fal
     bits = np.zeros((B, kb * Z), dtype=np.uint8)
     iters = np.full(B, max_iter, dtype=np.int64)
     ok = np.zeros(B, dtype=bool)
+    crc_ok = np.zeros(B, dtype=bool)
+    flag = np.zeros(B, dtype=bool) if cb_crc is None else np.asarray(cb_crc, dtype=bool).copy()
     L_out = np.zeros((B, n_eff, Z), dtype=L.dtype)
     active = np.arange(B)
 
@@ -146,7 +157,11 @@ def layered_oms(llr, bg, Z, m_eff, max_iter, early_term, arith=F64, return_L=Fal
         last = it == max_iter
         if early_term or last:
             s_ok = _syndrome_ok(L, rows)
-            done = s_ok if early_term else np.ones_like(s_ok)
+            c_ok = np.zeros_like(s_ok)
+            if flag.any():
+                hard = (L[flag, :kb, :] < 0).reshape(int(flag.sum()), kb * Z).astype(np.uint8)
+                c_ok[flag] = crc.cb_ok(hard).astype(bool)
+            done = (s_ok | c_ok) if early_term else np.zeros_like(s_ok)
             if last:
                 done = np.ones_like(s_ok)
             if done.any():
@@ -154,16 +169,19 @@ def layered_oms(llr, bg, Z, m_eff, max_iter, early_term, arith=F64, return_L=Fal
                 bits[g] = (L[done, :kb, :] < 0).reshape(done.sum(), kb * Z).astype(np.uint8)
                 iters[g] = it
                 ok[g] = s_ok[done]
+                crc_ok[g] = c_ok[done]
                 L_out[g] = L[done]
                 keep = ~done
                 active = active[keep]
                 L = L[keep]
+                flag = flag[keep]
                 R = [r[keep] for r in R]
             if active.size == 0:
                 break
+    out = (bits, iters, ok) + ((crc_ok,) if with_crc else ())
     if return_L:
-        return bits, iters, ok, L_out.reshape(B, n_eff * Z)
-    return bits, iters, ok
+        return out + (L_out.reshape(B, n_eff * Z),)
+    return out
 
 
 def pack_bits(bits: np.ndarray) -> np.ndarray:
@@ -173,9 +191,13 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
     return (b << np.arange(32, dtype=np.uint64)).sum(axis=2).astype(np.uint32)
 
 
-def status_word(iters, ok):
-    """Status per code block: iterations in bits 0..15, syndrome-zero flag in bit 16."""
-    return (np.asarray(iters, dtype=np.int64) | (np.asarray(ok, dtype=np.int64) << 16)).astype(np.int32)
+def status_word(iters, ok, crc_ok=None):
+    """Status per code block: iterations in bits 0..15, syndrome-zero flag in bit 16, and in bit 17
+    the flag of a block with its own CRC whose final information bits pass it."""
+    st = np.asarray(iters, dtype=np.int64) | (np.asarray(ok, dtype=np.int64) << 16)
+    if crc_ok is not None:
+        st |= np.asarray(crc_ok, dtype=np.int64) << 17
+    return st.astype(np.int32)
 
 
 def decode_workload(w, llr, max_iter, early_term, arith=F64, cb_index=None, return_L=False):
@@ -200,17 +222,19 @@ def decode_workload(w, llr, max_iter, early_term, arith=F64, cb_index=None, retu
         bg = w.bgs[b]
         n = (bg.kb + m_eff) * Z
         x = np.stack([llr[int(w.cbs[i]["llr_offset"]):int(w.cbs[i]["llr_offset"]) + n] for i in members])
-        res = layered_oms(x, bg, Z, m_eff, max_iter, early_term, arith, return_L=return_L)
-        bits, iters, ok = res[:3]
+        flags = np.array([int(w.cbs[i]["flags"]) & 1 for i in members], dtype=bool)
+        res = layered_oms(x, bg, Z, m_eff, max_iter, early_term, arith, return_L=return_L, cb_crc=flags,
+                          with_crc=True)
+        bits, iters, ok, c_ok = res[:4]
         pw = pack_bits(bits)
-        st = status_word(iters, ok)
+        st = status_word(iters, ok, c_ok)
         for r, i in enumerate(members):
             o = int(w.cbs[i]["bits_word_offset"])
             words[o:o + pw.shape[1]] = pw[r]
             status[i] = st[r]
             if return_L:
                 lo = int(w.cbs[i]["llr_offset"])
-                Lbuf[lo:lo + n] = res[3][r]
+                Lbuf[lo:lo + n] = res[4][r]
     if return_L:
         return words, status, Lbuf
     return words, status

@@ -9,8 +9,10 @@ d_e = 1 when eMBB user e's packet in the TTI decodes correctly, else 0
 so r(t) lies in [-1, 0]: 0 when every user decodes, -1 when all fail and the
 users fill the N subcarriers.  goodput_bits(t) = sum_e d_e * A_e counts the
 delivered payload bits.  A TB's bits are its code blocks' K information bits
-in code-block order; its A payload bits plus 24 CRC bits are checked with
-``crc.tb_ok``.
+in code-block order, less the last 24 of each block that carries its own CRC;
+its A payload bits plus 24 CRC bits are checked with ``crc.tb_ok``, and d_e = 1
+needs that check and every code-block CRC of the TB (``crc.cb_ok``) to pass:
+all CRC bits the transmitter attached must match.
 """
 from __future__ import annotations
 
@@ -25,15 +27,21 @@ def unpack_words(words: np.ndarray, n_bits: int) -> np.ndarray:
     return b.reshape(-1)[:n_bits].astype(np.uint8)
 
 
+def cb_bits(w, words, i) -> np.ndarray:
+    """The K received information bits of code block ``i``."""
+    c = w.cbs[i]
+    K = w.bgs[int(c["bg"])].kb * int(c["Z"])
+    o = int(c["bits_word_offset"])
+    return unpack_words(words[o:o + K // 32], K)
+
+
 def tb_bitstream(w, words, t) -> np.ndarray:
     """The (A + 24) received bits of TB ``t`` from the packed decoder output."""
     tb = w.tbs[t]
     parts = []
     for i in range(int(tb["first_cb"]), int(tb["first_cb"]) + int(tb["n_cb"])):
-        c = w.cbs[i]
-        K = w.bgs[int(c["bg"])].kb * int(c["Z"])
-        o = int(c["bits_word_offset"])
-        parts.append(unpack_words(words[o:o + K // 32], K))
+        b = cb_bits(w, words, i)
+        parts.append(b[:b.size - 24] if int(w.cbs[i]["flags"]) & 1 else b)
     return np.concatenate(parts)
 
 
@@ -47,6 +55,11 @@ def tb_crc_goodput(w, words):
     for _, items in by_len.items():
         ts = [t for t, _ in items]
         d[ts] = crc.tb_ok(np.stack([s for _, s in items]))
+    for t in range(w.n_tb):
+        tb = w.tbs[t]
+        for i in range(int(tb["first_cb"]), int(tb["first_cb"]) + int(tb["n_cb"])):
+            if int(w.cbs[i]["flags"]) & 1 and not crc.cb_ok(cb_bits(w, words, i))[0]:
+                d[t] = 0
     n_slots = w.n_slots
     gb = np.zeros(n_slots, dtype=np.int64)
     gs = np.zeros(n_slots, dtype=np.int64)

@@ -55,7 +55,10 @@ class CbDescC(ctypes.Structure):
     _fields_ = [("bg", ctypes.c_int32), ("Z", ctypes.c_int32), ("Qm", ctypes.c_int32), ("E", ctypes.c_int32),
                 ("re_offset", ctypes.c_int64), ("mask_word_offset", ctypes.c_int64),
                 ("llr_offset", ctypes.c_int64), ("bits_word_offset", ctypes.c_int64),
-                ("inv_sigma2", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("inv_sigma2", ctypes.c_float), ("flags", ctypes.c_int32)]
+
+
+CB_FLAG_CRC24B = 1  # the code block's last 24 information bits are a CRC (0x800063) of the others
 
 
 class TbDescC(ctypes.Structure):

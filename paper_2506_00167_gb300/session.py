@@ -22,12 +22,11 @@ DEFAULT_SAT = {"f32": (0, 0, 0), "i8": (63, 63, 127), "i16": (1023, 1023, 32767)
 
 def _as_struct_array(arr: np.ndarray, np_dtype: np.dtype) -> np.ndarray:
     a = np.ascontiguousarray(arr)
-    if a.dtype.itemsize != np_dtype.itemsize or set(a.dtype.names or ()) - {"_pad"} - set(np_dtype.names):
+    if a.dtype.itemsize != np_dtype.itemsize or set(a.dtype.names or ()) - set(np_dtype.names):
         raise TypeError("descriptor array does not match the C layout")
     out = np.zeros(a.shape[0], dtype=np_dtype)
     for name in np_dtype.names:
-        src = "_pad" if (name == "reserved" and "reserved" not in a.dtype.names) else name
-        out[name] = a[src]
+        out[name] = a[name]
     return out
 
 

@@ -43,8 +43,7 @@ def test_descriptor_layouts_agree():
     assert ctypes.sizeof(abi.CbDescC) == CB_DTYPE.itemsize == 56
     assert ctypes.sizeof(abi.TbDescC) == TB_DTYPE.itemsize == 20
     for name, (_, off) in abi.CB_NP.fields.items():
-        src = "_pad" if name == "reserved" else name
-        assert CB_DTYPE.fields[src][1] == off, name
+        assert CB_DTYPE.fields[name][1] == off, name
     for name, (_, off) in abi.TB_NP.fields.items():
         assert TB_DTYPE.fields[name][1] == off
 

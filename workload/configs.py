@@ -41,8 +41,9 @@ CB_DTYPE = np.dtype([
     ("bg", "<i4"), ("Z", "<i4"), ("Qm", "<i4"), ("E", "<i4"),
     ("re_offset", "<i8"), ("mask_word_offset", "<i8"),
     ("llr_offset", "<i8"), ("bits_word_offset", "<i8"),
-    ("inv_sigma2", "<f4"), ("_pad", "<i4"),
+    ("inv_sigma2", "<f4"), ("flags", "<i4"),
 ])
+CB_FLAG_CRC24B = 1  # the code block's last 24 bits are a CRC (0x800063) of its first K - 24
 assert CB_DTYPE.itemsize == 56
 
 TB_DTYPE = np.dtype([
@@ -127,11 +128,14 @@ def _pack_bits(bits: np.ndarray) -> np.ndarray:
 
 
 def build(name: str, bgs: list, specs: list, slot_widths: list, punct: list, seed: int,
-          interleave: bool = True, snr_db=None, z_set=None, noiseless: bool = False) -> Workload:
+          interleave: bool = True, snr_db=None, z_set=None, noiseless: bool = False,
+          cb_crc: bool = False) -> Workload:
     """Run the Tx chain for ``specs`` and lay the result out for the receiver.
 
     ``punct[s]`` is a (14, slot_widths[s]) boolean map of slot ``s``'s punctured
-    resource elements.  ``noiseless`` skips the AWGN (tests).
+    resource elements.  ``noiseless`` skips the AWGN (tests).  ``cb_crc``: every
+    TB of more than one code block carries a CRC-24 (0x800063) per code block,
+    so its payload is A = n_cb (K - 24) - 24 bits; single-block TBs have none.
     """
     n_tb = len(specs)
     rng_payload = np_stream(seed, 1)
@@ -149,10 +153,11 @@ def build(name: str, bgs: list, specs: list, slot_widths: list, punct: list, see
             raise ValueError("E must be a multiple of Qm")
         n_re = sp.E // sp.Qm
         n_eff = bg.n_eff(sp.Z, sp.E)
-        tb_rows.append((len(cb_rows), sp.n_cb, sp.width, sp.slot, sp.n_cb * K - 24))
+        seg = cb_crc and sp.n_cb > 1
+        tb_rows.append((len(cb_rows), sp.n_cb, sp.width, sp.slot, sp.n_cb * (K - 24 * seg) - 24))
         for j in range(sp.n_cb):
             cb_rows.append((sp.bg, sp.Z, sp.Qm, sp.E, re_off, mask_off, llr_off, bits_off,
-                            np.float32(1.0 / sp.sigma2), 0))
+                            np.float32(1.0 / sp.sigma2), CB_FLAG_CRC24B if seg else 0))
             per_cb.append((t, j, n_re))
             re_off += n_re
             mask_off += -(-n_re // 32)
@@ -177,8 +182,14 @@ def build(name: str, bgs: list, specs: list, slot_widths: list, punct: list, see
             sp = specs[t]
             K = bgs[sp.bg].kb * sp.Z
             first = int(tbs[t]["first_cb"])
-            for j in range(sp.n_cb):
-                cb_info[first + j] = tbbits[row, j * K:(j + 1) * K]
+            if cbs[first]["flags"] & CB_FLAG_CRC24B:
+                segs = tbbits[row].reshape(sp.n_cb, K - 24)
+                cw_info = tx.crc24_attach(segs, tx.CRC24B_POLY)
+                for j in range(sp.n_cb):
+                    cb_info[first + j] = cw_info[j]
+            else:
+                for j in range(sp.n_cb):
+                    cb_info[first + j] = tbbits[row, j * K:(j + 1) * K]
 
     # ---- encode / rate match / modulate per shape group
     groups: dict[tuple, list] = {}
@@ -336,7 +347,7 @@ def draw_tb_shape(rng, bgs):
 
 
 def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int = 3,
-          spread_db: float = 3.0, noiseless: bool = False) -> Workload:
+          spread_db: float = 3.0, noiseless: bool = False, cb_crc: bool = False) -> Workload:
     """Uneven batch: per TB, BG in {bg1, bg2}, Z in {32..384}, R ~ U[0.3, 0.9] (BG1-shaped below 1/3
     repeats the circular buffer), Qm in {2,4,6,8}.
 
@@ -345,7 +356,8 @@ def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int 
     the bands.  Es/N0 per TB ~ U[op - spread, op + spread] around
     ``operating_point_db``.  Each slot carries 1-4 URLLC arrivals (Poisson(2)
     redrawn until in [1, 4]), each on a uniform mini-slot and 4-12 contiguous
-    PRBs at a uniform start.
+    PRBs at a uniform start.  ``cb_crc``: TBs of more than one code block carry
+    a CRC per code block (payload n_cb (K - 24) - 24 bits).
     """
     bgs = default_bgs()
     rng = np_stream(seed, 3)
@@ -377,7 +389,7 @@ def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int 
         widths.append(sc0)
         punct.append(P)
     w = build("mixed", bgs, specs, widths, punct, seed, snr_db=snrs, z_set=list(MIX_Z),
-              noiseless=noiseless)
+              noiseless=noiseless, cb_crc=cb_crc)
     w.meta.update(dict(name="mixed", max_iter=10, early_term=1, mode="i8", offset=0.5))
     return w
 
@@ -415,6 +427,38 @@ def repetition(n_per_shape: int = 24, seed: int = 12, noiseless: bool = False) -
     return w
 
 
+def segmented(n_tb: int = 24, seed: int = 13, spread_db=(-1.0, 2.0), noiseless: bool = False) -> Workload:
+    """Segmented TBs with a CRC per code block: 2-4 code blocks each, BG1-shaped Z=32 or BG2-shaped
+    Z in {32, 64}, R ~ U[0.4, 0.6], QPSK or 16-QAM, Es/N0 around the operating point; one TB per slot,
+    1-2 URLLC mini-slot runs of 1-3 PRBs per slot."""
+    bgs = default_bgs()
+    rng = np_stream(seed, 5)
+    specs, widths, punct, snrs = [], [], [], []
+    shapes = [(0, 32), (1, 32), (1, 64)]
+    for t in range(n_tb):
+        b, Z = shapes[int(rng.integers(0, len(shapes)))]
+        Qm = (2, 4)[int(rng.integers(0, 2))]
+        R = float(rng.uniform(0.4, 0.6))
+        K = bgs[b].kb * Z
+        E = Qm * int(round(K / (R * Qm)))
+        n_cb = 2 + int(rng.integers(0, 3))
+        width = 12 * -(-n_cb * (E // Qm) // (12 * N_SYM))
+        snr = operating_point_db(R, Qm) + float(rng.uniform(*spread_db))
+        specs.append(TBSpec(t, b, Z, Qm, E, n_cb, float(es_n0_sigma2(snr)), 0, width))
+        snrs.append(snr)
+        P = np.zeros((N_SYM, width), dtype=bool)
+        for _ in range(1 + int(rng.integers(0, 2))):
+            m = int(rng.integers(0, N_MINISLOT))
+            ln = min(12 * (1 + int(rng.integers(0, 3))), width)
+            st = int(rng.integers(0, width - ln + 1))
+            P[2 * m:2 * m + 2, st:st + ln] = True
+        punct.append(P)
+        widths.append(width)
+    w = build("segmented", bgs, specs, widths, punct, seed, snr_db=snrs, noiseless=noiseless, cb_crc=True)
+    w.meta.update(dict(name="segmented", max_iter=10, early_term=1, mode="f32", offset=0.5))
+    return w
+
+
 def subset(w: Workload, tb_index) -> Workload:
     """A workload holding only the listed transport blocks (offsets re-based, slots renumbered)."""
     tb_index = list(tb_index)
@@ -436,7 +480,7 @@ def subset(w: Workload, tb_index) -> Workload:
             mask.append(w.mask[int(c["mask_word_offset"]):int(c["mask_word_offset"]) + nmw])
             info.append(w.info_words[int(c["bits_word_offset"]):int(c["bits_word_offset"]) + kw])
             cb_rows.append((int(c["bg"]), Z, int(c["Qm"]), int(c["E"]), re_off, mask_off, llr_off, bits_off,
-                            c["inv_sigma2"], 0))
+                            c["inv_sigma2"], int(c["flags"])))
             if w.snr_db is not None:
                 snr.append(w.snr_db[i])
             re_off += n_re

@@ -45,8 +45,10 @@ def draw_pattern_id(rng) -> int:
     return int(sum(1 << m for m in range(N_MINISLOT) if bits[m]))
 
 
-def tb_pool(n_tb: int, seed: int = 5, max_cb: int = 16, snr_range_db=(0.0, 3.0), noiseless: bool = False):
-    """A Workload of n_tb independent TBs (one per 'slot'), codebook-punctured.
+def tb_pool(n_tb: int, seed: int = 5, max_cb: int = 16, snr_range_db=(0.0, 3.0), noiseless: bool = False,
+            cb_crc: bool = False):
+    """A Workload of n_tb independent TBs (one per 'slot'), codebook-punctured; ``cb_crc``: multi-block TBs
+    carry a CRC per code block.
 
     Es/N0 per TB ~ U[op + snr_range_db[0], op + snr_range_db[1]] with op the
     shape's operating point: the served stream is link-adapted to sit at or
@@ -69,7 +71,7 @@ def tb_pool(n_tb: int, seed: int = 5, max_cb: int = 16, snr_range_db=(0.0, 3.0),
         widths.append(12 * n_prb)
         snrs.append(snr)
     w = build("serve_pool", bgs, specs, widths, punct, seed, snr_db=snrs,
-              z_set=[32, 64, 128, 256, 384], noiseless=noiseless)
+              z_set=[32, 64, 128, 256, 384], noiseless=noiseless, cb_crc=cb_crc)
     w.meta.update(dict(max_iter=10, early_term=1, mode="i8"))
     return w
 

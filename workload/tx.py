@@ -12,6 +12,9 @@ Conventions fixed here (and restated by the receiver side):
   taken most-significant (first) bit first, no reflection, no final xor; one
   CRC per transport block (TB) of ``A`` payload bits.  The TB's ``A + 24``
   bits fill its code blocks in order, ``K = kb * Z`` bits each, with no filler.
+* Per-code-block CRC (optional, TBs of more than one code block): each code
+  block takes ``K - 24`` of the TB's bits and appends 24 CRC bits of
+  generator 0x800063 over them (same conventions), so ``A + 24 = n_cb (K - 24)``.
 * Systematic encoding: ``c[0:K] = info``; core parity by the dual-diagonal
   closed form; extension parity is the sum of its row's other blocks.
 * Rate matching (redundancy version 0): bit ``e`` of the ``E`` transmitted
@@ -34,33 +37,34 @@ import numpy as np
 from .basegraph import BaseGraph
 
 CRC24_POLY = 0x864CFB  # x^24 + x^23 + x^18 + x^17 + x^14 + x^11 + x^10 + x^7 + x^6 + x^5 + x^4 + x^3 + x + 1
+CRC24B_POLY = 0x800063  # x^24 + x^23 + x^6 + x^5 + x + 1 (per code block)
 QAM_NORM = {2: np.sqrt(2.0), 4: np.sqrt(10.0), 6: np.sqrt(42.0), 8: np.sqrt(170.0)}
 
 
 # --------------------------------------------------------------------------- CRC attach
-def _xpow_mod_table(n: int) -> np.ndarray:
+def _xpow_mod_table(n: int, poly: int) -> np.ndarray:
     """rows[i] = bits of x^(24 + n - 1 - i) mod g, i.e. the parity contribution of message bit i."""
-    cur = CRC24_POLY  # x^24 mod g: the low 24 bits of g
+    cur = poly  # x^24 mod g: the low 24 bits of g
     vals = np.empty(n, dtype=np.int64)  # vals[j] = x^(24 + j) mod g
     for j in range(n):
         vals[j] = cur
         cur <<= 1  # multiply by x, then reduce
         if cur & (1 << 24):
-            cur = (cur ^ (CRC24_POLY | (1 << 24))) & 0xFFFFFF
+            cur = (cur ^ (poly | (1 << 24))) & 0xFFFFFF
     # message bit i has weight x^(n - 1 - i); first output bit is the x^23 coefficient
     return ((vals[::-1, None] >> (23 - np.arange(24))[None, :]) & 1).astype(np.uint8)
 
 
-_CRC_TABLE_CACHE: dict[int, np.ndarray] = {}
+_CRC_TABLE_CACHE: dict[tuple, np.ndarray] = {}
 
 
-def crc24_attach(payload: np.ndarray) -> np.ndarray:
-    """Append 24 CRC bits to each row of ``payload`` (uint8 bits, shape (n_tb, A))."""
+def crc24_attach(payload: np.ndarray, poly: int = CRC24_POLY) -> np.ndarray:
+    """Append 24 CRC bits of generator ``poly`` to each row of ``payload`` (uint8 bits, shape (n, A))."""
     payload = np.asarray(payload, dtype=np.uint8)
     n_tb, A = payload.shape
-    if A not in _CRC_TABLE_CACHE:
-        _CRC_TABLE_CACHE[A] = _xpow_mod_table(A).astype(np.float32)
-    G = _CRC_TABLE_CACHE[A]
+    if (A, poly) not in _CRC_TABLE_CACHE:
+        _CRC_TABLE_CACHE[(A, poly)] = _xpow_mod_table(A, poly).astype(np.float32)
+    G = _CRC_TABLE_CACHE[(A, poly)]
     crc = (payload.astype(np.float32) @ G).astype(np.int64) & 1  # exact: sums <= A < 2^24
     return np.concatenate([payload, crc.astype(np.uint8)], axis=1)
 
