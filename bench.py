@@ -45,12 +45,12 @@ def _oracle_chunk(args):
     return int(sum(w.bgs[int(c["bg"])].kb * int(c["Z"]) for c in w.cbs)), int((out["d"] == 0).sum())
 
 
-def make_workload(name: str, rank: int = 0, n: int | None = None):
+def make_workload(name: str, rank: int = 0, n: int | None = None, cb_crc: bool = False):
     from workload import large_fp32, mixed, tiny_fp32
     if name == "large":
         return large_fp32(n_cw=n or 4096, seed=2 + 1000 * rank)
     if name == "mixed":
-        return mixed(n_slots=n or 512, seed=3 + 1000 * rank)
+        return mixed(n_slots=n or 512, seed=3 + 1000 * rank, cb_crc=cb_crc)
     if name == "tiny":
         return tiny_fp32(seed=1000 * rank)
     raise ValueError(name)
@@ -207,7 +207,7 @@ def load_peaks():
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    w = make_workload(args.config)
+    w = make_workload(args.config, cb_crc=args.cb_crc)
     mi, et = w.meta["max_iter"], bool(w.meta["early_term"])
     mode = "f64"
     cores = os.cpu_count() or 1
@@ -340,7 +340,7 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     t_gen = time.perf_counter()
-    w = tb_pool(args.serve_pool, seed=5)
+    w = tb_pool(args.serve_pool, seed=5, cb_crc=args.cb_crc)
     raw, mask_base = pool_bytes(w)
     host = torch.from_numpy(raw).pin_memory()
     gen_s = time.perf_counter() - t_gen
@@ -351,7 +351,7 @@ def run_serving(args):
     curves = {}
     for loops in args.serve_loops:
         srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000,
-                     loops_per_sm=loops)
+                     loops_per_sm=loops, cb_crc=args.cb_crc)
         # warm-up
         warm = base_recs[:64].copy()
         warm["tag"] = np.arange(warm.size)
@@ -404,6 +404,7 @@ def run_serving(args):
              "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9)}
     res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
                                    "mixed shapes, 128-entry URLLC codebook, INT8 service",
+                       "cb_crc": bool(args.cb_crc),
                        "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
                        "loads": curves, "fp32_unbatched_plain": plain}}
     print(json.dumps(res), flush=True)
@@ -608,6 +609,8 @@ def main():
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
     ap.add_argument("--serve", action="store_true", help="replay the served request stream instead")
+    ap.add_argument("--cb-crc", action="store_true",
+                    help="mixed / served TBs of several code blocks carry a CRC per code block (CRC-aided exit)")
     ap.add_argument("--policy", action="store_true", help="time the puncturing allocations (RP, SeF, enforcer)")
     ap.add_argument("--policy-tti", type=int, default=5000)
     ap.add_argument("--serve-slots", type=int, default=8000)
@@ -655,7 +658,7 @@ def main():
 
     from paper_2506_00167_gb300 import Session
 
-    w = make_workload(args.config, rank, args.n)
+    w = make_workload(args.config, rank, args.n, args.cb_crc)
     mode = args.mode or w.meta.get("mode", "f32")
     mi, et = w.meta["max_iter"], bool(w.meta["early_term"])
     dev = torch.device("cuda", local)
@@ -834,8 +837,10 @@ def main():
             "data": "synthetic (seeded Tx chain: CRC-24, QC-LDPC encode, 16-QAM, AWGN, URLLC puncture masks)",
             "config": {"workload": {"large": "4096 x BG1-shaped Z=384 K=8448 R=1/2 16-QAM, Es/N0 6-12 dB, "
                                              "<=10 iter + ET",
-                                    "mixed": "512 slots x 8 UEs mixed BG/Z/R/Qm",
+                                    "mixed": "512 slots x 8 UEs mixed BG/Z/R/Qm"
+                                             + (", CRC-24B per code block" if args.cb_crc else ""),
                                     "tiny": "8x16 Z=16 QPSK"}[args.config],
+                       "cb_crc": bool(args.cb_crc),
                        "code_blocks": w.n_cb, "transport_blocks": w.n_tb, "info_bits_per_step": info_bits,
                        "mean_iters": float(np.mean(status & 0xFFFF)),
                        "l2": "inputs larger than L2 (symbols %.0f MB + LLRs %.0f MB per step)"

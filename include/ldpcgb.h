@@ -114,7 +114,14 @@ typedef struct {
  *   bits_word_offset first uint32 of its kb * Z / 32 decoded information
  *                    words: bit i of the block is bit i % 32 of word i / 32
  *   inv_sigma2       1 / noise variance per symbol
+ *   flags            0, or LDPC_CB_CRC24B: the block's last 24 information
+ *                    bits are a CRC of its first K - 24 (K = kb * Z) under
+ *                    g_B(x) = x^24 + x^23 + x^6 + x^5 + x + 1 (register from 0,
+ *                    first bit highest degree), NR-style segmentation.  The
+ *                    decoder then also stops a block whose hard decision
+ *                    passes that CRC, and the TB check leaves those bits out.
  */
+#define LDPC_CB_CRC24B 1
 typedef struct {
   int32_t bg, Z, Qm, E;
   int64_t re_offset;
@@ -122,13 +129,16 @@ typedef struct {
   int64_t llr_offset;
   int64_t bits_word_offset;
   float inv_sigma2;
-  int32_t reserved; /* must be 0 */
+  int32_t flags; /* 0 or LDPC_CB_CRC24B */
 } ldpc_cb_desc;
 
 /*
  * One transport block (one eMBB user in one slot): code blocks
  * [first_cb, first_cb + n_cb) carry its payload_bits + 24 CRC bits in order;
- * n_sc is n_e, the user's subcarriers; slot indexes the slot_N array.
+ * n_sc is n_e, the user's subcarriers; slot indexes the slot_N array.  Either
+ * no block of the TB has LDPC_CB_CRC24B and payload_bits = sum(K) - 24, or
+ * every block has it and payload_bits = sum(K - 24) - 24 (the TB's bits are
+ * each block's first K - 24 bits, in block order).
  */
 typedef struct {
   int32_t first_cb, n_cb, n_sc, slot, payload_bits;
@@ -208,8 +218,11 @@ LDPC_API int puncture_demap(ldpc_session *s, const ldpc_batch *b, const void *sy
  * L[v_j] = Q_j + R'_j.  Integer modes saturate Q and L at post_sat and clamp
  * |Q| at msg_sat before the minimum.  After every iteration the hard decision
  * [L < 0] is checked against the m_eff rows; with early termination a block
- * stops at the first zero syndrome.  Writes each block's kb*Z information bits
- * to bits_dev and status_dev[cb] = iterations | (syndrome_zero << 16).
+ * stops at the first zero syndrome or, for a block with LDPC_CB_CRC24B, at the
+ * first hard decision whose information bits pass its CRC.  Writes each
+ * block's kb*Z information bits to bits_dev and status_dev[cb] = iterations |
+ * (syndrome_zero << 16) | (cb_crc_passed << 17) (bit 17 only for blocks with
+ * LDPC_CB_CRC24B, from the final hard decision).
  * The paper's decoder is a toolbox function (Sec. VI-D "UE"); this is the
  * algorithm this library fixes in its place.
  */
@@ -220,7 +233,9 @@ LDPC_API int decode_batch(ldpc_session *s, const ldpc_batch *b, const void *llr_
  * Transport-block CRC-24 check and per-slot goodput and reward.  d_e = 1 iff
  * the TB's (payload_bits + 24) decoded bits are a multiple of
  * g(x) = 0x1864CFB (register from 0, first bit highest degree) -- the same
- * test as comparing received and recomputed CRC bits (Sec. VI-D "UE Feedback").
+ * test as comparing received and recomputed CRC bits (Sec. VI-D "UE Feedback")
+ * -- and, for a segmented TB with LDPC_CB_CRC24B, every block's K bits are a
+ * multiple of g_B(x) = 0x1800063: every attached CRC bit must match.
  * Per slot t:  goodput_bits[t] = sum_e d_e * payload_bits_e;
  *              goodput_sc[t]   = sum_e d_e * n_e               (eq. 1)
  *              reward[t]       = (1/N_t) * sum_e (d_e - 1) n_e  (eq. 2)
@@ -307,12 +322,15 @@ typedef struct {
   int32_t loops_per_sm;      /* 1: one device loop per SM, check messages in shared memory (lowest
                               * latency per code block); 2 (or 0, the default): two loops per SM, messages in
                               * device memory (twice the code blocks in flight, ~8 % slower each) */
-  int32_t reserved;          /* must be 0 */
+  int32_t flags;             /* 0, or LDPC_SERVE_CB_CRC: accept TBs whose code blocks carry their own CRC
+                              * (the loop then runs its variant with the code-block CRC exit) */
 } ldpc_serve_desc;
+#define LDPC_SERVE_CB_CRC 1
 
 typedef struct {
   int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16 */
-  int32_t n_sc, payload_bits;   /* n_e; payload_bits = n_cb * kb * Z - 24 */
+  int32_t n_sc, payload_bits;   /* n_e; payload_bits = n_cb * kb * Z - 24, or, for n_cb > 1 with a CRC
+                                 * per code block (LDPC_CB_CRC24B), n_cb * (kb * Z - 24) - 24 */
   float inv_sigma2;
   int64_t sym_offset;           /* bytes into host_pool (8-aligned): n_cb * E/Qm float2, block after block */
   int64_t mask_offset;          /* bytes into host_pool (4-aligned): n_cb * ceil(E/Qm/32) words */

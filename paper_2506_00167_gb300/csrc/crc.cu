@@ -7,12 +7,18 @@
 // reward = (1/N) sum_e (d_e - 1) n_e (Sec. V-A, eq. 2), and the delivered
 // payload bits.
 //
-// One block per slot, one warp per TB.  A TB of W words is split into 32
-// contiguous segments; each lane runs its segment through a byte-table LFSR
-// from state 0, giving seg(x) * x^24 mod g, then shifts it into place by one
-// GF(2) multiply with x^(32 * words after the segment) mod g (a per-batch
-// table) and the warp xor-reduces.  No atomics: the block reduces the slot's
-// sums in shared memory, so results are deterministic.
+// A segmented TB (every block with LDPC_CB_CRC24B) runs its CRC over each
+// block's first K - 24 bits only, and each block's K bits must also be a
+// multiple of g_B(x): d_e needs every check to pass.
+//
+// One block per slot, one warp per TB.  The TB's bytes, prefixed by the zero
+// bytes that make them whole words (leading zeros leave a zero register
+// unchanged), are split into 32 runs of whole words; each lane runs its run
+// through a byte-table LFSR from state 0, giving seg(x) * x^24 mod g, shifts
+// it into place by one GF(2) multiply with x^(32 * words after the run) mod g
+// (a per-batch table) and the warp xor-reduces.  A block's own CRC is the
+// same over its K / 32 words with g_B's tables.  No atomics: the block
+// reduces the slot's sums in shared memory, so results are deterministic.
 #include "crc_core.cuh"
 
 namespace ldpcgb {
@@ -21,12 +27,25 @@ namespace {
 
 using namespace crccore;
 
+// TB bytes carried by one code block.
+__device__ __forceinline__ int tb_bytes_of(const CbDev& c, int seg) { return ((c.kb * c.Z) >> 3) - 3 * seg; }
+
+__device__ __forceinline__ uint32_t warp_xor(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
 __global__ void __launch_bounds__(kCrcBlock) tb_crc_goodput_kernel(const CrcArgs a) {
   __shared__ uint32_t s_tab[256];
+  __shared__ uint32_t s_tab_b[256];
   __shared__ unsigned long long s_gb[kCrcBlock / 32];
   __shared__ uint32_t s_gs[kCrcBlock / 32];
   __shared__ uint32_t s_fail[kCrcBlock / 32];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tab[i] = a.crc_table[i];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    s_tab[i] = a.crc_table[i];
+    s_tab_b[i] = a.crc_table_b[i];
+  }
   __syncthreads();
 
   const int slot = blockIdx.x;
@@ -39,41 +58,63 @@ __global__ void __launch_bounds__(kCrcBlock) tb_crc_goodput_kernel(const CrcArgs
 
   for (int i = t0 + warp; i < t1; i += kCrcBlock / 32) {
     const TbDev tb = a.tbs[a.slot_tbs[i]];
-    const int W = tb.words;
+    const int pad = (-tb.bytes) & 3;
+    const int W = (tb.bytes + pad) >> 2;
     const int per = (W + 31) >> 5;
     const int w0 = min(W, lane * per);
     const int w1 = min(W, w0 + per);
     uint32_t state = 0;
     if (w0 < w1) {
-      // find the code block holding TB word w0
+      const int b_end = 4 * w1 - pad;
+      int b = max(0, 4 * w0 - pad);
+      // find the code block holding TB byte b
       int cbi = tb.first_cb;
       int cb_first = 0;
-      int cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
-      while (w0 >= cb_first + cb_words) {
-        cb_first += cb_words;
+      int cb_bytes = tb_bytes_of(a.cbs[cbi], tb.seg);
+      while (b >= cb_first + cb_bytes) {
+        cb_first += cb_bytes;
         ++cbi;
-        cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
+        cb_bytes = tb_bytes_of(a.cbs[cbi], tb.seg);
       }
       const uint32_t* src = a.bits + a.cbs[cbi].bits_off;
-      for (int w = w0; w < w1; ++w) {
-        if (w >= cb_first + cb_words) {
-          cb_first += cb_words;
+      int jw = -1;
+      uint32_t word = 0;
+      for (; b < b_end; ++b) {
+        if (b >= cb_first + cb_bytes) {
+          cb_first += cb_bytes;
           ++cbi;
-          cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
+          cb_bytes = tb_bytes_of(a.cbs[cbi], tb.seg);
           src = a.bits + a.cbs[cbi].bits_off;
+          jw = -1;
         }
-        const uint32_t v = __brev(src[w - cb_first]);  // bit 31 = first bit in time
-#pragma unroll
-        for (int b = 3; b >= 0; --b) {
-          const uint32_t byte = (v >> (8 * b)) & 0xFFu;
-          state = ((state << 8) & 0xFFFFFFu) ^ s_tab[((state >> 16) ^ byte) & 0xFFu];
+        const int j = b - cb_first;
+        if ((j >> 2) != jw) {
+          jw = j >> 2;
+          word = src[jw];
         }
+        state = crc_byte_step(state, msb_first_byte(word, j), s_tab);
       }
       state = gf2_mulmod(state, a.xpow32[W - w1]);
     }
+    uint32_t d = warp_xor(state) == 0u ? 1u : 0u;
+    if (tb.seg) {
+      for (int c = tb.first_cb; c < tb.first_cb + tb.n_cb; ++c) {
+        const CbDev cb = a.cbs[c];
+        const int Wc = (cb.kb * cb.Z) >> 5;
+        const int pc = (Wc + 31) >> 5;
+        const int v0 = min(Wc, lane * pc);
+        const int v1 = min(Wc, v0 + pc);
+        const uint32_t* src = a.bits + cb.bits_off;
+        uint32_t st = 0;
+        for (int w = v0; w < v1; ++w) {
+          const uint32_t v = src[w];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) state ^= __shfl_xor_sync(0xFFFFFFFFu, state, o);
-    const uint32_t d = state == 0u ? 1u : 0u;
+          for (int j = 0; j < 4; ++j) st = crc_byte_step(st, msb_first_byte(v, j), s_tab_b);
+        }
+        if (v0 < v1) st = gf2_mulmod(st, a.xpow32_b[Wc - v1], kPolyFullB);
+        if (warp_xor(st) != 0u) d = 0u;
+      }
+    }
     if (lane == 0) {
       a.d[a.slot_tbs[i]] = static_cast<uint8_t>(d);
       gb += d * static_cast<unsigned long long>(tb.payload_bits);

@@ -46,7 +46,7 @@ namespace {
 
 using namespace core;
 
-template <typename LT, typename MT, bool SAT, bool RGLOBAL>
+template <typename LT, typename MT, bool SAT, bool RGLOBAL, bool CRC>
 __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const DecodeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
         group_sync(Z, g, wmask);
       }
       int it = 1;
-      bool ok = false;
+      bool ok = false, crc_ok = false;
+      const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
       RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
@@ -157,15 +158,21 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
         }
         if (a.early_term || it == a.max_iter) {
           bool bad;
+          uint32_t cr = 0;
+          const uint32_t* ptab = a.cbcrc + a.shapes[item.shape].crc_off;
           if (wide) {
             hard_bitmap(L, hb, cb.n_eff, k, Z);
             group_sync(Z, g, wmask);
             bad = syndrome_bitmap(s_tab, rows, hb, m, k, Z);
+            if (has_crc) cr = cb_crc_part_hb(hb, ptab, cb.kb, k, Z);
           } else {
             bad = syndrome_direct(s_tab, rows, m, k, Z, L);
+            if (has_crc) cr = cb_crc_part(L, ptab, cb.kb, k, Z);
           }
           ok = !group_any(Z, g, wmask, bad);
-          if (ok && a.early_term) break;
+          // after that barrier the bitmap's parity words are free: scratch for the CRC's XOR
+          if (has_crc) crc_ok = group_xor_zero(Z, g, wmask, cr, hb + cb.kb * (Z >> 5), k);
+          if ((ok || crc_ok) && a.early_term) break;
           if (it == a.max_iter) break;
         }
       }
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
           if (k == 0) out[c >> 1] = (b0 & 0xFFFFu) | (b1 << 16);
         }
       }
-      if (k == 0) a.status[cbi] = it | (ok ? (1 << 16) : 0);
+      if (k == 0) a.status[cbi] = it | (ok ? (1 << 16) : 0) | (crc_ok ? (1 << 17) : 0);
     }
     __syncthreads();  // the next item's copies overwrite this item's shared memory
   }
@@ -199,7 +206,7 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
 // RGLOBAL: the three message words per check live in a global scratch slot
 // per resident group, and the int8 LLRs are read straight from global memory
 // (one 32-bit load per four variables of each block) instead of being staged.
-template <bool RGLOBAL>
+template <bool RGLOBAL, bool CRC>
 __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(const DecodeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
@@ -334,20 +341,34 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
           group_sync(Z, g, 0xFFFFFFFFu);
           const bool badA = !doneA && syndrome_bitmap(s_tab, rows, hbA, mA, k, Z);
           const bool badB = !doneB && syndrome_bitmap(s_tab, rows, hbB, mB, k, Z);
+          const bool crcA = CRC && !doneA && (A.flags & LDPC_CB_CRC24B) != 0;
+          const bool crcB = CRC && !doneB && (Bc.flags & LDPC_CB_CRC24B) != 0;
+          uint32_t rA = 0, rB = 0;
+          if (crcA || crcB) {
+            const uint32_t* ptab = a.cbcrc + sh.crc_off;
+            if (crcA) rA = cb_crc_part_hb(hbA, ptab, A.kb, k, Z);
+            if (crcB) rB = cb_crc_part_hb(hbB, ptab, A.kb, k, Z);
+          }
           const bool okA = !group_any(Z, g, 0xFFFFFFFFu, badA);
           const bool okB = !group_any(Z, g, 0xFFFFFFFFu, badB);
+          bool cA = false, cB = false;
+          if (crcA || crcB) {  // both blocks' XORs meet in their bitmaps' (now free) parity words
+            const bool zA = group_xor_zero2(Z, g, rA, rB, hbA + A.kb * (Z >> 5), hbB + A.kb * (Z >> 5), k, &cB);
+            cA = crcA && zA;
+            cB = crcB && cB;
+          }
           const bool last = it == a.max_iter;
           const int nw = A.kb * (Z >> 5);
-          if (!doneA && ((okA && a.early_term) || last)) {
+          if (!doneA && (((okA || cA) && a.early_term) || last)) {
             uint32_t* out = a.bits + A.bits_off;
             for (int i = k; i < nw; i += Z) out[i] = hbA[i];
-            if (k == 0) a.status[ia] = it | (okA ? (1 << 16) : 0);
+            if (k == 0) a.status[ia] = it | (okA ? (1 << 16) : 0) | (cA ? (1 << 17) : 0);
             doneA = true;
           }
-          if (!doneB && ((okB && a.early_term) || last)) {
+          if (!doneB && (((okB || cB) && a.early_term) || last)) {
             uint32_t* out = a.bits + Bc.bits_off;
             for (int i = k; i < nw; i += Z) out[i] = hbB[i];
-            if (k == 0) a.status[ib] = it | (okB ? (1 << 16) : 0);
+            if (k == 0) a.status[ib] = it | (okB ? (1 << 16) : 0) | (cB ? (1 << 17) : 0);
             doneB = true;
           }
           if (doneA && doneB) break;
@@ -358,29 +379,34 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
   }
 }
 
-template <bool RG>
+template <bool RG, bool CRC>
 const void* decode_kernel_ptr(int mode) {
   switch (mode) {
-    case LDPC_F32: return reinterpret_cast<const void*>(&oms_decode_kernel<float, float, false, RG>);
-    case LDPC_I8: return reinterpret_cast<const void*>(&oms_decode_kernel<int8_t, uint8_t, true, RG>);
-    default: return reinterpret_cast<const void*>(&oms_decode_kernel<int16_t, uint16_t, true, RG>);
+    case LDPC_F32: return reinterpret_cast<const void*>(&oms_decode_kernel<float, float, false, RG, CRC>);
+    case LDPC_I8: return reinterpret_cast<const void*>(&oms_decode_kernel<int8_t, uint8_t, true, RG, CRC>);
+    default: return reinterpret_cast<const void*>(&oms_decode_kernel<int16_t, uint16_t, true, RG, CRC>);
   }
 }
 
-const void* kernel_for(int mode, bool rglobal) {
-  return rglobal ? decode_kernel_ptr<true>(mode) : decode_kernel_ptr<false>(mode);
+template <bool CRC>
+const void* kernel_for(int mode, int base) {
+  if (base == kKindPairI8) return reinterpret_cast<const void*>(&oms_decode_i8x2_kernel<false, CRC>);
+  if (base == kKindPairI8Global) return reinterpret_cast<const void*>(&oms_decode_i8x2_kernel<true, CRC>);
+  return base == kKindGlobal ? decode_kernel_ptr<true, CRC>(mode) : decode_kernel_ptr<false, CRC>(mode);
 }
 
 }  // namespace
 
+// kind = base kind | kKindCrc: the variant with the code-block CRC exit is
+// launched only for launches holding a block with LDPC_CB_CRC24B; without
+// it the kernel is the plain decoder, register allocation included.
 const void* kernel_kind(int mode, int kind) {
-  if (kind == kKindPairI8) return reinterpret_cast<const void*>(&oms_decode_i8x2_kernel<false>);
-  if (kind == kKindPairI8Global) return reinterpret_cast<const void*>(&oms_decode_i8x2_kernel<true>);
-  return kernel_for(mode, kind == kKindGlobal);
+  const int base = kind & ~kKindCrc;
+  return (kind & kKindCrc) ? kernel_for<true>(mode, base) : kernel_for<false>(mode, base);
 }
 
 cudaError_t decode_prepare(int mode) {
-  for (int kind = 0; kind < kKinds; ++kind) {
+  for (int kind = 0; kind < 2 * kKindCrc; ++kind) {
     if (kind_is_pair(kind) && mode != LDPC_I8) continue;
     cudaError_t e = cudaFuncSetAttribute(kernel_kind(mode, kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSmem);

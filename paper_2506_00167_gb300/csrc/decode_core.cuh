@@ -293,6 +293,73 @@ __device__ __forceinline__ bool syndrome_direct(const uint32_t* __restrict__ tab
   return bad != 0;
 }
 
+// ---- CRC-aided exit for blocks that carry their own CRC (LDPC_CB_CRC24B).
+// Bit p = c * Z + k of the K = kb * Z information bits stands for x^(K-1-p);
+// the block passes iff sum_p bit_p * (x^(K-1-p) mod g_B) is 0 over GF(2).
+// ptab[p] holds that remainder, so thread k XORs the entries of its kb bits
+// (column c, row k) and the group XORs the threads' sums.
+template <typename LT>
+__device__ __forceinline__ uint32_t cb_crc_part(const LT* __restrict__ L, const uint32_t* __restrict__ ptab,
+                                                int kb, int k, int Z) {
+  uint32_t r = 0;
+  for (int c = 0; c < kb; ++c) {
+    const uint32_t t = __ldg(ptab + c * Z + k);
+    r ^= (L[c * Z + k] < LT(0)) ? t : 0u;
+  }
+  return r;
+}
+
+// The same from the hard-decision bitmap (Z % 32 == 0): a warp reads one
+// word per column, a broadcast.
+__device__ __forceinline__ uint32_t cb_crc_part_hb(const uint32_t* __restrict__ hb,
+                                                   const uint32_t* __restrict__ ptab, int kb, int k, int Z) {
+  const int W = Z >> 5;
+  const int w = k >> 5;
+  const int b = k & 31;
+  uint32_t r = 0;
+  for (int c = 0; c < kb; ++c) {
+    const uint32_t t = __ldg(ptab + c * Z + k);
+    r ^= ((hb[c * W + w] >> b) & 1u) ? t : 0u;
+  }
+  return r;
+}
+
+// Is the XOR of r over the group's Z threads zero?  For Z > 32 the warps
+// meet in `scratch` (Z / 32 words), which no thread of the group may touch
+// between the preceding group barrier and the next one after this call.
+__device__ __forceinline__ bool group_xor_zero(int Z, int g, uint32_t wmask, uint32_t r, uint32_t* scratch, int k) {
+  r = __reduce_xor_sync(wmask, r);
+  if (Z <= 32) return r == 0u;
+  if ((k & 31) == 0) scratch[k >> 5] = r;
+  named_bar_sync(1 + g, Z);
+  uint32_t t = 0;
+  for (int w = 0; w < (Z >> 5); ++w) t ^= scratch[w];
+  return t == 0u;
+}
+
+// Two XOR reductions at once (Z % 32 == 0, whole warps): returns whether rA's
+// total is zero and sets *zB for rB's.
+__device__ __forceinline__ bool group_xor_zero2(int Z, int g, uint32_t rA, uint32_t rB, uint32_t* scrA,
+                                                uint32_t* scrB, int k, bool* zB) {
+  rA = __reduce_xor_sync(0xFFFFFFFFu, rA);
+  rB = __reduce_xor_sync(0xFFFFFFFFu, rB);
+  if (Z > 32) {
+    if ((k & 31) == 0) {
+      scrA[k >> 5] = rA;
+      scrB[k >> 5] = rB;
+    }
+    named_bar_sync(1 + g, Z);
+    rA = 0;
+    rB = 0;
+    for (int w = 0; w < (Z >> 5); ++w) {
+      rA ^= scrA[w];
+      rB ^= scrB[w];
+    }
+  }
+  *zB = rB == 0u;
+  return rA == 0u;
+}
+
 }  // namespace core
 }  // namespace ldpcgb
 

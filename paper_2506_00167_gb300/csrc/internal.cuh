@@ -30,13 +30,14 @@ struct ShapeDev {
   int32_t tab_off;    // first word of this shape's table
   int32_t row_off;    // row words, relative to tab_off
   int32_t tab_words;  // multiple of 4 (whole table, 16-byte granules)
+  int32_t crc_off;    // first word of its code-block CRC position table (kb * Z words)
 };
 
 // Per code block geometry, computed on the host at batch creation.
 struct CbDev {
   int32_t shape, Z, Qm, E;
   int32_t t0, m_eff, n_eff, n_re;
-  int32_t kb, pad0;
+  int32_t kb, flags;  // flags: LDPC_CB_CRC24B
   int64_t re_off, mask_off, llr_off, bits_off;
   float inv_sigma2;
   int32_t pad1;
@@ -60,7 +61,10 @@ struct DemapTile {
 };
 
 struct TbDev {
-  int32_t first_cb, n_cb, n_sc, slot, payload_bits, words;
+  int32_t first_cb, n_cb, n_sc, slot, payload_bits;
+  int32_t bytes;  // (payload_bits + 24) / 8: the bytes the TB CRC runs over
+  int32_t seg;    // 1: every block carries its own CRC (its last 3 bytes are not TB bytes)
+  int32_t pad;
 };
 
 struct DecodeArgs {
@@ -81,6 +85,7 @@ struct DecodeArgs {
   int32_t hdr_bytes;        // edge table + mbarrier + item slot, 16-byte multiple
   int32_t max_iter, early_term;
   float beta, msg_sat, post_sat;
+  const uint32_t* cbcrc;    // code-block CRC position tables (ShapeDev::crc_off), for LDPC_CB_CRC24B blocks
 };
 
 struct DemapArgs {
@@ -101,6 +106,8 @@ struct CrcArgs {
   const int32_t* slot_N;
   const uint32_t* crc_table;  // 256 entries
   const uint32_t* xpow32;     // x^(32 m) mod g, m = 0..max_words
+  const uint32_t* crc_table_b;  // the same two tables for the code-block generator g_B
+  const uint32_t* xpow32_b;     // m = 0..largest block's words
   const uint32_t* bits;
   uint8_t* d;
   uint64_t* goodput_bits;
@@ -115,13 +122,19 @@ void set_error(const std::string& msg);
 // Decoder kernel kinds: messages in shared memory, in global memory, or the
 // INT8 kernel that decodes two code blocks per thread group (messages in
 // shared or in global memory).
+// Either can carry kKindCrc: the variant with the code-block CRC exit.
 constexpr int kKindShared = 0;
 constexpr int kKindGlobal = 1;
 constexpr int kKindPairI8 = 2;
 constexpr int kKindPairI8Global = 3;
 constexpr int kKinds = 4;
-constexpr bool kind_is_pair(int kind) { return kind == kKindPairI8 || kind == kKindPairI8Global; }
-constexpr bool kind_is_global(int kind) { return kind == kKindGlobal || kind == kKindPairI8Global; }
+constexpr int kKindCrc = 4;
+constexpr bool kind_is_pair(int kind) {
+  return (kind & ~kKindCrc) == kKindPairI8 || (kind & ~kKindCrc) == kKindPairI8Global;
+}
+constexpr bool kind_is_global(int kind) {
+  return (kind & ~kKindCrc) == kKindGlobal || (kind & ~kKindCrc) == kKindPairI8Global;
+}
 cudaError_t launch_decode(int mode, int kind, dim3 grid, dim3 block, int smem, cudaStream_t st,
                           const DecodeArgs& a);
 cudaError_t decode_occupancy(int mode, int kind, int block, int smem, int* blocks_per_sm);

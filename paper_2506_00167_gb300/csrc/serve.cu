@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kServeBlock = 384;
 constexpr int kMaxTbCb = 16;
+constexpr int kServeXpowWords = kMaxTbCb * 8448 / 32 * 2;  // TB CRC shift table: words of the largest TB
 
 struct ServeItem {  // host ring entry
   int32_t req, cb0, count, n_items;
@@ -38,7 +39,8 @@ struct ServeItem {  // host ring entry
 
 struct ServeReq {  // host record per request slot
   uint64_t tag;
-  int32_t n_cb, words, shape, pad;
+  int32_t n_cb, words, shape;
+  int32_t seg;         // 1: every code block ends in its own CRC (LDPC_CB_CRC24B)
   int64_t bits_off;    // arena word offset of the TB's decoded bits (contiguous)
   int64_t status_off;  // arena word offset of its status words
   int64_t result_off;  // byte offset into the result pool, -1 for none
@@ -84,6 +86,9 @@ struct ServeArgs {
   uint8_t* result_pool;
   const uint32_t* crc_table;
   const uint32_t* xpow32;
+  const uint32_t* crc_table_b;  // code-block CRC: byte table, x^(32 m) mod g_B, position tables
+  const uint32_t* xpow32_b;
+  const uint32_t* cbcrc;
   int32_t hdr_bytes, interleave, max_iter, early_term;
   float q_scale, llr_sat, beta, msg_sat, post_sat;
   uint64_t idle_ns;
@@ -171,7 +176,9 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
 // (block, group) and each check parks its Q values in the posterior slots
 // between its passes, so the loop fits 80 registers and two 384-thread blocks
 // share an SM: twice the code blocks in flight at a modest cost per block.
-template <typename LT, typename MT, bool SAT, bool TWO>
+// CRC: the variant with the code-block CRC exit (a service started with
+// LDPC_SERVE_CB_CRC); without it the loop is the plain decoder.
+template <typename LT, typename MT, bool SAT, bool TWO, bool CRC>
 __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const ServeArgs a) {
   using namespace core;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -246,7 +253,8 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       const int m = cb.m_eff;
       const bool wide = (Z & 31) == 0;
       int it = 1;
-      bool ok = false;
+      bool ok = false, crc_ok = false;
+      const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
       RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
@@ -259,15 +267,21 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
         }
         if (a.early_term || it == a.max_iter) {
           bool bad;
+          uint32_t cr = 0;
+          const uint32_t* ptab = a.cbcrc + a.shapes[cb.shape].sh.crc_off;
           if (wide) {
             hard_bitmap(L, hb, cb.n_eff, k, Z);
             group_sync(Z, g, wmask);
             bad = syndrome_bitmap(s_tab, rows, hb, m, k, Z);
+            if (has_crc) cr = cb_crc_part_hb(hb, ptab, cb.kb, k, Z);
           } else {
             bad = syndrome_direct(s_tab, rows, m, k, Z, L);
+            if (has_crc) cr = cb_crc_part(L, ptab, cb.kb, k, Z);
           }
           ok = !group_any(Z, g, wmask, bad);
-          if (ok && a.early_term) break;
+          // after that barrier the bitmap's parity words are free: scratch for the CRC's XOR
+          if (has_crc) crc_ok = group_xor_zero(Z, g, wmask, cr, hb + cb.kb * (Z >> 5), k);
+          if ((ok || crc_ok) && a.early_term) break;
           if (it == a.max_iter) break;
         }
       }
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
           if (k == 0) out[c >> 1] = (b0 & 0xFFFFu) | (b1 << 16);
         }
       }
-      if (k == 0) a.arena[cb.llr_off] = static_cast<uint32_t>(it | (ok ? (1 << 16) : 0));
+      if (k == 0) a.arena[cb.llr_off] = static_cast<uint32_t>(it | (ok ? (1 << 16) : 0) | (crc_ok ? (1 << 17) : 0));
     }
     // ---- request bookkeeping: the block finishing the last item completes the TB
     __threadfence();
@@ -302,27 +316,61 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       const uint64_t tag = ld_sys(&rq->tag);
       const int n_cb = ld_sys(&rq->n_cb);
       const int W = ld_sys(&rq->words);
+      const int seg = ld_sys(&rq->seg);
       const int64_t bits_off = ld_sys(&rq->bits_off);
       const int64_t status_off = ld_sys(&rq->status_off);
       const int64_t result_off = ld_sys(&rq->result_off);
       const volatile uint32_t* bits = a.arena + bits_off;
       if (tid < 32) {
         using namespace crccore;
-        const int per = (W + 31) >> 5;
-        const int w0 = min(W, lane * per);
-        const int w1 = min(W, w0 + per);
+        // TB CRC over each block's first K/8 - 3*seg bytes (the blocks' K/32
+        // words lie back to back), zero-prefixed to whole words as in the
+        // batch CRC kernel
+        const int kw = W / n_cb;                  // words per block
+        const int cbb = 4 * kw - 3 * seg;         // TB bytes per block
+        const int tbytes = n_cb * cbb;
+        const int pad = (-tbytes) & 3;
+        const int VW = (tbytes + pad) >> 2;
+        const int per = (VW + 31) >> 5;
+        const int w0 = min(VW, lane * per);
+        const int w1 = min(VW, w0 + per);
         uint32_t state = 0;
-        for (int w = w0; w < w1; ++w) {
-          const uint32_t v = __brev(bits[w]);
-#pragma unroll
-          for (int bb = 3; bb >= 0; --bb) {
-            const uint32_t byte = (v >> (8 * bb)) & 0xFFu;
-            state = ((state << 8) & 0xFFFFFFu) ^ a.crc_table[((state >> 16) ^ byte) & 0xFFu];
+        int b = max(0, 4 * w0 - pad);
+        int blk = b / cbb;
+        int j = b - blk * cbb;
+        int jw = -1;
+        uint32_t v = 0;
+        for (; b < 4 * w1 - pad; ++b) {
+          if ((j >> 2) != jw) {
+            jw = j >> 2;
+            v = bits[blk * kw + jw];
+          }
+          state = crc_byte_step(state, msb_first_byte(v, j), a.crc_table);
+          if (++j == cbb) {
+            ++blk;
+            j = 0;
+            jw = -1;
           }
         }
-        if (w0 < w1) state = gf2_mulmod(state, a.xpow32[W - w1]);
+        if (w0 < w1) state = gf2_mulmod(state, a.xpow32[VW - w1]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) state ^= __shfl_xor_sync(0xFFFFFFFFu, state, o);
+        // and each block's own CRC
+        for (int c = 0; seg && c < n_cb; ++c) {
+          const int pc = (kw + 31) >> 5;
+          const int v0 = min(kw, lane * pc);
+          const int v1 = min(kw, v0 + pc);
+          uint32_t st = 0;
+          for (int w = v0; w < v1; ++w) {
+            const uint32_t v = bits[c * kw + w];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st = crc_byte_step(st, msb_first_byte(v, j), a.crc_table_b);
+          }
+          if (v0 < v1) st = gf2_mulmod(st, a.xpow32_b[kw - v1], kPolyFullB);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) st ^= __shfl_xor_sync(0xFFFFFFFFu, st, o);
+          state |= st;
+        }
         uint32_t st = lane < n_cb ? a.arena[status_off + lane] : (1u << 16);
         uint32_t iters = st & 0xFFFFu;
         uint32_t okb = (st >> 16) & 1u;
@@ -360,16 +408,19 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
   }
 }
 
-template <bool TWO>
+template <bool TWO, bool CRC>
 const void* serve_kernel_for(int mode) {
   switch (mode) {
-    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false, TWO>);
-    case LDPC_I8: return reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, TWO>);
-    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true, TWO>);
+    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false, TWO, CRC>);
+    case LDPC_I8: return reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, TWO, CRC>);
+    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true, TWO, CRC>);
   }
 }
 
-const void* serve_kernel_ptr(int mode, bool two) { return two ? serve_kernel_for<true>(mode) : serve_kernel_for<false>(mode); }
+const void* serve_kernel_ptr(int mode, bool two, bool crc) {
+  if (crc) return two ? serve_kernel_for<true, true>(mode) : serve_kernel_for<false, true>(mode);
+  return two ? serve_kernel_for<true, false>(mode) : serve_kernel_for<false, false>(mode);
+}
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -441,6 +492,7 @@ struct ldpc_server {
   uint32_t* crc_table = nullptr;
   uint8_t* rscratch = nullptr;
   bool two = true;  // two loops per SM (messages in device memory)
+  bool cb_crc = false;  // LDPC_SERVE_CB_CRC: TBs with code-block CRCs accepted
   std::vector<ServeShape> hshapes;
   ServeArgs args{};
   int smem = 0, grid = 0;
@@ -492,7 +544,7 @@ void free_server(ldpc_server* v) {
 
 int launch_loop(ldpc_server* v) {
   void* kargs[] = {&v->args};
-  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two), dim3(v->grid), dim3(kServeBlock), kargs,
+  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two, v->cb_crc), dim3(v->grid), dim3(kServeBlock), kargs,
                                    static_cast<size_t>(v->smem), v->stream);
   if (e != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop launch: ") + cudaGetErrorString(e));
   e = cudaEventRecord(v->done_ev, v->stream);
@@ -538,6 +590,8 @@ int session_shape_count(ldpc_session* s);
 int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh);
 int session_shape_lookup(ldpc_session* s, int bg, int Z);
 const uint32_t* session_crc_table(ldpc_session* s);
+void session_cb_crc_tables(ldpc_session* s, const uint32_t** table_b, const uint32_t** xpow32_b,
+                           const uint32_t** positions);
 }  // namespace ldpcgb
 
 extern "C" {
@@ -546,13 +600,14 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
   try {
     if (!s || !d || !out || !d->host_pool || d->max_inflight < 1 || d->max_inflight > 65536 ||
         d->arena_bytes < 1024 || d->idle_timeout_us < 1 || d->loops_per_sm < 0 || d->loops_per_sm > 2 ||
-        d->reserved != 0)
+        (d->flags & ~LDPC_SERVE_CB_CRC))
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
     *out = nullptr;
     auto* v = new (std::nothrow) ldpc_server();
     if (!v) return srv_fail(LDPC_ENOMEM, "host allocation");
     v->s = s;
     v->two = d->loops_per_sm != 1;
+    v->cb_crc = (d->flags & LDPC_SERVE_CB_CRC) != 0;
     int interleave = 1, max_iter = 10, et = 1, sms = 0;
     float q_scale = 4, llr_sat = 63, beta = 1, msg_sat = 63, post_sat = 127;
     session_serve_info(s, &v->mode, &interleave, &max_iter, &et, &q_scale, &llr_sat, &beta, &msg_sat, &post_sat,
@@ -594,13 +649,13 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     }
     v->smem = smem;
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode, v->two));
+    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode, v->two, v->cb_crc));
     if (e == cudaSuccess && smem + static_cast<int>(fa.sharedSizeBytes) > kMaxSmem) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode, v->two), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode, v->two, v->cb_crc), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode, v->two), kServeBlock, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode, v->two, v->cb_crc), kServeBlock, smem);
     if (e != cudaSuccess || per_sm < 1) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, std::string("serve loop does not fit an SM (") + std::to_string(smem) +
@@ -631,7 +686,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       free_server(v);
       return rc;
     }
-    std::vector<uint32_t> xp(kMaxTbCb * 8448 / 32 * 2 + 1);
+    std::vector<uint32_t> xp(kServeXpowWords + 1);
     {
       uint32_t cur = 1;
       for (size_t m = 0; m < xp.size(); ++m) {
@@ -697,6 +752,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     a.result_pool = res_dev;
     a.crc_table = session_crc_table(s);
     a.xpow32 = v->xpow32;
+    session_cb_crc_tables(s, &a.crc_table_b, &a.xpow32_b, &a.cbcrc);
     a.hdr_bytes = hdr;
     a.interleave = interleave;
     a.max_iter = max_iter;
@@ -742,7 +798,12 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
         tb.E % tb.Qm || tb.E > 2 * (sd.nb * tb.Z - t0))  // the circular buffer may wrap once
       return srv_fail(LDPC_EINVAL, at + "bad n_cb, Qm or E");
     const int K = sd.kb * tb.Z;
-    if (K % 32 || tb.payload_bits != tb.n_cb * K - 24) return srv_fail(LDPC_EINVAL, at + "payload_bits");
+    const bool seg = tb.n_cb > 1 && tb.payload_bits == tb.n_cb * (K - 24) - 24;
+    if (K % 32 || (tb.payload_bits != tb.n_cb * K - 24 && !seg)) return srv_fail(LDPC_EINVAL, at + "payload_bits");
+    if (seg && !v->cb_crc)
+      return srv_fail(LDPC_EINVAL, at + "code-block CRCs need a service started with LDPC_SERVE_CB_CRC");
+    if (static_cast<int64_t>(tb.n_cb) * (K / 32) >= static_cast<int64_t>(kServeXpowWords))
+      return srv_fail(LDPC_EINVAL, at + "transport block too large");
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
     if (tb.sym_offset < 0 || tb.sym_offset % 8 || tb.mask_offset < 0 || tb.mask_offset % 4 ||
@@ -789,6 +850,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     rq.n_cb = tb.n_cb;
     rq.words = tb.n_cb * (K / 32);
     rq.shape = shape;
+    rq.seg = (tb.n_cb > 1 && tb.payload_bits == tb.n_cb * (K - 24) - 24) ? 1 : 0;
     rq.bits_off = off;
     rq.status_off = off + static_cast<int64_t>(tb.n_cb) * (K / 32);
     rq.result_off = tb.result_offset;
@@ -804,6 +866,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       c.n_eff = sd.kb + m_eff;
       c.n_re = n_re;
       c.kb = sd.kb;
+      c.flags = rq.seg ? LDPC_CB_CRC24B : 0;
       c.re_off = tb.sym_offset / 8 + static_cast<int64_t>(j) * n_re;
       c.mask_off = tb.mask_offset / 4 + static_cast<int64_t>(j) * mw;
       c.llr_off = rq.status_off + j;  // status word index in the arena

@@ -36,6 +36,9 @@ struct ldpc_session {
   std::map<std::pair<int, int>, int> tiles;        // (bg, Z) -> code blocks per work item
   int strategy = LDPC_PLAN_MIXED;
   uint32_t* d_crc_table = nullptr;
+  uint32_t* d_crc_table_b = nullptr;  // byte table of the code-block generator g_B
+  uint32_t* d_xpow32_b = nullptr;     // x^(32 m) mod g_B, m = 0..largest block's words
+  uint32_t* d_cbcrc = nullptr;        // per shape: x^(K-1-p) mod g_B, p = 0..K-1
   uint32_t* d_err = nullptr;
 };
 
@@ -135,24 +138,49 @@ int align16(int x) { return (x + 15) & ~15; }
 
 bool z_supported(int Z) { return Z == 16 || (Z >= 32 && Z <= kMaxZ && Z % 32 == 0); }
 
-uint32_t crc_byte_entry(uint32_t v) {
+constexpr uint32_t kGenA = 0x1864CFBu;  // g(x) of the transport-block CRC, x^24 term included
+constexpr uint32_t kGenB = 0x1800063u;  // g_B(x) of the code-block CRC
+
+uint32_t crc_byte_entry(uint32_t v, uint32_t gen) {
   uint32_t r = v << 16;
-  for (int i = 0; i < 8; ++i) r = (r & 0x800000u) ? (((r << 1) ^ 0x864CFBu) & 0xFFFFFFu) : ((r << 1) & 0xFFFFFFu);
+  for (int i = 0; i < 8; ++i) {
+    r <<= 1;
+    if (r & 0x1000000u) r ^= gen;
+  }
   return r;
 }
 
+std::vector<uint32_t> crc_byte_table(uint32_t gen) {
+  std::vector<uint32_t> t(256);
+  for (uint32_t v = 0; v < 256; ++v) t[v] = crc_byte_entry(v, gen);
+  return t;
+}
+
 // x^(32 m) mod g for m = 0..n.
-std::vector<uint32_t> xpow32_table(int n) {
+std::vector<uint32_t> xpow32_table(int n, uint32_t gen = kGenA) {
   std::vector<uint32_t> t(n + 1);
   uint32_t cur = 1;  // x^0
   for (int m = 0; m <= n; ++m) {
     t[m] = cur;
     for (int i = 0; i < 32; ++i) {  // multiply by x^32, one bit at a time
       cur <<= 1;
-      if (cur & 0x1000000u) cur ^= 0x1864CFBu;
+      if (cur & 0x1000000u) cur ^= gen;
     }
   }
   return t;
+}
+
+// Bit p of a K-bit block (first in time = highest degree) is the coefficient
+// of x^(K-1-p): appends x^(K-1-p) mod g_B for p = 0..K-1.
+void cb_crc_positions(int K, std::vector<uint32_t>& out) {
+  const size_t base = out.size();
+  out.resize(base + K);
+  uint32_t cur = 1;
+  for (int p = K - 1; p >= 0; --p) {
+    out[base + p] = cur;
+    cur <<= 1;
+    if (cur & 0x1000000u) cur ^= kGenB;
+  }
 }
 
 // Edge table of base graph g at lifting Z for a launch whose dummy slot is at
@@ -375,6 +403,10 @@ int plan_decode(ldpc_session* s, ldpc_batch* b) {
       items.push_back(c.it);
     }
     L.item_count = static_cast<int>(items.size()) - L.item_begin;
+    // the variant with the code-block CRC exit only where a block needs it
+    for (const auto& c : list)
+      for (int i : c.cbs)
+        if (b->cbs[i].flags & LDPC_CB_CRC24B) L.kind |= kKindCrc;
     L.G = gmax;
     L.block = (block + 31) & ~31;
     L.smem = smem;
@@ -410,6 +442,9 @@ int session_free(ldpc_session* s) {
   if (!s) return LDPC_OK;
   cudaSetDevice(s->device);
   cudaFree(s->d_crc_table);
+  cudaFree(s->d_crc_table_b);
+  cudaFree(s->d_xpow32_b);
+  cudaFree(s->d_cbcrc);
   cudaFree(s->d_err);
   delete s;
   return LDPC_OK;
@@ -455,6 +490,13 @@ int session_shape_lookup(ldpc_session* s, int bg, int Z) {
 }
 
 const uint32_t* session_crc_table(ldpc_session* s) { return s->d_crc_table; }
+
+void session_cb_crc_tables(ldpc_session* s, const uint32_t** table_b, const uint32_t** xpow32_b,
+                           const uint32_t** positions) {
+  *table_b = s->d_crc_table_b;
+  *xpow32_b = s->d_xpow32_b;
+  *positions = s->d_cbcrc;
+}
 
 }  // namespace ldpcgb
 
@@ -543,11 +585,17 @@ int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
       s->bgs.push_back(h);
     }
 
-    // ---- (base graph, Z) pairs; their edge tables are built per batch launch
+    // ---- (base graph, Z) pairs; their edge tables are built per batch launch,
+    // their code-block CRC position tables here
+    std::vector<uint32_t> cbcrc;
+    int max_cb_words = 0;
     for (int b = 0; b < static_cast<int>(s->bgs.size()); ++b) {
       const auto& g = s->bgs[b];
       for (int Z : s->zset) {
         ShapeDev sh{};
+        sh.crc_off = static_cast<int32_t>(cbcrc.size());
+        cb_crc_positions(g.kb * Z, cbcrc);
+        max_cb_words = std::max(max_cb_words, g.kb * Z / 32);
         sh.bg = b;
         sh.Z = Z;
         sh.mb = g.mb;
@@ -559,10 +607,11 @@ int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
         s->shapes.push_back(sh);
       }
     }
-    std::vector<uint32_t> crc_tab(256);
-    for (uint32_t v = 0; v < 256; ++v) crc_tab[v] = crc_byte_entry(v);
     int rc;
-    if ((rc = upload(s, &s->d_crc_table, crc_tab, nullptr, nullptr)) ||
+    if ((rc = upload(s, &s->d_crc_table, crc_byte_table(kGenA), nullptr, nullptr)) ||
+        (rc = upload(s, &s->d_crc_table_b, crc_byte_table(kGenB), nullptr, nullptr)) ||
+        (rc = upload(s, &s->d_xpow32_b, xpow32_table(max_cb_words, kGenB), nullptr, nullptr)) ||
+        (rc = upload(s, &s->d_cbcrc, cbcrc, nullptr, nullptr)) ||
         (rc = upload(s, &s->d_err, std::vector<uint32_t>(4, 0u), nullptr, nullptr))) {
       session_free(s);
       return rc;
@@ -625,8 +674,9 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       // rate matching reads a circular buffer of the nb*Z - t0 positions from t0; it may wrap once
       if (c.E <= 0 || c.E % c.Qm || c.E > 2 * (g.nb * c.Z - t0))
         return bail(LDPC_EINVAL, at + "E must be a positive multiple of Qm with E <= 2 (nb*Z - t0)");
-      if (c.re_offset < 0 || c.mask_word_offset < 0 || c.llr_offset < 0 || c.bits_word_offset < 0 || c.reserved)
-        return bail(LDPC_EINVAL, at + "negative offset or nonzero reserved field");
+      if (c.re_offset < 0 || c.mask_word_offset < 0 || c.llr_offset < 0 || c.bits_word_offset < 0 ||
+          (c.flags & ~LDPC_CB_CRC24B))
+        return bail(LDPC_EINVAL, at + "negative offset or unknown flag");
       if ((c.llr_offset * esz) % 16) return bail(LDPC_EINVAL, at + "llr_offset must be 16-byte aligned");
       if ((g.kb * c.Z) % 32) return bail(LDPC_EINVAL, at + "kb*Z must be a multiple of 32");
       if (!(c.inv_sigma2 >= 0.f)) return bail(LDPC_EINVAL, at + "inv_sigma2 must be >= 0");
@@ -644,6 +694,7 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       d.n_eff = g.kb + m_eff;
       d.n_re = c.E / c.Qm;
       d.kb = g.kb;
+      d.flags = c.flags;
       d.re_off = c.re_offset;
       d.mask_off = c.mask_word_offset;
       d.llr_off = c.llr_offset;
@@ -691,11 +742,28 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
             x.n_sc < 0)
           return bail(LDPC_EINVAL, at + "bad code-block range, slot or n_sc");
         int64_t bits = 0;
-        for (int i = x.first_cb; i < x.first_cb + x.n_cb; ++i)
+        int n_flag = 0;
+        for (int i = x.first_cb; i < x.first_cb + x.n_cb; ++i) {
           bits += static_cast<int64_t>(b->cbs[i].kb) * b->cbs[i].Z;
-        if (x.payload_bits != bits - 24) return bail(LDPC_EINVAL, at + "payload_bits must be sum(K) - 24");
-        tv[t] = TbDev{x.first_cb, x.n_cb, x.n_sc, x.slot, x.payload_bits, static_cast<int32_t>(bits / 32)};
-        max_words = std::max(max_words, static_cast<int>(bits / 32));
+          n_flag += (b->cbs[i].flags & LDPC_CB_CRC24B) ? 1 : 0;
+        }
+        const int seg = n_flag > 0 ? 1 : 0;
+        if (n_flag != 0 && n_flag != x.n_cb)
+          return bail(LDPC_EINVAL, at + "LDPC_CB_CRC24B must be set on all or none of its code blocks");
+        bits -= 24 * n_flag;
+        if (x.payload_bits != bits - 24)
+          return bail(LDPC_EINVAL, at + "payload_bits must be sum(K) - 24 (sum(K - 24) - 24 with code-block CRCs)");
+        if (bits > (int64_t(1) << 30)) return bail(LDPC_EINVAL, at + "too many bits");
+        TbDev td{};
+        td.first_cb = x.first_cb;
+        td.n_cb = x.n_cb;
+        td.n_sc = x.n_sc;
+        td.slot = x.slot;
+        td.payload_bits = x.payload_bits;
+        td.bytes = static_cast<int32_t>(bits / 8);
+        td.seg = seg;
+        tv[t] = td;
+        max_words = std::max(max_words, static_cast<int>((bits / 8 + 3) / 4));
         per_slot[x.slot].push_back(t);
       }
       std::vector<int32_t> start(n_slots + 1, 0), list;
@@ -875,6 +943,7 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
     a.hdr_bytes = L.hdr_bytes;
     a.max_iter = s->max_iter;
     a.early_term = s->early_term;
+    a.cbcrc = s->d_cbcrc;
     if (s->mode == LDPC_F32) {
       a.beta = s->beta_f32;
       a.msg_sat = 3.0e38f;
@@ -904,6 +973,8 @@ int tb_crc_goodput(ldpc_session* s, const ldpc_batch* b, const uint32_t* bits_de
   a.slot_N = b->d_slot_N;
   a.crc_table = s->d_crc_table;
   a.xpow32 = b->d_xpow32;
+  a.crc_table_b = s->d_crc_table_b;
+  a.xpow32_b = s->d_xpow32_b;
   a.bits = bits_dev;
   a.d = d_dev;
   a.goodput_bits = goodput_bits_dev;

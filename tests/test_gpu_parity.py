@@ -16,7 +16,7 @@ from oracle import demap as odemap
 from oracle import goodput as ogood
 from oracle import path as opath
 from workload import large_fp32, mixed, tiny_fp32
-from workload.configs import repetition
+from workload.configs import repetition, segmented
 from workload.basegraph import tree_base_graph
 
 from gpu_helpers import LLR_NP, batch_for, device_inputs, session_for, to_np_u32
@@ -33,6 +33,9 @@ def _workloads():
         "large": large_fp32(n_cw=10, snr_points=(6, 8, 10, 12)),
         "mixed": mixed(n_slots=3, ues_per_slot=4, max_cb=3),
         "repetition": repetition(n_per_shape=8),   # rate matching wraps the circular buffer
+        # segmented TBs with a CRC per code block: CRC-aided exit and the segmented TB check
+        "segmented": segmented(n_tb=12, spread_db=(-2.0, 1.0)),
+        "mixed_seg": mixed(n_slots=3, ues_per_slot=4, max_cb=3, cb_crc=True, spread_db=2.0),
     }
 
 
@@ -93,7 +96,7 @@ def test_demap_quantised_within_one_lsb(wls, name, mode):
 
 # ------------------------------------------------------------------ decode
 @pytest.mark.parametrize("mode", ["i8", "i16"])
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "segmented", "mixed_seg"])
 def test_decode_integer_bit_exact(wls, name, mode):
     w = wls[name]
     mi, et = _params(w)
@@ -110,7 +113,7 @@ def test_decode_integer_bit_exact(wls, name, mode):
     assert s.device_errors() == 0
 
 
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "segmented", "mixed_seg"])
 def test_decode_f32_bit_exact_vs_oracle_float32(wls, name):
     w = wls[name]
     mi, et = _params(w)
@@ -146,7 +149,7 @@ def test_decode_f32_against_float64_oracle(wls, name):
 
 
 # ------------------------------------------------------------------ CRC, goodput, reward
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "segmented", "mixed_seg"])
 def test_crc_goodput_reward_exact(wls, name):
     w = wls[name]
     mi, et = _params(w)
@@ -156,6 +159,12 @@ def test_crc_goodput_reward_exact(wls, name):
     for t in range(0, w.n_tb, 3):
         o = int(w.cbs[int(w.tbs[t]["first_cb"])]["bits_word_offset"])
         words[o] ^= np.uint32(1 << 7)
+    # and, in TBs with code-block CRCs, one CRC bit of their last block (outside the TB's own stream)
+    for t in range(1, w.n_tb, 3):
+        c = w.cbs[int(w.tbs[t]["first_cb"]) + int(w.tbs[t]["n_cb"]) - 1]
+        if int(c["flags"]) & 1:
+            K = w.bgs[int(c["bg"])].kb * int(c["Z"])
+            words[int(c["bits_word_offset"]) + (K - 5) // 32] ^= np.uint32(1 << ((K - 5) % 32))
     d, gb, gs, r = ogood.tb_crc_goodput(w, words)
     s = session_for(w, "f32")
     b = batch_for(s, w)
@@ -172,7 +181,7 @@ def test_crc_goodput_reward_exact(wls, name):
 
 # ------------------------------------------------------------------ whole path
 @pytest.mark.parametrize("mode", ["f32", "i8"])
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "mixed_seg"])
 def test_full_path_matches_oracle(wls, name, mode):
     # both sides run the whole path from the same symbols and masks; each
     # demaps on its own (float32 here, float64 in the oracle), so a marginal

@@ -173,3 +173,38 @@ def test_one_loop_per_sm_matches_the_batch_path(pool):
             assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
     finally:
         srv.stop()
+
+
+@pytest.mark.parametrize("loops", [1, 2])
+def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(loops):
+    """TBs whose code blocks carry their own CRC (payload n_cb (K - 24) - 24): the service infers that from
+    payload_bits, stops blocks on a passing CRC and checks every CRC, like the batch path, bit for bit."""
+    w = tb_pool(24, seed=17, max_cb=6, cb_crc=True)
+    assert (w.cbs["flags"] == 1).any()
+    raw, mask_base = pool_bytes(w)
+    host = torch.from_numpy(raw).pin_memory()
+    n = w.n_tb
+    words = [_tb_words(w, t) for t in range(n)]
+    offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
+    res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
+    s = session_for(w, "i8")
+    plain = Server(session_for(w, "i8"), host, None, arena_bytes=1 << 24, max_inflight=8, loops_per_sm=loops)
+    try:
+        seg = int(np.flatnonzero(w.tbs["n_cb"] > 1)[0])
+        with pytest.raises(LdpcError, match="LDPC_SERVE_CB_CRC"):
+            plain.submit(tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=[seg], tags=[0]))
+    finally:
+        plain.stop()
+    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=64, loops_per_sm=loops, cb_crc=True)
+    try:
+        recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
+        done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
+        assert sorted(done["tag"].tolist()) == list(range(n))
+        d_ref, bits_ref = _batch_reference(w, range(n))
+        for r in done:
+            t = int(r["tag"])
+            assert int(r["d"]) == int(d_ref[t]), t
+            assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
+        assert 0 < int(done["d"].sum()) < n  # both outcomes occur at these SNRs
+    finally:
+        srv.stop()
