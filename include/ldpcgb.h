@@ -102,11 +102,15 @@ typedef struct {
 } ldpc_session_desc;
 
 /*
- * One code block.  Transmitted bit e is codeword position t0 + (e mod Ncb),
- * t0 = n_punct_cols * Z, Ncb = nb * Z - t0 (a circular buffer read from its
- * start; E > Ncb repeats it and the receiver adds the LLRs of a position;
- * E <= 2 Ncb); the decoder works on n_eff = kb + m_eff columns with
- * m_eff = min(mb, max(mc, ceil((E + t0) / Z) - kb)) rows.
+ * One code block.  Transmitted bit e is codeword position
+ * t0 + ((k0 + e) mod Ncb), t0 = n_punct_cols * Z, Ncb = nb * Z - t0 (a
+ * circular buffer read from the start k0 of the redundancy version; bits that
+ * land on one position -- E > Ncb -- have their LLRs added; E <= 2 Ncb); the
+ * decoder works on n_eff = kb + m_eff columns with
+ * m_eff = min(mb, max(mc, ceil((t0 + last) / Z) - kb)) rows, last = Ncb if
+ * k0 + E > Ncb, else k0 + E.  k0 = 0 for redundancy version 0; versions 1-3
+ * (flags) follow NR's table: k0 = (17, 33, 56) * Z when Ncb = 66 Z and
+ * (13, 25, 43) * Z when Ncb = 50 Z (other graphs: version 0 only).
  *   re_offset        first complex symbol (float2) of the block, E / Qm of them
  *   mask_word_offset first uint32 of its puncture mask: bit r % 32 of word
  *                    r / 32 set = resource element r was taken by URLLC
@@ -114,14 +118,18 @@ typedef struct {
  *   bits_word_offset first uint32 of its kb * Z / 32 decoded information
  *                    words: bit i of the block is bit i % 32 of word i / 32
  *   inv_sigma2       1 / noise variance per symbol
- *   flags            0, or LDPC_CB_CRC24B: the block's last 24 information
- *                    bits are a CRC of its first K - 24 (K = kb * Z) under
+ *   flags            LDPC_CB_CRC24B: the block's last 24 information bits
+ *                    are a CRC of its first K - 24 (K = kb * Z) under
  *                    g_B(x) = x^24 + x^23 + x^6 + x^5 + x + 1 (register from 0,
  *                    first bit highest degree), NR-style segmentation.  The
  *                    decoder then also stops a block whose hard decision
  *                    passes that CRC, and the TB check leaves those bits out.
+ *                    Bits 1-2 (LDPC_CB_RV(rv)): the redundancy version sent.
  */
 #define LDPC_CB_CRC24B 1
+#define LDPC_CB_RV_SHIFT 1
+#define LDPC_CB_RV_MASK (3 << LDPC_CB_RV_SHIFT)
+#define LDPC_CB_RV(rv) ((rv) << LDPC_CB_RV_SHIFT)
 typedef struct {
   int32_t bg, Z, Qm, E;
   int64_t re_offset;
@@ -129,7 +137,7 @@ typedef struct {
   int64_t llr_offset;
   int64_t bits_word_offset;
   float inv_sigma2;
-  int32_t flags; /* 0 or LDPC_CB_CRC24B */
+  int32_t flags; /* LDPC_CB_CRC24B | LDPC_CB_RV(rv) */
 } ldpc_cb_desc;
 
 /*
@@ -328,7 +336,8 @@ typedef struct {
 #define LDPC_SERVE_CB_CRC 1
 
 typedef struct {
-  int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16 */
+  int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16;
+                                 * redundancy version 0 */
   int32_t n_sc, payload_bits;   /* n_e; payload_bits = n_cb * kb * Z - 24, or, for n_cb > 1 with a CRC
                                  * per code block (LDPC_CB_CRC24B), n_cb * (kb * Z - 24) - 24 */
   float inv_sigma2;

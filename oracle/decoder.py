@@ -37,7 +37,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import crc
-from .demap import bg_geometry
+from .demap import bg_geometry, rv_of
 
 
 @dataclass(frozen=True)
@@ -216,7 +216,7 @@ def decode_workload(w, llr, max_iter, early_term, arith=F64, cb_index=None, retu
         c = w.cbs[i]
         bg = w.bgs[int(c["bg"])]
         Z, E = int(c["Z"]), int(c["E"])
-        _, m_eff, n_eff = bg_geometry(bg, Z, E)
+        _, m_eff, n_eff = bg_geometry(bg, Z, E, rv_of(c))
         groups.setdefault((int(c["bg"]), Z, m_eff), []).append(int(i))
     for (b, Z, m_eff), members in groups.items():
         bg = w.bgs[b]

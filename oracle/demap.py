@@ -16,12 +16,16 @@ unit average energy.
 
 Rate dematching: the Qm bits of resource element r are rate-matched bits
 e = i * (E / Qm) + r (i < Qm) with the row-column interleaver, or
-e = r * Qm + i without it; bit e is codeword position t0 + (e mod Ncb), a
-circular buffer of Ncb = nb * Z - t0 positions (redundancy version 0; E > Ncb
-repeats it), and the LLRs of all bits that land on one position are added
-(LLR combining); positions never transmitted hold LLR 0.
-The decoded length is n_eff * Z with n_eff = kb + m_eff and
-m_eff = min(mb, max(mc, ceil((E + t0) / Z) - kb)), t0 = n_punct_cols * Z.
+e = r * Qm + i without it; bit e is codeword position t0 + ((k0 + e) mod Ncb),
+a circular buffer of Ncb = nb * Z - t0 positions read from the start k0 of the
+redundancy version (0 for version 0; versions 1-3 follow NR's table, 3GPP
+TS 38.212 rate matching: k0 = (17, 33, 56) Z for a 66 Z buffer and
+(13, 25, 43) Z for a 50 Z buffer, the sizes of NR's two base graphs; the paper
+sends one transmission per TTI and names no version, Sec. VI-A), and the LLRs
+of all bits that land on one position are added (LLR combining); positions
+never transmitted hold LLR 0.  The decoded length is n_eff * Z with
+n_eff = kb + m_eff and m_eff = min(mb, max(mc, ceil((t0 + last) / Z) - kb)),
+t0 = n_punct_cols * Z, last = Ncb if k0 + E > Ncb else k0 + E.
 
 INT modes quantise q = clamp(round_half_away(scale * lambda), -sat, sat).
 """
@@ -64,16 +68,37 @@ def maxlog_llr(y: np.ndarray, Qm: int, inv_sigma2) -> np.ndarray:
     return out * np.asarray(inv_sigma2, dtype=np.float64)
 
 
-def geometry(mb, nb, kb, mc, n_punct_cols, Z, E):
-    """(t0, m_eff, n_eff) for a code block that transmits E bits."""
+K0_UNITS = {66: (0, 17, 33, 56), 50: (0, 13, 25, 43)}  # k0 / Z per redundancy version, by Ncb / Z
+
+
+def start_k0(nb, n_punct_cols, Z, rv):
+    """Start of redundancy version rv in the circular buffer."""
+    if rv == 0:
+        return 0
+    units = K0_UNITS.get(nb - n_punct_cols)
+    if units is None:
+        raise ValueError("redundancy versions 1-3 need a 66 Z or 50 Z buffer")
+    return units[rv] * Z
+
+
+def geometry(mb, nb, kb, mc, n_punct_cols, Z, E, rv=0):
+    """(t0, m_eff, n_eff) for a code block that transmits E bits of redundancy version rv."""
     t0 = n_punct_cols * Z
-    cols = -(-(E + t0) // Z)
+    ncb = nb * Z - t0
+    k0 = start_k0(nb, n_punct_cols, Z, rv)
+    last = ncb if k0 + E > ncb else k0 + E
+    cols = -(-(t0 + last) // Z)
     m_eff = min(mb, max(mc, cols - kb))
     return t0, m_eff, kb + m_eff
 
 
-def bg_geometry(bg, Z, E):
-    return geometry(bg.mb, bg.nb, bg.kb, bg.mc, bg.n_punct_cols, Z, E)
+def bg_geometry(bg, Z, E, rv=0):
+    return geometry(bg.mb, bg.nb, bg.kb, bg.mc, bg.n_punct_cols, Z, E, rv)
+
+
+def rv_of(c) -> int:
+    """Redundancy version of a code-block descriptor (bits 1-2 of its flags)."""
+    return (int(c["flags"]) >> 1) & 3
 
 
 def unpack_mask(words: np.ndarray, n: int) -> np.ndarray:
@@ -82,9 +107,10 @@ def unpack_mask(words: np.ndarray, n: int) -> np.ndarray:
     return bits.reshape(-1)[:n].astype(bool)
 
 
-def demap_cb(y, mask_bits, bg, Z, Qm, E, inv_sigma2, interleave=True) -> np.ndarray:
+def demap_cb(y, mask_bits, bg, Z, Qm, E, inv_sigma2, interleave=True, rv=0) -> np.ndarray:
     """One code block: symbols + puncture mask -> LLRs at codeword positions (n_eff*Z,)."""
-    t0, m_eff, n_eff = bg_geometry(bg, Z, E)
+    t0, m_eff, n_eff = bg_geometry(bg, Z, E, rv)
+    k0 = start_k0(bg.nb, bg.n_punct_cols, Z, rv)
     n_re = E // Qm
     lam = maxlog_llr(y[:n_re], Qm, inv_sigma2)          # (n_re, Qm)
     lam[np.asarray(mask_bits[:n_re], dtype=bool)] = 0.0  # puncture flushing
@@ -93,7 +119,7 @@ def demap_cb(y, mask_bits, bg, Z, Qm, E, inv_sigma2, interleave=True) -> np.ndar
     r = np.arange(n_re)
     for i in range(Qm):
         e = i * n_re + r if interleave else r * Qm + i
-        np.add.at(out, t0 + e % ncb, lam[:, i])
+        np.add.at(out, t0 + (k0 + e) % ncb, lam[:, i])
     return out
 
 
@@ -117,6 +143,6 @@ def demap_workload(w, cb_index=None, interleave=True):
         ro, mo, lo = int(c["re_offset"]), int(c["mask_word_offset"]), int(c["llr_offset"])
         mbits = unpack_mask(w.mask[mo:mo + -(-n_re // 32)], n_re)
         v = demap_cb(w.sym[ro:ro + n_re], mbits, bg, Z, Qm, E,
-                     float(np.float32(c["inv_sigma2"])), interleave)
+                     float(np.float32(c["inv_sigma2"])), interleave, rv_of(c))
         out[lo:lo + v.size] = v
     return out

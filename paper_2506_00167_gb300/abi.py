@@ -59,6 +59,7 @@ class CbDescC(ctypes.Structure):
 
 
 CB_FLAG_CRC24B = 1  # the code block's last 24 information bits are a CRC (0x800063) of the others
+CB_RV_SHIFT = 1     # flags bits 1-2: the redundancy version sent (LDPC_CB_RV)
 
 
 class TbDescC(ctypes.Structure):

@@ -64,7 +64,31 @@ __global__ void __launch_bounds__(kCrcBlock) tb_crc_goodput_kernel(const CrcArgs
     const int w0 = min(W, lane * per);
     const int w1 = min(W, w0 + per);
     uint32_t state = 0;
-    if (w0 < w1) {
+    if (w0 < w1 && !tb.seg) {
+      // whole code blocks: every block's words in order (pad is 0)
+      int cbi = tb.first_cb;
+      int cb_first = 0;
+      int cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
+      while (w0 >= cb_first + cb_words) {
+        cb_first += cb_words;
+        ++cbi;
+        cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
+      }
+      const uint32_t* src = a.bits + a.cbs[cbi].bits_off;
+      for (int w = w0; w < w1; ++w) {
+        if (w >= cb_first + cb_words) {
+          cb_first += cb_words;
+          ++cbi;
+          cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
+          src = a.bits + a.cbs[cbi].bits_off;
+        }
+        const uint32_t v = src[w - cb_first];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) state = crc_byte_step(state, msb_first_byte(v, j), s_tab);
+      }
+      state = gf2_mulmod(state, a.xpow32[W - w1]);
+    } else if (w0 < w1) {
+      // segments of K/8 - 3 bytes: byte by byte
       const int b_end = 4 * w1 - pad;
       int b = max(0, 4 * w0 - pad);
       // find the code block holding TB byte b

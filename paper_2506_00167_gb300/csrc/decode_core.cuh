@@ -294,32 +294,37 @@ __device__ __forceinline__ bool syndrome_direct(const uint32_t* __restrict__ tab
 }
 
 // ---- CRC-aided exit for blocks that carry their own CRC (LDPC_CB_CRC24B).
-// Bit p = c * Z + k of the K = kb * Z information bits stands for x^(K-1-p);
-// the block passes iff sum_p bit_p * (x^(K-1-p) mod g_B) is 0 over GF(2).
-// ptab[p] holds that remainder, so thread k XORs the entries of its kb bits
-// (column c, row k) and the group XORs the threads' sums.
+// Bit p of the K = kb * Z information bits stands for x^(K-1-p); the block
+// passes iff the XOR of x^(K-1-p) mod g_B over its set bits is 0.  btab holds,
+// for every byte j of the block and every byte value v, the XOR of those
+// remainders over v's set bits (bit i of v = block bit 8j + i); the threads
+// XOR the entries of their bytes and the group XORs the threads' sums.
+
+// Z < 32 (Z = 16): thread k's bits c * Z + k, one entry each.
 template <typename LT>
-__device__ __forceinline__ uint32_t cb_crc_part(const LT* __restrict__ L, const uint32_t* __restrict__ ptab,
+__device__ __forceinline__ uint32_t cb_crc_part(const LT* __restrict__ L, const uint32_t* __restrict__ btab,
                                                 int kb, int k, int Z) {
   uint32_t r = 0;
   for (int c = 0; c < kb; ++c) {
-    const uint32_t t = __ldg(ptab + c * Z + k);
-    r ^= (L[c * Z + k] < LT(0)) ? t : 0u;
+    const int p = c * Z + k;
+    const uint32_t t = __ldg(btab + (p >> 3) * 256 + (1 << (p & 7)));
+    r ^= (L[p] < LT(0)) ? t : 0u;
   }
   return r;
 }
 
-// The same from the hard-decision bitmap (Z % 32 == 0): a warp reads one
-// word per column, a broadcast.
+// Z % 32 == 0, from the hard-decision bitmap: information word m (block bits
+// 32m .. 32m+31) is bitmap word m; thread k takes words k, k + Z, ..., four
+// byte entries each.
 __device__ __forceinline__ uint32_t cb_crc_part_hb(const uint32_t* __restrict__ hb,
-                                                   const uint32_t* __restrict__ ptab, int kb, int k, int Z) {
-  const int W = Z >> 5;
-  const int w = k >> 5;
-  const int b = k & 31;
+                                                   const uint32_t* __restrict__ btab, int kb, int k, int Z) {
+  const int nw = kb * (Z >> 5);
   uint32_t r = 0;
-  for (int c = 0; c < kb; ++c) {
-    const uint32_t t = __ldg(ptab + c * Z + k);
-    r ^= ((hb[c * W + w] >> b) & 1u) ? t : 0u;
+  for (int m = k; m < nw; m += Z) {
+    const uint32_t w = hb[m];
+    const uint32_t* t = btab + m * 1024;
+    r ^= __ldg(t + (w & 0xFFu)) ^ __ldg(t + 256 + ((w >> 8) & 0xFFu)) ^ __ldg(t + 512 + ((w >> 16) & 0xFFu)) ^
+         __ldg(t + 768 + (w >> 24));
   }
   return r;
 }

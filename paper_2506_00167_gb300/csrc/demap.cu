@@ -11,13 +11,14 @@
 // each thread kDemapPerThread of them, kDemapBlock apart: all of a thread's
 // symbol and mask-word loads are issued before any arithmetic, so enough
 // bytes are in flight per SM to keep HBM busy.  Each resource element gives
-// Qm LLRs, written to its interleaved codeword position t0 + i * (E/Qm) + r --
-// for a fixed bit plane i consecutive threads write consecutive positions, so
-// every store is coalesced.  The first tile of each code block also
-// zero-fills the positions never transmitted.  When rate matching wraps the
-// circular buffer (E > Ncb), this kernel writes the first pass and
-// demap_repeat_kernel then rewrites the repeated positions with the sum of
-// their two LLRs.
+// Qm LLRs, written to its interleaved codeword position t0 + i * (E/Qm) + r
+// (offset by the redundancy version's start k0, modulo the buffer) -- for a
+// fixed bit plane i consecutive threads write consecutive positions, so every
+// store is coalesced but at the buffer's wrap point.  The first tile of each
+// code block also zero-fills the positions never transmitted.  When rate
+// matching repeats the circular buffer (E > Ncb), this kernel writes the
+// first pass and demap_repeat_kernel then rewrites the repeated positions
+// with the sum of their two LLRs.
 #include "demap_core.cuh"
 
 namespace ldpcgb {
@@ -55,15 +56,18 @@ __global__ void __launch_bounds__(kDemapBlock) demap_kernel(const DemapArgs a) {
   if (tile.re_start == 0) {  // positions never transmitted hold LLR 0
     LT* out = static_cast<LT*>(a.llr) + cb.llr_off;
     for (int p = threadIdx.x; p < cb.t0; p += blockDim.x) out[p] = LT(0);
-    const int tail0 = cb.t0 + min(cb.E, cb.n_eff * cb.Z - cb.t0);
-    const int n = cb.n_eff * cb.Z;
-    for (int p = tail0 + threadIdx.x; p < n; p += blockDim.x) out[p] = LT(0);
+    // buffer offsets k0 + j (mod Ncb) for j from E to Ncb: those the version does not reach
+    const int ncb = cb.n_eff * cb.Z - cb.t0;
+    for (int j = min(cb.E, ncb) + threadIdx.x; j < ncb; j += blockDim.x) {
+      const int q = cb.k0 + j;
+      out[cb.t0 + (q >= ncb ? q - ncb : q)] = LT(0);
+    }
   }
 }
 
-// Repeated bits e2 in [Ncb, E) of a block whose rate matching wraps: position
-// e2 - Ncb gets lambda(e2 - Ncb) + lambda(e2), one thread per repeated bit,
-// after demap_kernel has written the first pass.
+// Repeated bits e2 in [Ncb, E) of a block whose rate matching wraps: buffer
+// offset (k0 + e2) mod Ncb gets lambda(e2 - Ncb) + lambda(e2), one thread per
+// repeated bit, after demap_kernel has written the first pass.
 template <typename LT>
 __global__ void __launch_bounds__(kDemapBlock) demap_repeat_kernel(const DemapArgs a) {
   const DemapTile tile = a.tiles[blockIdx.x];
@@ -86,7 +90,8 @@ __global__ void __launch_bounds__(kDemapBlock) demap_repeat_kernel(const DemapAr
     default: v = bit_llr<8>(e2 - ncb, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm) +
                  bit_llr<8>(e2, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm); break;
   }
-  static_cast<LT*>(a.llr)[cb.llr_off + cb.t0 + e2 - ncb] = to_llr<LT>(v, a.q_scale, a.llr_sat);
+  const int q = cb.k0 + e2 - ncb;  // the buffer offset both bits land on
+  static_cast<LT*>(a.llr)[cb.llr_off + cb.t0 + (q >= ncb ? q - ncb : q)] = to_llr<LT>(v, a.q_scale, a.llr_sat);
 }
 
 }  // namespace

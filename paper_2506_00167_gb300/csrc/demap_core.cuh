@@ -65,13 +65,15 @@ __device__ __forceinline__ LT to_llr(float lam, float q_scale, float sat) {
   }
 }
 
-// Rate matching reads a circular buffer of the Ncb = n_eff * Z - t0 codeword
-// positions from t0 (redundancy version 0): rate-matched bit e lands on
-// position t0 + (e mod Ncb), so when E > Ncb the buffer repeats and the two
-// LLRs of a position are added (LLR combining; E <= 2 Ncb).  The thread that
-// owns bit e < Ncb writes the position, adding the LLR of bit e + Ncb when it
-// was sent; it demaps that bit's resource element itself, so each position is
-// written once and the sum is always taken in the same order.
+// Rate matching reads a circular buffer of the Ncb = nb * Z - t0 codeword
+// positions from t0: rate-matched bit e lands on position
+// t0 + ((k0 + e) mod Ncb), k0 the start of the redundancy version, so when
+// E > Ncb the buffer repeats and the two LLRs of a position are added (LLR
+// combining; E <= 2 Ncb).  The serving loop sends redundancy version 0 only
+// (k0 = 0): there the thread that owns bit e < Ncb writes the position, adding
+// the LLR of bit e + Ncb when it was sent; it demaps that bit's resource
+// element itself, so each position is written once and the sum is always
+// taken in the same order.
 
 // Max-log LLR of rate-matched bit e (0 for a punctured resource element);
 // sym/msk point at the code block's symbols and mask words.
@@ -114,7 +116,10 @@ __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_si
 // Batch form: writes the first pass over the circular buffer only; the
 // positions that also received a repetition are rewritten with the combined
 // LLR by a second kernel (demap.cu), so this hot loop carries no repetition
-// work.
+// work.  Bit e < Ncb lands on buffer offset (k0 + e) mod Ncb: k0 is the start
+// of the redundancy version.  Here Ncb is taken as n_eff * Z - t0, which is
+// the buffer's length whenever the bits sent wrap it and otherwise covers
+// every offset sent, so the offsets agree.
 template <typename LT, int Qm>
 __device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, int r, float2 y, uint32_t mask_word) {
   const bool punct = (mask_word >> (r & 31)) & 1u;
@@ -126,7 +131,9 @@ __device__ __forceinline__ void demap_re(const DemapArgs& a, const CbDev& cb, in
 #pragma unroll
   for (int i = 0; i < Qm; ++i) {
     const int e = a.interleave ? i * cb.n_re + r : r * Qm + i;
-    if (e < ncb) out[e] = punct ? LT(0) : to_llr<LT>(lam[i], a.q_scale, a.llr_sat);
+    int q = cb.k0 + e;
+    q = q >= ncb ? q - ncb : q;
+    if (e < ncb) out[q] = punct ? LT(0) : to_llr<LT>(lam[i], a.q_scale, a.llr_sat);
   }
 }
 

@@ -30,7 +30,7 @@ struct ShapeDev {
   int32_t tab_off;    // first word of this shape's table
   int32_t row_off;    // row words, relative to tab_off
   int32_t tab_words;  // multiple of 4 (whole table, 16-byte granules)
-  int32_t crc_off;    // first word of its code-block CRC position table (kb * Z words)
+  int32_t crc_off;    // first word of its code-block CRC byte table (kb * Z * 32 words)
 };
 
 // Per code block geometry, computed on the host at batch creation.
@@ -40,7 +40,7 @@ struct CbDev {
   int32_t kb, flags;  // flags: LDPC_CB_CRC24B
   int64_t re_off, mask_off, llr_off, bits_off;
   float inv_sigma2;
-  int32_t pad1;
+  int32_t k0;  // start of the redundancy version in the circular buffer (0 for version 0)
 };
 
 // One decoder work item: `count` code blocks of one shape, listed from
@@ -85,7 +85,7 @@ struct DecodeArgs {
   int32_t hdr_bytes;        // edge table + mbarrier + item slot, 16-byte multiple
   int32_t max_iter, early_term;
   float beta, msg_sat, post_sat;
-  const uint32_t* cbcrc;    // code-block CRC position tables (ShapeDev::crc_off), for LDPC_CB_CRC24B blocks
+  const uint32_t* cbcrc;    // code-block CRC byte tables (ShapeDev::crc_off), for LDPC_CB_CRC24B blocks
 };
 
 struct DemapArgs {

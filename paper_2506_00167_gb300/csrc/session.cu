@@ -38,7 +38,7 @@ struct ldpc_session {
   uint32_t* d_crc_table = nullptr;
   uint32_t* d_crc_table_b = nullptr;  // byte table of the code-block generator g_B
   uint32_t* d_xpow32_b = nullptr;     // x^(32 m) mod g_B, m = 0..largest block's words
-  uint32_t* d_cbcrc = nullptr;        // per shape: x^(K-1-p) mod g_B, p = 0..K-1
+  uint32_t* d_cbcrc = nullptr;        // per shape: the code-block CRC byte table (K * 32 words)
   uint32_t* d_err = nullptr;
 };
 
@@ -170,16 +170,27 @@ std::vector<uint32_t> xpow32_table(int n, uint32_t gen = kGenA) {
   return t;
 }
 
-// Bit p of a K-bit block (first in time = highest degree) is the coefficient
-// of x^(K-1-p): appends x^(K-1-p) mod g_B for p = 0..K-1.
-void cb_crc_positions(int K, std::vector<uint32_t>& out) {
-  const size_t base = out.size();
-  out.resize(base + K);
-  uint32_t cur = 1;
+// Code-block CRC table of a K-bit block (first bit in time = highest
+// degree): bit p stands for x^(K-1-p), and byte j (bits 8j .. 8j+7, bit 8j+i
+// as bit i) with value v contributes XOR_{i: v_i = 1} x^(K-1-8j-i) mod g_B.
+// Appends those 256 values for every byte j: K * 32 words.
+void cb_crc_byte_table(int K, std::vector<uint32_t>& out) {
+  std::vector<uint32_t> single(K);
+  uint32_t cur = 1;  // x^0, for bit K-1
   for (int p = K - 1; p >= 0; --p) {
-    out[base + p] = cur;
+    single[p] = cur;
     cur <<= 1;
     if (cur & 0x1000000u) cur ^= kGenB;
+  }
+  const size_t base = out.size();
+  out.resize(base + static_cast<size_t>(K) * 32);
+  for (int j = 0; j < K / 8; ++j) {
+    uint32_t* t = out.data() + base + static_cast<size_t>(j) * 256;
+    t[0] = 0;
+    for (int v = 1; v < 256; ++v) {
+      const int i = __builtin_ctz(static_cast<unsigned>(v));
+      t[v] = t[v & (v - 1)] ^ single[8 * j + i];
+    }
   }
 }
 
@@ -594,7 +605,7 @@ int ldpc_session_create(const ldpc_session_desc* d, ldpc_session** out) {
       for (int Z : s->zset) {
         ShapeDev sh{};
         sh.crc_off = static_cast<int32_t>(cbcrc.size());
-        cb_crc_positions(g.kb * Z, cbcrc);
+        cb_crc_byte_table(g.kb * Z, cbcrc);
         max_cb_words = std::max(max_cb_words, g.kb * Z / 32);
         sh.bg = b;
         sh.Z = Z;
@@ -675,12 +686,26 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       if (c.E <= 0 || c.E % c.Qm || c.E > 2 * (g.nb * c.Z - t0))
         return bail(LDPC_EINVAL, at + "E must be a positive multiple of Qm with E <= 2 (nb*Z - t0)");
       if (c.re_offset < 0 || c.mask_word_offset < 0 || c.llr_offset < 0 || c.bits_word_offset < 0 ||
-          (c.flags & ~LDPC_CB_CRC24B))
+          (c.flags & ~(LDPC_CB_CRC24B | LDPC_CB_RV_MASK)))
         return bail(LDPC_EINVAL, at + "negative offset or unknown flag");
+      // start of the redundancy version: NR's table for buffers of 66 Z and 50 Z positions
+      const int rv = (c.flags & LDPC_CB_RV_MASK) >> LDPC_CB_RV_SHIFT;
+      const int ncb = g.nb * c.Z - t0;
+      int k0 = 0;
+      if (rv != 0) {
+        static const int units66[4] = {0, 17, 33, 56}, units50[4] = {0, 13, 25, 43};
+        if (g.nb - g.npc == 66)
+          k0 = units66[rv] * c.Z;
+        else if (g.nb - g.npc == 50)
+          k0 = units50[rv] * c.Z;
+        else
+          return bail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
+      }
       if ((c.llr_offset * esz) % 16) return bail(LDPC_EINVAL, at + "llr_offset must be 16-byte aligned");
       if ((g.kb * c.Z) % 32) return bail(LDPC_EINVAL, at + "kb*Z must be a multiple of 32");
       if (!(c.inv_sigma2 >= 0.f)) return bail(LDPC_EINVAL, at + "inv_sigma2 must be >= 0");
-      const int cols = (c.E + t0 + c.Z - 1) / c.Z;
+      // columns up to the last position sent; a version that wraps the buffer reaches them all
+      const int cols = k0 + c.E > ncb ? g.nb : (t0 + k0 + c.E + c.Z - 1) / c.Z;
       const int m_eff = std::min(g.mb, std::max(g.mc, cols - g.kb));
       if (g.maxcol_upto[m_eff - 1] >= g.kb + m_eff)
         return bail(LDPC_EINVAL, at + "a decoded row uses a column beyond the decoded ones (base graph order)");
@@ -695,6 +720,7 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
       d.n_re = c.E / c.Qm;
       d.kb = g.kb;
       d.flags = c.flags;
+      d.k0 = k0;
       d.re_off = c.re_offset;
       d.mask_off = c.mask_word_offset;
       d.llr_off = c.llr_offset;

@@ -16,7 +16,7 @@ from oracle import demap as odemap
 from oracle import goodput as ogood
 from oracle import path as opath
 from workload import large_fp32, mixed, tiny_fp32
-from workload.configs import repetition, segmented
+from workload.configs import redundancy_versions, repetition, segmented
 from workload.basegraph import tree_base_graph
 
 from gpu_helpers import LLR_NP, batch_for, device_inputs, session_for, to_np_u32
@@ -36,6 +36,8 @@ def _workloads():
         # segmented TBs with a CRC per code block: CRC-aided exit and the segmented TB check
         "segmented": segmented(n_tb=12, spread_db=(-2.0, 1.0)),
         "mixed_seg": mixed(n_slots=3, ues_per_slot=4, max_cb=3, cb_crc=True, spread_db=2.0),
+        # redundancy versions 0-3: buffer starts inside the buffer, wraps, repetition
+        "redundancy": redundancy_versions(n_per=2, rates=(0.5, 0.3, 0.2)),
     }
 
 
@@ -57,7 +59,7 @@ def _params(w):
 
 
 # ------------------------------------------------------------------ demap
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "redundancy"])
 def test_demap_f32_matches_oracle(wls, name):
     w = wls[name]
     s = session_for(w, "f32")
@@ -75,7 +77,7 @@ def test_demap_f32_matches_oracle(wls, name):
 
 
 @pytest.mark.parametrize("mode", ["i8", "i16"])
-@pytest.mark.parametrize("name", ["large", "mixed", "repetition"])
+@pytest.mark.parametrize("name", ["large", "mixed", "repetition", "redundancy"])
 def test_demap_quantised_within_one_lsb(wls, name, mode):
     w = wls[name]
     s = session_for(w, mode)
@@ -96,7 +98,7 @@ def test_demap_quantised_within_one_lsb(wls, name, mode):
 
 # ------------------------------------------------------------------ decode
 @pytest.mark.parametrize("mode", ["i8", "i16"])
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "segmented", "mixed_seg"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "segmented", "mixed_seg", "redundancy"])
 def test_decode_integer_bit_exact(wls, name, mode):
     w = wls[name]
     mi, et = _params(w)
@@ -113,7 +115,7 @@ def test_decode_integer_bit_exact(wls, name, mode):
     assert s.device_errors() == 0
 
 
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "segmented", "mixed_seg"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "repetition", "segmented", "mixed_seg", "redundancy"])
 def test_decode_f32_bit_exact_vs_oracle_float32(wls, name):
     w = wls[name]
     mi, et = _params(w)
@@ -181,7 +183,7 @@ def test_crc_goodput_reward_exact(wls, name):
 
 # ------------------------------------------------------------------ whole path
 @pytest.mark.parametrize("mode", ["f32", "i8"])
-@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "mixed_seg"])
+@pytest.mark.parametrize("name", ["tiny", "large", "mixed", "mixed_seg", "redundancy"])
 def test_full_path_matches_oracle(wls, name, mode):
     # both sides run the whole path from the same symbols and masks; each
     # demaps on its own (float32 here, float64 in the oracle), so a marginal

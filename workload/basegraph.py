@@ -82,18 +82,37 @@ class BaseGraph:
         """First transmitted codeword position."""
         return self.n_punct_cols * Z
 
-    def m_eff(self, Z: int, E: int) -> int:
-        """Rows decoded for a code block that sends E bits from position t0.
+    def ncb(self, Z: int) -> int:
+        """Length of the circular buffer: the positions [t0, nb*Z)."""
+        return self.nb * Z - self.t0(Z)
 
-        Columns at or beyond ceil((E + t0) / Z) are never transmitted; an
-        extension row whose own parity column is one of them only ever sends
-        0 to its other variables, so it is dropped.  Core rows are always kept.
+    def k0(self, Z: int, rv: int) -> int:
+        """Start of redundancy version rv in the circular buffer: NR's table (3GPP TS 38.212,
+        rate matching) for buffers of 66 Z and 50 Z positions, the sizes of its two base graphs;
+        other graphs send redundancy version 0 only."""
+        if rv == 0:
+            return 0
+        table = {66: (0, 17, 33, 56), 50: (0, 13, 25, 43)}
+        n = self.nb - self.n_punct_cols
+        if n not in table or not 0 <= rv <= 3:
+            raise ValueError("redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions")
+        return table[n][rv] * Z
+
+    def m_eff(self, Z: int, E: int, rv: int = 0) -> int:
+        """Rows decoded for a code block that sends E bits from buffer position k0(rv).
+
+        Columns beyond the last position sent are never transmitted (a
+        transmission that wraps the buffer reaches all of them); an extension
+        row whose own parity column is one of them only ever sends 0 to its
+        other variables, so it is dropped.  Core rows are always kept.
         """
-        cols = -(-(E + self.t0(Z)) // Z)
+        k0 = self.k0(Z, rv)
+        last = self.ncb(Z) if k0 + E > self.ncb(Z) else k0 + E
+        cols = -(-(last + self.t0(Z)) // Z)
         return min(self.mb, max(self.mc, cols - self.kb))
 
-    def n_eff(self, Z: int, E: int) -> int:
-        return self.kb + self.m_eff(Z, E)
+    def n_eff(self, Z: int, E: int, rv: int = 0) -> int:
+        return self.kb + self.m_eff(Z, E, rv)
 
 
 SHAPES = {

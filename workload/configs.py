@@ -44,6 +44,7 @@ CB_DTYPE = np.dtype([
     ("inv_sigma2", "<f4"), ("flags", "<i4"),
 ])
 CB_FLAG_CRC24B = 1  # the code block's last 24 bits are a CRC (0x800063) of its first K - 24
+CB_RV_SHIFT = 1     # flags bits 1-2: the redundancy version sent
 assert CB_DTYPE.itemsize == 56
 
 TB_DTYPE = np.dtype([
@@ -66,6 +67,7 @@ class TBSpec:
     sigma2: float
     sc0: int           # first subcarrier of the band in the slot grid
     width: int         # band width in subcarriers (= n_e, the SCs of the allocation)
+    rv: int = 0        # redundancy version of every code block of the TB
 
 
 @dataclass
@@ -103,8 +105,13 @@ class Workload:
         """(BaseGraph, Z, t0, m_eff, n_eff) of code block i."""
         c = self.cbs[i]
         bg = self.bgs[int(c["bg"])]
-        Z, E = int(c["Z"]), int(c["E"])
-        return bg, Z, bg.t0(Z), bg.m_eff(Z, E), bg.n_eff(Z, E)
+        Z, E, rv = int(c["Z"]), int(c["E"]), cb_rv(c)
+        return bg, Z, bg.t0(Z), bg.m_eff(Z, E, rv), bg.n_eff(Z, E, rv)
+
+
+def cb_rv(c) -> int:
+    """Redundancy version of a code-block descriptor."""
+    return (int(c["flags"]) >> CB_RV_SHIFT) & 3
 
 
 def default_bgs() -> list:
@@ -152,12 +159,12 @@ def build(name: str, bgs: list, specs: list, slot_widths: list, punct: list, see
         if sp.E % sp.Qm:
             raise ValueError("E must be a multiple of Qm")
         n_re = sp.E // sp.Qm
-        n_eff = bg.n_eff(sp.Z, sp.E)
+        n_eff = bg.n_eff(sp.Z, sp.E, sp.rv)
         seg = cb_crc and sp.n_cb > 1
         tb_rows.append((len(cb_rows), sp.n_cb, sp.width, sp.slot, sp.n_cb * (K - 24 * seg) - 24))
         for j in range(sp.n_cb):
             cb_rows.append((sp.bg, sp.Z, sp.Qm, sp.E, re_off, mask_off, llr_off, bits_off,
-                            np.float32(1.0 / sp.sigma2), CB_FLAG_CRC24B if seg else 0))
+                            np.float32(1.0 / sp.sigma2), (CB_FLAG_CRC24B if seg else 0) | (sp.rv << CB_RV_SHIFT)))
             per_cb.append((t, j, n_re))
             re_off += n_re
             mask_off += -(-n_re // 32)
@@ -194,13 +201,15 @@ def build(name: str, bgs: list, specs: list, slot_widths: list, punct: list, see
     # ---- encode / rate match / modulate per shape group
     groups: dict[tuple, list] = {}
     for i, c in enumerate(cbs):
-        groups.setdefault((int(c["bg"]), int(c["Z"]), int(c["E"]), int(c["Qm"])), []).append(i)
-    for (b, Z, E, Qm), idx in sorted(groups.items()):
+        groups.setdefault((int(c["bg"]), int(c["Z"]), int(c["E"]), int(c["Qm"]), cb_rv(c)), []).append(i)
+    for (b, Z, E, Qm, rv), idx in sorted(groups.items()):
         bg = bgs[b]
         info = np.stack([cb_info[i] for i in idx])
-        n_cols = min(bg.nb, -(-(E + bg.t0(Z)) // Z))  # E beyond the circular buffer repeats it
+        k0 = bg.k0(Z, rv)
+        # columns up to the last position sent (a transmission that wraps the buffer reaches them all)
+        n_cols = bg.nb if k0 + E > bg.ncb(Z) else -(-(bg.t0(Z) + k0 + E) // Z)
         cw = tx.encode(bg, Z, info, n_cols=n_cols)
-        e = tx.rate_match(bg, Z, cw, E)
+        e = tx.rate_match(bg, Z, cw, E, rv)
         re_bits = tx.interleave(e, Qm, interleave)
         x = tx.qam_map(re_bits)  # (B, n_re)
         sig2 = np.array([1.0 / float(cbs[i]["inv_sigma2"]) for i in idx])
@@ -456,6 +465,40 @@ def segmented(n_tb: int = 24, seed: int = 13, spread_db=(-1.0, 2.0), noiseless: 
         widths.append(width)
     w = build("segmented", bgs, specs, widths, punct, seed, snr_db=snrs, noiseless=noiseless, cb_crc=True)
     w.meta.update(dict(name="segmented", max_iter=10, early_term=1, mode="f32", offset=0.5))
+    return w
+
+
+def redundancy_versions(n_per: int = 3, seed: int = 14, noiseless: bool = False, rates=(0.5, 0.3)) -> Workload:
+    """Code blocks of every redundancy version: BG1-shaped Z=64 and BG2-shaped Z=32, R in ``rates``,
+    16-QAM, one code block per TB and slot, Es/N0 0-3 dB above the operating point, one URLLC mini-slot
+    run per slot.  Versions 1-3 start inside the circular buffer (leaving systematic columns unsent) and
+    wrap it."""
+    bgs = default_bgs()
+    rng = np_stream(seed, 6)
+    specs, widths, punct, snrs = [], [], [], []
+    for b, Z in [(0, 64), (1, 32)]:
+        bg = bgs[b]
+        for R in rates:
+            Qm = 4
+            K = bg.kb * Z
+            E = Qm * int(round(K / (R * Qm)))
+            n_re = E // Qm
+            width = 12 * -(-n_re // (12 * N_SYM))
+            for rv in range(4):
+                for _ in range(n_per):
+                    slot = len(specs)
+                    snr = operating_point_db(R, Qm) + float(rng.uniform(0.0, 3.0))
+                    specs.append(TBSpec(slot, b, Z, Qm, E, 1, float(es_n0_sigma2(snr)), 0, width, rv))
+                    snrs.append(snr)
+                    P = np.zeros((N_SYM, width), dtype=bool)
+                    m = int(rng.integers(0, N_MINISLOT))
+                    ln = min(12, width)
+                    st = int(rng.integers(0, width - ln + 1))
+                    P[2 * m:2 * m + 2, st:st + ln] = True
+                    punct.append(P)
+                    widths.append(width)
+    w = build("redundancy", bgs, specs, widths, punct, seed, snr_db=snrs, noiseless=noiseless)
+    w.meta.update(dict(name="redundancy", max_iter=10, early_term=1, mode="f32", offset=0.5))
     return w
 
 

@@ -17,10 +17,11 @@ Conventions fixed here (and restated by the receiver side):
   generator 0x800063 over them (same conventions), so ``A + 24 = n_cb (K - 24)``.
 * Systematic encoding: ``c[0:K] = info``; core parity by the dual-diagonal
   closed form; extension parity is the sum of its row's other blocks.
-* Rate matching (redundancy version 0): bit ``e`` of the ``E`` transmitted
-  bits is codeword position ``t0 + (e mod Ncb)`` with ``t0 = n_punct_cols * Z``
-  and ``Ncb = nb * Z - t0``: positions ``[t0, t0 + E)`` when ``E <= Ncb``, a
-  second pass over the buffer from its start otherwise (``E <= 2 Ncb``).
+* Rate matching: bit ``e`` of the ``E`` transmitted bits is codeword position
+  ``t0 + ((k0 + e) mod Ncb)`` with ``t0 = n_punct_cols * Z``, ``Ncb = nb * Z -
+  t0`` and ``k0`` the start of the redundancy version (0 for version 0; NR's
+  table for versions 1-3, see ``BaseGraph.k0``): positions ``[t0, t0 + E)`` for
+  version 0 and ``E <= Ncb``, around the buffer otherwise (``E <= 2 Ncb``).
 * Interleaver (flag, default on): the E bits are written row-wise into ``Qm``
   rows of ``E / Qm`` and read column-wise, so resource element ``r`` carries
   bits ``e[i * (E / Qm) + r]`` for ``i < Qm``.
@@ -119,19 +120,19 @@ def encode(bg: BaseGraph, Z: int, info: np.ndarray, n_cols: int | None = None) -
 
 
 # --------------------------------------------------------------------------- rate match + QAM
-def rate_match(bg: BaseGraph, Z: int, cw: np.ndarray, E: int) -> np.ndarray:
-    """Redundancy version 0 from a circular buffer of the codeword positions [t0, nb*Z): bit e is
-    position t0 + (e mod Ncb), Ncb = nb*Z - t0, so E > Ncb repeats the buffer from its start (at most
-    once: E <= 2 Ncb)."""
+def rate_match(bg: BaseGraph, Z: int, cw: np.ndarray, E: int, rv: int = 0) -> np.ndarray:
+    """Redundancy version rv from a circular buffer of the codeword positions [t0, nb*Z): bit e is
+    position t0 + ((k0 + e) mod Ncb), Ncb = nb*Z - t0, so a version that runs past the buffer's end
+    continues from its start (at most two passes: E <= 2 Ncb)."""
     t0 = bg.t0(Z)
-    ncb = bg.nb * Z - t0
+    ncb = bg.ncb(Z)
+    k0 = bg.k0(Z, rv)
     if E > 2 * ncb:
         raise ValueError("E exceeds two passes over the circular buffer")
-    if t0 + E <= cw.shape[1]:
-        return cw[:, t0:t0 + E]
-    if cw.shape[1] < bg.nb * Z:
-        raise ValueError("repetition needs the whole codeword")
-    return cw[:, t0 + np.arange(E) % ncb]
+    pos = t0 + (k0 + np.arange(E)) % ncb
+    if pos.max() >= cw.shape[1]:
+        raise ValueError("the codeword does not reach the positions sent")
+    return cw[:, pos]
 
 
 def interleave(e: np.ndarray, Qm: int, enabled: bool = True) -> np.ndarray:
