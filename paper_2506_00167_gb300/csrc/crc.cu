@@ -11,14 +11,15 @@
 // block's first K - 24 bits only, and each block's K bits must also be a
 // multiple of g_B(x): d_e needs every check to pass.
 //
-// One block per slot, one warp per TB.  The TB's bytes, prefixed by the zero
-// bytes that make them whole words (leading zeros leave a zero register
-// unchanged), are split into 32 runs of whole words; each lane runs its run
-// through a byte-table LFSR from state 0, giving seg(x) * x^24 mod g, shifts
-// it into place by one GF(2) multiply with x^(32 * words after the run) mod g
-// (a per-batch table) and the warp xor-reduces.  A block's own CRC is the
-// same over its K / 32 words with g_B's tables.  No atomics: the block
-// reduces the slot's sums in shared memory, so results are deterministic.
+// One block per slot, one warp per TB.  The TB's blocks' words, back to
+// back, are split into 32 runs of whole words; each lane runs the TB bytes of
+// its run (all four of a word, one of a segmented block's last word) through
+// a byte-table LFSR from state 0, giving seg(x) * x^24 mod g, shifts it into
+// place -- times x^(8 * TB bytes after the run) mod g: one GF(2) multiply by
+// x^(32 m) from a per-batch table, then a zero byte per remaining byte -- and
+// the warp xor-reduces.  A block's own CRC is the same over its K / 32 words
+// with g_B's tables.  No atomics: the block reduces the slot's sums in shared
+// memory, so results are deterministic.
 #include "crc_core.cuh"
 
 namespace ldpcgb {
@@ -58,18 +59,20 @@ __global__ void __launch_bounds__(kCrcBlock) tb_crc_goodput_kernel(const CrcArgs
 
   for (int i = t0 + warp; i < t1; i += kCrcBlock / 32) {
     const TbDev tb = a.tbs[a.slot_tbs[i]];
-    const int pad = (-tb.bytes) & 3;
-    const int W = (tb.bytes + pad) >> 2;
+    // the TB's blocks' words back to back, W in all; the last word of a block
+    // with its own CRC holds one TB byte (its other three are that CRC)
+    int W = 0;
+    for (int c = tb.first_cb; c < tb.first_cb + tb.n_cb; ++c) W += (a.cbs[c].kb * a.cbs[c].Z) >> 5;
     const int per = (W + 31) >> 5;
     const int w0 = min(W, lane * per);
     const int w1 = min(W, w0 + per);
     uint32_t state = 0;
-    if (w0 < w1 && !tb.seg) {
-      // whole code blocks: every block's words in order (pad is 0)
+    int after = 0;  // TB bytes after this lane's words
+    {
       int cbi = tb.first_cb;
       int cb_first = 0;
       int cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
-      while (w0 >= cb_first + cb_words) {
+      while (w0 >= cb_first + cb_words && cbi + 1 < tb.first_cb + tb.n_cb) {
         cb_first += cb_words;
         ++cbi;
         cb_words = (a.cbs[cbi].kb * a.cbs[cbi].Z) >> 5;
@@ -83,42 +86,17 @@ __global__ void __launch_bounds__(kCrcBlock) tb_crc_goodput_kernel(const CrcArgs
           src = a.bits + a.cbs[cbi].bits_off;
         }
         const uint32_t v = src[w - cb_first];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) state = crc_byte_step(state, msb_first_byte(v, j), s_tab);
+        const int nbytes = (tb.seg && w == cb_first + cb_words - 1) ? 1 : 4;
+        for (int j = 0; j < nbytes; ++j) state = crc_byte_step(state, msb_first_byte(v, j), s_tab);
       }
-      state = gf2_mulmod(state, a.xpow32[W - w1]);
-    } else if (w0 < w1) {
-      // segments of K/8 - 3 bytes: byte by byte
-      const int b_end = 4 * w1 - pad;
-      int b = max(0, 4 * w0 - pad);
-      // find the code block holding TB byte b
-      int cbi = tb.first_cb;
-      int cb_first = 0;
-      int cb_bytes = tb_bytes_of(a.cbs[cbi], tb.seg);
-      while (b >= cb_first + cb_bytes) {
-        cb_first += cb_bytes;
-        ++cbi;
-        cb_bytes = tb_bytes_of(a.cbs[cbi], tb.seg);
-      }
-      const uint32_t* src = a.bits + a.cbs[cbi].bits_off;
-      int jw = -1;
-      uint32_t word = 0;
-      for (; b < b_end; ++b) {
-        if (b >= cb_first + cb_bytes) {
-          cb_first += cb_bytes;
-          ++cbi;
-          cb_bytes = tb_bytes_of(a.cbs[cbi], tb.seg);
-          src = a.bits + a.cbs[cbi].bits_off;
-          jw = -1;
-        }
-        const int j = b - cb_first;
-        if ((j >> 2) != jw) {
-          jw = j >> 2;
-          word = src[jw];
-        }
-        state = crc_byte_step(state, msb_first_byte(word, j), s_tab);
-      }
-      state = gf2_mulmod(state, a.xpow32[W - w1]);
+      // TB bytes after word w1: the rest of block cbi, then whole blocks
+      if (w1 < cb_first + cb_words) after = 4 * (cb_first + cb_words - w1) - 3 * tb.seg;
+      for (int c = cbi + 1; c < tb.first_cb + tb.n_cb; ++c) after += tb_bytes_of(a.cbs[c], tb.seg);
+    }
+    if (w0 < w1) {
+      // times x^(8 * after): x^(32 * (after / 4)) by table, then one zero byte per remaining byte
+      state = gf2_mulmod(state, a.xpow32[after >> 2]);
+      for (int j = 0; j < (after & 3); ++j) state = crc_byte_step(state, 0u, s_tab);
     }
     uint32_t d = warp_xor(state) == 0u ? 1u : 0u;
     if (tb.seg) {

@@ -313,3 +313,30 @@ def test_invalid_descriptors_rejected_on_host():
     tbs["payload_bits"][0] += 1
     with pytest.raises(LdpcError, match="payload"):
         s.batch(w.cbs, tbs, w.slot_N)
+
+
+def test_invalid_block_flags_rejected_on_host(wls):
+    from paper_2506_00167_gb300 import LdpcError
+    w = wls["segmented"]
+    s = session_for(w, "f32")
+    bad = w.cbs.copy()
+    bad["flags"][0] |= 8                                    # no such flag
+    with pytest.raises(LdpcError, match="flag"):
+        s.batch(bad)
+    # a TB whose blocks disagree on carrying a CRC
+    bad = w.cbs.copy()
+    bad["flags"][int(w.tbs["first_cb"][0])] = 0
+    with pytest.raises(LdpcError, match="all or none"):
+        s.batch(bad, w.tbs, w.slot_N)
+    # payload_bits must account for the block CRCs
+    tbs = w.tbs.copy()
+    tbs["payload_bits"][0] += 24
+    with pytest.raises(LdpcError, match="payload"):
+        s.batch(w.cbs, tbs, w.slot_N)
+    # redundancy versions 1-3 need a 66 Z or 50 Z buffer: not the tiny graph's
+    t = wls["tiny"]
+    st = session_for(t, "f32")
+    bad = t.cbs.copy()
+    bad["flags"][0] = 1 << 1
+    with pytest.raises(LdpcError, match="redundancy"):
+        st.batch(bad)
