@@ -45,17 +45,21 @@ def tb_bitstream(w, words, t) -> np.ndarray:
     return np.concatenate(parts)
 
 
-def tb_crc_goodput(w, words):
-    """(d uint8 (n_tb,), goodput_bits int64 (n_slots,), goodput_sc int64 (n_slots,), reward float64 (n_slots,))."""
+def tb_crc_goodput(w, words, tb_index=None):
+    """(d uint8 (n_tb,), goodput_bits int64 (n_slots,), goodput_sc int64 (n_slots,), reward float64 (n_slots,)).
+
+    ``tb_index``: check only the listed TBs; the others get d = 0 and the per-slot sums cover the listed
+    ones only."""
     d = np.zeros(w.n_tb, dtype=np.uint8)
+    listed = range(w.n_tb) if tb_index is None else [int(t) for t in tb_index]
     by_len: dict = {}
-    for t in range(w.n_tb):
+    for t in listed:
         s = tb_bitstream(w, words, t)
         by_len.setdefault(s.size, []).append((t, s))
     for _, items in by_len.items():
         ts = [t for t, _ in items]
         d[ts] = crc.tb_ok(np.stack([s for _, s in items]))
-    for t in range(w.n_tb):
+    for t in listed:
         tb = w.tbs[t]
         for i in range(int(tb["first_cb"]), int(tb["first_cb"]) + int(tb["n_cb"])):
             if int(w.cbs[i]["flags"]) & 1 and not crc.cb_ok(cb_bits(w, words, i))[0]:
@@ -64,7 +68,7 @@ def tb_crc_goodput(w, words):
     gb = np.zeros(n_slots, dtype=np.int64)
     gs = np.zeros(n_slots, dtype=np.int64)
     fail_sc = np.zeros(n_slots, dtype=np.int64)
-    for t in range(w.n_tb):
+    for t in listed:
         tb = w.tbs[t]
         s = int(tb["slot"])
         n_e = int(tb["n_sc"])
