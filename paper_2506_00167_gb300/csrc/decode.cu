@@ -18,9 +18,9 @@
 //   distinct banks (Z a multiple of 32);
 // * the launch's edge tables and every group's channel LLRs are staged into
 //   shared memory by bulk (TMA-engine) copies completing on one mbarrier;
-// * the edges of a row are read four at a time (two 128-bit loads: column
-//   bases, shifts); rows are padded to a multiple of four with edges that read
-//   a per-group dummy slot whose value can never be a row minimum;
+// * the edges of a row are read two at a time (one 128-bit load: two column
+//   bases, two shifts); rows are padded to an even degree with an edge that
+//   reads a per-group dummy slot whose value can never be a row minimum;
 // * check-to-variable messages are stored compressed per check: the two
 //   smallest offset magnitudes, the argmin edge and one sign bit per edge
 //   (12 bytes FP32, 6 bytes INT8, 8 bytes INT16 per check) -- in shared

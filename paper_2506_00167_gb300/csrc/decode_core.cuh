@@ -62,10 +62,33 @@ __device__ __forceinline__ int rot(int k, uint32_t s, int Z) {
 // thread's compressed message record.  None of it is written by other threads
 // during a layer, so the next row's copy is loaded before the layer barrier
 // and only the posterior loads wait for it.
+static_assert(kChunk == 2 || kChunk == 4, "edge-table chunks of 2 or 4 edges");
+
+struct Chunk {
+  uint32_t b[kChunk], s[kChunk];  // column bases, shifts
+};
+
+__device__ __forceinline__ Chunk load_chunk(const uint32_t* tab, int c) {
+  Chunk ch;
+  if constexpr (kChunk == 2) {
+    const uint4 v = *reinterpret_cast<const uint4*>(tab + 4 * c);
+    ch.b[0] = v.x;
+    ch.b[1] = v.y;
+    ch.s[0] = v.z;
+    ch.s[1] = v.w;
+  } else {
+    const uint4 B = *reinterpret_cast<const uint4*>(tab + 8 * c);
+    const uint4 S = *reinterpret_cast<const uint4*>(tab + 8 * c + 4);
+    ch.b[0] = B.x, ch.b[1] = B.y, ch.b[2] = B.z, ch.b[3] = B.w;
+    ch.s[0] = S.x, ch.s[1] = S.y, ch.s[2] = S.z, ch.s[3] = S.w;
+  }
+  return ch;
+}
+
 struct RowIn {
   const uint32_t* tab;
   int deg;
-  uint4 B, S;
+  Chunk c0;
   float r1, r2;
   uint32_t mo;
 };
@@ -77,8 +100,7 @@ __device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, ui
   RowIn r;
   r.tab = s_tab + (info & 0xFFFFu);
   r.deg = static_cast<int>(info >> 16);
-  r.B = *reinterpret_cast<const uint4*>(r.tab);
-  r.S = *reinterpret_cast<const uint4*>(r.tab + 4);
+  r.c0 = load_chunk(r.tab, 0);
   if constexpr (sizeof(MT) == 4) {  // float: both magnitudes in one 8-byte record
     const float2 rr = reinterpret_cast<const float2*>(mag1)[rec];
     r.r1 = rr.x;
@@ -91,9 +113,8 @@ __device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, ui
   return r;
 }
 
-// One lifted check (l, k): row data in `in` (chunk c's column bases at
-// tab[8c .. 8c+3], shifts at tab[8c+4 .. 8c+7]).  Runs both passes, writes
-// the posteriors and the new record.
+// One lifted check (l, k): row data in `in` (chunk c at tab[2 kChunk c ..]).
+// Runs both passes, writes the posteriors and the new record.
 //
 // The record keeps the signs of the Q_j of the last update (edge j at bit
 // deg-1-j) and the argmin edge in bits 27..31; the sign of the stored message
@@ -125,27 +146,24 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
   // large whatever the sign
   const uint32_t par_o = 0u - (static_cast<uint32_t>(__popc(mo << 5)) & 1u);
   uint32_t sgn = SAT ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u)) : ((mo ^ par_o) << (32 - deg));
-  const int nch = (deg + 3) >> 2;
+  const int nch = (deg + kChunk - 1) / kChunk;
 
-  float q[LEAN ? 1 : kMaxChunks * 4];
-  int addr[kMaxChunks * 4];
+  float q[LEAN ? 1 : kMaxChunks * kChunk];
+  int addr[kMaxChunks * kChunk];
   float min1 = 3.0e38f, min2 = 3.0e38f;  // SAT modes: keys |Q| * 32 + j
   uint32_t qs = 0;                       // Q sign bits, first edge highest
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
-    const uint4 B = c == 0 ? in.B : *reinterpret_cast<const uint4*>(tab + 8 * c);
-    const uint4 S = c == 0 ? in.S : *reinterpret_cast<const uint4*>(tab + 8 * c + 4);
-    addr[4 * c + 0] = static_cast<int>(B.x) + rot(k, S.x, Z);
-    addr[4 * c + 1] = static_cast<int>(B.y) + rot(k, S.y, Z);
-    addr[4 * c + 2] = static_cast<int>(B.z) + rot(k, S.z, Z);
-    addr[4 * c + 3] = static_cast<int>(B.w) + rot(k, S.w, Z);
-    float lv[4];
+    const Chunk ch = c == 0 ? in.c0 : load_chunk(tab, c);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) lv[i] = ld_val(L, addr[4 * c + i]);
+    for (int i = 0; i < kChunk; ++i) addr[kChunk * c + i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
+    float lv[kChunk];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = 4 * c + i;
+    for (int i = 0; i < kChunk; ++i) lv[i] = ld_val(L, addr[kChunk * c + i]);
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i) {
+      const int j = kChunk * c + i;
       const float m = (j == idx_o) ? r2 : r1;
       const float r = __uint_as_float(__float_as_uint(m) | (sgn & 0x80000000u));
       sgn <<= 1;
@@ -182,12 +200,12 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
-    float qv[4];
+    float qv[kChunk];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) qv[i] = LEAN ? ld_val(L, addr[4 * c + i]) : q[LEAN ? 0 : 4 * c + i];
+    for (int i = 0; i < kChunk; ++i) qv[i] = LEAN ? ld_val(L, addr[kChunk * c + i]) : q[LEAN ? 0 : kChunk * c + i];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = 4 * c + i;
+    for (int i = 0; i < kChunk; ++i) {
+      const int j = kChunk * c + i;
       bool is_min;
       if (SAT) {
         is_min = (j == idx);
@@ -208,7 +226,7 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
     st_val(mag1, rec, n1);
     st_val(mag2, rec, n2);
   }
-  meta[rec] = (qs >> (4 * nch - deg)) | (static_cast<uint32_t>(idx) << 27);
+  meta[rec] = (qs >> (kChunk * nch - deg)) | (static_cast<uint32_t>(idx) << 27);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
@@ -228,8 +246,8 @@ __device__ __forceinline__ void zero_records(MT* mag1, MT* mag2, uint32_t* meta,
 
 // Edge e of a row whose chunks start at `tab`: (column base, shift).
 __device__ __forceinline__ uint2 edge_at(const uint32_t* tab, int e) {
-  const int c = e >> 2, i = e & 3;
-  return make_uint2(tab[8 * c + i], tab[8 * c + 4 + i]);
+  const int c = e / kChunk, i = e % kChunk;
+  return make_uint2(tab[2 * kChunk * c + i], tab[2 * kChunk * c + kChunk + i]);
 }
 
 // Z % 32 == 0: hard decisions of all n_eff columns into the bitmap hb
@@ -425,8 +443,8 @@ __device__ __forceinline__ PairIn load_pair_row(const uint32_t* __restrict__ s_t
 
 // Address of edge e of a row (tab = the row's chunks) for check k.
 __device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int Z) {
-  const uint32_t* t = tab + 8 * (e >> 2) + (e & 3);
-  return static_cast<int>(t[0]) + rot(k, t[4], Z);
+  const uint32_t* t = tab + 2 * kChunk * (e / kChunk) + (e % kChunk);
+  return static_cast<int>(t[0]) + rot(k, t[kChunk], Z);
 }
 
 // Stored form (v2): magnitudes as above; Q-sign history of the last update,
@@ -456,26 +474,23 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const __half2 I = __hsub2(as_h2((s2 & 0x001F001Fu) | 0x64006400u), h1024);
   const __half2 h32 = __float2half2_rn(32.0f);
   const __half2 npost = __hneg2(post);
-  const int nch = (deg + 3) >> 2;
+  const int nch = (deg + kChunk - 1) / kChunk;
 
-  int addr[kMaxChunks * 4];
+  int addr[kMaxChunks * kChunk];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
   uint32_t acc1 = 0, acc2 = 0;  // Q signs: each new edge enters at bits 15 / 31
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
-    const uint4 B = *reinterpret_cast<const uint4*>(tab + 8 * c);
-    const uint4 S = *reinterpret_cast<const uint4*>(tab + 8 * c + 4);
-    addr[4 * c + 0] = static_cast<int>(B.x) + rot(k, S.x, Z);
-    addr[4 * c + 1] = static_cast<int>(B.y) + rot(k, S.y, Z);
-    addr[4 * c + 2] = static_cast<int>(B.z) + rot(k, S.z, Z);
-    addr[4 * c + 3] = static_cast<int>(B.w) + rot(k, S.w, Z);
-    uint32_t lv[4];
+    const Chunk ch = load_chunk(tab, c);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) lv[i] = L[addr[4 * c + i]];
+    for (int i = 0; i < kChunk; ++i) addr[kChunk * c + i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
+    uint32_t lv[kChunk];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = 4 * c + i;
+    for (int i = 0; i < kChunk; ++i) lv[i] = L[addr[kChunk * c + i]];
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i) {
+      const int j = kChunk * c + i;
       const __half2 J = __float2half2_rn(static_cast<float>(j));
       const uint32_t eq = __heq2_mask(I, J);
       // (edge 27 can only be padding, whose sign does not matter)
@@ -510,15 +525,15 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
-    uint32_t qv[4];
+    uint32_t qv[kChunk];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) qv[i] = L[addr[4 * c + i]];
+    for (int i = 0; i < kChunk; ++i) qv[i] = L[addr[kChunk * c + i]];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kChunk; ++i) {
       const uint32_t rb = N1s ^ (qv[i] & 0x80008000u);
       __half2 v = __hadd2(as_h2(qv[i]), as_h2(rb));
       v = __hmin2(__hmax2(v, npost), post);
-      L[addr[4 * c + i]] = as_u32(v);  // padding edges write the dummy slot
+      L[addr[kChunk * c + i]] = as_u32(v);  // padding edges write the dummy slot
     }
   }
   {
@@ -527,7 +542,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     L[aA] = (L[aA] & 0xFFFF0000u) | (v & 0x0000FFFFu);
     L[aB] = (L[aB] & 0x0000FFFFu) | (v & 0xFFFF0000u);
   }
-  const int n_all = 4 * nch;
+  const int n_all = kChunk * nch;
   const int n1 = n_all < 16 ? n_all : 16;
   const int n2 = n_all - 16;
   mags[rec] = nA1 | (nB1 << 8) | (nA2 << 16) | (nB2 << 24);

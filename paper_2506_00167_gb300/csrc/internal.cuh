@@ -12,7 +12,8 @@
 namespace ldpcgb {
 
 constexpr int kMaxDeg = 27;      // sign bits 0..26 + 5-bit argmin index in one word
-constexpr int kMaxChunks = 7;    // edges are processed four at a time: 7 * 4 >= kMaxDeg
+constexpr int kChunk = 2;        // edges per edge-table chunk: kChunk column bases, then kChunk shifts
+constexpr int kMaxChunks = (kMaxDeg + kChunk - 1) / kChunk;
 constexpr int kMaxZ = 384;
 constexpr int kMaxSmem = 232448; // 227 KB dynamic shared memory per block (sm_100 family)
 constexpr int kDecodeMaxBlock = 384;  // decoder blocks: two of them share an SM's registers
@@ -20,11 +21,11 @@ constexpr int kTileMaxBlock = 512;    // largest G * Z a tile may request
 constexpr int kCrcBlock = 256;
 
 // One (base graph, Z) pair as one decoder launch sees it.  Its edge table is,
-// per row, chunks of four edges as 8 words: four column bases (col * Z) then
-// four shifts (V mod Z); a row's last chunk is padded with edges whose base
-// is the launch's dummy slot and whose shift is 0.  Then one word per row,
-// start | (degree << 16) (start in words from the table base); then padding
-// to a multiple of 4 words.
+// per row, chunks of kChunk edges as 2 * kChunk words (one 16-byte load for
+// kChunk = 2): the column bases (col * Z), then the shifts (V mod Z); a row's
+// last chunk is padded with edges whose base is the launch's dummy slot and
+// whose shift is 0.  Then one word per row, start | (degree << 16) (start in
+// words from the table base); then padding to a multiple of 4 words.
 struct ShapeDev {
   int32_t bg, Z, mb, nb, kb, mc, npc;
   int32_t tab_off;    // first word of this shape's table

@@ -202,13 +202,14 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     for (int r = 0; r < mb; ++r) {
       const int deg = static_cast<int>(cols[r].size());
       const int start = words;
-      for (int c = 0; c < (deg + 3) / 4; ++c) {
-        if (words + 8 > kMaxTabWords) {
+      // chunks of kChunk edges: the column bases, then the shifts (the decoder's table layout)
+      for (int c = 0; c < (deg + kChunk - 1) / kChunk; ++c) {
+        if (words + 2 * kChunk > kMaxTabWords) {
           set_error("decode_uniform_noalloc: edge table too large");
           return LDPC_EINVAL;
         }
-        for (int i = 0; i < 4; ++i) sa.tab[words++] = 4 * c + i < deg ? cols[r][4 * c + i] : dummy;
-        for (int i = 0; i < 4; ++i) sa.tab[words++] = 4 * c + i < deg ? shs[r][4 * c + i] : 0;
+        for (int i = 0; i < kChunk; ++i) sa.tab[words++] = kChunk * c + i < deg ? cols[r][kChunk * c + i] : dummy;
+        for (int i = 0; i < kChunk; ++i) sa.tab[words++] = kChunk * c + i < deg ? shs[r][kChunk * c + i] : 0;
       }
       rowinfo.push_back(static_cast<uint32_t>(start) | (static_cast<uint32_t>(deg) << 16));
     }

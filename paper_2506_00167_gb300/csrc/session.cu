@@ -195,8 +195,9 @@ void cb_crc_byte_table(int K, std::vector<uint32_t>& out) {
 }
 
 // Edge table of base graph g at lifting Z for a launch whose dummy slot is at
-// element `dummy`: per row, chunks of 4 edges (4 bases, 4 shifts), the last
-// chunk padded with (dummy, 0); then one word per row: start | deg << 16.
+// element `dummy`: per row, chunks of kChunk edges (kChunk bases, kChunk
+// shifts), the last chunk padded with (dummy, 0); then one word per row:
+// start | deg << 16.
 void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh) {
   sh.tab_off = static_cast<int32_t>(tabs.size());
   std::vector<uint32_t> row_info;
@@ -210,9 +211,15 @@ void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32
     }
     const int deg = static_cast<int>(cols.size());
     const int start = static_cast<int>(tabs.size()) - sh.tab_off;
-    for (int c = 0; c < (deg + 3) / 4; ++c) {
-      for (int i = 0; i < 4; ++i) tabs.push_back(static_cast<uint32_t>(4 * c + i < deg ? cols[4 * c + i] : dummy));
-      for (int i = 0; i < 4; ++i) tabs.push_back(static_cast<uint32_t>(4 * c + i < deg ? sh_[4 * c + i] : 0));
+    for (int c = 0; c < (deg + kChunk - 1) / kChunk; ++c) {
+      for (int i = 0; i < kChunk; ++i) {
+        const int j = kChunk * c + i;
+        tabs.push_back(static_cast<uint32_t>(j < deg ? cols[j] : dummy));
+      }
+      for (int i = 0; i < kChunk; ++i) {
+        const int j = kChunk * c + i;
+        tabs.push_back(static_cast<uint32_t>(j < deg ? sh_[j] : 0));
+      }
     }
     row_info.push_back(static_cast<uint32_t>(start) | (static_cast<uint32_t>(deg) << 16));
   }
