@@ -19,8 +19,10 @@
 // * the launch's edge tables and every group's channel LLRs are staged into
 //   shared memory by bulk (TMA-engine) copies completing on one mbarrier;
 // * the edges of a row are read two at a time (one 128-bit load: two column
-//   bases, two shifts); rows are padded to an even degree with an edge that
-//   reads a per-group dummy slot whose value can never be a row minimum;
+//   bases, two shifts); the table pads rows to an even degree with an edge
+//   on a per-group dummy slot whose value can never be a row minimum, which
+//   the paired INT8 kernel processes (cheaper than a run-time tail there) and
+//   this kernel skips (an odd row's last edge runs after its whole chunks);
 // * check-to-variable messages are stored compressed per check: the two
 //   smallest offset magnitudes, the argmin edge and one sign bit per edge
 //   (12 bytes FP32, 6 bytes INT8, 8 bytes INT16 per check) -- in shared

@@ -113,8 +113,49 @@ __device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, ui
   return r;
 }
 
+// Pass 1 for edge j at posterior slot a (value lv): Q_j = L - R_j, its sign
+// into qs, |Q_j| (integer modes: the key |Q_j| * 32 + j) into the two minima.
+template <typename LT, bool SAT, bool LEAN>
+__device__ __forceinline__ float pass1_edge(LT* __restrict__ L, int a, float lv, int j, int idx_o, float r1,
+                                            float r2, uint32_t& sgn, float& min1, float& min2, uint32_t& qs,
+                                            float msg_sat, float post_sat) {
+  const float m = (j == idx_o) ? r2 : r1;
+  const float r = __uint_as_float(__float_as_uint(m) | (sgn & 0x80000000u));
+  sgn <<= 1;
+  float Q = lv - r;
+  if (SAT) Q = fminf(fmaxf(Q, -post_sat), post_sat);
+  if constexpr (LEAN) st_val(L, a, Q);  // Q waits in the posterior's slot for pass 2
+  qs = __funnelshift_l(__float_as_uint(Q), qs, 1);
+  float v = fabsf(Q);
+  if (SAT) v = fmaf(fminf(v, msg_sat), 32.0f, static_cast<float>(j));
+  min2 = fminf(min2, fmaxf(min1, v));
+  min1 = fminf(min1, v);
+  return Q;
+}
+
+// Pass 2 for edge j: L = Q_j + R'_j, R'_j the other edges' minimum carrying
+// the parity and Q_j's sign.
+template <typename LT, bool SAT>
+__device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, int j, int& idx, float min1,
+                                           float n1s, float n2s, float post_sat) {
+  bool is_min;
+  if (SAT) {
+    is_min = (j == idx);
+  } else {
+    is_min = (fabsf(qv) == min1);
+    idx = is_min ? j : idx;
+  }
+  const float m = is_min ? n2s : n1s;
+  const uint32_t rb = __float_as_uint(m) ^ (__float_as_uint(qv) & 0x80000000u);
+  float v = qv + __uint_as_float(rb);
+  if (SAT) v = fminf(fmaxf(v, -post_sat), post_sat);
+  st_val(L, a, v);
+}
+
 // One lifted check (l, k): row data in `in` (chunk c at tab[2 kChunk c ..]).
-// Runs both passes, writes the posteriors and the new record.
+// Runs both passes, writes the posteriors and the new record.  The whole
+// chunks run unrolled; the deg % kChunk edges of a last, partial chunk run
+// after them (the table's padding entries are never touched).
 //
 // The record keeps the signs of the Q_j of the last update (edge j at bit
 // deg-1-j) and the argmin edge in bits 27..31; the sign of the stored message
@@ -131,30 +172,26 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
                                              float msg_sat, float post_sat) {
-  // integer modes: the dummy slot is reset to +post_sat so a padding edge's
-  // |Q| saturates at msg_sat and (edge index larger) never beats a real edge;
-  // float: 1e30 absorbs every update and needs no reset
-  if constexpr (SAT) st_val(L, dummy, post_sat);
+  (void)dummy;
   const uint32_t* tab = in.tab;
   const int deg = in.deg;
   const float r1 = in.r1, r2 = in.r2;
   const uint32_t mo = in.mo;
   const int idx_o = static_cast<int>(mo >> 27);
-  // sign of R_j = stored Q-sign bit ^ parity, edge 0's moved to bit 31.  In
-  // the integer modes the positions past deg read as negative, so padding
-  // edges see Q = dummy + |R| (large and positive); the float dummy (1e30) is
-  // large whatever the sign
+  // sign of R_j = stored Q-sign bit ^ parity, edge 0's moved to bit 31
   const uint32_t par_o = 0u - (static_cast<uint32_t>(__popc(mo << 5)) & 1u);
-  uint32_t sgn = SAT ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u)) : ((mo ^ par_o) << (32 - deg));
-  const int nch = (deg + kChunk - 1) / kChunk;
+  uint32_t sgn = (mo ^ par_o) << (32 - deg);
+  const int nfull = deg / kChunk;
+  const int ntail = deg - kChunk * nfull;
 
   float q[LEAN ? 1 : kMaxChunks * kChunk];
   int addr[kMaxChunks * kChunk];
+  int addr_t[kChunk - 1];  // the partial chunk's edges
   float min1 = 3.0e38f, min2 = 3.0e38f;  // SAT modes: keys |Q| * 32 + j
   uint32_t qs = 0;                       // Q sign bits, first edge highest
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
-    if (c >= nch) break;
+    if (c >= nfull) break;
     const Chunk ch = c == 0 ? in.c0 : load_chunk(tab, c);
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) addr[kChunk * c + i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
@@ -164,20 +201,22 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) {
       const int j = kChunk * c + i;
-      const float m = (j == idx_o) ? r2 : r1;
-      const float r = __uint_as_float(__float_as_uint(m) | (sgn & 0x80000000u));
-      sgn <<= 1;
-      float Q = lv[i] - r;
-      if (SAT) Q = fminf(fmaxf(Q, -post_sat), post_sat);
-      if constexpr (LEAN)
-        st_val(L, addr[j], Q);  // Q waits in the posterior's slot for pass 2
-      else
-        q[j] = Q;
-      qs = __funnelshift_l(__float_as_uint(Q), qs, 1);
-      float a = fabsf(Q);
-      if (SAT) a = fmaf(fminf(a, msg_sat), 32.0f, static_cast<float>(j));
-      min2 = fminf(min2, fmaxf(min1, a));
-      min1 = fminf(min1, a);
+      const float Q = pass1_edge<LT, SAT, LEAN>(L, addr[j], lv[i], j, idx_o, r1, r2, sgn, min1, min2, qs, msg_sat,
+                                                post_sat);
+      if constexpr (!LEAN) q[j] = Q;
+    }
+  }
+  float qt[kChunk - 1];
+  if (ntail) {
+    const Chunk ch = nfull == 0 ? in.c0 : load_chunk(tab, nfull);
+#pragma unroll
+    for (int i = 0; i < kChunk - 1; ++i) {
+      if (i < ntail) {
+        const int j = kChunk * nfull + i;
+        addr_t[i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
+        qt[i] = pass1_edge<LT, SAT, LEAN>(L, addr_t[i], ld_val(L, addr_t[i]), j, idx_o, r1, r2, sgn, min1, min2,
+                                          qs, msg_sat, post_sat);
+      }
     }
   }
   float n1, n2;
@@ -192,33 +231,28 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
     n2 = fmaxf(min2 - beta, 0.0f);
   }
   // magnitudes carrying the parity in their sign bit: the sign of R'_j is
-  // parity ^ sign(Q_j), one xor with Q_j's sign bit (padding edges have
-  // positive Q and add nothing to the parity)
+  // parity ^ sign(Q_j), one xor with Q_j's sign bit
   const uint32_t pm = static_cast<uint32_t>(__popc(qs)) << 31;
   const float n1s = __uint_as_float(__float_as_uint(n1) | pm);
   const float n2s = __uint_as_float(__float_as_uint(n2) | pm);
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
-    if (c >= nch) break;
+    if (c >= nfull) break;
     float qv[kChunk];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) qv[i] = LEAN ? ld_val(L, addr[kChunk * c + i]) : q[LEAN ? 0 : kChunk * c + i];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) {
       const int j = kChunk * c + i;
-      bool is_min;
-      if (SAT) {
-        is_min = (j == idx);
-      } else {
-        is_min = (fabsf(qv[i]) == min1);
-        idx = is_min ? j : idx;
-      }
-      const float m = is_min ? n2s : n1s;
-      const uint32_t rb = __float_as_uint(m) ^ (__float_as_uint(qv[i]) & 0x80000000u);
-      float v = qv[i] + __uint_as_float(rb);
-      if (SAT) v = fminf(fmaxf(v, -post_sat), post_sat);
-      st_val(L, addr[j], v);  // padding edges write the dummy slot
+      pass2_edge<LT, SAT>(L, addr[j], qv[i], j, idx, min1, n1s, n2s, post_sat);
     }
+  }
+  if (ntail) {
+#pragma unroll
+    for (int i = 0; i < kChunk - 1; ++i)
+      if (i < ntail)
+        pass2_edge<LT, SAT>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : qt[i], kChunk * nfull + i, idx, min1, n1s,
+                            n2s, post_sat);
   }
   if constexpr (sizeof(MT) == 4) {
     reinterpret_cast<float2*>(mag1)[rec] = make_float2(n1, n2);
@@ -226,7 +260,7 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
     st_val(mag1, rec, n1);
     st_val(mag2, rec, n2);
   }
-  meta[rec] = (qs >> (kChunk * nch - deg)) | (static_cast<uint32_t>(idx) << 27);
+  meta[rec] = qs | (static_cast<uint32_t>(idx) << 27);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
