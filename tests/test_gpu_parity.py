@@ -340,3 +340,43 @@ def test_invalid_block_flags_rejected_on_host(wls):
     bad["flags"][0] = 1 << 1
     with pytest.raises(LdpcError, match="redundancy"):
         st.batch(bad)
+
+
+def _extreme_degree_graph():
+    """4 x 30 base matrix with rows of the largest (27) and smallest (2) degree the decoders accept, an even
+    and an odd one (no code structure: the decoders only see LLRs)."""
+    from workload.basegraph import custom_base_graph
+    rng = np.random.default_rng(77)
+    ent = {(0, c): int(rng.integers(0, 384)) for c in range(27)}          # degree 27: columns 0..26
+    ent.update({(1, 26): 5, (1, 27): 300})                                 # degree 2
+    ent.update({(2, 0): 7, (2, 13): 200, (2, 27): 31, (2, 28): 0})         # degree 4
+    ent.update({(3, 1): 90, (3, 2): 2, (3, 3): 383, (3, 28): 64, (3, 29): 1})  # degree 5
+    return custom_base_graph("extreme", 4, 30, 26, 4, 0, ent)
+
+
+@pytest.mark.parametrize("mode", ["f32", "i8", "i16"])
+def test_extreme_row_degrees_match_oracle(mode):
+    # the sign-history and argmin packing at its limits (edges 0 and 26 of a 27-edge row), the odd last
+    # edge, a degree-2 row; Z = 16 (half-warp groups), 32 and 64; an odd block count (a pair without its
+    # second block in the paired INT8 kernel)
+    from workload.configs import TBSpec, build
+    bg = _extreme_degree_graph()
+    assert sorted(np.bincount(bg.row).tolist()) == [2, 4, 5, 27]
+    specs, widths, punct = [], [], []
+    for i, Z in enumerate([16, 32, 32, 32, 64, 64, 64, 32, 16]):
+        E = bg.nb * Z
+        width = 12 * -(-(E // 2) // (12 * 14))
+        specs.append(TBSpec(i, 0, Z, 2, E, 1, 0.9, 0, width))
+        widths.append(width)
+        punct.append(np.zeros((14, width), bool))
+    w = build("extreme", [bg], specs, widths, punct, seed=5, z_set=[16, 32, 64])
+    llr = _oracle_llr_for_mode(w, mode)
+    want_bits, want_status = odec.decode_workload(w, llr, 5, False, ARITH[mode])
+    s = session_for(w, mode, max_iter=5, early_term=False)
+    b = s.batch(w.cbs)
+    bits = torch.zeros(b.info.bits_words, dtype=torch.int32, device="cuda")
+    status = torch.zeros(b.n_cb, dtype=torch.int32, device="cuda")
+    s.decode_batch(b, torch.from_numpy(llr.astype(LLR_NP[mode])).cuda(), bits, status)
+    assert np.array_equal(to_np_u32(bits), want_bits)
+    assert np.array_equal(status.cpu().numpy(), want_status)
+    assert s.device_errors() == 0
