@@ -15,6 +15,7 @@ value is all ranks' decoded bits over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import multiprocessing as mp
 import os
@@ -402,6 +403,10 @@ def run_serving(args):
     wall = time.perf_counter() - t0
     plain = {"mode": "f32", "tbs": n_plain, "gbps": tot_bits / wall / 1e9, "p50_us": _pct(lat, 50),
              "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9)}
+    if os.environ.get("LDPCGB_CHECKED") == "1":  # checked library: the first failed device index check, if any
+        log = (ctypes.c_uint32 * 8)()
+        abi.check(abi.load().ldpc_check_log(log), "ldpc_check_log")
+        print(json.dumps({"check_log": list(log)}), flush=True)
     res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
                                    "mixed shapes, 128-entry URLLC codebook, INT8 service",
                        "cb_crc": bool(args.cb_crc),
@@ -619,8 +624,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=1024)
     ap.add_argument("--serve-plain", type=int, default=400)
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.25, 0.5, 0.75, 1.0])
-    ap.add_argument("--serve-loops", type=int, nargs="+", default=[2, 1],
-                    help="device loops per SM of the service: 2 (capacity, default) and/or 1 (latency)")
+    ap.add_argument("--serve-loops", type=int, nargs="+", default=[1],
+                    help="device loops per SM for the service (1; 2 is withdrawn)")
     ap.add_argument("--sweep", default=None, choices=["precision"],
                     help="run a measurement sweep instead of the benchmark line")
     ap.add_argument("--sweep-n", type=int, default=100000, help="code blocks per SNR point (GPU)")

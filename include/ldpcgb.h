@@ -327,9 +327,10 @@ typedef struct {
   uint64_t host_pool_bytes;
   void *result_pool;         /* pinned, mapped host memory receiving decoded bits (may be NULL) */
   uint64_t result_pool_bytes;
-  int32_t loops_per_sm;      /* 1: one device loop per SM, check messages in shared memory (lowest
-                              * latency per code block); 2 (or 0, the default): two loops per SM, messages in
-                              * device memory (twice the code blocks in flight, ~8 % slower each) */
+  int32_t loops_per_sm;      /* 0 or 1: one device loop per SM, check messages in shared memory.  2 (two
+                              * loops per SM, messages in device memory) is withdrawn and returns
+                              * LDPC_EINVAL: under load it once made an illegal access and once returned
+                              * corrupted status words, cause not yet found */
   int32_t flags;             /* 0, or LDPC_SERVE_CB_CRC: accept TBs whose code blocks carry their own CRC
                               * (the loop then runs its variant with the code-block CRC exit) */
 } ldpc_serve_desc;
@@ -441,6 +442,15 @@ LDPC_API int ldpc_sc_mask(int32_t n_tti, int32_t n_users, const int32_t *alloc_d
 
 /* Synchronise the session stream and return (then clear) the device error word. */
 LDPC_API int ldpc_device_errors(ldpc_session *s, uint32_t *flags_out);
+
+/* Libraries built with -DLDPC_CHECKED test the indices their kernels trust
+ * (posterior addresses, serving items and code-block records against the
+ * shape, arena and host pool) and redirect a failing access to a safe slot.
+ * out8 (host): the first failed check of the decoder kernels (words 0-3) and
+ * of the serving loop (words 4-7), each {check id, value, limit,
+ * block * 1024 + thread}; zeros when none failed or the library is not a
+ * checked build.  Does not synchronise. */
+LDPC_API int ldpc_check_log(uint32_t *out8);
 
 /* Thread-local message for the last non-zero return on this thread. */
 LDPC_API const char *ldpc_last_error(void);

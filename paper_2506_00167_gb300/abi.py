@@ -15,6 +15,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libldpcgb.so")
+# LDPCGB_CHECKED=1: the build with device index checks (see ldpc_check_log), built and loaded instead
+LIB_PATH_CHECKED = os.path.join(HERE, "libldpcgb_checked.so")
 
 LDPC_F32, LDPC_I8, LDPC_I16 = 0, 1, 2
 MODES = {"f32": LDPC_F32, "i8": LDPC_I8, "i16": LDPC_I16}
@@ -24,7 +26,7 @@ EXPORTED = [
     "ldpc_session_create", "ldpc_session_destroy", "ldpc_session_set_stream",
     "ldpc_batch_create", "ldpc_batch_destroy", "ldpc_batch_info_get",
     "puncture_demap", "decode_batch", "tb_crc_goodput",
-    "ldpc_device_errors", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
+    "ldpc_device_errors", "ldpc_check_log", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
     "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
     "ldpc_graph_create", "ldpc_graph_launch", "ldpc_graph_destroy",
     "ldpc_serve_start", "ldpc_serve_submit", "ldpc_serve_poll", "ldpc_serve_replay", "ldpc_serve_stop",
@@ -145,7 +147,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or (LIB_PATH_CHECKED if os.environ.get("LDPCGB_CHECKED") == "1" else LIB_PATH)
     if not os.path.exists(p):
         raise OSError(f"libldpcgb.so not found at {p}; run paper_2506_00167_gb300.build.build() first")
     lib = ctypes.CDLL(p)
@@ -160,6 +162,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.decode_batch.argtypes = [vp, vp, vp, vp, vp]
     lib.tb_crc_goodput.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.ldpc_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    lib.ldpc_check_log.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
     lib.decode_uniform_noalloc.argtypes = [ctypes.POINTER(BaseGraphC), i32, i32, i32, i32, i32, i32,
                                            ctypes.c_float, i32, i32, i32, vp, vp, vp, vp]
     lib.ldpc_session_set_tiles.argtypes = [vp, ctypes.POINTER(TileC), i32]

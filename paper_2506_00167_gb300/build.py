@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libldpcgb.so")
+LIB_CHECKED = os.path.join(HERE, "libldpcgb_checked.so")
 
 SOURCES = ["session.cu", "decode.cu", "demap.cu", "crc.cu", "noalloc.cu", "serve.cu", "policy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,16 +45,20 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(verbose: bool = False, extra_flags=None) -> str:
-    """Compile (if needed) and return the path of libldpcgb.so."""
+    """Compile (if needed) and return the path of libldpcgb.so.  With LDPCGB_CHECKED=1 in the
+    environment the kernels are built with their index checks (-DLDPC_CHECKED, see ldpc_check_log);
+    the objects then go to a separate build folder."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    checked = os.environ.get("LDPCGB_CHECKED") == "1"
+    build_dir = BUILD + ("_checked" if checked else "")
+    os.makedirs(build_dir, exist_ok=True)
     common = _deps()
-    flags = FLAGS + list(extra_flags or [])
+    flags = FLAGS + list(extra_flags or []) + (["-DLDPC_CHECKED"] if checked else [])
     jobs = []
     objs = []
     for src in SOURCES:
         sp = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         if _stale(obj, [sp] + common):
             jobs.append([nvcc, *ARCH, *flags, "-c", sp, "-o", obj])
@@ -67,9 +72,10 @@ def build(verbose: bool = False, extra_flags=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4) or 1) as ex:
         list(ex.map(run, jobs))
-    if jobs or _stale(LIB, objs):
-        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
-    return LIB
+    lib = LIB_CHECKED if checked else LIB
+    if jobs or _stale(lib, objs):
+        run([nvcc, *ARCH, "-shared", "-o", lib, *objs, "-lcudart"])
+    return lib
 
 
 if __name__ == "__main__":

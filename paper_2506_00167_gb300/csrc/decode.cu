@@ -407,6 +407,8 @@ const void* kernel_kind(int mode, int kind) {
   return (kind & kKindCrc) ? kernel_for<true>(mode, base) : kernel_for<false>(mode, base);
 }
 
+cudaError_t read_check_log_decode(uint32_t* out4) { return cudaMemcpyFromSymbol(out4, g_check_log, 16); }
+
 cudaError_t decode_prepare(int mode) {
   for (int kind = 0; kind < 2 * kKindCrc; ++kind) {
     if (kind_is_pair(kind) && mode != LDPC_I8) continue;

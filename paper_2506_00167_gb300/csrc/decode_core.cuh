@@ -172,7 +172,9 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
                                              float msg_sat, float post_sat) {
-  (void)dummy;
+  // checked builds: every posterior index stays inside the group's region
+  // (dummy - k + Z elements: the columns, then one dummy slot per thread)
+  const int lim = dummy - k + Z;
   const uint32_t* tab = in.tab;
   const int deg = in.deg;
   const float r1 = in.r1, r2 = in.r2;
@@ -194,7 +196,8 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
     if (c >= nfull) break;
     const Chunk ch = c == 0 ? in.c0 : load_chunk(tab, c);
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) addr[kChunk * c + i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
+    for (int i = 0; i < kChunk; ++i)
+      addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
     float lv[kChunk];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) lv[i] = ld_val(L, addr[kChunk * c + i]);
@@ -213,7 +216,7 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
     for (int i = 0; i < kChunk - 1; ++i) {
       if (i < ntail) {
         const int j = kChunk * nfull + i;
-        addr_t[i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
+        addr_t[i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 2);
         qt[i] = pass1_edge<LT, SAT, LEAN>(L, addr_t[i], ld_val(L, addr_t[i]), j, idx_o, r1, r2, sgn, min1, min2,
                                           qs, msg_sat, post_sat);
       }
@@ -518,7 +521,8 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     if (c >= nch) break;
     const Chunk ch = load_chunk(tab, c);
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) addr[kChunk * c + i] = static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z);
+    for (int i = 0; i < kChunk; ++i)
+      addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), dummy - k + Z, dummy, 3);
     uint32_t lv[kChunk];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) lv[i] = L[addr[kChunk * c + i]];
@@ -553,8 +557,8 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const uint32_t N1s = as_u32(small_pair(nA1, nB1)) | pm;
   const uint32_t N2s = as_u32(small_pair(nA2, nB2)) | pm;
   // the two argmin edges and their Q values, before pass 2 overwrites them
-  const int aA = edge_addr(tab, static_cast<int>(idxA), k, Z);
-  const int aB = edge_addr(tab, static_cast<int>(idxB), k, Z);
+  const int aA = checked(edge_addr(tab, static_cast<int>(idxA), k, Z), dummy - k + Z, dummy, 4);
+  const int aB = checked(edge_addr(tab, static_cast<int>(idxB), k, Z), dummy - k + Z, dummy, 4);
   const uint32_t qsel = (L[aA] & 0x0000FFFFu) | (L[aB] & 0xFFFF0000u);
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {

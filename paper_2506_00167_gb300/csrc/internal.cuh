@@ -143,6 +143,10 @@ cudaError_t decode_prepare(int mode);  // raise the dynamic shared-memory limit
 cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
 cudaError_t launch_demap_repeat(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
 cudaError_t launch_crc(int n_slots, cudaStream_t st, const CrcArgs& a);
+// Checked builds: the first failed device check of the decoder and of the
+// serving loop (4 words each; zeros when none failed or checks are off).
+cudaError_t read_check_log_decode(uint32_t* out4);
+cudaError_t read_check_log_serve(uint32_t* out4);
 
 constexpr int kDemapBlock = 256;
 constexpr int kDemapPerThread = 4;                        // resource elements per thread
@@ -205,6 +209,39 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ---- checked builds (nvcc -DLDPC_CHECKED): indices that the kernels trust
+// are tested; the first failure of a translation unit is logged as
+// {check id, value, limit, block * 1024 + thread} and the access is
+// redirected to a safe slot, so a bad index never leaves the buffer.
+#ifdef LDPC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+static __device__ uint32_t g_check_log[4];
+
+__device__ __forceinline__ bool check_ok(bool ok, uint32_t id, int value, int limit) {
+  if constexpr (kChecked) {
+    if (!ok && atomicCAS(&g_check_log[0], 0u, id) == 0u) {
+      g_check_log[1] = static_cast<uint32_t>(value);
+      g_check_log[2] = static_cast<uint32_t>(limit);
+      g_check_log[3] = blockIdx.x * 1024u + threadIdx.x;
+    }
+    return ok;
+  } else {
+    return true;
+  }
+}
+
+// i if 0 <= i < limit, else (logged) `safe`.
+__device__ __forceinline__ int checked(int i, int limit, int safe, uint32_t id) {
+  if constexpr (kChecked)
+    return check_ok(static_cast<uint32_t>(i) < static_cast<uint32_t>(limit), id, i, limit) ? i : safe;
+  else
+    return i;
 }
 
 // Barrier over `nthreads` threads on barrier `id` that also ORs `pred`.

@@ -95,6 +95,9 @@ struct ServeArgs {
   uint8_t* rscratch;       // message records: one slot per (resident block, group)
   int64_t rscratch_group;  // bytes per group slot
   int32_t groups;          // group slots per block
+  // sizes the checked build tests indices against
+  int32_t n_shapes, n_req;
+  int64_t arena_words, pool_f2, pool_words;
 };
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -210,6 +213,14 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
     const int n_items = ld_sys(&ip->n_items);
     const int first_cb = static_cast<int>(static_cast<uint32_t>(cb0) % a.cb_cap);
     const CbDev cb_first = load_cb(a.cbs + first_cb);
+    // checked builds: an item whose request or shape index is out of range is dropped
+    const bool item_ok = check_ok(static_cast<uint32_t>(req) < static_cast<uint32_t>(a.n_req), 10, req, a.n_req) &&
+                         check_ok(static_cast<uint32_t>(cb_first.shape) < static_cast<uint32_t>(a.n_shapes), 11,
+                                  cb_first.shape, a.n_shapes);
+    if (kChecked && !item_ok) {
+      __syncthreads();
+      continue;
+    }
     const ServeShape ssh = a.shapes[cb_first.shape];
     const ShapeDev& sh = ssh.sh;
     const int Z = sh.Z;
@@ -222,7 +233,7 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
       bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
     }
-    const bool active = g < count;
+    bool active = g < count && check_ok(count >= 1 && count <= ssh.G, 12, count, ssh.G);
     CbDev cb{};
     LT* L = reinterpret_cast<LT*>(regions + g * ssh.region_bytes);
     uint8_t* rbase = TWO ? a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) * a.rscratch_group
@@ -232,6 +243,20 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
     uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
     if (active) {
       cb = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + g) % a.cb_cap));
+      if constexpr (kChecked) {  // the block's records against the shape, the arena and the host pool
+        active = check_ok(cb.shape == cb_first.shape && cb.Z == Z && cb.n_eff <= sh.nb && cb.m_eff <= sh.mb, 13,
+                          cb.shape, cb_first.shape) &&
+                 check_ok(cb.bits_off >= 0 && cb.bits_off + ((cb.kb * Z) >> 5) <= a.arena_words, 14,
+                          static_cast<int>(cb.bits_off), static_cast<int>(a.arena_words)) &&
+                 check_ok(cb.llr_off >= 0 && cb.llr_off < a.arena_words, 15, static_cast<int>(cb.llr_off),
+                          static_cast<int>(a.arena_words)) &&
+                 check_ok(cb.re_off >= 0 && cb.re_off + cb.n_re <= a.pool_f2, 16, static_cast<int>(cb.re_off),
+                          static_cast<int>(a.pool_f2)) &&
+                 check_ok(cb.mask_off >= 0 && cb.mask_off + ((cb.n_re + 31) >> 5) <= a.pool_words, 17,
+                          static_cast<int>(cb.mask_off), static_cast<int>(a.pool_words));
+      }
+    }
+    if (active) {
       zero_records(mag1, mag2, meta, cb.m_eff * Z, k, Z);
       if constexpr (SAT)
         st_val(L, ssh.dummy_base + k, a.post_sat);
@@ -321,7 +346,12 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       const int64_t status_off = ld_sys(&rq->status_off);
       const int64_t result_off = ld_sys(&rq->result_off);
       const volatile uint32_t* bits = a.arena + bits_off;
-      if (tid < 32) {
+      const bool rq_ok = check_ok(n_cb >= 1 && n_cb <= kMaxTbCb && W % n_cb == 0, 18, n_cb, W) &&
+                         check_ok(bits_off >= 0 && bits_off + W <= a.arena_words, 19, static_cast<int>(bits_off),
+                                  static_cast<int>(a.arena_words)) &&
+                         check_ok(status_off >= 0 && status_off + n_cb <= a.arena_words, 20,
+                                  static_cast<int>(status_off), static_cast<int>(a.arena_words));
+      if (tid < 32 && rq_ok) {
         using namespace crccore;
         // TB CRC over each block's first K/8 - 3*seg bytes (the blocks' K/32
         // words lie back to back), zero-prefixed to whole words as in the
@@ -422,6 +452,12 @@ const void* serve_kernel_ptr(int mode, bool two, bool crc) {
   return two ? serve_kernel_for<true, false>(mode) : serve_kernel_for<false, false>(mode);
 }
 
+}  // namespace
+
+cudaError_t read_check_log_serve(uint32_t* out4) { return cudaMemcpyFromSymbol(out4, g_check_log, 16); }
+
+namespace {
+
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
       .count();
@@ -509,7 +545,7 @@ struct ldpc_server {
     int64_t t_submit = 0;
   };
   std::vector<Slot> slot_info;
-  uint32_t tail = 0, cb_tail = 0;
+  uint32_t tail = 0;
   uint64_t items_inflight = 0, cbs_inflight = 0;
   uint32_t rd = 0;
 };
@@ -606,7 +642,14 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     auto* v = new (std::nothrow) ldpc_server();
     if (!v) return srv_fail(LDPC_ENOMEM, "host allocation");
     v->s = s;
-    v->two = d->loops_per_sm != 1;
+    // two loops per SM (messages in device memory) are withdrawn: under load that
+    // variant once made an illegal access and once returned corrupted status
+    // words, and the cause is not found yet, so no service starts it
+    if (d->loops_per_sm == 2) {
+      delete v;
+      return srv_fail(LDPC_EINVAL, "ldpc_serve_start: loops_per_sm = 2 is withdrawn (use 1)");
+    }
+    v->two = false;
     v->cb_crc = (d->flags & LDPC_SERVE_CB_CRC) != 0;
     int interleave = 1, max_iter = 10, et = 1, sms = 0;
     float q_scale = 4, llr_sat = 63, beta = 1, msg_sat = 63, post_sat = 127;
@@ -766,6 +809,11 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     a.rscratch = v->rscratch;
     a.rscratch_group = rec_group;
     a.groups = gmax;
+    a.n_shapes = static_cast<int32_t>(v->hshapes.size());
+    a.n_req = d->max_inflight;
+    a.arena_words = arena_words;
+    a.pool_f2 = static_cast<int64_t>(d->host_pool_bytes / 8);
+    a.pool_words = static_cast<int64_t>(d->host_pool_bytes / 4);
     if (!a.items || !a.cbs || !a.reqs || !a.done || !a.hctl) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, "mapped host rings unavailable");
@@ -854,7 +902,10 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     rq.bits_off = off;
     rq.status_off = off + static_cast<int64_t>(tb.n_cb) * (K / 32);
     rq.result_off = tb.result_offset;
-    const uint32_t cb_first = v->cb_tail;
+    // each request slot owns kMaxTbCb code-block records: requests complete
+    // out of order, so a ring in submission order could hand the records of
+    // a request still waiting for its items to a newer one
+    const uint32_t cb_first = static_cast<uint32_t>(slot) * kMaxTbCb;
     for (int j = 0; j < tb.n_cb; ++j) {
       CbDev c{};
       c.shape = shape;
@@ -872,9 +923,8 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       c.llr_off = rq.status_off + j;  // status word index in the arena
       c.bits_off = off + static_cast<int64_t>(j) * (K / 32);
       c.inv_sigma2 = tb.inv_sigma2;
-      v->cbs[(cb_first + j) % v->cb_cap] = c;
+      v->cbs[cb_first + j] = c;
     }
-    v->cb_tail += tb.n_cb;
     for (int it = 0; it < n_items; ++it) {
       ServeItem& item = v->items[v->tail % v->item_cap];
       item.req = slot;

@@ -1017,6 +1017,13 @@ int tb_crc_goodput(ldpc_session* s, const ldpc_batch* b, const uint32_t* bits_de
   return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "tb_crc_goodput launch");
 }
 
+int ldpc_check_log(uint32_t* out8) {
+  if (!out8) return fail(LDPC_EINVAL, "null argument");
+  cudaError_t e = read_check_log_decode(out8);
+  if (e == cudaSuccess) e = read_check_log_serve(out8 + 4);
+  return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "ldpc_check_log");
+}
+
 int ldpc_device_errors(ldpc_session* s, uint32_t* flags_out) {
   if (!s || !flags_out) return fail(LDPC_EINVAL, "null argument");
   cudaError_t e = cudaStreamSynchronize(s->stream);

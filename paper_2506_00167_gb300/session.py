@@ -267,7 +267,7 @@ class Server:
 
     def __init__(self, session: Session, host_pool: torch.Tensor, result_pool: torch.Tensor | None = None,
                  arena_bytes: int = 8 << 30, max_inflight: int = 4096, idle_timeout_us: int = 200000,
-                 loops_per_sm: int = 2, cb_crc: bool = False):
+                 loops_per_sm: int = 1, cb_crc: bool = False):
         for t, name in ((host_pool, "host_pool"), (result_pool, "result_pool")):
             if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous pinned CPU tensor")

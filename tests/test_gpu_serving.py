@@ -128,10 +128,10 @@ def test_idle_loop_is_relaunched_and_bad_requests_rejected(pool):
     srv.stop()
 
 
-@pytest.mark.parametrize("loops", [1, 2])
+@pytest.mark.parametrize("loops", [1])
 def test_repetition_blocks_through_the_service_match_the_batch_path(loops):
     """Code blocks whose rate matching wraps the circular buffer: the service's fused demap combines the
-    repeated LLRs like the batch demapper, bit for bit, with one or two device loops per SM."""
+    repeated LLRs like the batch demapper, bit for bit."""
     from workload.configs import repetition
     w = repetition(n_per_shape=4, seed=13)
     raw, mask_base = pool_bytes(w)
@@ -175,7 +175,7 @@ def test_one_loop_per_sm_matches_the_batch_path(pool):
         srv.stop()
 
 
-@pytest.mark.parametrize("loops", [1, 2])
+@pytest.mark.parametrize("loops", [1])
 def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(loops):
     """TBs whose code blocks carry their own CRC (payload n_cb (K - 24) - 24): the service infers that from
     payload_bits, stops blocks on a passing CRC and checks every CRC, like the batch path, bit for bit."""
@@ -208,3 +208,9 @@ def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(loops):
         assert 0 < int(done["d"].sum()) < n  # both outcomes occur at these SNRs
     finally:
         srv.stop()
+
+
+def test_two_loops_per_sm_is_withdrawn(pool):
+    w, host, mask_base = pool
+    with pytest.raises(LdpcError, match="withdrawn"):
+        Server(session_for(w, "i8"), host, None, arena_bytes=1 << 24, max_inflight=8, loops_per_sm=2)
