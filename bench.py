@@ -374,7 +374,8 @@ def run_serving(args):
                           "p50_us": _pct(lat_us, 50), "p99_us": _pct(lat_us, 99), "p999_us": _pct(lat_us, 99.9),
                           "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
                           "tb_crc_ok_frac": float(np.mean(done["d"])),
-                          "mean_max_iters": float(np.mean(done["max_iters"]))})
+                          "mean_max_iters": float(np.mean(done["max_iters"])),
+                          **_stall_stats(done)})
             print(json.dumps({"serving_point": loads[-1]}), flush=True)
         srv.stop()
         curves[f"{loops}_loops_per_sm"] = loads
@@ -413,6 +414,22 @@ def run_serving(args):
                        "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
                        "loads": curves, "fp32_unbatched_plain": plain}}
     print(json.dumps(res), flush=True)
+
+
+def _stall_stats(done):
+    """Where the time of the slowest requests went: the longest pause between consecutive completions as
+    the device wrote them and as the host collected them, and how late the host collected the slowest
+    request's completion (relative to the median host-minus-device offset)."""
+    td = np.sort(done["t_device_ns"].astype(np.int64))
+    th = np.sort(done["t_complete_ns"].astype(np.int64))
+    off = done["t_complete_ns"].astype(np.int64) - done["t_device_ns"].astype(np.int64)
+    lat = done["t_complete_ns"] - done["t_submit_ns"]
+    worst = int(np.argmax(lat))
+    admit_wait = (done["t_admit_ns"] - done["t_submit_ns"]) / 1e3
+    return {"max_gap_device_us": float(np.diff(td).max() / 1e3) if td.size > 1 else 0.0,
+            "max_gap_host_us": float(np.diff(th).max() / 1e3) if th.size > 1 else 0.0,
+            "worst_host_lag_us": float((off[worst] - np.median(off)) / 1e3),
+            "worst_admit_wait_us": float(admit_wait[worst]), "max_admit_wait_us": float(admit_wait.max())}
 
 
 # ----------------------------------------------------------------------------- main arm

@@ -356,6 +356,9 @@ typedef struct {
   int32_t status;               /* 0, or LDPC_ETIMEOUT if the service stopped before it completed */
   int64_t t_submit_ns;          /* host steady clock at submission (replay: the scheduled arrival) */
   int64_t t_complete_ns;        /* host steady clock when the completion was collected */
+  int64_t t_device_ns;          /* device global timer when the loop wrote the completion (own time base:
+                                 * for differences between completions) */
+  int64_t t_admit_ns;           /* host steady clock when the request was admitted */
 } ldpc_serve_done;
 
 /* Allocate the arena and rings and start the device loop on a private stream. */

@@ -99,7 +99,8 @@ class ServeTbC(ctypes.Structure):
 class ServeDoneC(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("d", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("all_syndrome_ok", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("t_submit_ns", ctypes.c_int64), ("t_complete_ns", ctypes.c_int64)]
+                ("t_submit_ns", ctypes.c_int64), ("t_complete_ns", ctypes.c_int64),
+                ("t_device_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64)]
 
 
 class BatchInfoC(ctypes.Structure):

@@ -17,11 +17,14 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <limits>
 #include <map>
+#include <set>
 #include <new>
 #include <string>
 #include <vector>
 
+#include "arena.h"
 #include "crc_core.cuh"
 #include "decode_core.cuh"
 #include "demap_core.cuh"
@@ -50,6 +53,7 @@ struct ServeDone {  // device -> host completion record
   uint64_t tag;
   int32_t d, max_iters, all_ok, req;
   uint32_t seq, pad;
+  uint64_t t_dev;  // global timer at the write
 };
 
 struct HostCtl {  // host-written control words
@@ -59,7 +63,13 @@ struct HostCtl {  // host-written control words
 };
 
 struct DevCtl {  // device counters
-  uint32_t head, done, err, pad;
+  uint32_t head, done, err;
+  uint32_t exits;  // blocks of the current loop launch that have left it (zeroed at each launch)
+};
+
+struct LoopCtl {  // device-written, host-mapped: lets the host see the loop end without a driver call
+  uint32_t exited_epoch;  // launch number of the last loop all of whose blocks have exited
+  uint32_t pad[15];
 };
 
 struct ServeShape {  // one (bg, Z) shape with its shared-memory layout in the loop
@@ -80,6 +90,8 @@ struct ServeArgs {
   uint32_t done_cap;
   const HostCtl* hctl;
   DevCtl* dctl;
+  LoopCtl* lctl;
+  uint32_t epoch;  // this launch's number
   uint32_t* counts;  // per request slot: items finished
   uint32_t* arena;
   const uint8_t* host_pool;
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
     if (!__syncthreads_and(got)) {
       if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
       mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
-      return;
+      break;
     }
 
     if (active) {
@@ -280,14 +292,14 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       int it = 1;
       bool ok = false, crc_ok = false;
       const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
-      RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
+      RowIn row = load_row<MT, !TWO>(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
           check_update<LT, MT, SAT, TWO>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
                                           a.msg_sat, a.post_sat);
           // the next row's table and record are ready before the barrier
           const int ln = l + 1 < m ? l + 1 : 0;
-          row = load_row(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
+          row = load_row<MT, !TWO>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {
@@ -401,7 +413,8 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
           for (int o = 16; o > 0; o >>= 1) st ^= __shfl_xor_sync(0xFFFFFFFFu, st, o);
           state |= st;
         }
-        uint32_t st = lane < n_cb ? a.arena[status_off + lane] : (1u << 16);
+        // status words come from other SMs' blocks: read past this SM's L1 like the bits
+        uint32_t st = lane < n_cb ? ld_sys(a.arena + status_off + lane) : (1u << 16);
         uint32_t iters = st & 0xFFFFu;
         uint32_t okb = (st >> 16) & 1u;
 #pragma unroll
@@ -429,12 +442,22 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
         rec->max_iters = static_cast<int32_t>(s_res[1]);
         rec->all_ok = static_cast<int32_t>(s_res[2]);
         rec->req = req;
+        rec->t_dev = gtimer();
         __threadfence_system();
         rec->seq = slot + 1u;
         __threadfence_system();
       }
     }
     __syncthreads();
+  }
+  // the last block to leave tells the host (in mapped memory) that this launch is over
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&a.dctl->exits, 1u) + 1u == gridDim.x) {
+      __threadfence_system();
+      *reinterpret_cast<volatile uint32_t*>(&a.lctl->exited_epoch) = a.epoch;
+    }
   }
 }
 
@@ -466,37 +489,7 @@ int64_t now_ns() {
 int align16s(int x) { return (x + 15) & ~15; }
 
 // First-fit allocator over arena words with coalescing frees.
-struct Arena {
-  std::map<int64_t, int64_t> free_;  // offset -> length
-  explicit Arena(int64_t words) { free_[0] = words; }
-  int64_t alloc(int64_t n) {
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        const int64_t off = it->first;
-        const int64_t rest = it->second - n;
-        free_.erase(it);
-        if (rest) free_[off + n] = rest;
-        return off;
-      }
-    }
-    return -1;
-  }
-  void release(int64_t off, int64_t n) {
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-};
+
 
 }  // namespace
 }  // namespace ldpcgb
@@ -510,8 +503,10 @@ struct ldpc_server {
   cudaStream_t stream = nullptr;
   cudaEvent_t done_ev = nullptr;
   bool running = false;
+  uint32_t epoch = 0;  // loop launches so far
   // host-mapped rings
   HostCtl* hctl = nullptr;
+  LoopCtl* lctl = nullptr;
   ServeItem* items = nullptr;
   CbDev* cbs = nullptr;
   ServeReq* reqs = nullptr;
@@ -560,6 +555,7 @@ int srv_fail(int code, const std::string& m) {
 void free_server(ldpc_server* v) {
   if (!v) return;
   cudaFreeHost(v->hctl);
+  cudaFreeHost(v->lctl);
   cudaFreeHost(v->items);
   cudaFreeHost(v->cbs);
   cudaFreeHost(v->reqs);
@@ -579,6 +575,9 @@ void free_server(ldpc_server* v) {
 }
 
 int launch_loop(ldpc_server* v) {
+  v->args.epoch = ++v->epoch;
+  cudaError_t z = cudaMemsetAsync(&v->args.dctl->exits, 0, sizeof(uint32_t), v->stream);
+  if (z != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop reset: ") + cudaGetErrorString(z));
   void* kargs[] = {&v->args};
   cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two, v->cb_crc), dim3(v->grid), dim3(kServeBlock), kargs,
                                    static_cast<size_t>(v->smem), v->stream);
@@ -592,8 +591,9 @@ int launch_loop(ldpc_server* v) {
 // Relaunch the device loop if it has exited (idle limit reached).
 int ensure_running(ldpc_server* v) {
   if (v->running) {
-    const cudaError_t q = cudaEventQuery(v->done_ev);
-    if (q == cudaErrorNotReady) return LDPC_OK;
+    // no driver call while the loop runs: its last block writes the launch number when it leaves
+    if (reinterpret_cast<volatile uint32_t*>(&v->lctl->exited_epoch)[0] != v->epoch) return LDPC_OK;
+    const cudaError_t q = cudaEventSynchronize(v->done_ev);  // it has left: the kernel ends at once
     if (q != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop: ") + cudaGetErrorString(q));
     v->running = false;
   }
@@ -723,7 +723,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     v->done_cap = static_cast<uint32_t>(d->max_inflight);
     int rc;
     const int64_t arena_words = static_cast<int64_t>(d->arena_bytes / 4);
-    if ((rc = host_alloc(&v->hctl, 1)) || (rc = host_alloc(&v->items, v->item_cap)) ||
+    if ((rc = host_alloc(&v->hctl, 1)) || (rc = host_alloc(&v->lctl, 1)) || (rc = host_alloc(&v->items, v->item_cap)) ||
         (rc = host_alloc(&v->cbs, v->cb_cap)) || (rc = host_alloc(&v->reqs, d->max_inflight)) ||
         (rc = host_alloc(&v->done, v->done_cap))) {
       free_server(v);
@@ -789,6 +789,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     a.done_cap = v->done_cap;
     a.hctl = dev_ptr(v->hctl);
     a.dctl = v->dctl;
+    a.lctl = dev_ptr(v->lctl);
     a.counts = v->counts;
     a.arena = v->arena;
     a.host_pool = pool_dev;
@@ -814,7 +815,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     a.arena_words = arena_words;
     a.pool_f2 = static_cast<int64_t>(d->host_pool_bytes / 8);
     a.pool_words = static_cast<int64_t>(d->host_pool_bytes / 4);
-    if (!a.items || !a.cbs || !a.reqs || !a.done || !a.hctl) {
+    if (!a.items || !a.cbs || !a.reqs || !a.done || !a.hctl || !a.lctl) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, "mapped host rings unavailable");
     }
@@ -964,6 +965,8 @@ int ldpc_serve_poll(ldpc_server* v, ldpc_serve_done* out, int32_t cap, int32_t* 
     o.status = 0;
     o.t_submit_ns = si.t_submit;
     o.t_complete_ns = now_ns();
+    o.t_device_ns = static_cast<int64_t>(rec->t_dev);
+    o.t_admit_ns = si.t_submit;
     out[n++] = o;
     v->alloc->release(si.arena_off, si.arena_words);
     v->items_inflight -= si.n_items;

@@ -38,7 +38,8 @@ def _wait(srv, n, timeout=20.0):
 
 
 def _batch_reference(w, idx):
-    """The same TBs through the batch path (puncture_demap + decode_batch + tb_crc_goodput)."""
+    """The same TBs through the batch path (puncture_demap + decode_batch + tb_crc_goodput): d_e, bits and
+    the most iterations of any code block, per TB."""
     sub = subset(w, idx)
     s = session_for(sub, "i8")
     b = s.batch(sub.cbs, sub.tbs, sub.slot_N)
@@ -46,12 +47,16 @@ def _batch_reference(w, idx):
     out = s.run(b, sym, mask, b.alloc_outputs())
     torch.cuda.synchronize()
     bits = out["bits"].cpu().numpy().view(np.uint32)
+    status = out["status"].cpu().numpy()
     per_tb = []
+    iters = []
     for t in range(sub.n_tb):
-        c = sub.cbs[int(sub.tbs[t]["first_cb"])]
+        first, n = int(sub.tbs[t]["first_cb"]), int(sub.tbs[t]["n_cb"])
+        c = sub.cbs[first]
         o = int(c["bits_word_offset"])
         per_tb.append(bits[o:o + _tb_words(sub, t)].copy())
-    return out["d"].cpu().numpy()[:sub.n_tb], per_tb
+        iters.append(int((status[first:first + n] & 0xFFFF).max()))
+    return out["d"].cpu().numpy()[:sub.n_tb], per_tb, iters
 
 
 def test_result_is_the_same_alone_and_in_the_mix(pool):
@@ -81,10 +86,12 @@ def test_result_is_the_same_alone_and_in_the_mix(pool):
     for t in alone:
         assert d_mix[t] == d_alone[t]
         assert np.array_equal(res[base + offs[t]:base + offs[t + 1]].numpy().view(np.uint32), bits_alone[t])
-    # and both equal the batch path bit for bit
-    d_ref, bits_ref = _batch_reference(w, range(n))
+    # and both equal the batch path bit for bit, iteration counts included
+    d_ref, bits_ref, it_ref = _batch_reference(w, range(n))
+    it_mix = {int(r["tag"]): int(r["max_iters"]) for r in done}
     for t in range(n):
         assert d_mix[t] == int(d_ref[t]), t
+        assert it_mix[t] == it_ref[t], t
         assert np.array_equal(res[base + offs[t]:base + offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
     assert 0 < sum(d_mix.values()) <= n
     lat = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
@@ -146,7 +153,7 @@ def test_repetition_blocks_through_the_service_match_the_batch_path(loops):
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
-        d_ref, bits_ref = _batch_reference(w, range(n))
+        d_ref, bits_ref, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
             assert int(r["d"]) == int(d_ref[t]), t
@@ -166,7 +173,7 @@ def test_one_loop_per_sm_matches_the_batch_path(pool):
     try:
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
-        d_ref, bits_ref = _batch_reference(w, range(n))
+        d_ref, bits_ref, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
             assert int(r["d"]) == int(d_ref[t]), t
@@ -200,7 +207,7 @@ def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(loops):
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
-        d_ref, bits_ref = _batch_reference(w, range(n))
+        d_ref, bits_ref, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
             assert int(r["d"]) == int(d_ref[t]), t
