@@ -88,16 +88,12 @@ __device__ __forceinline__ Chunk load_chunk(const uint32_t* tab, int c) {
 struct RowIn {
   const uint32_t* tab;
   int deg;
-  Chunk c0, c1;  // c1: loaded only by load_row<MT, true> (may lie past a one-chunk row: then unused)
+  Chunk c0;
   float r1, r2;
   uint32_t mo;
 };
 
-// TWO_CHUNKS: prefetch the row's second chunk too (the register-resident
-// update of the single-loop service, which has registers to spare and is
-// latency-bound); every row is followed in the table by more words (the next
-// row or the row words), so the load stays inside the table.
-template <typename MT, bool TWO_CHUNKS = false>
+template <typename MT>
 __device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, uint32_t info,
                                           const MT* __restrict__ mag1, const MT* __restrict__ mag2,
                                           const uint32_t* __restrict__ meta, int rec) {
@@ -105,7 +101,6 @@ __device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, ui
   r.tab = s_tab + (info & 0xFFFFu);
   r.deg = static_cast<int>(info >> 16);
   r.c0 = load_chunk(r.tab, 0);
-  if constexpr (TWO_CHUNKS) r.c1 = load_chunk(r.tab, 1);
   if constexpr (sizeof(MT) == 4) {  // float: both magnitudes in one 8-byte record
     const float2 rr = reinterpret_cast<const float2*>(mag1)[rec];
     r.r1 = rr.x;
@@ -188,72 +183,42 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
   // sign of R_j = stored Q-sign bit ^ parity, edge 0's moved to bit 31
   const uint32_t par_o = 0u - (static_cast<uint32_t>(__popc(mo << 5)) & 1u);
   uint32_t sgn = (mo ^ par_o) << (32 - deg);
-  // whole chunks kG at a time (their posterior loads issued together: two
-  // chunks when the Q values stay in registers, where the single-block loop is
-  // latency-bound; one when they are parked), then up to kG - 1 whole chunks,
-  // then the partial chunk's edges
-  constexpr int kG = LEAN ? 1 : 2;
-  constexpr int kSteps = kMaxChunks / kG;
   const int nfull = deg / kChunk;
-  const int nstep = nfull / kG;
-  const int nrest = nfull - kG * nstep;
   const int ntail = deg - kChunk * nfull;
 
-  float q[LEAN ? 1 : kSteps * kG * kChunk];
-  int addr[kSteps * kG * kChunk];
-  int addr_r[kG * kChunk];  // the whole chunks after the steps (kG - 1 of them at most)
-  int addr_t[kChunk - 1];   // the partial chunk's edges
-  float q_r[kG * kChunk], q_t[kChunk - 1];
+  float q[LEAN ? 1 : kMaxChunks * kChunk];
+  int addr[kMaxChunks * kChunk];
+  int addr_t[kChunk - 1];  // the partial chunk's edges
   float min1 = 3.0e38f, min2 = 3.0e38f;  // SAT modes: keys |Q| * 32 + j
   uint32_t qs = 0;                       // Q sign bits, first edge highest
 #pragma unroll
-  for (int st = 0; st < kSteps; ++st) {
-    if (st >= nstep) break;
-    float lv[kG * kChunk];
+  for (int c = 0; c < kMaxChunks; ++c) {
+    if (c >= nfull) break;
+    const Chunk ch = c == 0 ? in.c0 : load_chunk(tab, c);
 #pragma unroll
-    for (int g = 0; g < kG; ++g) {
-      const int c = kG * st + g;
-      const Chunk ch = c == 0 ? in.c0 : (!LEAN && c == 1 ? in.c1 : load_chunk(tab, c));
+    for (int i = 0; i < kChunk; ++i)
+      addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
+    float lv[kChunk];
 #pragma unroll
-      for (int i = 0; i < kChunk; ++i)
-        addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
-    }
+    for (int i = 0; i < kChunk; ++i) lv[i] = ld_val(L, addr[kChunk * c + i]);
 #pragma unroll
-    for (int e = 0; e < kG * kChunk; ++e) lv[e] = ld_val(L, addr[kG * kChunk * st + e]);
-#pragma unroll
-    for (int e = 0; e < kG * kChunk; ++e) {
-      const int j = kG * kChunk * st + e;
-      const float Q = pass1_edge<LT, SAT, LEAN>(L, addr[j], lv[e], j, idx_o, r1, r2, sgn, min1, min2, qs, msg_sat,
+    for (int i = 0; i < kChunk; ++i) {
+      const int j = kChunk * c + i;
+      const float Q = pass1_edge<LT, SAT, LEAN>(L, addr[j], lv[i], j, idx_o, r1, r2, sgn, min1, min2, qs, msg_sat,
                                                 post_sat);
       if constexpr (!LEAN) q[j] = Q;
     }
   }
-#pragma unroll
-  for (int g = 0; g < kG - 1; ++g) {
-    if (g < nrest) {
-      const int c = kG * nstep + g;
-      const Chunk ch = c == 0 ? in.c0 : (!LEAN && c == 1 ? in.c1 : load_chunk(tab, c));
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i)
-        addr_r[kChunk * g + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
-      float lv[kChunk];
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i) lv[i] = ld_val(L, addr_r[kChunk * g + i]);
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i)
-        q_r[kChunk * g + i] = pass1_edge<LT, SAT, LEAN>(L, addr_r[kChunk * g + i], lv[i], kChunk * c + i, idx_o, r1,
-                                                        r2, sgn, min1, min2, qs, msg_sat, post_sat);
-    }
-  }
+  float qt[kChunk - 1];
   if (ntail) {
-    const Chunk ch = nfull == 0 ? in.c0 : (!LEAN && nfull == 1 ? in.c1 : load_chunk(tab, nfull));
+    const Chunk ch = nfull == 0 ? in.c0 : load_chunk(tab, nfull);
 #pragma unroll
     for (int i = 0; i < kChunk - 1; ++i) {
       if (i < ntail) {
         const int j = kChunk * nfull + i;
         addr_t[i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 2);
-        q_t[i] = pass1_edge<LT, SAT, LEAN>(L, addr_t[i], ld_val(L, addr_t[i]), j, idx_o, r1, r2, sgn, min1, min2,
-                                           qs, msg_sat, post_sat);
+        qt[i] = pass1_edge<LT, SAT, LEAN>(L, addr_t[i], ld_val(L, addr_t[i]), j, idx_o, r1, r2, sgn, min1, min2,
+                                          qs, msg_sat, post_sat);
       }
     }
   }
@@ -274,35 +239,22 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
   const float n1s = __uint_as_float(__float_as_uint(n1) | pm);
   const float n2s = __uint_as_float(__float_as_uint(n2) | pm);
 #pragma unroll
-  for (int st = 0; st < kSteps; ++st) {
-    if (st >= nstep) break;
-    float qv[kG * kChunk];
+  for (int c = 0; c < kMaxChunks; ++c) {
+    if (c >= nfull) break;
+    float qv[kChunk];
 #pragma unroll
-    for (int e = 0; e < kG * kChunk; ++e)
-      qv[e] = LEAN ? ld_val(L, addr[kG * kChunk * st + e]) : q[LEAN ? 0 : kG * kChunk * st + e];
+    for (int i = 0; i < kChunk; ++i) qv[i] = LEAN ? ld_val(L, addr[kChunk * c + i]) : q[LEAN ? 0 : kChunk * c + i];
 #pragma unroll
-    for (int e = 0; e < kG * kChunk; ++e) {
-      const int j = kG * kChunk * st + e;
-      pass2_edge<LT, SAT>(L, addr[j], qv[e], j, idx, min1, n1s, n2s, post_sat);
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < kG - 1; ++g) {
-    if (g < nrest) {
-      const int c = kG * nstep + g;
-      float qv[kChunk];
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i) qv[i] = LEAN ? ld_val(L, addr_r[kChunk * g + i]) : q_r[kChunk * g + i];
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i)
-        pass2_edge<LT, SAT>(L, addr_r[kChunk * g + i], qv[i], kChunk * c + i, idx, min1, n1s, n2s, post_sat);
+    for (int i = 0; i < kChunk; ++i) {
+      const int j = kChunk * c + i;
+      pass2_edge<LT, SAT>(L, addr[j], qv[i], j, idx, min1, n1s, n2s, post_sat);
     }
   }
   if (ntail) {
 #pragma unroll
     for (int i = 0; i < kChunk - 1; ++i)
       if (i < ntail)
-        pass2_edge<LT, SAT>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : q_t[i], kChunk * nfull + i, idx, min1, n1s,
+        pass2_edge<LT, SAT>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : qt[i], kChunk * nfull + i, idx, min1, n1s,
                             n2s, post_sat);
   }
   if constexpr (sizeof(MT) == 4) {

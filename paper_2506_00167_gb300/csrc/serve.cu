@@ -292,14 +292,14 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       int it = 1;
       bool ok = false, crc_ok = false;
       const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
-      RowIn row = load_row<MT, !TWO>(s_tab, rows[0], mag1, mag2, meta, k);
+      RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
           check_update<LT, MT, SAT, TWO>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
                                           a.msg_sat, a.post_sat);
           // the next row's table and record are ready before the barrier
           const int ln = l + 1 < m ? l + 1 : 0;
-          row = load_row<MT, !TWO>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
+          row = load_row(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {
