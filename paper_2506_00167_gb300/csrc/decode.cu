@@ -148,14 +148,14 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
       int it = 1;
       bool ok = false, crc_ok = false;
       const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
-      RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
+      RowIn<kChunk> row = load_row<kChunk>(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
           check_update<LT, MT, SAT, true>(row, k, Z, L, mag1, mag2, meta, l * Z + k, item.dummy_base + k, a.beta,
                                          a.msg_sat, a.post_sat);
           // the next row's table and record are ready before the barrier
           const int ln = l + 1 < m ? l + 1 : 0;
-          row = load_row(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
+          row = load_row<kChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {
@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
           if (wide) {
             hard_bitmap(L, hb, cb.n_eff, k, Z);
             group_sync(Z, g, wmask);
-            bad = syndrome_bitmap(s_tab, rows, hb, m, k, Z);
+            bad = syndrome_bitmap<kChunk>(s_tab, rows, hb, m, k, Z);
             if (has_crc) cr = cb_crc_part_hb(hb, ptab, cb.kb, k, Z);
           } else {
-            bad = syndrome_direct(s_tab, rows, m, k, Z, L);
+            bad = syndrome_direct<kChunk>(s_tab, rows, m, k, Z, L);
             if (has_crc) cr = cb_crc_part(L, ptab, cb.kb, k, Z);
           }
           ok = !group_any(Z, g, wmask, bad);
@@ -341,8 +341,8 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
         if (a.early_term || it == a.max_iter) {
           hard_bitmap_x2(L, hbA, hbB, A.n_eff, k, Z);
           group_sync(Z, g, 0xFFFFFFFFu);
-          const bool badA = !doneA && syndrome_bitmap(s_tab, rows, hbA, mA, k, Z);
-          const bool badB = !doneB && syndrome_bitmap(s_tab, rows, hbB, mB, k, Z);
+          const bool badA = !doneA && syndrome_bitmap<kChunk>(s_tab, rows, hbA, mA, k, Z);
+          const bool badB = !doneB && syndrome_bitmap<kChunk>(s_tab, rows, hbB, mB, k, Z);
           const bool crcA = CRC && !doneA && (A.flags & LDPC_CB_CRC24B) != 0;
           const bool crcB = CRC && !doneB && (Bc.flags & LDPC_CB_CRC24B) != 0;
           uint32_t rA = 0, rB = 0;

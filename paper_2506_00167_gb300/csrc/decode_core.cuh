@@ -62,15 +62,16 @@ __device__ __forceinline__ int rot(int k, uint32_t s, int Z) {
 // thread's compressed message record.  None of it is written by other threads
 // during a layer, so the next row's copy is loaded before the layer barrier
 // and only the posterior loads wait for it.
-static_assert(kChunk == 2 || kChunk == 4, "edge-table chunks of 2 or 4 edges");
-
+template <int CH>
 struct Chunk {
-  uint32_t b[kChunk], s[kChunk];  // column bases, shifts
+  static_assert(CH == 2 || CH == 4, "edge-table chunks of 2 or 4 edges");
+  uint32_t b[CH], s[CH];  // column bases, shifts
 };
 
-__device__ __forceinline__ Chunk load_chunk(const uint32_t* tab, int c) {
-  Chunk ch;
-  if constexpr (kChunk == 2) {
+template <int CH>
+__device__ __forceinline__ Chunk<CH> load_chunk(const uint32_t* tab, int c) {
+  Chunk<CH> ch;
+  if constexpr (CH == 2) {
     const uint4 v = *reinterpret_cast<const uint4*>(tab + 4 * c);
     ch.b[0] = v.x;
     ch.b[1] = v.y;
@@ -85,22 +86,23 @@ __device__ __forceinline__ Chunk load_chunk(const uint32_t* tab, int c) {
   return ch;
 }
 
+template <int CH>
 struct RowIn {
   const uint32_t* tab;
   int deg;
-  Chunk c0;
+  Chunk<CH> c0;
   float r1, r2;
   uint32_t mo;
 };
 
-template <typename MT>
-__device__ __forceinline__ RowIn load_row(const uint32_t* __restrict__ s_tab, uint32_t info,
-                                          const MT* __restrict__ mag1, const MT* __restrict__ mag2,
-                                          const uint32_t* __restrict__ meta, int rec) {
-  RowIn r;
+template <int CH, typename MT>
+__device__ __forceinline__ RowIn<CH> load_row(const uint32_t* __restrict__ s_tab, uint32_t info,
+                                              const MT* __restrict__ mag1, const MT* __restrict__ mag2,
+                                              const uint32_t* __restrict__ meta, int rec) {
+  RowIn<CH> r;
   r.tab = s_tab + (info & 0xFFFFu);
   r.deg = static_cast<int>(info >> 16);
-  r.c0 = load_chunk(r.tab, 0);
+  r.c0 = load_chunk<CH>(r.tab, 0);
   if constexpr (sizeof(MT) == 4) {  // float: both magnitudes in one 8-byte record
     const float2 rr = reinterpret_cast<const float2*>(mag1)[rec];
     r.r1 = rr.x;
@@ -152,9 +154,9 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
   st_val(L, a, v);
 }
 
-// One lifted check (l, k): row data in `in` (chunk c at tab[2 kChunk c ..]).
+// One lifted check (l, k): row data in `in` (chunk c at tab[2 CH c ..]).
 // Runs both passes, writes the posteriors and the new record.  The whole
-// chunks run unrolled; the deg % kChunk edges of a last, partial chunk run
+// chunks run unrolled; the deg % CH edges of a last, partial chunk run
 // after them (the table's padding entries are never touched).
 //
 // The record keeps the signs of the Q_j of the last update (edge j at bit
@@ -167,14 +169,22 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
 // slots during the layer) and pass 2 reads it back, instead of holding the
 // row's Q values in registers: one shared store and load more per edge for
 // about 30 fewer registers, which lets two 384-thread blocks share an SM.
-template <typename LT, typename MT, bool SAT, bool LEAN>
-__device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* __restrict__ L,
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH>
+__device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
                                              float msg_sat, float post_sat) {
   // checked builds: every posterior index stays inside the group's region
   // (dummy - k + Z elements: the columns, then one dummy slot per thread)
   const int lim = dummy - k + Z;
+  // PAD (the register-resident form): an odd row's padding edge is processed
+  // like a real one, on this thread's dummy slot (which can never be a
+  // minimum), instead of a separate tail: the latency-bound single loop runs
+  // faster with the uniform chunk loop.  Integer modes reset the dummy slot
+  // so that the padding edge's |Q| saturates (and, with the larger index,
+  // never beats a real edge).
+  constexpr bool PAD = !LEAN;
+  if constexpr (PAD && SAT) st_val(L, dummy, post_sat);
   const uint32_t* tab = in.tab;
   const int deg = in.deg;
   const float r1 = in.r1, r2 = in.r2;
@@ -182,40 +192,43 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
   const int idx_o = static_cast<int>(mo >> 27);
   // sign of R_j = stored Q-sign bit ^ parity, edge 0's moved to bit 31
   const uint32_t par_o = 0u - (static_cast<uint32_t>(__popc(mo << 5)) & 1u);
-  uint32_t sgn = (mo ^ par_o) << (32 - deg);
-  const int nfull = deg / kChunk;
-  const int ntail = deg - kChunk * nfull;
+  // (integer modes with PAD: positions past deg read as negative, so the
+  // padding edge sees Q = dummy + |R|, large and positive)
+  uint32_t sgn = (PAD && SAT) ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u))
+                              : ((mo ^ par_o) << (32 - deg));
+  const int nfull = PAD ? (deg + CH - 1) / CH : deg / CH;
+  const int ntail = PAD ? 0 : deg - CH * nfull;
 
-  float q[LEAN ? 1 : kMaxChunks * kChunk];
-  int addr[kMaxChunks * kChunk];
-  int addr_t[kChunk - 1];  // the partial chunk's edges
+  float q[LEAN ? 1 : MaxChunks<CH>::value * CH];
+  int addr[MaxChunks<CH>::value * CH];
+  int addr_t[CH - 1];  // the partial chunk's edges
   float min1 = 3.0e38f, min2 = 3.0e38f;  // SAT modes: keys |Q| * 32 + j
   uint32_t qs = 0;                       // Q sign bits, first edge highest
 #pragma unroll
-  for (int c = 0; c < kMaxChunks; ++c) {
+  for (int c = 0; c < MaxChunks<CH>::value; ++c) {
     if (c >= nfull) break;
-    const Chunk ch = c == 0 ? in.c0 : load_chunk(tab, c);
+    const Chunk<CH> ch = c == 0 ? in.c0 : load_chunk<CH>(tab, c);
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i)
-      addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
-    float lv[kChunk];
+    for (int i = 0; i < CH; ++i)
+      addr[CH * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
+    float lv[CH];
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) lv[i] = ld_val(L, addr[kChunk * c + i]);
+    for (int i = 0; i < CH; ++i) lv[i] = ld_val(L, addr[CH * c + i]);
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) {
-      const int j = kChunk * c + i;
+    for (int i = 0; i < CH; ++i) {
+      const int j = CH * c + i;
       const float Q = pass1_edge<LT, SAT, LEAN>(L, addr[j], lv[i], j, idx_o, r1, r2, sgn, min1, min2, qs, msg_sat,
                                                 post_sat);
       if constexpr (!LEAN) q[j] = Q;
     }
   }
-  float qt[kChunk - 1];
+  float qt[CH - 1];
   if (ntail) {
-    const Chunk ch = nfull == 0 ? in.c0 : load_chunk(tab, nfull);
+    const Chunk<CH> ch = nfull == 0 ? in.c0 : load_chunk<CH>(tab, nfull);
 #pragma unroll
-    for (int i = 0; i < kChunk - 1; ++i) {
+    for (int i = 0; i < CH - 1; ++i) {
       if (i < ntail) {
-        const int j = kChunk * nfull + i;
+        const int j = CH * nfull + i;
         addr_t[i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 2);
         qt[i] = pass1_edge<LT, SAT, LEAN>(L, addr_t[i], ld_val(L, addr_t[i]), j, idx_o, r1, r2, sgn, min1, min2,
                                           qs, msg_sat, post_sat);
@@ -239,22 +252,22 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
   const float n1s = __uint_as_float(__float_as_uint(n1) | pm);
   const float n2s = __uint_as_float(__float_as_uint(n2) | pm);
 #pragma unroll
-  for (int c = 0; c < kMaxChunks; ++c) {
+  for (int c = 0; c < MaxChunks<CH>::value; ++c) {
     if (c >= nfull) break;
-    float qv[kChunk];
+    float qv[CH];
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) qv[i] = LEAN ? ld_val(L, addr[kChunk * c + i]) : q[LEAN ? 0 : kChunk * c + i];
+    for (int i = 0; i < CH; ++i) qv[i] = LEAN ? ld_val(L, addr[CH * c + i]) : q[LEAN ? 0 : CH * c + i];
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) {
-      const int j = kChunk * c + i;
+    for (int i = 0; i < CH; ++i) {
+      const int j = CH * c + i;
       pass2_edge<LT, SAT>(L, addr[j], qv[i], j, idx, min1, n1s, n2s, post_sat);
     }
   }
   if (ntail) {
 #pragma unroll
-    for (int i = 0; i < kChunk - 1; ++i)
+    for (int i = 0; i < CH - 1; ++i)
       if (i < ntail)
-        pass2_edge<LT, SAT>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : qt[i], kChunk * nfull + i, idx, min1, n1s,
+        pass2_edge<LT, SAT>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : qt[i], CH * nfull + i, idx, min1, n1s,
                             n2s, post_sat);
   }
   if constexpr (sizeof(MT) == 4) {
@@ -263,7 +276,7 @@ __device__ __forceinline__ void check_update(const RowIn& in, int k, int Z, LT* 
     st_val(mag1, rec, n1);
     st_val(mag2, rec, n2);
   }
-  meta[rec] = qs | (static_cast<uint32_t>(idx) << 27);
+  meta[rec] = (PAD ? qs >> (CH * nfull - deg) : qs) | (static_cast<uint32_t>(idx) << 27);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
@@ -282,9 +295,10 @@ __device__ __forceinline__ void zero_records(MT* mag1, MT* mag2, uint32_t* meta,
 }
 
 // Edge e of a row whose chunks start at `tab`: (column base, shift).
+template <int CH>
 __device__ __forceinline__ uint2 edge_at(const uint32_t* tab, int e) {
-  const int c = e / kChunk, i = e % kChunk;
-  return make_uint2(tab[2 * kChunk * c + i], tab[2 * kChunk * c + kChunk + i]);
+  const int c = e / CH, i = e % CH;
+  return make_uint2(tab[2 * CH * c + i], tab[2 * CH * c + CH + i]);
 }
 
 // Z % 32 == 0: hard decisions of all n_eff columns into the bitmap hb
@@ -304,6 +318,7 @@ __device__ __forceinline__ void hard_bitmap(const LT* __restrict__ L, uint32_t* 
 // Z % 32 == 0: is any of this thread's (row, word) syndrome words nonzero?
 // Row l's syndrome is XOR_j rot(hb[c_j], s_j); word ww of rot(B, s) is the
 // funnel shift of words ww + s/32 and ww + s/32 + 1 (mod Z/32) by s % 32.
+template <int CH>
 __device__ __forceinline__ bool syndrome_bitmap(const uint32_t* __restrict__ tab, const uint32_t* __restrict__ rows,
                                                 const uint32_t* __restrict__ hb, int m_eff, int k, int Z) {
   const int W = Z >> 5;
@@ -316,7 +331,7 @@ __device__ __forceinline__ bool syndrome_bitmap(const uint32_t* __restrict__ tab
     const int deg = static_cast<int>(info >> 16);
     uint32_t x = 0;
     for (int e = 0; e < deg; ++e) {
-      const uint2 bs = edge_at(rt, e);
+      const uint2 bs = edge_at<CH>(rt, e);
       const int s = static_cast<int>(bs.y);
       const uint32_t* col = hb + (bs.x >> 5);
       int i0 = ww + (s >> 5);
@@ -330,7 +345,7 @@ __device__ __forceinline__ bool syndrome_bitmap(const uint32_t* __restrict__ tab
 }
 
 // Z < 32 (Z = 16): parity of this thread's check in every decoded row.
-template <typename LT>
+template <int CH, typename LT>
 __device__ __forceinline__ bool syndrome_direct(const uint32_t* __restrict__ tab, const uint32_t* __restrict__ rows,
                                                 int m_eff, int k, int Z, const LT* __restrict__ L) {
   uint32_t bad = 0;
@@ -340,7 +355,7 @@ __device__ __forceinline__ bool syndrome_direct(const uint32_t* __restrict__ tab
     const int deg = static_cast<int>(info >> 16);
     uint32_t p = 0;
     for (int e = 0; e < deg; ++e) {
-      const uint2 bs = edge_at(rt, e);
+      const uint2 bs = edge_at<CH>(rt, e);
       p ^= (L[static_cast<int>(bs.x) + rot(k, bs.y, Z)] < LT(0)) ? 1u : 0u;
     }
     bad |= p;
@@ -519,7 +534,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
-    const Chunk ch = load_chunk(tab, c);
+    const Chunk<kChunk> ch = load_chunk<kChunk>(tab, c);
 #pragma unroll
     for (int i = 0; i < kChunk; ++i)
       addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), dummy - k + Z, dummy, 3);

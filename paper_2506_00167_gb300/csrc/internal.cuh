@@ -12,8 +12,13 @@
 namespace ldpcgb {
 
 constexpr int kMaxDeg = 27;      // sign bits 0..26 + 5-bit argmin index in one word
-constexpr int kChunk = 2;        // edges per edge-table chunk: kChunk column bases, then kChunk shifts
-constexpr int kMaxChunks = (kMaxDeg + kChunk - 1) / kChunk;
+constexpr int kChunk = 2;        // edges per edge-table chunk of the batch decoders: bases, then shifts
+constexpr int kServeChunk = 4;   // the same for the serving loop (its latency-bound loop wants four)
+template <int CH>
+struct MaxChunks {
+  static constexpr int value = (kMaxDeg + CH - 1) / CH;
+};
+constexpr int kMaxChunks = MaxChunks<kChunk>::value;
 constexpr int kMaxZ = 384;
 constexpr int kMaxSmem = 232448; // 227 KB dynamic shared memory per block (sm_100 family)
 constexpr int kDecodeMaxBlock = 384;  // decoder blocks: two of them share an SM's registers
@@ -21,8 +26,9 @@ constexpr int kTileMaxBlock = 512;    // largest G * Z a tile may request
 constexpr int kCrcBlock = 256;
 
 // One (base graph, Z) pair as one decoder launch sees it.  Its edge table is,
-// per row, chunks of kChunk edges as 2 * kChunk words (one 16-byte load for
-// kChunk = 2): the column bases (col * Z), then the shifts (V mod Z); a row's
+// per row, chunks of CH edges as 2 * CH words (CH = kChunk for the batch
+// decoders, kServeChunk for the serving loop; one 16-byte load per chunk for
+// CH = 2): the column bases (col * Z), then the shifts (V mod Z); a row's
 // last chunk is padded with edges whose base is the launch's dummy slot and
 // whose shift is 0.  Then one word per row, start | (degree << 16) (start in
 // words from the table base); then padding to a multiple of 4 words.

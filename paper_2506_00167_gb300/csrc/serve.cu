@@ -292,14 +292,14 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       int it = 1;
       bool ok = false, crc_ok = false;
       const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
-      RowIn row = load_row(s_tab, rows[0], mag1, mag2, meta, k);
+      RowIn<kServeChunk> row = load_row<kServeChunk>(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
           check_update<LT, MT, SAT, TWO>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
                                           a.msg_sat, a.post_sat);
           // the next row's table and record are ready before the barrier
           const int ln = l + 1 < m ? l + 1 : 0;
-          row = load_row(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
+          row = load_row<kServeChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
           group_sync(Z, g, wmask);
         }
         if (a.early_term || it == a.max_iter) {
@@ -309,10 +309,10 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
           if (wide) {
             hard_bitmap(L, hb, cb.n_eff, k, Z);
             group_sync(Z, g, wmask);
-            bad = syndrome_bitmap(s_tab, rows, hb, m, k, Z);
+            bad = syndrome_bitmap<kServeChunk>(s_tab, rows, hb, m, k, Z);
             if (has_crc) cr = cb_crc_part_hb(hb, ptab, cb.kb, k, Z);
           } else {
-            bad = syndrome_direct(s_tab, rows, m, k, Z, L);
+            bad = syndrome_direct<kServeChunk>(s_tab, rows, m, k, Z, L);
             if (has_crc) cr = cb_crc_part(L, ptab, cb.kb, k, Z);
           }
           ok = !group_any(Z, g, wmask, bad);
@@ -623,7 +623,8 @@ namespace ldpcgb {
 int session_serve_info(ldpc_session* s, int* mode, int* interleave, int* max_iter, int* early_term, float* q_scale,
                        float* llr_sat, float* beta, float* msg_sat, float* post_sat, int* num_sms);
 int session_shape_count(ldpc_session* s);
-int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh);
+int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh,
+                        int chunk);
 int session_shape_lookup(ldpc_session* s, int bg, int Z);
 const uint32_t* session_crc_table(ldpc_session* s);
 void session_cb_crc_tables(ldpc_session* s, const uint32_t** table_b, const uint32_t** xpow32_b,
@@ -666,10 +667,10 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       ServeShape ss{};
       ShapeDev sd{};
       std::vector<uint32_t> tmp;
-      session_shape_table(s, i, 0, tmp, sd);  // geometry only
+      session_shape_table(s, i, 0, tmp, sd, kServeChunk);  // geometry only
       const int Z = sd.Z;
       ss.dummy_base = sd.nb * Z;
-      session_shape_table(s, i, ss.dummy_base, tabs, sd);
+      session_shape_table(s, i, ss.dummy_base, tabs, sd, kServeChunk);
       ss.sh = sd;
       tw = std::max(tw, sd.tab_words);
       ss.rec_cap = sd.mb * Z;

@@ -195,10 +195,11 @@ void cb_crc_byte_table(int K, std::vector<uint32_t>& out) {
 }
 
 // Edge table of base graph g at lifting Z for a launch whose dummy slot is at
-// element `dummy`: per row, chunks of kChunk edges (kChunk bases, kChunk
+// element `dummy`: per row, chunks of `chunk` edges (the bases, then the
 // shifts), the last chunk padded with (dummy, 0); then one word per row:
 // start | deg << 16.
-void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh) {
+void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh,
+                 int chunk = kChunk) {
   sh.tab_off = static_cast<int32_t>(tabs.size());
   std::vector<uint32_t> row_info;
   const int ne = static_cast<int>(g.row.size());
@@ -211,13 +212,13 @@ void build_table(const ldpc_session::Bg& g, int Z, int dummy, std::vector<uint32
     }
     const int deg = static_cast<int>(cols.size());
     const int start = static_cast<int>(tabs.size()) - sh.tab_off;
-    for (int c = 0; c < (deg + kChunk - 1) / kChunk; ++c) {
-      for (int i = 0; i < kChunk; ++i) {
-        const int j = kChunk * c + i;
+    for (int c = 0; c < (deg + chunk - 1) / chunk; ++c) {
+      for (int i = 0; i < chunk; ++i) {
+        const int j = chunk * c + i;
         tabs.push_back(static_cast<uint32_t>(j < deg ? cols[j] : dummy));
       }
-      for (int i = 0; i < kChunk; ++i) {
-        const int j = kChunk * c + i;
+      for (int i = 0; i < chunk; ++i) {
+        const int j = chunk * c + i;
         tabs.push_back(static_cast<uint32_t>(j < deg ? sh_[j] : 0));
       }
     }
@@ -496,9 +497,10 @@ int session_serve_info(ldpc_session* s, int* mode, int* interleave, int* max_ite
 
 int session_shape_count(ldpc_session* s) { return static_cast<int>(s->shapes.size()); }
 
-int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh) {
+int session_shape_table(ldpc_session* s, int shape, int dummy, std::vector<uint32_t>& tabs, ShapeDev& sh,
+                        int chunk) {
   sh = s->shapes[shape];
-  build_table(s->bgs[sh.bg], sh.Z, dummy, tabs, sh);
+  build_table(s->bgs[sh.bg], sh.Z, dummy, tabs, sh, chunk);
   return LDPC_OK;
 }
 
