@@ -352,7 +352,7 @@ def run_serving(args):
     curves = {}
     for loops in args.serve_loops:
         srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000,
-                     loops_per_sm=loops, cb_crc=args.cb_crc)
+                     loops_per_sm=loops, cb_crc=args.cb_crc, paired=not args.serve_unpaired)
         # warm-up
         warm = base_recs[:64].copy()
         warm["tag"] = np.arange(warm.size)
@@ -410,7 +410,7 @@ def run_serving(args):
         print(json.dumps({"check_log": list(log)}), flush=True)
     res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
                                    "mixed shapes, 128-entry URLLC codebook, INT8 service",
-                       "cb_crc": bool(args.cb_crc),
+                       "cb_crc": bool(args.cb_crc), "paired": not args.serve_unpaired,
                        "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
                        "loads": curves, "fp32_unbatched_plain": plain}}
     print(json.dumps(res), flush=True)
@@ -633,6 +633,8 @@ def main():
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
     ap.add_argument("--serve", action="store_true", help="replay the served request stream instead")
+    ap.add_argument("--serve-unpaired", action="store_true",
+                    help="INT8 service: one code block per thread group instead of two")
     ap.add_argument("--cb-crc", action="store_true",
                     help="mixed / served TBs of several code blocks carry a CRC per code block (CRC-aided exit)")
     ap.add_argument("--policy", action="store_true", help="time the puncturing allocations (RP, SeF, enforcer)")

@@ -331,10 +331,14 @@ typedef struct {
                               * loops per SM, messages in device memory) is withdrawn and returns
                               * LDPC_EINVAL: under load it once made an illegal access and once returned
                               * corrupted status words, cause not yet found */
-  int32_t flags;             /* 0, or LDPC_SERVE_CB_CRC: accept TBs whose code blocks carry their own CRC
-                              * (the loop then runs its variant with the code-block CRC exit) */
+  int32_t flags;             /* LDPC_SERVE_CB_CRC: accept TBs whose code blocks carry their own CRC (the
+                              * loop then runs its variant with the code-block CRC exit).
+                              * LDPC_SERVE_UNPAIRED: an INT8 service decodes one code block per thread
+                              * group (by default two, in half2 arithmetic: the batch decoder's paired
+                              * form; more blocks in flight per SM) */
 } ldpc_serve_desc;
 #define LDPC_SERVE_CB_CRC 1
+#define LDPC_SERVE_UNPAIRED 2
 
 typedef struct {
   int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16;

@@ -87,6 +87,7 @@ class ServeDescC(ctypes.Structure):
 
 
 SERVE_CB_CRC = 1  # ldpc_serve_desc.flags: accept TBs with code-block CRCs
+SERVE_UNPAIRED = 2  # ldpc_serve_desc.flags: INT8 service decodes one code block per thread group
 
 
 class ServeTbC(ctypes.Structure):

@@ -96,8 +96,9 @@ __device__ __noinline__ float bit_llr(int e, int n_re, int interleave, float inv
 
 // Resource element r of a code block (symbol y, punctured or not) into its
 // codeword positions, `out` pointing at the block's position t0.
-template <typename LT, int Qm, typename LoadSym, typename LoadMask>
-__device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, LT* out, int r, int n_re,
+// `out` is an LT* or any type whose out[e] takes an LT.
+template <typename LT, int Qm, typename Out, typename LoadSym, typename LoadMask>
+__device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, Out out, int r, int n_re,
                                               int E, int ncb, int interleave, float q_scale, float llr_sat,
                                               LoadSym ld_sym, LoadMask ld_msk) {
   float lam[Qm];

@@ -163,15 +163,35 @@ __device__ CbDev load_cb(const CbDev* p) {
   return c;
 }
 
+// Where the demapper writes: a block's LLRs (LT values), or one half of each
+// half2 posterior word of the paired INT8 loop (half 0: block A, 1: block B).
 template <typename LT>
-__device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, LT* L, int k, int Z) {
+struct PlainOut {
+  LT* p;
+  __device__ PlainOut shift(int n) const { return PlainOut{p + n}; }
+  __device__ LT& operator[](int i) const { return p[i]; }
+};
+
+struct PairLaneOut {
+  __half* p;
+  int lane;
+  struct Ref {
+    __half* q;
+    __device__ void operator=(int8_t v) const { *q = __short2half_rn(v); }
+  };
+  __device__ PairLaneOut shift(int n) const { return PairLaneOut{p + 2 * n, lane}; }
+  __device__ Ref operator[](int i) const { return Ref{p + 2 * i + lane}; }
+};
+
+template <typename LT, typename Out>
+__device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, Out L, int k, int Z) {
   using namespace demapcore;
   const int ncb = cb.n_eff * Z - cb.t0;  // circular buffer: E > ncb repeats it
   for (int p = k; p < cb.t0; p += Z) L[p] = LT(0);
   for (int p = cb.t0 + min(cb.E, ncb) + k; p < cb.n_eff * Z; p += Z) L[p] = LT(0);
   const float2* sym = reinterpret_cast<const float2*>(a.host_pool) + cb.re_off;
   const uint32_t* msk = reinterpret_cast<const uint32_t*>(a.host_pool) + cb.mask_off;
-  LT* out = L + cb.t0;
+  const Out out = L.shift(cb.t0);
 #pragma unroll 4
   for (int r = k; r < cb.n_re; r += Z) {
     const float2 y = ld_pool_f2(sym + r);
@@ -183,6 +203,126 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
       case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
       case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
       default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+    }
+  }
+}
+
+// Per-item bookkeeping, by every thread of the block: the block that finishes
+// a request's last item runs its TB CRC-24 (and the code-block CRCs of a
+// segmented TB), copies the bits to the result pool and writes the completion
+// record (sequence word last, after a system fence).
+__device__ __forceinline__ void finish_item(const ServeArgs& a, int req, int n_items, int tid, int lane, int* s_last,
+                                            uint32_t* s_res) {
+  // ---- request bookkeeping: the block finishing the last item completes the TB
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t prev = atomicAdd(a.counts + req, 1u);
+    *s_last = (prev + 1u == static_cast<uint32_t>(n_items)) ? 1 : 0;
+    if (*s_last) {
+      a.counts[req] = 0u;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (*s_last) {
+    const ServeReq* rq = a.reqs + req;
+    const uint64_t tag = ld_sys(&rq->tag);
+    const int n_cb = ld_sys(&rq->n_cb);
+    const int W = ld_sys(&rq->words);
+    const int seg = ld_sys(&rq->seg);
+    const int64_t bits_off = ld_sys(&rq->bits_off);
+    const int64_t status_off = ld_sys(&rq->status_off);
+    const int64_t result_off = ld_sys(&rq->result_off);
+    const volatile uint32_t* bits = a.arena + bits_off;
+    const bool rq_ok = check_ok(n_cb >= 1 && n_cb <= kMaxTbCb && W % n_cb == 0, 18, n_cb, W) &&
+                       check_ok(bits_off >= 0 && bits_off + W <= a.arena_words, 19, static_cast<int>(bits_off),
+                                static_cast<int>(a.arena_words)) &&
+                       check_ok(status_off >= 0 && status_off + n_cb <= a.arena_words, 20,
+                                static_cast<int>(status_off), static_cast<int>(a.arena_words));
+    if (tid < 32 && rq_ok) {
+      using namespace crccore;
+      // TB CRC over each block's first K/8 - 3*seg bytes (the blocks' K/32
+      // words lie back to back), zero-prefixed to whole words as in the
+      // batch CRC kernel
+      const int kw = W / n_cb;                  // words per block
+      const int cbb = 4 * kw - 3 * seg;         // TB bytes per block
+      const int tbytes = n_cb * cbb;
+      const int pad = (-tbytes) & 3;
+      const int VW = (tbytes + pad) >> 2;
+      const int per = (VW + 31) >> 5;
+      const int w0 = min(VW, lane * per);
+      const int w1 = min(VW, w0 + per);
+      uint32_t state = 0;
+      int b = max(0, 4 * w0 - pad);
+      int blk = b / cbb;
+      int j = b - blk * cbb;
+      int jw = -1;
+      uint32_t v = 0;
+      for (; b < 4 * w1 - pad; ++b) {
+        if ((j >> 2) != jw) {
+          jw = j >> 2;
+          v = bits[blk * kw + jw];
+        }
+        state = crc_byte_step(state, msb_first_byte(v, j), a.crc_table);
+        if (++j == cbb) {
+          ++blk;
+          j = 0;
+          jw = -1;
+        }
+      }
+      if (w0 < w1) state = gf2_mulmod(state, a.xpow32[VW - w1]);
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) state ^= __shfl_xor_sync(0xFFFFFFFFu, state, o);
+      // and each block's own CRC
+      for (int c = 0; seg && c < n_cb; ++c) {
+        const int pc = (kw + 31) >> 5;
+        const int v0 = min(kw, lane * pc);
+        const int v1 = min(kw, v0 + pc);
+        uint32_t st = 0;
+        for (int w = v0; w < v1; ++w) {
+          const uint32_t v = bits[c * kw + w];
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) st = crc_byte_step(st, msb_first_byte(v, j), a.crc_table_b);
+        }
+        if (v0 < v1) st = gf2_mulmod(st, a.xpow32_b[kw - v1], kPolyFullB);
+  #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) st ^= __shfl_xor_sync(0xFFFFFFFFu, st, o);
+        state |= st;
+      }
+      // status words come from other SMs' blocks: read past this SM's L1 like the bits
+      uint32_t st = lane < n_cb ? ld_sys(a.arena + status_off + lane) : (1u << 16);
+      uint32_t iters = st & 0xFFFFu;
+      uint32_t okb = (st >> 16) & 1u;
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        iters = max(iters, __shfl_xor_sync(0xFFFFFFFFu, iters, o));
+        okb &= __shfl_xor_sync(0xFFFFFFFFu, okb, o);
+      }
+      if (lane == 0) {
+        s_res[0] = state == 0u ? 1u : 0u;
+        s_res[1] = iters;
+        s_res[2] = okb;
+      }
+    }
+    if (result_off >= 0) {
+      volatile uint32_t* res = reinterpret_cast<volatile uint32_t*>(a.result_pool + result_off);
+      for (int i = tid; i < W; i += blockDim.x) res[i] = bits[i];
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t slot = atomicAdd(&a.dctl->done, 1u);
+      volatile ServeDone* rec = a.done + (slot % a.done_cap);
+      rec->tag = tag;
+      rec->d = static_cast<int32_t>(s_res[0]);
+      rec->max_iters = static_cast<int32_t>(s_res[1]);
+      rec->all_ok = static_cast<int32_t>(s_res[2]);
+      rec->req = req;
+      rec->t_dev = gtimer();
+      __threadfence_system();
+      rec->seq = slot + 1u;
+      __threadfence_system();
     }
   }
 }
@@ -274,7 +414,7 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
         st_val(L, ssh.dummy_base + k, a.post_sat);
       else
         L[ssh.dummy_base + k] = LT(kBigF);
-      demap_into_smem(a, cb, L, k, Z);  // puncture flushing + max-log, straight into shared memory
+      demap_into_smem<LT>(a, cb, PlainOut<LT>{L}, k, Z);  // puncture flushing + max-log, straight into shared memory
     }
     const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
     phase ^= 1u;
@@ -336,118 +476,185 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       }
       if (k == 0) a.arena[cb.llr_off] = static_cast<uint32_t>(it | (ok ? (1 << 16) : 0) | (crc_ok ? (1 << 17) : 0));
     }
-    // ---- request bookkeeping: the block finishing the last item completes the TB
+    finish_item(a, req, n_items, tid, lane, &s_last, s_res);
+    __syncthreads();
+  }
+  // the last block to leave tells the host (in mapped memory) that this launch is over
+  __syncthreads();
+  if (tid == 0) {
     __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-      const uint32_t prev = atomicAdd(a.counts + req, 1u);
-      s_last = (prev + 1u == static_cast<uint32_t>(n_items)) ? 1 : 0;
-      if (s_last) {
-        a.counts[req] = 0u;
-        __threadfence();
-      }
-    }
-    __syncthreads();
-    if (s_last) {
-      const ServeReq* rq = a.reqs + req;
-      const uint64_t tag = ld_sys(&rq->tag);
-      const int n_cb = ld_sys(&rq->n_cb);
-      const int W = ld_sys(&rq->words);
-      const int seg = ld_sys(&rq->seg);
-      const int64_t bits_off = ld_sys(&rq->bits_off);
-      const int64_t status_off = ld_sys(&rq->status_off);
-      const int64_t result_off = ld_sys(&rq->result_off);
-      const volatile uint32_t* bits = a.arena + bits_off;
-      const bool rq_ok = check_ok(n_cb >= 1 && n_cb <= kMaxTbCb && W % n_cb == 0, 18, n_cb, W) &&
-                         check_ok(bits_off >= 0 && bits_off + W <= a.arena_words, 19, static_cast<int>(bits_off),
-                                  static_cast<int>(a.arena_words)) &&
-                         check_ok(status_off >= 0 && status_off + n_cb <= a.arena_words, 20,
-                                  static_cast<int>(status_off), static_cast<int>(a.arena_words));
-      if (tid < 32 && rq_ok) {
-        using namespace crccore;
-        // TB CRC over each block's first K/8 - 3*seg bytes (the blocks' K/32
-        // words lie back to back), zero-prefixed to whole words as in the
-        // batch CRC kernel
-        const int kw = W / n_cb;                  // words per block
-        const int cbb = 4 * kw - 3 * seg;         // TB bytes per block
-        const int tbytes = n_cb * cbb;
-        const int pad = (-tbytes) & 3;
-        const int VW = (tbytes + pad) >> 2;
-        const int per = (VW + 31) >> 5;
-        const int w0 = min(VW, lane * per);
-        const int w1 = min(VW, w0 + per);
-        uint32_t state = 0;
-        int b = max(0, 4 * w0 - pad);
-        int blk = b / cbb;
-        int j = b - blk * cbb;
-        int jw = -1;
-        uint32_t v = 0;
-        for (; b < 4 * w1 - pad; ++b) {
-          if ((j >> 2) != jw) {
-            jw = j >> 2;
-            v = bits[blk * kw + jw];
-          }
-          state = crc_byte_step(state, msb_first_byte(v, j), a.crc_table);
-          if (++j == cbb) {
-            ++blk;
-            j = 0;
-            jw = -1;
-          }
-        }
-        if (w0 < w1) state = gf2_mulmod(state, a.xpow32[VW - w1]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) state ^= __shfl_xor_sync(0xFFFFFFFFu, state, o);
-        // and each block's own CRC
-        for (int c = 0; seg && c < n_cb; ++c) {
-          const int pc = (kw + 31) >> 5;
-          const int v0 = min(kw, lane * pc);
-          const int v1 = min(kw, v0 + pc);
-          uint32_t st = 0;
-          for (int w = v0; w < v1; ++w) {
-            const uint32_t v = bits[c * kw + w];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) st = crc_byte_step(st, msb_first_byte(v, j), a.crc_table_b);
-          }
-          if (v0 < v1) st = gf2_mulmod(st, a.xpow32_b[kw - v1], kPolyFullB);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) st ^= __shfl_xor_sync(0xFFFFFFFFu, st, o);
-          state |= st;
-        }
-        // status words come from other SMs' blocks: read past this SM's L1 like the bits
-        uint32_t st = lane < n_cb ? ld_sys(a.arena + status_off + lane) : (1u << 16);
-        uint32_t iters = st & 0xFFFFu;
-        uint32_t okb = (st >> 16) & 1u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          iters = max(iters, __shfl_xor_sync(0xFFFFFFFFu, iters, o));
-          okb &= __shfl_xor_sync(0xFFFFFFFFu, okb, o);
-        }
-        if (lane == 0) {
-          s_res[0] = state == 0u ? 1u : 0u;
-          s_res[1] = iters;
-          s_res[2] = okb;
-        }
-      }
-      if (result_off >= 0) {
-        volatile uint32_t* res = reinterpret_cast<volatile uint32_t*>(a.result_pool + result_off);
-        for (int i = tid; i < W; i += blockDim.x) res[i] = bits[i];
-      }
+    if (atomicAdd(&a.dctl->exits, 1u) + 1u == gridDim.x) {
       __threadfence_system();
+      *reinterpret_cast<volatile uint32_t*>(&a.lctl->exited_epoch) = a.epoch;
+    }
+  }
+}
+
+// INT8 service, two code blocks per thread group (the batch decoder's paired
+// form: half2 posteriors, block A in the low half, B in the high half; every
+// INT8 intermediate is an integer exact in fp16).  One loop per SM; an item
+// holds up to 2 G blocks of one TB (identical geometry), group g decodes
+// blocks 2g and 2g+1; check messages (three words per check) live in a
+// device-memory slot per (block, group), the posteriors, both hard-decision
+// bitmaps and the edge table (chunks of kChunk edges) in shared memory.
+template <bool CRC>
+__global__ void __launch_bounds__(kServeBlock, 1) serve_pair_kernel(const ServeArgs a) {
+  using namespace core;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
+  uint8_t* regions = smem + a.hdr_bytes;
+  __shared__ long long s_claim;
+  __shared__ int s_last;
+  __shared__ uint32_t s_res[3];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int beta = static_cast<int>(a.beta);
+  const __half2 msg = __float2half2_rn(a.msg_sat);
+  const __half2 post = __float2half2_rn(a.post_sat);
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (;;) {
+    if (tid == 0) s_claim = claim_item(a);
+    __syncthreads();
+    const long long idx = s_claim;
+    if (idx < 0) break;
+    const ServeItem* ip = a.items + (static_cast<uint32_t>(idx) % a.item_cap);
+    const int req = ld_sys(&ip->req), cb0 = ld_sys(&ip->cb0), count = ld_sys(&ip->count);
+    const int n_items = ld_sys(&ip->n_items);
+    const CbDev cb_first = load_cb(a.cbs + static_cast<uint32_t>(cb0) % a.cb_cap);
+    const bool item_ok = check_ok(static_cast<uint32_t>(req) < static_cast<uint32_t>(a.n_req), 10, req, a.n_req) &&
+                         check_ok(static_cast<uint32_t>(cb_first.shape) < static_cast<uint32_t>(a.n_shapes), 11,
+                                  cb_first.shape, a.n_shapes);
+    if (kChecked && !item_ok) {
       __syncthreads();
-      if (tid == 0) {
-        const uint32_t slot = atomicAdd(&a.dctl->done, 1u);
-        volatile ServeDone* rec = a.done + (slot % a.done_cap);
-        rec->tag = tag;
-        rec->d = static_cast<int32_t>(s_res[0]);
-        rec->max_iters = static_cast<int32_t>(s_res[1]);
-        rec->all_ok = static_cast<int32_t>(s_res[2]);
-        rec->req = req;
-        rec->t_dev = gtimer();
-        __threadfence_system();
-        rec->seq = slot + 1u;
-        __threadfence_system();
+      continue;
+    }
+    const ServeShape ssh = a.shapes[cb_first.shape];
+    const ShapeDev& sh = ssh.sh;
+    const int Z = sh.Z;
+    const int g = tid / Z;
+    const int k = tid - g * Z;
+
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
+      bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
+    }
+    const int pairs = (count + 1) >> 1;
+    bool active = g < pairs && check_ok(count >= 1 && count <= 2 * ssh.G, 12, count, 2 * ssh.G);
+    const bool hasB = 2 * g + 1 < count;
+    uint8_t* reg = regions + g * ssh.region_bytes;
+    uint32_t* L = reinterpret_cast<uint32_t*>(reg);
+    uint32_t* hbA = reinterpret_cast<uint32_t*>(reg + ssh.L_bytes);
+    uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + ssh.L_bytes + ssh.hb_bytes);
+    uint32_t* mags = reinterpret_cast<uint32_t*>(a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) *
+                                                               a.rscratch_group);
+    uint32_t* sg1 = mags + ssh.rec_cap;
+    uint32_t* sg2 = sg1 + ssh.rec_cap;
+    CbDev A{}, B{};
+    if (active) {
+      A = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g) % a.cb_cap));
+      if (hasB) B = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g + 1) % a.cb_cap));
+      if constexpr (kChecked) {
+        for (int h = 0; h < (hasB ? 2 : 1); ++h) {
+          const CbDev& c = h ? B : A;
+          active = active &&
+                   check_ok(c.shape == cb_first.shape && c.Z == Z && c.n_eff == A.n_eff && c.m_eff == A.m_eff &&
+                                c.n_eff <= sh.nb && c.m_eff <= sh.mb, 13, c.shape, cb_first.shape) &&
+                   check_ok(c.bits_off >= 0 && c.bits_off + ((c.kb * Z) >> 5) <= a.arena_words, 14,
+                            static_cast<int>(c.bits_off), static_cast<int>(a.arena_words)) &&
+                   check_ok(c.llr_off >= 0 && c.llr_off < a.arena_words, 15, static_cast<int>(c.llr_off),
+                            static_cast<int>(a.arena_words)) &&
+                   check_ok(c.re_off >= 0 && c.re_off + c.n_re <= a.pool_f2, 16, static_cast<int>(c.re_off),
+                            static_cast<int>(a.pool_f2)) &&
+                   check_ok(c.mask_off >= 0 && c.mask_off + ((c.n_re + 31) >> 5) <= a.pool_words, 17,
+                            static_cast<int>(c.mask_off), static_cast<int>(a.pool_words));
+        }
       }
     }
+    if (active) {
+      for (int r = k; r < A.m_eff * Z; r += Z) {
+        mags[r] = 0u;
+        sg1[r] = 0u;
+        sg2[r] = 0u;
+      }
+      // both blocks' LLRs into the two halves of the posterior words (B's half 0 without a second block)
+      __half* Lh = reinterpret_cast<__half*>(L);
+      demap_into_smem<int8_t>(a, A, PairLaneOut{Lh, 0}, k, Z);
+      if (hasB) {
+        demap_into_smem<int8_t>(a, B, PairLaneOut{Lh, 1}, k, Z);
+      } else {
+        for (int p = k; p < A.n_eff * Z; p += Z) Lh[2 * p + 1] = __float2half(0.0f);
+      }
+    }
+    const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
+    phase ^= 1u;
+    if (!__syncthreads_and(got)) {
+      if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
+      mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
+      break;
+    }
+
+    if (active) {
+      const uint32_t* rows = s_tab + sh.row_off;
+      const int m = A.m_eff;
+      const int dummy = ssh.dummy_base + k;
+      bool doneA = false, doneB = !hasB;
+      PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
+      for (int it = 1;; ++it) {
+        for (int l = 0; l < m; ++l) {
+          check_update_x2(prow, k, Z, L, mags, sg1, sg2, l * Z + k, dummy, beta, msg, post);
+          const int ln = l + 1 < m ? l + 1 : 0;
+          prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
+          group_sync(Z, g, 0xFFFFFFFFu);
+        }
+        if (a.early_term || it == a.max_iter) {
+          hard_bitmap_x2(L, hbA, hbB, A.n_eff, k, Z);
+          group_sync(Z, g, 0xFFFFFFFFu);
+          const bool badA = !doneA && syndrome_bitmap<kChunk>(s_tab, rows, hbA, m, k, Z);
+          const bool badB = !doneB && syndrome_bitmap<kChunk>(s_tab, rows, hbB, m, k, Z);
+          const bool crcA = CRC && !doneA && (A.flags & LDPC_CB_CRC24B) != 0;
+          const bool crcB = CRC && !doneB && (B.flags & LDPC_CB_CRC24B) != 0;
+          uint32_t rA = 0, rB = 0;
+          if (crcA || crcB) {
+            const uint32_t* ptab = a.cbcrc + sh.crc_off;
+            if (crcA) rA = cb_crc_part_hb(hbA, ptab, A.kb, k, Z);
+            if (crcB) rB = cb_crc_part_hb(hbB, ptab, A.kb, k, Z);
+          }
+          const bool okA = !group_any(Z, g, 0xFFFFFFFFu, badA);
+          const bool okB = !group_any(Z, g, 0xFFFFFFFFu, badB);
+          bool cA = false, cB = false;
+          if (crcA || crcB) {  // both blocks' XORs meet in their bitmaps' (now free) parity words
+            const bool zA = group_xor_zero2(Z, g, rA, rB, hbA + A.kb * (Z >> 5), hbB + A.kb * (Z >> 5), k, &cB);
+            cA = crcA && zA;
+            cB = crcB && cB;
+          }
+          const bool last = it == a.max_iter;
+          const int nw = A.kb * (Z >> 5);
+          if (!doneA && (((okA || cA) && a.early_term) || last)) {
+            uint32_t* out = a.arena + A.bits_off;
+            for (int i = k; i < nw; i += Z) out[i] = hbA[i];
+            if (k == 0) a.arena[A.llr_off] = static_cast<uint32_t>(it | (okA ? (1 << 16) : 0) | (cA ? (1 << 17) : 0));
+            doneA = true;
+          }
+          if (!doneB && (((okB || cB) && a.early_term) || last)) {
+            uint32_t* out = a.arena + B.bits_off;
+            for (int i = k; i < nw; i += Z) out[i] = hbB[i];
+            if (k == 0) a.arena[B.llr_off] = static_cast<uint32_t>(it | (okB ? (1 << 16) : 0) | (cB ? (1 << 17) : 0));
+            doneB = true;
+          }
+          if (doneA && doneB) break;
+        }
+      }
+    }
+    finish_item(a, req, n_items, tid, lane, &s_last, s_res);
     __syncthreads();
   }
   // the last block to leave tells the host (in mapped memory) that this launch is over
@@ -470,7 +677,9 @@ const void* serve_kernel_for(int mode) {
   }
 }
 
-const void* serve_kernel_ptr(int mode, bool two, bool crc) {
+const void* serve_kernel_ptr(int mode, bool two, bool crc, bool pair) {
+  if (pair) return crc ? reinterpret_cast<const void*>(&serve_pair_kernel<true>)
+                       : reinterpret_cast<const void*>(&serve_pair_kernel<false>);
   if (crc) return two ? serve_kernel_for<true, true>(mode) : serve_kernel_for<false, true>(mode);
   return two ? serve_kernel_for<true, false>(mode) : serve_kernel_for<false, false>(mode);
 }
@@ -523,6 +732,7 @@ struct ldpc_server {
   uint32_t* crc_table = nullptr;
   uint8_t* rscratch = nullptr;
   bool two = true;  // two loops per SM (messages in device memory)
+  bool pair = false;  // INT8: two code blocks per thread group (serve_pair_kernel)
   bool cb_crc = false;  // LDPC_SERVE_CB_CRC: TBs with code-block CRCs accepted
   std::vector<ServeShape> hshapes;
   ServeArgs args{};
@@ -579,7 +789,7 @@ int launch_loop(ldpc_server* v) {
   cudaError_t z = cudaMemsetAsync(&v->args.dctl->exits, 0, sizeof(uint32_t), v->stream);
   if (z != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop reset: ") + cudaGetErrorString(z));
   void* kargs[] = {&v->args};
-  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two, v->cb_crc), dim3(v->grid), dim3(kServeBlock), kargs,
+  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair), dim3(v->grid), dim3(kServeBlock), kargs,
                                    static_cast<size_t>(v->smem), v->stream);
   if (e != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop launch: ") + cudaGetErrorString(e));
   e = cudaEventRecord(v->done_ev, v->stream);
@@ -637,7 +847,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
   try {
     if (!s || !d || !out || !d->host_pool || d->max_inflight < 1 || d->max_inflight > 65536 ||
         d->arena_bytes < 1024 || d->idle_timeout_us < 1 || d->loops_per_sm < 0 || d->loops_per_sm > 2 ||
-        (d->flags & ~LDPC_SERVE_CB_CRC))
+        (d->flags & ~(LDPC_SERVE_CB_CRC | LDPC_SERVE_UNPAIRED)))
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
     *out = nullptr;
     auto* v = new (std::nothrow) ldpc_server();
@@ -657,7 +867,9 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     session_serve_info(s, &v->mode, &interleave, &max_iter, &et, &q_scale, &llr_sat, &beta, &msg_sat, &post_sat,
                        &sms);
     cudaGetDevice(&v->device);
+    v->pair = v->mode == LDPC_I8 && !(d->flags & LDPC_SERVE_UNPAIRED);
     const int esz = v->mode == LDPC_F32 ? 4 : (v->mode == LDPC_I8 ? 1 : 2);
+    const int chunk = v->pair ? kChunk : kServeChunk;  // the paired update reads two-edge chunks
     // ---- per-shape tables and layouts, sized for the largest block of the shape
     std::vector<uint32_t> tabs;
     int tw = 0;
@@ -667,18 +879,24 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       ServeShape ss{};
       ShapeDev sd{};
       std::vector<uint32_t> tmp;
-      session_shape_table(s, i, 0, tmp, sd, kServeChunk);  // geometry only
+      session_shape_table(s, i, 0, tmp, sd, chunk);  // geometry only
       const int Z = sd.Z;
       ss.dummy_base = sd.nb * Z;
-      session_shape_table(s, i, ss.dummy_base, tabs, sd, kServeChunk);
+      session_shape_table(s, i, ss.dummy_base, tabs, sd, chunk);
       ss.sh = sd;
       tw = std::max(tw, sd.tab_words);
       ss.rec_cap = sd.mb * Z;
-      ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
       ss.hb_bytes = (Z % 32 == 0) ? align16s(sd.nb * (Z / 32) * 4) : 0;
-      const int rec_bytes = 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
-      ss.region_bytes = ss.L_bytes + ss.hb_bytes + (v->two ? 0 : rec_bytes);
-      rec_group = std::max<int64_t>(rec_group, rec_bytes);
+      if (v->pair) {  // half2 posteriors, two bitmaps; three message words per check in device memory
+        ss.L_bytes = align16s((sd.nb + 1) * Z * 4);
+        ss.region_bytes = ss.L_bytes + 2 * ss.hb_bytes;
+        rec_group = std::max<int64_t>(rec_group, 3 * align16s(ss.rec_cap * 4));
+      } else {
+        ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
+        const int rec_bytes = 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
+        ss.region_bytes = ss.L_bytes + ss.hb_bytes + (v->two ? 0 : rec_bytes);
+        rec_group = std::max<int64_t>(rec_group, rec_bytes);
+      }
       ss.G = std::max(1, kServeBlock / Z);
       if (Z > 32) ss.G = std::min(ss.G, 15);
       v->hshapes.push_back(ss);
@@ -688,18 +906,18 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     for (auto& ss : v->hshapes) {
       while (ss.G > 1 && hdr + ss.G * ss.region_bytes > kMaxSmem) --ss.G;
       if (ss.sh.Z == 16 && ss.G > 1 && (ss.G & 1)) --ss.G;
-      ss.feasible = hdr + ss.G * ss.region_bytes <= kMaxSmem;
+      ss.feasible = hdr + ss.G * ss.region_bytes <= kMaxSmem && (!v->pair || ss.sh.Z % 32 == 0);
       if (ss.feasible) smem = std::max(smem, hdr + ss.G * ss.region_bytes);
     }
     v->smem = smem;
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode, v->two, v->cb_crc));
+    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair));
     if (e == cudaSuccess && smem + static_cast<int>(fa.sharedSizeBytes) > kMaxSmem) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode, v->two, v->cb_crc), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode, v->two, v->cb_crc), kServeBlock, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair), kServeBlock, smem);
     if (e != cudaSuccess || per_sm < 1) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, std::string("serve loop does not fit an SM (") + std::to_string(smem) +
@@ -710,7 +928,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     int gmax = 1;
     for (auto& ss : v->hshapes)
       if (ss.feasible) gmax = std::max(gmax, ss.G);
-    if (v->two) {
+    if (v->two || v->pair) {
       e = cudaMalloc(&v->rscratch, static_cast<size_t>(v->grid) * gmax * rec_group);
       if (e != cudaSuccess) {
         free_server(v);
@@ -880,7 +1098,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const int mw = (n_re + 31) / 32;
     const int cols = (tb.E + t0 + tb.Z - 1) / tb.Z;
     const int m_eff = std::min(sd.mb, std::max(sd.mc, cols - sd.kb));
-    const int G = std::max(1, std::min(ss.G, tb.n_cb));
+    const int G = std::max(1, std::min(v->pair ? 2 * ss.G : ss.G, tb.n_cb));  // code blocks per item
     const int n_items = (tb.n_cb + G - 1) / G;
     if (v->free_slots.empty() || v->items_inflight + n_items > v->item_cap || v->cbs_inflight + tb.n_cb > v->cb_cap)
       break;

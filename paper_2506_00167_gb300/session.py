@@ -263,11 +263,12 @@ class Server:
     requests' symbols and masks, and receiving decoded bits.  Requests are
     numpy arrays of ``abi.SERVE_TB_NP``.  ``cb_crc``: accept TBs whose code
     blocks carry their own CRC (the loop runs its CRC-exit variant).
+    ``paired``: an INT8 service decodes two code blocks per thread group.
     """
 
     def __init__(self, session: Session, host_pool: torch.Tensor, result_pool: torch.Tensor | None = None,
                  arena_bytes: int = 8 << 30, max_inflight: int = 4096, idle_timeout_us: int = 200000,
-                 loops_per_sm: int = 1, cb_crc: bool = False):
+                 loops_per_sm: int = 1, cb_crc: bool = False, paired: bool = True):
         for t, name in ((host_pool, "host_pool"), (result_pool, "result_pool")):
             if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous pinned CPU tensor")
@@ -276,7 +277,7 @@ class Server:
                            host_pool.numel() * host_pool.element_size(),
                            result_pool.data_ptr() if result_pool is not None else None,
                            result_pool.numel() * result_pool.element_size() if result_pool is not None else 0,
-                           int(loops_per_sm), abi.SERVE_CB_CRC if cb_crc else 0)
+                           int(loops_per_sm), (abi.SERVE_CB_CRC if cb_crc else 0) | (0 if paired else abi.SERVE_UNPAIRED))
         h = ctypes.c_void_p()
         abi.check(abi.load().ldpc_serve_start(session.handle, ctypes.byref(d), ctypes.byref(h)), "ldpc_serve_start")
         self.handle = h.value
