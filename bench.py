@@ -350,9 +350,11 @@ def run_serving(args):
     sess = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
     base_recs = tb_records(w, mask_base, abi.SERVE_TB_NP)
     curves = {}
-    for loops in args.serve_loops:
+    runs = [(f, lp, th) for f in args.serve_form for lp in args.serve_loops
+            for th in (args.serve_pair_threshold if f == "auto" else [0])]
+    for form, loops, thr in runs:
         srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000,
-                     loops_per_sm=loops, cb_crc=args.cb_crc, paired=not args.serve_unpaired)
+                     loops_per_sm=loops, cb_crc=args.cb_crc, paired=SERVE_FORMS[form], pair_threshold=thr)
         # warm-up
         warm = base_recs[:64].copy()
         warm["tag"] = np.arange(warm.size)
@@ -362,12 +364,16 @@ def run_serving(args):
             t_arr, pidx = arrivals(args.serve_slots, n_ue=40, tb_per_slot=load, n_pool=w.n_tb, seed=6)
             recs = base_recs[pidx].copy()
             recs["tag"] = np.arange(recs.size)
+            st0 = srv.stats()
             t0 = time.perf_counter()
             done = srv.replay(recs, t_arr, timeout_ms=60000)
             wall = time.perf_counter() - t0
+            st1 = srv.stats()
+            n_single = st1["items_single"] - st0["items_single"]
+            n_paired = st1["items_paired"] - st0["items_paired"]
             lat_us = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
             bits = int(kbits[pidx].sum())
-            loads.append({"loops_per_sm": loops, "tb_per_ue_per_slot": load, "requests": int(recs.size),
+            loads.append({"form": form, "pair_threshold": thr, "loops_per_sm": loops, "tb_per_ue_per_slot": load, "requests": int(recs.size),
                           "code_blocks": int(recs["n_cb"].sum()),
                           "offered_gbps": bits / (args.serve_slots * SLOT_NS / 1e9) / 1e9,
                           "served_gbps": bits / wall / 1e9, "wall_s": wall,
@@ -375,10 +381,12 @@ def run_serving(args):
                           "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
                           "tb_crc_ok_frac": float(np.mean(done["d"])),
                           "mean_max_iters": float(np.mean(done["max_iters"])),
+                          "items_single": int(n_single), "items_paired": int(n_paired),
+                          "loop_launches": int(st1["launches"] - st0["launches"]),
                           **_stall_stats(done)})
             print(json.dumps({"serving_point": loads[-1]}), flush=True)
         srv.stop()
-        curves[f"{loops}_loops_per_sm"] = loads
+        curves[f"{form}{thr or ''}_{loops}_loops_per_sm"] = loads
     # FP32 unbatched plain path: one TB at a time, synchronised
     sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
     n_plain = min(args.serve_plain, w.n_tb)
@@ -410,10 +418,13 @@ def run_serving(args):
         print(json.dumps({"check_log": list(log)}), flush=True)
     res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
                                    "mixed shapes, 128-entry URLLC codebook, INT8 service",
-                       "cb_crc": bool(args.cb_crc), "paired": not args.serve_unpaired,
+                       "cb_crc": bool(args.cb_crc), "forms": args.serve_form,
                        "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
                        "loads": curves, "fp32_unbatched_plain": plain}}
     print(json.dumps(res), flush=True)
+
+
+SERVE_FORMS = {"auto": "auto", "paired": True, "single": False}
 
 
 def _stall_stats(done):
@@ -633,8 +644,12 @@ def main():
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
     ap.add_argument("--serve", action="store_true", help="replay the served request stream instead")
-    ap.add_argument("--serve-unpaired", action="store_true",
-                    help="INT8 service: one code block per thread group instead of two")
+    ap.add_argument("--serve-form", choices=sorted(SERVE_FORMS), nargs="+", default=["auto"],
+                    help="INT8 service: pair code blocks by load (auto), always, or never (single); "
+                         "several run one after the other")
+    ap.add_argument("--serve-pair-threshold", type=int, nargs="+", default=[0],
+                    help="auto form: pair a request when more work items than this would be in flight "
+                         "(0: one per loop thread block); several run one after the other")
     ap.add_argument("--cb-crc", action="store_true",
                     help="mixed / served TBs of several code blocks carry a CRC per code block (CRC-aided exit)")
     ap.add_argument("--policy", action="store_true", help="time the puncturing allocations (RP, SeF, enforcer)")

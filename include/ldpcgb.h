@@ -333,12 +333,22 @@ typedef struct {
                               * corrupted status words, cause not yet found */
   int32_t flags;             /* LDPC_SERVE_CB_CRC: accept TBs whose code blocks carry their own CRC (the
                               * loop then runs its variant with the code-block CRC exit).
-                              * LDPC_SERVE_UNPAIRED: an INT8 service decodes one code block per thread
-                              * group (by default two, in half2 arithmetic: the batch decoder's paired
-                              * form; more blocks in flight per SM) */
+                              * INT8 services decode a request's code blocks in one of two forms, chosen
+                              * per request at admission: single (one block per thread group, check
+                              * messages in shared memory: the lower latency per block) or paired (two
+                              * blocks per thread group in half2 arithmetic, the batch decoder's paired
+                              * form: more blocks in flight per SM).  By default a request is paired when
+                              * the work items in flight together with its own single-form items would
+                              * exceed pair_threshold; LDPC_SERVE_UNPAIRED: never; LDPC_SERVE_PAIRED:
+                              * always (where the shape allows it, Z a multiple of 32).  Results are the
+                              * same bits either way; the two flags together are LDPC_EINVAL */
+  int32_t pair_threshold;    /* work items in flight above which INT8 requests are paired; 0: the number
+                              * of loop thread blocks (one per SM) */
+  int32_t reserved;          /* 0 */
 } ldpc_serve_desc;
 #define LDPC_SERVE_CB_CRC 1
 #define LDPC_SERVE_UNPAIRED 2
+#define LDPC_SERVE_PAIRED 4
 
 typedef struct {
   int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16;
@@ -377,6 +387,9 @@ LDPC_API int ldpc_serve_poll(ldpc_server *srv, ldpc_serve_done *out, int32_t cap
  * LDPC_ETIMEOUT if nothing completes for timeout_ms. */
 LDPC_API int ldpc_serve_replay(ldpc_server *srv, const ldpc_serve_tb *tbs, const int64_t *arrival_ns, int32_t n,
                                ldpc_serve_done *out, int32_t timeout_ms);
+/* Counters since start, out[0..n): requests admitted, work items admitted in the single form, in
+ * the paired form, device loop launches (later entries 0). */
+LDPC_API int ldpc_serve_stats(ldpc_server *srv, int64_t *out, int32_t n);
 /* Stop the device loop (bounded wait) and free the server. */
 LDPC_API int ldpc_serve_stop(ldpc_server *srv);
 

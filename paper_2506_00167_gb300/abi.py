@@ -29,7 +29,8 @@ EXPORTED = [
     "ldpc_device_errors", "ldpc_check_log", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
     "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
     "ldpc_graph_create", "ldpc_graph_launch", "ldpc_graph_destroy",
-    "ldpc_serve_start", "ldpc_serve_submit", "ldpc_serve_poll", "ldpc_serve_replay", "ldpc_serve_stop",
+    "ldpc_serve_start", "ldpc_serve_submit", "ldpc_serve_poll", "ldpc_serve_replay", "ldpc_serve_stats",
+    "ldpc_serve_stop",
     "ldpc_puncture_alloc", "ldpc_feasibility_enforce", "ldpc_sc_mask", "ldpc_rt_odu_codebook",
 ]
 POLICY_RP, POLICY_SEF = 0, 1
@@ -83,11 +84,12 @@ class ServeDescC(ctypes.Structure):
                 ("idle_timeout_us", ctypes.c_int32), ("host_pool", ctypes.c_void_p),
                 ("host_pool_bytes", ctypes.c_uint64), ("result_pool", ctypes.c_void_p),
                 ("result_pool_bytes", ctypes.c_uint64), ("loops_per_sm", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("pair_threshold", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 SERVE_CB_CRC = 1  # ldpc_serve_desc.flags: accept TBs with code-block CRCs
-SERVE_UNPAIRED = 2  # ldpc_serve_desc.flags: INT8 service decodes one code block per thread group
+SERVE_UNPAIRED = 2  # ldpc_serve_desc.flags: INT8 requests always in the single form
+SERVE_PAIRED = 4  # ldpc_serve_desc.flags: INT8 requests always in the paired form (where the shape allows)
 
 
 class ServeTbC(ctypes.Structure):
@@ -177,6 +179,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ldpc_serve_submit.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
     lib.ldpc_serve_poll.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
     lib.ldpc_serve_replay.argtypes = [vp, vp, vp, i32, vp, i32]
+    lib.ldpc_serve_stats.argtypes = [vp, vp, i32]
     lib.ldpc_serve_stop.argtypes = [vp]
     lib.ldpc_last_error.restype = ctypes.c_char_p
     lib.ldpc_version.restype = ctypes.c_char_p

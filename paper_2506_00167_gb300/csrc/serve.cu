@@ -38,6 +38,8 @@ constexpr int kServeXpowWords = kMaxTbCb * 8448 / 32 * 2;  // TB CRC shift table
 
 struct ServeItem {  // host ring entry
   int32_t req, cb0, count, n_items;
+  int32_t pair;  // INT8: decode the item's blocks two per thread group
+  int32_t pad;
 };
 
 struct ServeReq {  // host record per request slot
@@ -72,9 +74,12 @@ struct LoopCtl {  // device-written, host-mapped: lets the host see the loop end
   uint32_t pad[15];
 };
 
-struct ServeShape {  // one (bg, Z) shape with its shared-memory layout in the loop
-  ShapeDev sh;
-  int32_t G, region_bytes, L_bytes, hb_bytes, rec_cap, dummy_base, feasible, pad;
+struct ServeShape {  // one (bg, Z) shape with its shared-memory layouts in the loop
+  ShapeDev sh;   // table in four-edge chunks, for the single form
+  ShapeDev shp;  // table in two-edge chunks, for the paired form (INT8)
+  int32_t G, region_bytes, L_bytes, hb_bytes, rec_cap, dummy_base, feasible;
+  int32_t Gp, region_p, Lp_bytes, feasible_p;  // paired form: groups, region, posterior bytes
+  int32_t pad;
 };
 
 struct ServeArgs {
@@ -327,15 +332,259 @@ __device__ __forceinline__ void finish_item(const ServeArgs& a, int req, int n_i
   }
 }
 
-// TWO: two loops per SM.  The check messages live in a global slot per
-// (block, group) and each check parks its Q values in the posterior slots
-// between its passes, so the loop fits 80 registers and two 384-thread blocks
-// share an SM: twice the code blocks in flight at a modest cost per block.
-// CRC: the variant with the code-block CRC exit (a service started with
-// LDPC_SERVE_CB_CRC); without it the loop is the plain decoder.
-template <typename LT, typename MT, bool SAT, bool TWO, bool CRC>
-__global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const ServeArgs a) {
+// Decode of one item's blocks, one block per thread group (single form).
+// Loads the shape's table (bulk copy), demaps straight into shared memory,
+// runs the layered decoder, writes bits and status to the arena.  Returns
+// false if the table copy did not complete within its bounded wait.
+template <typename LT, typename MT, bool SAT, bool CRC>
+__device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape& ssh, const CbDev& cb_first,
+                                            int cb0, int count, uint32_t& phase, uint32_t* s_tab, uint64_t* s_bar,
+                                            uint8_t* regions) {
   using namespace core;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const ShapeDev& sh = ssh.sh;
+  const int Z = sh.Z;
+  const int g = tid / Z;
+  const int k = tid - g * Z;
+  const uint32_t wmask = (Z >= 32) ? 0xFFFFFFFFu : (((1u << Z) - 1u) << (lane & ~(Z - 1)));
+  if (tid == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
+    bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
+  }
+  bool active = g < count && check_ok(count >= 1 && count <= ssh.G, 12, count, ssh.G);
+  CbDev cb{};
+  LT* L = reinterpret_cast<LT*>(regions + g * ssh.region_bytes);
+  uint8_t* rbase = regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
+  MT* mag1 = reinterpret_cast<MT*>(rbase);
+  MT* mag2 = mag1 + ssh.rec_cap;
+  uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
+  if (active) {
+    cb = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + g) % a.cb_cap));
+    if constexpr (kChecked) {  // the block's records against the shape, the arena and the host pool
+      active = check_ok(cb.shape == cb_first.shape && cb.Z == Z && cb.n_eff <= sh.nb && cb.m_eff <= sh.mb, 13,
+                        cb.shape, cb_first.shape) &&
+               check_ok(cb.bits_off >= 0 && cb.bits_off + ((cb.kb * Z) >> 5) <= a.arena_words, 14,
+                        static_cast<int>(cb.bits_off), static_cast<int>(a.arena_words)) &&
+               check_ok(cb.llr_off >= 0 && cb.llr_off < a.arena_words, 15, static_cast<int>(cb.llr_off),
+                        static_cast<int>(a.arena_words)) &&
+               check_ok(cb.re_off >= 0 && cb.re_off + cb.n_re <= a.pool_f2, 16, static_cast<int>(cb.re_off),
+                        static_cast<int>(a.pool_f2)) &&
+               check_ok(cb.mask_off >= 0 && cb.mask_off + ((cb.n_re + 31) >> 5) <= a.pool_words, 17,
+                        static_cast<int>(cb.mask_off), static_cast<int>(a.pool_words));
+    }
+  }
+  if (active) {
+    zero_records(mag1, mag2, meta, cb.m_eff * Z, k, Z);
+    if constexpr (SAT)
+      st_val(L, ssh.dummy_base + k, a.post_sat);
+    else
+      L[ssh.dummy_base + k] = LT(kBigF);
+    demap_into_smem<LT>(a, cb, PlainOut<LT>{L}, k, Z);  // puncture flushing + max-log, straight into shared memory
+  }
+  const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
+  phase ^= 1u;
+  if (!__syncthreads_and(got)) {
+    if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
+    mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
+    return false;
+  }
+  if (active) {
+    const uint32_t* rows = s_tab + sh.row_off;
+    uint32_t* hb = reinterpret_cast<uint32_t*>(regions + g * ssh.region_bytes + ssh.L_bytes);
+    const int m = cb.m_eff;
+    const bool wide = (Z & 31) == 0;
+    int it = 1;
+    bool ok = false, crc_ok = false;
+    const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
+    RowIn<kServeChunk> row = load_row<kServeChunk>(s_tab, rows[0], mag1, mag2, meta, k);
+    for (;; ++it) {
+      for (int l = 0; l < m; ++l) {
+        check_update<LT, MT, SAT, false>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
+                                        a.msg_sat, a.post_sat);
+        // the next row's table and record are ready before the barrier
+        const int ln = l + 1 < m ? l + 1 : 0;
+        row = load_row<kServeChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
+        group_sync(Z, g, wmask);
+      }
+      if (a.early_term || it == a.max_iter) {
+        bool bad;
+        uint32_t cr = 0;
+        const uint32_t* ptab = a.cbcrc + sh.crc_off;
+        if (wide) {
+          hard_bitmap(L, hb, cb.n_eff, k, Z);
+          group_sync(Z, g, wmask);
+          bad = syndrome_bitmap<kServeChunk>(s_tab, rows, hb, m, k, Z);
+          if (has_crc) cr = cb_crc_part_hb(hb, ptab, cb.kb, k, Z);
+        } else {
+          bad = syndrome_direct<kServeChunk>(s_tab, rows, m, k, Z, L);
+          if (has_crc) cr = cb_crc_part(L, ptab, cb.kb, k, Z);
+        }
+        ok = !group_any(Z, g, wmask, bad);
+        // after that barrier the bitmap's parity words are free: scratch for the CRC's XOR
+        if (has_crc) crc_ok = group_xor_zero(Z, g, wmask, cr, hb + cb.kb * (Z >> 5), k);
+        if ((ok || crc_ok) && a.early_term) break;
+        if (it == a.max_iter) break;
+      }
+    }
+    uint32_t* out = a.arena + cb.bits_off;
+    if (wide) {
+      const int nw = cb.kb * (Z >> 5);
+      for (int i = k; i < nw; i += Z) out[i] = hb[i];
+    } else {
+      const int sh16 = lane & 16;
+      for (int c = 0; c < cb.kb; c += 2) {
+        const uint32_t b0 = __ballot_sync(wmask, L[c * Z + k] < LT(0)) >> sh16;
+        const uint32_t b1 = __ballot_sync(wmask, L[(c + 1) * Z + k] < LT(0)) >> sh16;
+        if (k == 0) out[c >> 1] = (b0 & 0xFFFFu) | (b1 << 16);
+      }
+    }
+    if (k == 0) a.arena[cb.llr_off] = static_cast<uint32_t>(it | (ok ? (1 << 16) : 0) | (crc_ok ? (1 << 17) : 0));
+  }
+  return true;
+}
+
+// The same for INT8 with two blocks per thread group (paired form, the batch
+// decoder's half2 arithmetic: block A in the low half, B in the high half;
+// every INT8 intermediate is an integer exact in fp16).  The item holds up to
+// 2 Gp blocks of one TB (identical geometry), group g decodes blocks 2g and
+// 2g+1; the three message words per check sit in a device-memory slot per
+// (block, group); the table (the shape's two-edge-chunk copy), posteriors and
+// both bitmaps in shared memory.
+template <bool CRC>
+__device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& ssh, const CbDev& cb_first, int cb0,
+                                          int count, uint32_t& phase, uint32_t* s_tab, uint64_t* s_bar,
+                                          uint8_t* regions) {
+  using namespace core;
+  const int tid = threadIdx.x;
+  const ShapeDev& sh = ssh.shp;
+  const int Z = sh.Z;
+  const int g = tid / Z;
+  const int k = tid - g * Z;
+  const int beta = static_cast<int>(a.beta);
+  const __half2 msg = __float2half2_rn(a.msg_sat);
+  const __half2 post = __float2half2_rn(a.post_sat);
+  if (tid == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
+    bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
+  }
+  const int pairs = (count + 1) >> 1;
+  bool active = g < pairs && check_ok(count >= 1 && count <= 2 * ssh.Gp, 12, count, 2 * ssh.Gp);
+  const bool hasB = 2 * g + 1 < count;
+  uint8_t* reg = regions + g * ssh.region_p;
+  uint32_t* L = reinterpret_cast<uint32_t*>(reg);
+  uint32_t* hbA = reinterpret_cast<uint32_t*>(reg + ssh.Lp_bytes);
+  uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + ssh.Lp_bytes + ssh.hb_bytes);
+  uint32_t* mags = reinterpret_cast<uint32_t*>(a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) *
+                                                             a.rscratch_group);
+  uint32_t* sg1 = mags + ssh.rec_cap;
+  uint32_t* sg2 = sg1 + ssh.rec_cap;
+  CbDev A{}, B{};
+  if (active) {
+    A = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g) % a.cb_cap));
+    if (hasB) B = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g + 1) % a.cb_cap));
+    if constexpr (kChecked) {
+      for (int h = 0; h < (hasB ? 2 : 1); ++h) {
+        const CbDev& c = h ? B : A;
+        active = active &&
+                 check_ok(c.shape == cb_first.shape && c.Z == Z && c.n_eff == A.n_eff && c.m_eff == A.m_eff &&
+                              c.n_eff <= sh.nb && c.m_eff <= sh.mb, 13, c.shape, cb_first.shape) &&
+                 check_ok(c.bits_off >= 0 && c.bits_off + ((c.kb * Z) >> 5) <= a.arena_words, 14,
+                          static_cast<int>(c.bits_off), static_cast<int>(a.arena_words)) &&
+                 check_ok(c.llr_off >= 0 && c.llr_off < a.arena_words, 15, static_cast<int>(c.llr_off),
+                          static_cast<int>(a.arena_words)) &&
+                 check_ok(c.re_off >= 0 && c.re_off + c.n_re <= a.pool_f2, 16, static_cast<int>(c.re_off),
+                          static_cast<int>(a.pool_f2)) &&
+                 check_ok(c.mask_off >= 0 && c.mask_off + ((c.n_re + 31) >> 5) <= a.pool_words, 17,
+                          static_cast<int>(c.mask_off), static_cast<int>(a.pool_words));
+      }
+    }
+  }
+  if (active) {
+    for (int r = k; r < A.m_eff * Z; r += Z) {
+      mags[r] = 0u;
+      sg1[r] = 0u;
+      sg2[r] = 0u;
+    }
+    // both blocks' LLRs into the two halves of the posterior words (B's half 0 without a second block)
+    __half* Lh = reinterpret_cast<__half*>(L);
+    demap_into_smem<int8_t>(a, A, PairLaneOut{Lh, 0}, k, Z);
+    if (hasB) {
+      demap_into_smem<int8_t>(a, B, PairLaneOut{Lh, 1}, k, Z);
+    } else {
+      for (int p = k; p < A.n_eff * Z; p += Z) Lh[2 * p + 1] = __float2half(0.0f);
+    }
+  }
+  const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
+  phase ^= 1u;
+  if (!__syncthreads_and(got)) {
+    if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
+    mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
+    return false;
+  }
+  if (active) {
+    const uint32_t* rows = s_tab + sh.row_off;
+    const int m = A.m_eff;
+    const int dummy = ssh.dummy_base + k;
+    bool doneA = false, doneB = !hasB;
+    PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
+    for (int it = 1;; ++it) {
+      for (int l = 0; l < m; ++l) {
+        check_update_x2(prow, k, Z, L, mags, sg1, sg2, l * Z + k, dummy, beta, msg, post);
+        const int ln = l + 1 < m ? l + 1 : 0;
+        prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
+        group_sync(Z, g, 0xFFFFFFFFu);
+      }
+      if (a.early_term || it == a.max_iter) {
+        hard_bitmap_x2(L, hbA, hbB, A.n_eff, k, Z);
+        group_sync(Z, g, 0xFFFFFFFFu);
+        const bool badA = !doneA && syndrome_bitmap<kChunk>(s_tab, rows, hbA, m, k, Z);
+        const bool badB = !doneB && syndrome_bitmap<kChunk>(s_tab, rows, hbB, m, k, Z);
+        const bool crcA = CRC && !doneA && (A.flags & LDPC_CB_CRC24B) != 0;
+        const bool crcB = CRC && !doneB && (B.flags & LDPC_CB_CRC24B) != 0;
+        uint32_t rA = 0, rB = 0;
+        if (crcA || crcB) {
+          const uint32_t* ptab = a.cbcrc + sh.crc_off;
+          if (crcA) rA = cb_crc_part_hb(hbA, ptab, A.kb, k, Z);
+          if (crcB) rB = cb_crc_part_hb(hbB, ptab, A.kb, k, Z);
+        }
+        const bool okA = !group_any(Z, g, 0xFFFFFFFFu, badA);
+        const bool okB = !group_any(Z, g, 0xFFFFFFFFu, badB);
+        bool cA = false, cB = false;
+        if (crcA || crcB) {  // both blocks' XORs meet in their bitmaps' (now free) parity words
+          const bool zA = group_xor_zero2(Z, g, rA, rB, hbA + A.kb * (Z >> 5), hbB + A.kb * (Z >> 5), k, &cB);
+          cA = crcA && zA;
+          cB = crcB && cB;
+        }
+        const bool last = it == a.max_iter;
+        const int nw = A.kb * (Z >> 5);
+        if (!doneA && (((okA || cA) && a.early_term) || last)) {
+          uint32_t* out = a.arena + A.bits_off;
+          for (int i = k; i < nw; i += Z) out[i] = hbA[i];
+          if (k == 0) a.arena[A.llr_off] = static_cast<uint32_t>(it | (okA ? (1 << 16) : 0) | (cA ? (1 << 17) : 0));
+          doneA = true;
+        }
+        if (!doneB && (((okB || cB) && a.early_term) || last)) {
+          uint32_t* out = a.arena + B.bits_off;
+          for (int i = k; i < nw; i += Z) out[i] = hbB[i];
+          if (k == 0) a.arena[B.llr_off] = static_cast<uint32_t>(it | (okB ? (1 << 16) : 0) | (cB ? (1 << 17) : 0));
+          doneB = true;
+        }
+        if (doneA && doneB) break;
+      }
+    }
+  }
+  return true;
+}
+
+// The persistent loop, one thread block per SM.  PAIRS (INT8): an item the
+// host flagged as paired runs pair_item, the others single_item -- the host
+// pairs while the service is loaded (more blocks in flight per SM) and not
+// while it is light (lower latency per block).
+template <typename LT, typename MT, bool SAT, bool CRC, bool PAIRS>
+__global__ void __launch_bounds__(kServeBlock, 1) serve_kernel(const ServeArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
@@ -354,15 +603,14 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
   uint32_t phase = 0;
 
   for (;;) {
-    if (tid == 0) {
-      s_claim = claim_item(a);  // -2 (idle): exit quietly, the host relaunches on demand
-    }
+    if (tid == 0) s_claim = claim_item(a);  // -2 (idle): exit quietly, the host relaunches on demand
     __syncthreads();
     const long long idx = s_claim;
     if (idx < 0) break;
     const ServeItem* ip = a.items + (static_cast<uint32_t>(idx) % a.item_cap);
     const int req = ld_sys(&ip->req), cb0 = ld_sys(&ip->cb0), count = ld_sys(&ip->count);
     const int n_items = ld_sys(&ip->n_items);
+    const bool paired = PAIRS && ld_sys(&ip->pair) != 0;
     const int first_cb = static_cast<int>(static_cast<uint32_t>(cb0) % a.cb_cap);
     const CbDev cb_first = load_cb(a.cbs + first_cb);
     // checked builds: an item whose request or shape index is out of range is dropped
@@ -374,108 +622,14 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
       continue;
     }
     const ServeShape ssh = a.shapes[cb_first.shape];
-    const ShapeDev& sh = ssh.sh;
-    const int Z = sh.Z;
-    const int g = tid / Z;
-    const int k = tid - g * Z;
-    const uint32_t wmask = (Z >= 32) ? 0xFFFFFFFFu : (((1u << Z) - 1u) << (lane & ~(Z - 1)));
-
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
-      bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
+    bool fine;
+    if constexpr (PAIRS) {
+      fine = paired ? pair_item<CRC>(a, ssh, cb_first, cb0, count, phase, s_tab, s_bar, regions)
+                    : single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, cb0, count, phase, s_tab, s_bar, regions);
+    } else {
+      fine = single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, cb0, count, phase, s_tab, s_bar, regions);
     }
-    bool active = g < count && check_ok(count >= 1 && count <= ssh.G, 12, count, ssh.G);
-    CbDev cb{};
-    LT* L = reinterpret_cast<LT*>(regions + g * ssh.region_bytes);
-    uint8_t* rbase = TWO ? a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) * a.rscratch_group
-                               : regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
-    MT* mag1 = reinterpret_cast<MT*>(rbase);
-    MT* mag2 = mag1 + ssh.rec_cap;
-    uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
-    if (active) {
-      cb = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + g) % a.cb_cap));
-      if constexpr (kChecked) {  // the block's records against the shape, the arena and the host pool
-        active = check_ok(cb.shape == cb_first.shape && cb.Z == Z && cb.n_eff <= sh.nb && cb.m_eff <= sh.mb, 13,
-                          cb.shape, cb_first.shape) &&
-                 check_ok(cb.bits_off >= 0 && cb.bits_off + ((cb.kb * Z) >> 5) <= a.arena_words, 14,
-                          static_cast<int>(cb.bits_off), static_cast<int>(a.arena_words)) &&
-                 check_ok(cb.llr_off >= 0 && cb.llr_off < a.arena_words, 15, static_cast<int>(cb.llr_off),
-                          static_cast<int>(a.arena_words)) &&
-                 check_ok(cb.re_off >= 0 && cb.re_off + cb.n_re <= a.pool_f2, 16, static_cast<int>(cb.re_off),
-                          static_cast<int>(a.pool_f2)) &&
-                 check_ok(cb.mask_off >= 0 && cb.mask_off + ((cb.n_re + 31) >> 5) <= a.pool_words, 17,
-                          static_cast<int>(cb.mask_off), static_cast<int>(a.pool_words));
-      }
-    }
-    if (active) {
-      zero_records(mag1, mag2, meta, cb.m_eff * Z, k, Z);
-      if constexpr (SAT)
-        st_val(L, ssh.dummy_base + k, a.post_sat);
-      else
-        L[ssh.dummy_base + k] = LT(kBigF);
-      demap_into_smem<LT>(a, cb, PlainOut<LT>{L}, k, Z);  // puncture flushing + max-log, straight into shared memory
-    }
-    const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
-    phase ^= 1u;
-    if (!__syncthreads_and(got)) {
-      if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
-      mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
-      break;
-    }
-
-    if (active) {
-      const uint32_t* rows = s_tab + sh.row_off;
-      uint32_t* hb = reinterpret_cast<uint32_t*>(regions + g * ssh.region_bytes + ssh.L_bytes);
-      const int m = cb.m_eff;
-      const bool wide = (Z & 31) == 0;
-      int it = 1;
-      bool ok = false, crc_ok = false;
-      const bool has_crc = CRC && (cb.flags & LDPC_CB_CRC24B) != 0;
-      RowIn<kServeChunk> row = load_row<kServeChunk>(s_tab, rows[0], mag1, mag2, meta, k);
-      for (;; ++it) {
-        for (int l = 0; l < m; ++l) {
-          check_update<LT, MT, SAT, TWO>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
-                                          a.msg_sat, a.post_sat);
-          // the next row's table and record are ready before the barrier
-          const int ln = l + 1 < m ? l + 1 : 0;
-          row = load_row<kServeChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
-          group_sync(Z, g, wmask);
-        }
-        if (a.early_term || it == a.max_iter) {
-          bool bad;
-          uint32_t cr = 0;
-          const uint32_t* ptab = a.cbcrc + a.shapes[cb.shape].sh.crc_off;
-          if (wide) {
-            hard_bitmap(L, hb, cb.n_eff, k, Z);
-            group_sync(Z, g, wmask);
-            bad = syndrome_bitmap<kServeChunk>(s_tab, rows, hb, m, k, Z);
-            if (has_crc) cr = cb_crc_part_hb(hb, ptab, cb.kb, k, Z);
-          } else {
-            bad = syndrome_direct<kServeChunk>(s_tab, rows, m, k, Z, L);
-            if (has_crc) cr = cb_crc_part(L, ptab, cb.kb, k, Z);
-          }
-          ok = !group_any(Z, g, wmask, bad);
-          // after that barrier the bitmap's parity words are free: scratch for the CRC's XOR
-          if (has_crc) crc_ok = group_xor_zero(Z, g, wmask, cr, hb + cb.kb * (Z >> 5), k);
-          if ((ok || crc_ok) && a.early_term) break;
-          if (it == a.max_iter) break;
-        }
-      }
-      uint32_t* out = a.arena + cb.bits_off;
-      if (wide) {
-        const int nw = cb.kb * (Z >> 5);
-        for (int i = k; i < nw; i += Z) out[i] = hb[i];
-      } else {
-        const int sh16 = lane & 16;
-        for (int c = 0; c < cb.kb; c += 2) {
-          const uint32_t b0 = __ballot_sync(wmask, L[c * Z + k] < LT(0)) >> sh16;
-          const uint32_t b1 = __ballot_sync(wmask, L[(c + 1) * Z + k] < LT(0)) >> sh16;
-          if (k == 0) out[c >> 1] = (b0 & 0xFFFFu) | (b1 << 16);
-        }
-      }
-      if (k == 0) a.arena[cb.llr_off] = static_cast<uint32_t>(it | (ok ? (1 << 16) : 0) | (crc_ok ? (1 << 17) : 0));
-    }
+    if (!fine) break;
     finish_item(a, req, n_items, tid, lane, &s_last, s_res);
     __syncthreads();
   }
@@ -490,198 +644,19 @@ __global__ void __launch_bounds__(kServeBlock, TWO ? 2 : 1) serve_kernel(const S
   }
 }
 
-// INT8 service, two code blocks per thread group (the batch decoder's paired
-// form: half2 posteriors, block A in the low half, B in the high half; every
-// INT8 intermediate is an integer exact in fp16).  One loop per SM; an item
-// holds up to 2 G blocks of one TB (identical geometry), group g decodes
-// blocks 2g and 2g+1; check messages (three words per check) live in a
-// device-memory slot per (block, group), the posteriors, both hard-decision
-// bitmaps and the edge table (chunks of kChunk edges) in shared memory.
 template <bool CRC>
-__global__ void __launch_bounds__(kServeBlock, 1) serve_pair_kernel(const ServeArgs a) {
-  using namespace core;
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + a.hdr_bytes - 16);
-  uint8_t* regions = smem + a.hdr_bytes;
-  __shared__ long long s_claim;
-  __shared__ int s_last;
-  __shared__ uint32_t s_res[3];
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int beta = static_cast<int>(a.beta);
-  const __half2 msg = __float2half2_rn(a.msg_sat);
-  const __half2 post = __float2half2_rn(a.post_sat);
-  if (tid == 0) {
-    mbar_init(s_bar, 1);
-    fence_proxy_async_smem();
-  }
-  __syncthreads();
-  uint32_t phase = 0;
-
-  for (;;) {
-    if (tid == 0) s_claim = claim_item(a);
-    __syncthreads();
-    const long long idx = s_claim;
-    if (idx < 0) break;
-    const ServeItem* ip = a.items + (static_cast<uint32_t>(idx) % a.item_cap);
-    const int req = ld_sys(&ip->req), cb0 = ld_sys(&ip->cb0), count = ld_sys(&ip->count);
-    const int n_items = ld_sys(&ip->n_items);
-    const CbDev cb_first = load_cb(a.cbs + static_cast<uint32_t>(cb0) % a.cb_cap);
-    const bool item_ok = check_ok(static_cast<uint32_t>(req) < static_cast<uint32_t>(a.n_req), 10, req, a.n_req) &&
-                         check_ok(static_cast<uint32_t>(cb_first.shape) < static_cast<uint32_t>(a.n_shapes), 11,
-                                  cb_first.shape, a.n_shapes);
-    if (kChecked && !item_ok) {
-      __syncthreads();
-      continue;
-    }
-    const ServeShape ssh = a.shapes[cb_first.shape];
-    const ShapeDev& sh = ssh.sh;
-    const int Z = sh.Z;
-    const int g = tid / Z;
-    const int k = tid - g * Z;
-
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(sh.tab_words) * 4u);
-      bulk_g2s(s_tab, a.tabs + sh.tab_off, static_cast<uint32_t>(sh.tab_words) * 4u, s_bar);
-    }
-    const int pairs = (count + 1) >> 1;
-    bool active = g < pairs && check_ok(count >= 1 && count <= 2 * ssh.G, 12, count, 2 * ssh.G);
-    const bool hasB = 2 * g + 1 < count;
-    uint8_t* reg = regions + g * ssh.region_bytes;
-    uint32_t* L = reinterpret_cast<uint32_t*>(reg);
-    uint32_t* hbA = reinterpret_cast<uint32_t*>(reg + ssh.L_bytes);
-    uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + ssh.L_bytes + ssh.hb_bytes);
-    uint32_t* mags = reinterpret_cast<uint32_t*>(a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) *
-                                                               a.rscratch_group);
-    uint32_t* sg1 = mags + ssh.rec_cap;
-    uint32_t* sg2 = sg1 + ssh.rec_cap;
-    CbDev A{}, B{};
-    if (active) {
-      A = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g) % a.cb_cap));
-      if (hasB) B = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g + 1) % a.cb_cap));
-      if constexpr (kChecked) {
-        for (int h = 0; h < (hasB ? 2 : 1); ++h) {
-          const CbDev& c = h ? B : A;
-          active = active &&
-                   check_ok(c.shape == cb_first.shape && c.Z == Z && c.n_eff == A.n_eff && c.m_eff == A.m_eff &&
-                                c.n_eff <= sh.nb && c.m_eff <= sh.mb, 13, c.shape, cb_first.shape) &&
-                   check_ok(c.bits_off >= 0 && c.bits_off + ((c.kb * Z) >> 5) <= a.arena_words, 14,
-                            static_cast<int>(c.bits_off), static_cast<int>(a.arena_words)) &&
-                   check_ok(c.llr_off >= 0 && c.llr_off < a.arena_words, 15, static_cast<int>(c.llr_off),
-                            static_cast<int>(a.arena_words)) &&
-                   check_ok(c.re_off >= 0 && c.re_off + c.n_re <= a.pool_f2, 16, static_cast<int>(c.re_off),
-                            static_cast<int>(a.pool_f2)) &&
-                   check_ok(c.mask_off >= 0 && c.mask_off + ((c.n_re + 31) >> 5) <= a.pool_words, 17,
-                            static_cast<int>(c.mask_off), static_cast<int>(a.pool_words));
-        }
-      }
-    }
-    if (active) {
-      for (int r = k; r < A.m_eff * Z; r += Z) {
-        mags[r] = 0u;
-        sg1[r] = 0u;
-        sg2[r] = 0u;
-      }
-      // both blocks' LLRs into the two halves of the posterior words (B's half 0 without a second block)
-      __half* Lh = reinterpret_cast<__half*>(L);
-      demap_into_smem<int8_t>(a, A, PairLaneOut{Lh, 0}, k, Z);
-      if (hasB) {
-        demap_into_smem<int8_t>(a, B, PairLaneOut{Lh, 1}, k, Z);
-      } else {
-        for (int p = k; p < A.n_eff * Z; p += Z) Lh[2 * p + 1] = __float2half(0.0f);
-      }
-    }
-    const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
-    phase ^= 1u;
-    if (!__syncthreads_and(got)) {
-      if (tid == 0) atomicOr(&a.dctl->err, LDPC_DEVERR_TMA_TIMEOUT);
-      mbar_wait_bounded(s_bar, phase ^ 1u, 1u << 20);
-      break;
-    }
-
-    if (active) {
-      const uint32_t* rows = s_tab + sh.row_off;
-      const int m = A.m_eff;
-      const int dummy = ssh.dummy_base + k;
-      bool doneA = false, doneB = !hasB;
-      PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
-      for (int it = 1;; ++it) {
-        for (int l = 0; l < m; ++l) {
-          check_update_x2(prow, k, Z, L, mags, sg1, sg2, l * Z + k, dummy, beta, msg, post);
-          const int ln = l + 1 < m ? l + 1 : 0;
-          prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
-          group_sync(Z, g, 0xFFFFFFFFu);
-        }
-        if (a.early_term || it == a.max_iter) {
-          hard_bitmap_x2(L, hbA, hbB, A.n_eff, k, Z);
-          group_sync(Z, g, 0xFFFFFFFFu);
-          const bool badA = !doneA && syndrome_bitmap<kChunk>(s_tab, rows, hbA, m, k, Z);
-          const bool badB = !doneB && syndrome_bitmap<kChunk>(s_tab, rows, hbB, m, k, Z);
-          const bool crcA = CRC && !doneA && (A.flags & LDPC_CB_CRC24B) != 0;
-          const bool crcB = CRC && !doneB && (B.flags & LDPC_CB_CRC24B) != 0;
-          uint32_t rA = 0, rB = 0;
-          if (crcA || crcB) {
-            const uint32_t* ptab = a.cbcrc + sh.crc_off;
-            if (crcA) rA = cb_crc_part_hb(hbA, ptab, A.kb, k, Z);
-            if (crcB) rB = cb_crc_part_hb(hbB, ptab, A.kb, k, Z);
-          }
-          const bool okA = !group_any(Z, g, 0xFFFFFFFFu, badA);
-          const bool okB = !group_any(Z, g, 0xFFFFFFFFu, badB);
-          bool cA = false, cB = false;
-          if (crcA || crcB) {  // both blocks' XORs meet in their bitmaps' (now free) parity words
-            const bool zA = group_xor_zero2(Z, g, rA, rB, hbA + A.kb * (Z >> 5), hbB + A.kb * (Z >> 5), k, &cB);
-            cA = crcA && zA;
-            cB = crcB && cB;
-          }
-          const bool last = it == a.max_iter;
-          const int nw = A.kb * (Z >> 5);
-          if (!doneA && (((okA || cA) && a.early_term) || last)) {
-            uint32_t* out = a.arena + A.bits_off;
-            for (int i = k; i < nw; i += Z) out[i] = hbA[i];
-            if (k == 0) a.arena[A.llr_off] = static_cast<uint32_t>(it | (okA ? (1 << 16) : 0) | (cA ? (1 << 17) : 0));
-            doneA = true;
-          }
-          if (!doneB && (((okB || cB) && a.early_term) || last)) {
-            uint32_t* out = a.arena + B.bits_off;
-            for (int i = k; i < nw; i += Z) out[i] = hbB[i];
-            if (k == 0) a.arena[B.llr_off] = static_cast<uint32_t>(it | (okB ? (1 << 16) : 0) | (cB ? (1 << 17) : 0));
-            doneB = true;
-          }
-          if (doneA && doneB) break;
-        }
-      }
-    }
-    finish_item(a, req, n_items, tid, lane, &s_last, s_res);
-    __syncthreads();
-  }
-  // the last block to leave tells the host (in mapped memory) that this launch is over
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(&a.dctl->exits, 1u) + 1u == gridDim.x) {
-      __threadfence_system();
-      *reinterpret_cast<volatile uint32_t*>(&a.lctl->exited_epoch) = a.epoch;
-    }
-  }
-}
-
-template <bool TWO, bool CRC>
-const void* serve_kernel_for(int mode) {
+const void* serve_kernel_for(int mode, bool pairs) {
   switch (mode) {
-    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false, TWO, CRC>);
-    case LDPC_I8: return reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, TWO, CRC>);
-    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true, TWO, CRC>);
+    case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false, CRC, false>);
+    case LDPC_I8:
+      return pairs ? reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, CRC, true>)
+                   : reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, CRC, false>);
+    default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true, CRC, false>);
   }
 }
 
-const void* serve_kernel_ptr(int mode, bool two, bool crc, bool pair) {
-  if (pair) return crc ? reinterpret_cast<const void*>(&serve_pair_kernel<true>)
-                       : reinterpret_cast<const void*>(&serve_pair_kernel<false>);
-  if (crc) return two ? serve_kernel_for<true, true>(mode) : serve_kernel_for<false, true>(mode);
-  return two ? serve_kernel_for<true, false>(mode) : serve_kernel_for<false, false>(mode);
+const void* serve_kernel_ptr(int mode, bool crc, bool pairs) {
+  return crc ? serve_kernel_for<true>(mode, pairs) : serve_kernel_for<false>(mode, pairs);
 }
 
 }  // namespace
@@ -731,8 +706,10 @@ struct ldpc_server {
   uint32_t* xpow32 = nullptr;
   uint32_t* crc_table = nullptr;
   uint8_t* rscratch = nullptr;
-  bool two = true;  // two loops per SM (messages in device memory)
-  bool pair = false;  // INT8: two code blocks per thread group (serve_pair_kernel)
+  bool pairs = false;        // INT8: items may run in the paired form (two code blocks per thread group)
+  bool always_pair = false;  // LDPC_SERVE_PAIRED: every item whose shape allows it
+  int64_t pair_threshold = 0;  // otherwise: pair when the items in flight would exceed this
+  int64_t stats[4] = {0, 0, 0, 0};  // requests, items single, items paired, loop launches
   bool cb_crc = false;  // LDPC_SERVE_CB_CRC: TBs with code-block CRCs accepted
   std::vector<ServeShape> hshapes;
   ServeArgs args{};
@@ -786,10 +763,11 @@ void free_server(ldpc_server* v) {
 
 int launch_loop(ldpc_server* v) {
   v->args.epoch = ++v->epoch;
+  ++v->stats[3];
   cudaError_t z = cudaMemsetAsync(&v->args.dctl->exits, 0, sizeof(uint32_t), v->stream);
   if (z != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop reset: ") + cudaGetErrorString(z));
   void* kargs[] = {&v->args};
-  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair), dim3(v->grid), dim3(kServeBlock), kargs,
+  cudaError_t e = cudaLaunchKernel(serve_kernel_ptr(v->mode, v->cb_crc, v->pairs), dim3(v->grid), dim3(kServeBlock), kargs,
                                    static_cast<size_t>(v->smem), v->stream);
   if (e != cudaSuccess) return srv_fail(LDPC_ECUDA, std::string("serve loop launch: ") + cudaGetErrorString(e));
   e = cudaEventRecord(v->done_ev, v->stream);
@@ -847,7 +825,8 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
   try {
     if (!s || !d || !out || !d->host_pool || d->max_inflight < 1 || d->max_inflight > 65536 ||
         d->arena_bytes < 1024 || d->idle_timeout_us < 1 || d->loops_per_sm < 0 || d->loops_per_sm > 2 ||
-        (d->flags & ~(LDPC_SERVE_CB_CRC | LDPC_SERVE_UNPAIRED)))
+        d->pair_threshold < 0 || (d->flags & ~(LDPC_SERVE_CB_CRC | LDPC_SERVE_UNPAIRED | LDPC_SERVE_PAIRED)) ||
+        ((d->flags & LDPC_SERVE_UNPAIRED) && (d->flags & LDPC_SERVE_PAIRED)))
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
     *out = nullptr;
     auto* v = new (std::nothrow) ldpc_server();
@@ -860,17 +839,19 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       delete v;
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: loops_per_sm = 2 is withdrawn (use 1)");
     }
-    v->two = false;
     v->cb_crc = (d->flags & LDPC_SERVE_CB_CRC) != 0;
     int interleave = 1, max_iter = 10, et = 1, sms = 0;
     float q_scale = 4, llr_sat = 63, beta = 1, msg_sat = 63, post_sat = 127;
     session_serve_info(s, &v->mode, &interleave, &max_iter, &et, &q_scale, &llr_sat, &beta, &msg_sat, &post_sat,
                        &sms);
     cudaGetDevice(&v->device);
-    v->pair = v->mode == LDPC_I8 && !(d->flags & LDPC_SERVE_UNPAIRED);
+    v->pairs = v->mode == LDPC_I8 && !(d->flags & LDPC_SERVE_UNPAIRED);
+    v->always_pair = v->pairs && (d->flags & LDPC_SERVE_PAIRED);
     const int esz = v->mode == LDPC_F32 ? 4 : (v->mode == LDPC_I8 ? 1 : 2);
-    const int chunk = v->pair ? kChunk : kServeChunk;  // the paired update reads two-edge chunks
-    // ---- per-shape tables and layouts, sized for the largest block of the shape
+    // ---- per-shape tables and layouts, sized for the largest block of the shape: the single
+    // form (four-edge chunks, check messages in shared memory) and, for INT8, the paired form
+    // (two-edge chunks, half2 posteriors, two bitmaps, three message words per check in a
+    // device-memory slot per group)
     std::vector<uint32_t> tabs;
     int tw = 0;
     int64_t rec_group = 0;
@@ -879,26 +860,28 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       ServeShape ss{};
       ShapeDev sd{};
       std::vector<uint32_t> tmp;
-      session_shape_table(s, i, 0, tmp, sd, chunk);  // geometry only
+      session_shape_table(s, i, 0, tmp, sd, kServeChunk);  // geometry only
       const int Z = sd.Z;
       ss.dummy_base = sd.nb * Z;
-      session_shape_table(s, i, ss.dummy_base, tabs, sd, chunk);
+      session_shape_table(s, i, ss.dummy_base, tabs, sd, kServeChunk);
       ss.sh = sd;
       tw = std::max(tw, sd.tab_words);
       ss.rec_cap = sd.mb * Z;
       ss.hb_bytes = (Z % 32 == 0) ? align16s(sd.nb * (Z / 32) * 4) : 0;
-      if (v->pair) {  // half2 posteriors, two bitmaps; three message words per check in device memory
-        ss.L_bytes = align16s((sd.nb + 1) * Z * 4);
-        ss.region_bytes = ss.L_bytes + 2 * ss.hb_bytes;
-        rec_group = std::max<int64_t>(rec_group, 3 * align16s(ss.rec_cap * 4));
-      } else {
-        ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
-        const int rec_bytes = 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
-        ss.region_bytes = ss.L_bytes + ss.hb_bytes + (v->two ? 0 : rec_bytes);
-        rec_group = std::max<int64_t>(rec_group, rec_bytes);
-      }
+      ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
+      ss.region_bytes = ss.L_bytes + ss.hb_bytes + 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
       ss.G = std::max(1, kServeBlock / Z);
       if (Z > 32) ss.G = std::min(ss.G, 15);
+      if (v->pairs && Z % 32 == 0) {
+        ShapeDev sp{};
+        session_shape_table(s, i, ss.dummy_base, tabs, sp, kChunk);
+        ss.shp = sp;
+        tw = std::max(tw, sp.tab_words);
+        ss.Lp_bytes = align16s((sd.nb + 1) * Z * 4);
+        ss.region_p = ss.Lp_bytes + 2 * ss.hb_bytes;
+        ss.Gp = ss.G;
+        rec_group = std::max<int64_t>(rec_group, 3 * align16s(ss.rec_cap * 4));
+      }
       v->hshapes.push_back(ss);
     }
     const int hdr = align16s(tw * 4) + 16;
@@ -906,18 +889,22 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     for (auto& ss : v->hshapes) {
       while (ss.G > 1 && hdr + ss.G * ss.region_bytes > kMaxSmem) --ss.G;
       if (ss.sh.Z == 16 && ss.G > 1 && (ss.G & 1)) --ss.G;
-      ss.feasible = hdr + ss.G * ss.region_bytes <= kMaxSmem && (!v->pair || ss.sh.Z % 32 == 0);
+      ss.feasible = hdr + ss.G * ss.region_bytes <= kMaxSmem;
       if (ss.feasible) smem = std::max(smem, hdr + ss.G * ss.region_bytes);
+      if (ss.Gp > 0) {
+        while (ss.Gp > 1 && hdr + ss.Gp * ss.region_p > kMaxSmem) --ss.Gp;
+        ss.feasible_p = hdr + ss.Gp * ss.region_p <= kMaxSmem;
+        if (ss.feasible_p) smem = std::max(smem, hdr + ss.Gp * ss.region_p);
+      }
     }
     v->smem = smem;
+    const void* fn = serve_kernel_ptr(v->mode, v->cb_crc, v->pairs);
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair));
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e == cudaSuccess && smem + static_cast<int>(fa.sharedSizeBytes) > kMaxSmem) e = cudaErrorInvalidValue;
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel_ptr(v->mode, v->two, v->cb_crc, v->pair), kServeBlock, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kServeBlock, smem);
     if (e != cudaSuccess || per_sm < 1) {
       free_server(v);
       return srv_fail(LDPC_ECUDA, std::string("serve loop does not fit an SM (") + std::to_string(smem) +
@@ -925,10 +912,11 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
                                       cudaGetErrorString(e));
     }
     v->grid = per_sm * sms;
-    int gmax = 1;
+    v->pair_threshold = d->pair_threshold > 0 ? d->pair_threshold : v->grid;
+    int gmax = 0;  // paired-form group slots per loop
     for (auto& ss : v->hshapes)
-      if (ss.feasible) gmax = std::max(gmax, ss.G);
-    if (v->two || v->pair) {
+      if (ss.feasible_p) gmax = std::max(gmax, ss.Gp);
+    if (gmax > 0) {
       e = cudaMalloc(&v->rscratch, static_cast<size_t>(v->grid) * gmax * rec_group);
       if (e != cudaSuccess) {
         free_server(v);
@@ -1059,7 +1047,8 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const int shape = session_shape_lookup(v->s, tb.bg, tb.Z);
     if (shape < 0) return srv_fail(LDPC_EINVAL, at + "unknown (bg, Z)");
     const ServeShape& ss = v->hshapes[shape];
-    if (!ss.feasible) return srv_fail(LDPC_EINVAL, at + "shape does not fit the serving loop's shared memory");
+    if (!ss.feasible && !(v->pairs && ss.feasible_p))
+      return srv_fail(LDPC_EINVAL, at + "shape does not fit the serving loop's shared memory");
     const ShapeDev& sd = ss.sh;
     const int t0 = sd.npc * tb.Z;
     if (tb.n_cb < 1 || tb.n_cb > kMaxTbCb || (tb.Qm != 2 && tb.Qm != 4 && tb.Qm != 6 && tb.Qm != 8) || tb.E <= 0 ||
@@ -1098,7 +1087,13 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const int mw = (n_re + 31) / 32;
     const int cols = (tb.E + t0 + tb.Z - 1) / tb.Z;
     const int m_eff = std::min(sd.mb, std::max(sd.mc, cols - sd.kb));
-    const int G = std::max(1, std::min(v->pair ? 2 * ss.G : ss.G, tb.n_cb));  // code blocks per item
+    // the form: paired when the service pairs always, when the items in flight with this
+    // request's single-form items would exceed the threshold, or when only that form fits
+    const int n_single = ss.feasible ? (tb.n_cb + ss.G - 1) / ss.G : 0;
+    const bool pair = v->pairs && ss.feasible_p &&
+                      (v->always_pair || !ss.feasible ||
+                       static_cast<int64_t>(v->items_inflight) + n_single > v->pair_threshold);
+    const int G = std::max(1, std::min(pair ? 2 * ss.Gp : ss.G, tb.n_cb));  // code blocks per item
     const int n_items = (tb.n_cb + G - 1) / G;
     if (v->free_slots.empty() || v->items_inflight + n_items > v->item_cap || v->cbs_inflight + tb.n_cb > v->cb_cap)
       break;
@@ -1151,10 +1146,13 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       item.cb0 = static_cast<int32_t>(cb_first + it * G);
       item.count = std::min(G, tb.n_cb - it * G);
       item.n_items = n_items;
+      item.pair = pair ? 1 : 0;
       ++v->tail;
     }
     v->items_inflight += n_items;
     v->cbs_inflight += tb.n_cb;
+    ++v->stats[0];
+    v->stats[pair ? 2 : 1] += n_items;
   }
   if (taken > 0) {
     std::atomic_thread_fence(std::memory_order_release);
@@ -1234,6 +1232,12 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
     if (now_ns() - last_progress > static_cast<int64_t>(timeout_ms) * 1000000ll)
       return srv_fail(LDPC_ETIMEOUT, "replay: no completion within the timeout");
   }
+  return LDPC_OK;
+}
+
+int ldpc_serve_stats(ldpc_server* v, int64_t* out, int32_t n) {
+  if (!v || n < 0 || (n > 0 && !out)) return srv_fail(LDPC_EINVAL, "bad stats arguments");
+  for (int i = 0; i < n; ++i) out[i] = i < 4 ? v->stats[i] : 0;
   return LDPC_OK;
 }
 

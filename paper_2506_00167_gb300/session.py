@@ -263,21 +263,29 @@ class Server:
     requests' symbols and masks, and receiving decoded bits.  Requests are
     numpy arrays of ``abi.SERVE_TB_NP``.  ``cb_crc``: accept TBs whose code
     blocks carry their own CRC (the loop runs its CRC-exit variant).
-    ``paired``: an INT8 service decodes two code blocks per thread group.
+    ``paired``: how an INT8 service decodes a request's code blocks -- ``"auto"``
+    (paired, two blocks per thread group, when more than ``pair_threshold``
+    work items would be in flight, 0 meaning one per loop thread block; single
+    otherwise), ``True`` (always paired where the shape allows) or ``False``
+    (always single).
     """
 
     def __init__(self, session: Session, host_pool: torch.Tensor, result_pool: torch.Tensor | None = None,
                  arena_bytes: int = 8 << 30, max_inflight: int = 4096, idle_timeout_us: int = 200000,
-                 loops_per_sm: int = 1, cb_crc: bool = False, paired: bool = True):
+                 loops_per_sm: int = 1, cb_crc: bool = False, paired: bool | str = "auto",
+                 pair_threshold: int = 0):
         for t, name in ((host_pool, "host_pool"), (result_pool, "result_pool")):
             if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous pinned CPU tensor")
         self._keep = (session, host_pool, result_pool)
+        if paired not in ("auto", True, False):
+            raise ValueError("paired must be 'auto', True or False")
+        form = 0 if paired == "auto" else (abi.SERVE_PAIRED if paired is True else abi.SERVE_UNPAIRED)
         d = abi.ServeDescC(int(arena_bytes), int(max_inflight), int(idle_timeout_us), host_pool.data_ptr(),
                            host_pool.numel() * host_pool.element_size(),
                            result_pool.data_ptr() if result_pool is not None else None,
                            result_pool.numel() * result_pool.element_size() if result_pool is not None else 0,
-                           int(loops_per_sm), (abi.SERVE_CB_CRC if cb_crc else 0) | (0 if paired else abi.SERVE_UNPAIRED))
+                           int(loops_per_sm), (abi.SERVE_CB_CRC if cb_crc else 0) | form, int(pair_threshold), 0)
         h = ctypes.c_void_p()
         abi.check(abi.load().ldpc_serve_start(session.handle, ctypes.byref(d), ctypes.byref(h)), "ldpc_serve_start")
         self.handle = h.value
@@ -302,6 +310,12 @@ class Server:
         abi.check(abi.load().ldpc_serve_replay(self.handle, a.ctypes.data, t.ctypes.data, a.size, out.ctypes.data,
                                                int(timeout_ms)), "ldpc_serve_replay")
         return out
+
+    def stats(self) -> dict:
+        """Counters since start: requests, items admitted single / paired, loop launches."""
+        out = (ctypes.c_int64 * 4)()
+        abi.check(abi.load().ldpc_serve_stats(self.handle, ctypes.cast(out, ctypes.c_void_p), 4), "ldpc_serve_stats")
+        return {"requests": out[0], "items_single": out[1], "items_paired": out[2], "launches": out[3]}
 
     def stop(self) -> None:
         if getattr(self, "handle", 0):

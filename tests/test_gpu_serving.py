@@ -13,6 +13,18 @@ from gpu_helpers import device_inputs, session_for
 
 pytestmark = pytest.mark.gpu
 
+# INT8 decode forms of the service: (paired, pair_threshold, which item counters must be nonzero).
+# "auto" with a threshold of 4 items: a burst starts single and pairs once 4 items are in flight.
+FORMS = [("auto", 4, ("items_single", "items_paired")), (True, 0, ("items_paired",)),
+         (False, 0, ("items_single",))]
+FORM_IDS = ["auto", "paired", "single"]
+
+
+def _check_forms(srv, must):
+    st = srv.stats()
+    for k in ("items_single", "items_paired"):
+        assert (st[k] > 0) == (k in must), st
+
 
 @pytest.fixture(scope="module")
 def pool():
@@ -135,8 +147,8 @@ def test_idle_loop_is_relaunched_and_bad_requests_rejected(pool):
     srv.stop()
 
 
-@pytest.mark.parametrize("loops", [1])
-def test_repetition_blocks_through_the_service_match_the_batch_path(loops):
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_repetition_blocks_through_the_service_match_the_batch_path(form):
     """Code blocks whose rate matching wraps the circular buffer: the service's fused demap combines the
     repeated LLRs like the batch demapper, bit for bit."""
     from workload.configs import repetition
@@ -148,11 +160,12 @@ def test_repetition_blocks_through_the_service_match_the_batch_path(loops):
     offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
     res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
     s = session_for(w, "i8")
-    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, loops_per_sm=loops)
+    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, paired=form[0], pair_threshold=form[1])
     try:
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
+        _check_forms(srv, form[2])
         d_ref, bits_ref, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
@@ -162,28 +175,44 @@ def test_repetition_blocks_through_the_service_match_the_batch_path(loops):
         srv.stop()
 
 
-def test_one_loop_per_sm_matches_the_batch_path(pool):
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_every_form_matches_the_batch_path(pool, form):
+    """Single, paired, and the two mixed in one burst (the per-request choice by load): bits, d_e and
+    iteration counts equal the batch path's."""
     w, host, mask_base = pool
     n = w.n_tb
     words = [_tb_words(w, t) for t in range(n)]
     offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
     res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
     s = session_for(w, "i8")
-    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=256, loops_per_sm=1)
+    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=256, paired=form[0], pair_threshold=form[1])
     try:
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
-        d_ref, bits_ref, _ = _batch_reference(w, range(n))
+        assert sorted(done["tag"].tolist()) == list(range(n))
+        _check_forms(srv, form[2])
+        st = srv.stats()
+        assert st["requests"] == n and st["launches"] >= 1
+        d_ref, bits_ref, it_ref = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
             assert int(r["d"]) == int(d_ref[t]), t
+            assert int(r["max_iters"]) == it_ref[t], t
             assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
     finally:
         srv.stop()
 
 
-@pytest.mark.parametrize("loops", [1])
-def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(loops):
+def test_form_flags_are_validated(pool):
+    w, host, mask_base = pool
+    with pytest.raises(ValueError):
+        Server(session_for(w, "i8"), host, None, arena_bytes=1 << 24, max_inflight=8, paired="sometimes")
+    with pytest.raises(LdpcError, match="EINVAL"):
+        Server(session_for(w, "i8"), host, None, arena_bytes=1 << 24, max_inflight=8, pair_threshold=-1)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(form):
     """TBs whose code blocks carry their own CRC (payload n_cb (K - 24) - 24): the service infers that from
     payload_bits, stops blocks on a passing CRC and checks every CRC, like the batch path, bit for bit."""
     w = tb_pool(24, seed=17, max_cb=6, cb_crc=True)
@@ -195,18 +224,20 @@ def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(loops):
     offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
     res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
     s = session_for(w, "i8")
-    plain = Server(session_for(w, "i8"), host, None, arena_bytes=1 << 24, max_inflight=8, loops_per_sm=loops)
+    plain = Server(session_for(w, "i8"), host, None, arena_bytes=1 << 24, max_inflight=8)
     try:
         seg = int(np.flatnonzero(w.tbs["n_cb"] > 1)[0])
         with pytest.raises(LdpcError, match="LDPC_SERVE_CB_CRC"):
             plain.submit(tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=[seg], tags=[0]))
     finally:
         plain.stop()
-    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=64, loops_per_sm=loops, cb_crc=True)
+    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=64, cb_crc=True, paired=form[0],
+                 pair_threshold=form[1])
     try:
         recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
+        _check_forms(srv, form[2])
         d_ref, bits_ref, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
