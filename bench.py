@@ -350,11 +350,13 @@ def run_serving(args):
     sess = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
     base_recs = tb_records(w, mask_base, abi.SERVE_TB_NP)
     curves = {}
-    runs = [(f, lp, th) for f in args.serve_form for lp in args.serve_loops
-            for th in (args.serve_pair_threshold if f == "auto" else [0])]
-    for form, loops, thr in runs:
+    runs = [(f, lp, th, rl) for f in args.serve_form for lp in args.serve_loops
+            for th in (args.serve_pair_threshold if f == "auto" else [0])
+            for rl in (args.serve_pair_release if f == "auto" else [0])]
+    for form, loops, thr, rel in runs:
         srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000,
-                     loops_per_sm=loops, cb_crc=args.cb_crc, paired=SERVE_FORMS[form], pair_threshold=thr)
+                     loops_per_sm=loops, cb_crc=args.cb_crc, paired=SERVE_FORMS[form], pair_threshold=thr,
+                     pair_release=rel)
         # warm-up
         warm = base_recs[:64].copy()
         warm["tag"] = np.arange(warm.size)
@@ -373,7 +375,7 @@ def run_serving(args):
             n_paired = st1["items_paired"] - st0["items_paired"]
             lat_us = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
             bits = int(kbits[pidx].sum())
-            loads.append({"form": form, "pair_threshold": thr, "loops_per_sm": loops, "tb_per_ue_per_slot": load, "requests": int(recs.size),
+            loads.append({"form": form, "pair_threshold": thr, "pair_release": rel, "loops_per_sm": loops, "tb_per_ue_per_slot": load, "requests": int(recs.size),
                           "code_blocks": int(recs["n_cb"].sum()),
                           "offered_gbps": bits / (args.serve_slots * SLOT_NS / 1e9) / 1e9,
                           "served_gbps": bits / wall / 1e9, "wall_s": wall,
@@ -383,10 +385,12 @@ def run_serving(args):
                           "mean_max_iters": float(np.mean(done["max_iters"])),
                           "items_single": int(n_single), "items_paired": int(n_paired),
                           "loop_launches": int(st1["launches"] - st0["launches"]),
+                          "host_longest_pass_us": st1["replay_longest_pass_ns"] / 1e3,
+                          "host_passes_over_1ms": int(st1["replay_passes_over_1ms"]),
                           **_stall_stats(done)})
             print(json.dumps({"serving_point": loads[-1]}), flush=True)
         srv.stop()
-        curves[f"{form}{thr or ''}_{loops}_loops_per_sm"] = loads
+        curves[f"{form}{thr or ''}{'-' + str(rel) if rel else ''}_{loops}_loops_per_sm"] = loads
     # FP32 unbatched plain path: one TB at a time, synchronised
     sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
     n_plain = min(args.serve_plain, w.n_tb)
@@ -650,6 +654,9 @@ def main():
     ap.add_argument("--serve-pair-threshold", type=int, nargs="+", default=[0],
                     help="auto form: pair a request when more work items than this would be in flight "
                          "(0: one per loop thread block); several run one after the other")
+    ap.add_argument("--serve-pair-release", type=int, nargs="+", default=[0],
+                    help="auto form: once pairing, keep pairing until the items in flight fall to this "
+                         "(0: the threshold)")
     ap.add_argument("--cb-crc", action="store_true",
                     help="mixed / served TBs of several code blocks carry a CRC per code block (CRC-aided exit)")
     ap.add_argument("--policy", action="store_true", help="time the puncturing allocations (RP, SeF, enforcer)")

@@ -339,12 +339,14 @@ typedef struct {
                               * blocks per thread group in half2 arithmetic, the batch decoder's paired
                               * form: more blocks in flight per SM).  By default a request is paired when
                               * the work items in flight together with its own single-form items would
-                              * exceed pair_threshold; LDPC_SERVE_UNPAIRED: never; LDPC_SERVE_PAIRED:
+                              * exceed pair_threshold (and, once pairing, until they fall to
+                              * pair_release); LDPC_SERVE_UNPAIRED: never; LDPC_SERVE_PAIRED:
                               * always (where the shape allows it, Z a multiple of 32).  Results are the
                               * same bits either way; the two flags together are LDPC_EINVAL */
-  int32_t pair_threshold;    /* work items in flight above which INT8 requests are paired; 0: the number
-                              * of loop thread blocks (one per SM) */
-  int32_t reserved;          /* 0 */
+  int32_t pair_threshold;    /* work items in flight above which INT8 requests are paired; 0: twice the
+                              * number of loop thread blocks (one per SM) */
+  int32_t pair_release;      /* once pairing, keep pairing until the items in flight fall to this many
+                              * (hysteresis); 0: the number of loop thread blocks; at most pair_threshold */
 } ldpc_serve_desc;
 #define LDPC_SERVE_CB_CRC 1
 #define LDPC_SERVE_UNPAIRED 2
@@ -387,8 +389,9 @@ LDPC_API int ldpc_serve_poll(ldpc_server *srv, ldpc_serve_done *out, int32_t cap
  * LDPC_ETIMEOUT if nothing completes for timeout_ms. */
 LDPC_API int ldpc_serve_replay(ldpc_server *srv, const ldpc_serve_tb *tbs, const int64_t *arrival_ns, int32_t n,
                                ldpc_serve_done *out, int32_t timeout_ms);
-/* Counters since start, out[0..n): requests admitted, work items admitted in the single form, in
- * the paired form, device loop launches (later entries 0). */
+/* Counters, out[0..n): since start, requests admitted, work items admitted in the single form, in
+ * the paired form, device loop launches; then, for the last ldpc_serve_replay, the longest pass of
+ * its host loop in ns and the number of passes longer than 1 ms (later entries 0). */
 LDPC_API int ldpc_serve_stats(ldpc_server *srv, int64_t *out, int32_t n);
 /* Stop the device loop (bounded wait) and free the server. */
 LDPC_API int ldpc_serve_stop(ldpc_server *srv);

@@ -84,7 +84,7 @@ class ServeDescC(ctypes.Structure):
                 ("idle_timeout_us", ctypes.c_int32), ("host_pool", ctypes.c_void_p),
                 ("host_pool_bytes", ctypes.c_uint64), ("result_pool", ctypes.c_void_p),
                 ("result_pool_bytes", ctypes.c_uint64), ("loops_per_sm", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("pair_threshold", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("pair_threshold", ctypes.c_int32), ("pair_release", ctypes.c_int32)]
 
 
 SERVE_CB_CRC = 1  # ldpc_serve_desc.flags: accept TBs with code-block CRCs

@@ -708,8 +708,12 @@ struct ldpc_server {
   uint8_t* rscratch = nullptr;
   bool pairs = false;        // INT8: items may run in the paired form (two code blocks per thread group)
   bool always_pair = false;  // LDPC_SERVE_PAIRED: every item whose shape allows it
-  int64_t pair_threshold = 0;  // otherwise: pair when the items in flight would exceed this
-  int64_t stats[4] = {0, 0, 0, 0};  // requests, items single, items paired, loop launches
+  int64_t pair_threshold = 0;  // otherwise: pair when the items in flight would exceed this,
+  int64_t pair_release = 0;    // and keep pairing until they fall to this
+  bool pairing = false;        // the current state of that choice
+  // requests, items single, items paired, loop launches; the last replay's longest pass of its
+  // host loop (ns) and its passes longer than 1 ms
+  int64_t stats[6] = {0, 0, 0, 0, 0, 0};
   bool cb_crc = false;  // LDPC_SERVE_CB_CRC: TBs with code-block CRCs accepted
   std::vector<ServeShape> hshapes;
   ServeArgs args{};
@@ -825,7 +829,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
   try {
     if (!s || !d || !out || !d->host_pool || d->max_inflight < 1 || d->max_inflight > 65536 ||
         d->arena_bytes < 1024 || d->idle_timeout_us < 1 || d->loops_per_sm < 0 || d->loops_per_sm > 2 ||
-        d->pair_threshold < 0 || (d->flags & ~(LDPC_SERVE_CB_CRC | LDPC_SERVE_UNPAIRED | LDPC_SERVE_PAIRED)) ||
+        d->pair_threshold < 0 || d->pair_release < 0 || (d->flags & ~(LDPC_SERVE_CB_CRC | LDPC_SERVE_UNPAIRED | LDPC_SERVE_PAIRED)) ||
         ((d->flags & LDPC_SERVE_UNPAIRED) && (d->flags & LDPC_SERVE_PAIRED)))
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
     *out = nullptr;
@@ -912,7 +916,9 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
                                       cudaGetErrorString(e));
     }
     v->grid = per_sm * sms;
-    v->pair_threshold = d->pair_threshold > 0 ? d->pair_threshold : v->grid;
+    // by default pairing starts above two items in flight per loop and stops at one
+    v->pair_threshold = d->pair_threshold > 0 ? d->pair_threshold : 2 * static_cast<int64_t>(v->grid);
+    v->pair_release = std::min<int64_t>(d->pair_release > 0 ? d->pair_release : v->grid, v->pair_threshold);
     int gmax = 0;  // paired-form group slots per loop
     for (auto& ss : v->hshapes)
       if (ss.feasible_p) gmax = std::max(gmax, ss.Gp);
@@ -1087,12 +1093,14 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const int mw = (n_re + 31) / 32;
     const int cols = (tb.E + t0 + tb.Z - 1) / tb.Z;
     const int m_eff = std::min(sd.mb, std::max(sd.mc, cols - sd.kb));
-    // the form: paired when the service pairs always, when the items in flight with this
-    // request's single-form items would exceed the threshold, or when only that form fits
+    // the form: paired when the service pairs always, when only that form fits, or by load:
+    // pairing starts once the items in flight with this request's single-form items would
+    // exceed the threshold and stops once they fall to the release level
     const int n_single = ss.feasible ? (tb.n_cb + ss.G - 1) / ss.G : 0;
-    const bool pair = v->pairs && ss.feasible_p &&
-                      (v->always_pair || !ss.feasible ||
-                       static_cast<int64_t>(v->items_inflight) + n_single > v->pair_threshold);
+    const int64_t load = static_cast<int64_t>(v->items_inflight) + n_single;
+    if (load > v->pair_threshold) v->pairing = true;
+    else if (load <= v->pair_release) v->pairing = false;
+    const bool pair = v->pairs && ss.feasible_p && (v->always_pair || !ss.feasible || v->pairing);
     const int G = std::max(1, std::min(pair ? 2 * ss.Gp : ss.G, tb.n_cb));  // code blocks per item
     const int n_items = (tb.n_cb + G - 1) / G;
     if (v->free_slots.empty() || v->items_inflight + n_items > v->item_cap || v->cbs_inflight + tb.n_cb > v->cb_cap)
@@ -1209,15 +1217,25 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
   int next = 0, got = 0;
   int64_t last_progress = t0;
   std::vector<ldpc_serve_done> buf(1024);
+  v->stats[4] = 0;
+  v->stats[5] = 0;
+  int64_t prev = t0;
   while (got < n) {
     const int64_t now = now_ns();
+    if (now - prev > v->stats[4]) v->stats[4] = now - prev;
+    if (now - prev > 1000000) ++v->stats[5];
+    prev = now;
     int due = next;
     while (due < n && sched[due] <= now) ++due;
-    if (due > next) {
+    // admission stops at the first request that does not fit: offer a bounded chunk at a time, so
+    // a backlog (a saturated service) costs no more host time per pass than a short queue
+    while (due > next) {
+      const int32_t chunk = std::min(due - next, 64);
       int32_t adm = 0;
-      const int rc = ldpc_serve_submit(v, tbs + next, due - next, &adm);
+      const int rc = ldpc_serve_submit(v, tbs + next, chunk, &adm);
       if (rc) return rc;
       next += adm;
+      if (adm < chunk) break;
     }
     int32_t k = 0;
     const int rc = ldpc_serve_poll(v, buf.data(), static_cast<int32_t>(buf.size()), &k);
@@ -1237,7 +1255,7 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
 
 int ldpc_serve_stats(ldpc_server* v, int64_t* out, int32_t n) {
   if (!v || n < 0 || (n > 0 && !out)) return srv_fail(LDPC_EINVAL, "bad stats arguments");
-  for (int i = 0; i < n; ++i) out[i] = i < 4 ? v->stats[i] : 0;
+  for (int i = 0; i < n; ++i) out[i] = i < 6 ? v->stats[i] : 0;
   return LDPC_OK;
 }
 

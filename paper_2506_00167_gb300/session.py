@@ -264,8 +264,9 @@ class Server:
     numpy arrays of ``abi.SERVE_TB_NP``.  ``cb_crc``: accept TBs whose code
     blocks carry their own CRC (the loop runs its CRC-exit variant).
     ``paired``: how an INT8 service decodes a request's code blocks -- ``"auto"``
-    (paired, two blocks per thread group, when more than ``pair_threshold``
-    work items would be in flight, 0 meaning one per loop thread block; single
+    (paired, two blocks per thread group, once more than ``pair_threshold``
+    work items would be in flight -- 0: two per loop thread block -- and until
+    they fall to ``pair_release`` -- 0: one per loop thread block; single
     otherwise), ``True`` (always paired where the shape allows) or ``False``
     (always single).
     """
@@ -273,7 +274,7 @@ class Server:
     def __init__(self, session: Session, host_pool: torch.Tensor, result_pool: torch.Tensor | None = None,
                  arena_bytes: int = 8 << 30, max_inflight: int = 4096, idle_timeout_us: int = 200000,
                  loops_per_sm: int = 1, cb_crc: bool = False, paired: bool | str = "auto",
-                 pair_threshold: int = 0):
+                 pair_threshold: int = 0, pair_release: int = 0):
         for t, name in ((host_pool, "host_pool"), (result_pool, "result_pool")):
             if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous pinned CPU tensor")
@@ -285,7 +286,8 @@ class Server:
                            host_pool.numel() * host_pool.element_size(),
                            result_pool.data_ptr() if result_pool is not None else None,
                            result_pool.numel() * result_pool.element_size() if result_pool is not None else 0,
-                           int(loops_per_sm), (abi.SERVE_CB_CRC if cb_crc else 0) | form, int(pair_threshold), 0)
+                           int(loops_per_sm), (abi.SERVE_CB_CRC if cb_crc else 0) | form, int(pair_threshold),
+                           int(pair_release))
         h = ctypes.c_void_p()
         abi.check(abi.load().ldpc_serve_start(session.handle, ctypes.byref(d), ctypes.byref(h)), "ldpc_serve_start")
         self.handle = h.value
@@ -306,16 +308,19 @@ class Server:
     def replay(self, tbs: np.ndarray, arrival_ns: np.ndarray, timeout_ms: int = 10000) -> np.ndarray:
         a = np.ascontiguousarray(tbs, dtype=abi.SERVE_TB_NP)
         t = np.ascontiguousarray(arrival_ns, dtype=np.int64)
-        out = np.zeros(a.size, dtype=abi.SERVE_DONE_NP)
+        out = np.empty(a.size, dtype=abi.SERVE_DONE_NP)
+        out.view(np.uint8)[:] = 0  # every page touched before the timed loop writes it
         abi.check(abi.load().ldpc_serve_replay(self.handle, a.ctypes.data, t.ctypes.data, a.size, out.ctypes.data,
                                                int(timeout_ms)), "ldpc_serve_replay")
         return out
 
     def stats(self) -> dict:
-        """Counters since start: requests, items admitted single / paired, loop launches."""
-        out = (ctypes.c_int64 * 4)()
-        abi.check(abi.load().ldpc_serve_stats(self.handle, ctypes.cast(out, ctypes.c_void_p), 4), "ldpc_serve_stats")
-        return {"requests": out[0], "items_single": out[1], "items_paired": out[2], "launches": out[3]}
+        """Counters since start (requests, items admitted single / paired, loop launches) and, for the last
+        replay, its host loop's longest pass (ns) and passes longer than 1 ms."""
+        out = (ctypes.c_int64 * 6)()
+        abi.check(abi.load().ldpc_serve_stats(self.handle, ctypes.cast(out, ctypes.c_void_p), 6), "ldpc_serve_stats")
+        return {"requests": out[0], "items_single": out[1], "items_paired": out[2], "launches": out[3],
+                "replay_longest_pass_ns": out[4], "replay_passes_over_1ms": out[5]}
 
     def stop(self) -> None:
         if getattr(self, "handle", 0):
