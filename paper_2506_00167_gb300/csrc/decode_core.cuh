@@ -169,7 +169,7 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
 // slots during the layer) and pass 2 reads it back, instead of holding the
 // row's Q values in registers: one shared store and load more per edge for
 // about 30 fewer registers, which lets two 384-thread blocks share an SM.
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH>
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int NF = -1>
 __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
@@ -196,7 +196,7 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
   // padding edge sees Q = dummy + |R|, large and positive)
   uint32_t sgn = (PAD && SAT) ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u))
                               : ((mo ^ par_o) << (32 - deg));
-  const int nfull = PAD ? (deg + CH - 1) / CH : deg / CH;
+  const int nfull = NF >= 0 ? NF : (PAD ? (deg + CH - 1) / CH : deg / CH);
   const int ntail = PAD ? 0 : deg - CH * nfull;
 
   float q[LEAN ? 1 : MaxChunks<CH>::value * CH];
@@ -277,6 +277,25 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
     st_val(mag2, rec, n2);
   }
   meta[rec] = (PAD ? qs >> (CH * nfull - deg) : qs) | (static_cast<uint32_t>(idx) << 27);
+}
+
+// The update with the row's number of chunks (whole chunks for LEAN, padded
+// ones otherwise) as a compile-time constant: one dispatch per row instead of
+// a compare and branch per chunk in each pass, and each row's passes run as
+// straight-line code.
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int NF = 1>
+__device__ __forceinline__ void check_update_by_degree(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
+                                                       MT* __restrict__ mag1, MT* __restrict__ mag2,
+                                                       uint32_t* __restrict__ meta, int rec, int dummy, float beta,
+                                                       float msg_sat, float post_sat) {
+  if constexpr (NF < MaxChunks<CH>::value) {
+    if ((LEAN ? in.deg / CH : (in.deg + CH - 1) / CH) != NF) {
+      check_update_by_degree<LT, MT, SAT, LEAN, CH, NF + 1>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta,
+                                                            msg_sat, post_sat);
+      return;
+    }
+  }
+  check_update<LT, MT, SAT, LEAN, CH, NF>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
@@ -508,6 +527,7 @@ __device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int 
 // Pass 2 writes every edge with the smaller magnitude; the argmin edge of
 // each block, whose message takes the second magnitude instead, is then
 // rewritten from its Q, read before pass 2 (the check owns the slot).
+template <int NCH = -1>
 __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
                                                 uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
                                                 uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
@@ -526,7 +546,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const __half2 I = __hsub2(as_h2((s2 & 0x001F001Fu) | 0x64006400u), h1024);
   const __half2 h32 = __float2half2_rn(32.0f);
   const __half2 npost = __hneg2(post);
-  const int nch = (deg + kChunk - 1) / kChunk;
+  const int nch = NCH >= 0 ? NCH : (deg + kChunk - 1) / kChunk;
 
   int addr[kMaxChunks * kChunk];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
@@ -602,6 +622,21 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   sg1[rec] = acc1 >> (16 - n1);
   const uint32_t a2 = n2 <= 0 ? 0u : (n2 <= 11 ? acc2 >> (11 - n2) : acc2 << (n2 - 11));
   sg2[rec] = (a2 & 0xFFE0FFE0u) | idxA | (idxB << 16);
+}
+
+// check_update_x2 with the row's chunk count as a compile-time constant.
+template <int NCH = 1>
+__device__ __forceinline__ void check_update_x2_by_degree(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
+                                                          uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
+                                                          uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
+                                                          __half2 msg, __half2 post) {
+  if constexpr (NCH < kMaxChunks) {
+    if ((in.deg + kChunk - 1) / kChunk != NCH) {
+      check_update_x2_by_degree<NCH + 1>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
+      return;
+    }
+  }
+  check_update_x2<NCH>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
 }
 
 // hard decisions of both blocks of a pair into their bitmaps

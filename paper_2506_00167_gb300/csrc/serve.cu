@@ -401,8 +401,8 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
     RowIn<kServeChunk> row = load_row<kServeChunk>(s_tab, rows[0], mag1, mag2, meta, k);
     for (;; ++it) {
       for (int l = 0; l < m; ++l) {
-        check_update<LT, MT, SAT, false>(row, k, Z, L, mag1, mag2, meta, l * Z + k, ssh.dummy_base + k, a.beta,
-                                        a.msg_sat, a.post_sat);
+        check_update_by_degree<LT, MT, SAT, false, kServeChunk>(row, k, Z, L, mag1, mag2, meta, l * Z + k,
+                                                                ssh.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
         // the next row's table and record are ready before the barrier
         const int ln = l + 1 < m ? l + 1 : 0;
         row = load_row<kServeChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
@@ -532,7 +532,7 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
     PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
     for (int it = 1;; ++it) {
       for (int l = 0; l < m; ++l) {
-        check_update_x2(prow, k, Z, L, mags, sg1, sg2, l * Z + k, dummy, beta, msg, post);
+        check_update_x2_by_degree(prow, k, Z, L, mags, sg1, sg2, l * Z + k, dummy, beta, msg, post);
         const int ln = l + 1 < m ? l + 1 : 0;
         prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
         group_sync(Z, g, 0xFFFFFFFFu);
