@@ -527,14 +527,18 @@ __device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int 
 // Pass 2 writes every edge with the smaller magnitude; the argmin edge of
 // each block, whose message takes the second magnitude instead, is then
 // rewritten from its Q, read before pass 2 (the check owns the slot).
-template <int NCH = -1>
+template <int DEG = -1>
 __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
                                                 uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
                                                 uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
                                                 __half2 msg, __half2 post) {
-  L[dummy] = as_u32(post);
+  // DEG >= 0: the row's degree is a compile-time constant and only its DEG
+  // edges are processed; otherwise a padding edge completes the last chunk
+  // (on this thread's dummy slot, which can never be a minimum)
+  constexpr bool EXACT = DEG >= 0;
+  if constexpr (!EXACT) L[dummy] = as_u32(post);
   const uint32_t* tab = in.tab;
-  const int deg = in.deg;
+  const int deg = EXACT ? DEG : in.deg;
   const uint32_t mg = in.mg, s1 = in.s1, s2 = in.s2;
   const __half2 h1024 = __float2half2_rn(1024.0f);
   // parity of each block's stored Q signs, as the two sign bits of a half2
@@ -546,7 +550,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const __half2 I = __hsub2(as_h2((s2 & 0x001F001Fu) | 0x64006400u), h1024);
   const __half2 h32 = __float2half2_rn(32.0f);
   const __half2 npost = __hneg2(post);
-  const int nch = NCH >= 0 ? NCH : (deg + kChunk - 1) / kChunk;
+  const int nch = (deg + kChunk - 1) / kChunk;
 
   int addr[kMaxChunks * kChunk];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
@@ -557,13 +561,16 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     const Chunk<kChunk> ch = load_chunk<kChunk>(tab, c);
 #pragma unroll
     for (int i = 0; i < kChunk; ++i)
-      addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), dummy - k + Z, dummy, 3);
+      if (!EXACT || kChunk * c + i < DEG)
+        addr[kChunk * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), dummy - k + Z, dummy, 3);
     uint32_t lv[kChunk];
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) lv[i] = L[addr[kChunk * c + i]];
+    for (int i = 0; i < kChunk; ++i)
+      if (!EXACT || kChunk * c + i < DEG) lv[i] = L[addr[kChunk * c + i]];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) {
       const int j = kChunk * c + i;
+      if (EXACT && j >= DEG) continue;
       const __half2 J = __float2half2_rn(static_cast<float>(j));
       const uint32_t eq = __heq2_mask(I, J);
       // (edge 27 can only be padding, whose sign does not matter)
@@ -600,13 +607,15 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     if (c >= nch) break;
     uint32_t qv[kChunk];
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) qv[i] = L[addr[kChunk * c + i]];
+    for (int i = 0; i < kChunk; ++i)
+      if (!EXACT || kChunk * c + i < DEG) qv[i] = L[addr[kChunk * c + i]];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) {
+      if (EXACT && kChunk * c + i >= DEG) continue;
       const uint32_t rb = N1s ^ (qv[i] & 0x80008000u);
       __half2 v = __hadd2(as_h2(qv[i]), as_h2(rb));
       v = __hmin2(__hmax2(v, npost), post);
-      L[addr[kChunk * c + i]] = as_u32(v);  // padding edges write the dummy slot
+      L[addr[kChunk * c + i]] = as_u32(v);  // (without EXACT, padding edges write the dummy slot)
     }
   }
   {
@@ -615,7 +624,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     L[aA] = (L[aA] & 0xFFFF0000u) | (v & 0x0000FFFFu);
     L[aB] = (L[aB] & 0x0000FFFFu) | (v & 0xFFFF0000u);
   }
-  const int n_all = kChunk * nch;
+  const int n_all = EXACT ? DEG : kChunk * nch;
   const int n1 = n_all < 16 ? n_all : 16;
   const int n2 = n_all - 16;
   mags[rec] = nA1 | (nB1 << 8) | (nA2 << 16) | (nB2 << 24);
@@ -624,19 +633,20 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   sg2[rec] = (a2 & 0xFFE0FFE0u) | idxA | (idxB << 16);
 }
 
-// check_update_x2 with the row's chunk count as a compile-time constant.
-template <int NCH = 1>
+// check_update_x2 with the row's degree as a compile-time constant (no padding
+// edge, straight-line passes).
+template <int DEG = 2>
 __device__ __forceinline__ void check_update_x2_by_degree(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
                                                           uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
                                                           uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
                                                           __half2 msg, __half2 post) {
-  if constexpr (NCH < kMaxChunks) {
-    if ((in.deg + kChunk - 1) / kChunk != NCH) {
-      check_update_x2_by_degree<NCH + 1>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
+  if constexpr (DEG < kMaxDeg) {
+    if (in.deg != DEG) {
+      check_update_x2_by_degree<DEG + 1>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
       return;
     }
   }
-  check_update_x2<NCH>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
+  check_update_x2<DEG>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
 }
 
 // hard decisions of both blocks of a pair into their bitmaps
