@@ -169,7 +169,7 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
 // slots during the layer) and pass 2 reads it back, instead of holding the
 // row's Q values in registers: one shared store and load more per edge for
 // about 30 fewer registers, which lets two 384-thread blocks share an SM.
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int NF = -1>
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int NF = -1, int DEG = -1>
 __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
@@ -183,10 +183,13 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
   // faster with the uniform chunk loop.  Integer modes reset the dummy slot
   // so that the padding edge's |Q| saturates (and, with the larger index,
   // never beats a real edge).
-  constexpr bool PAD = !LEAN;
+  // DEG >= 0: the row's degree is a compile-time constant; exactly its DEG
+  // edges are processed, chunk by chunk, with neither padding nor tail.
+  constexpr bool EXACT = DEG >= 0;
+  constexpr bool PAD = !LEAN && !EXACT;
   if constexpr (PAD && SAT) st_val(L, dummy, post_sat);
   const uint32_t* tab = in.tab;
-  const int deg = in.deg;
+  const int deg = EXACT ? DEG : in.deg;
   const float r1 = in.r1, r2 = in.r2;
   const uint32_t mo = in.mo;
   const int idx_o = static_cast<int>(mo >> 27);
@@ -196,8 +199,8 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
   // padding edge sees Q = dummy + |R|, large and positive)
   uint32_t sgn = (PAD && SAT) ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u))
                               : ((mo ^ par_o) << (32 - deg));
-  const int nfull = NF >= 0 ? NF : (PAD ? (deg + CH - 1) / CH : deg / CH);
-  const int ntail = PAD ? 0 : deg - CH * nfull;
+  const int nfull = EXACT ? (DEG + CH - 1) / CH : (NF >= 0 ? NF : (PAD ? (deg + CH - 1) / CH : deg / CH));
+  const int ntail = (PAD || EXACT) ? 0 : deg - CH * nfull;
 
   float q[LEAN ? 1 : MaxChunks<CH>::value * CH];
   int addr[MaxChunks<CH>::value * CH];
@@ -210,13 +213,16 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
     const Chunk<CH> ch = c == 0 ? in.c0 : load_chunk<CH>(tab, c);
 #pragma unroll
     for (int i = 0; i < CH; ++i)
-      addr[CH * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
+      if (!EXACT || CH * c + i < DEG)
+        addr[CH * c + i] = checked(static_cast<int>(ch.b[i]) + rot(k, ch.s[i], Z), lim, dummy, 1);
     float lv[CH];
 #pragma unroll
-    for (int i = 0; i < CH; ++i) lv[i] = ld_val(L, addr[CH * c + i]);
+    for (int i = 0; i < CH; ++i)
+      if (!EXACT || CH * c + i < DEG) lv[i] = ld_val(L, addr[CH * c + i]);
 #pragma unroll
     for (int i = 0; i < CH; ++i) {
       const int j = CH * c + i;
+      if (EXACT && j >= DEG) continue;
       const float Q = pass1_edge<LT, SAT, LEAN>(L, addr[j], lv[i], j, idx_o, r1, r2, sgn, min1, min2, qs, msg_sat,
                                                 post_sat);
       if constexpr (!LEAN) q[j] = Q;
@@ -256,10 +262,12 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
     if (c >= nfull) break;
     float qv[CH];
 #pragma unroll
-    for (int i = 0; i < CH; ++i) qv[i] = LEAN ? ld_val(L, addr[CH * c + i]) : q[LEAN ? 0 : CH * c + i];
+    for (int i = 0; i < CH; ++i)
+      if (!EXACT || CH * c + i < DEG) qv[i] = LEAN ? ld_val(L, addr[CH * c + i]) : q[LEAN ? 0 : CH * c + i];
 #pragma unroll
     for (int i = 0; i < CH; ++i) {
       const int j = CH * c + i;
+      if (EXACT && j >= DEG) continue;
       pass2_edge<LT, SAT>(L, addr[j], qv[i], j, idx, min1, n1s, n2s, post_sat);
     }
   }
@@ -296,6 +304,23 @@ __device__ __forceinline__ void check_update_by_degree(const RowIn<CH>& in, int 
     }
   }
   check_update<LT, MT, SAT, LEAN, CH, NF>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
+}
+
+// The update with the row's exact degree as a compile-time constant (DEG
+// from 2 to the largest degree): no padding edge and no tail.
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2>
+__device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
+                                                   MT* __restrict__ mag1, MT* __restrict__ mag2,
+                                                   uint32_t* __restrict__ meta, int rec, int dummy, float beta,
+                                                   float msg_sat, float post_sat) {
+  if constexpr (DEG < kMaxDeg) {
+    if (in.deg != DEG) {
+      check_update_exact<LT, MT, SAT, LEAN, CH, DEG + 1>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat,
+                                                         post_sat);
+      return;
+    }
+  }
+  check_update<LT, MT, SAT, LEAN, CH, -1, DEG>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2

@@ -401,8 +401,8 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
     RowIn<kServeChunk> row = load_row<kServeChunk>(s_tab, rows[0], mag1, mag2, meta, k);
     for (;; ++it) {
       for (int l = 0; l < m; ++l) {
-        check_update_by_degree<LT, MT, SAT, false, kServeChunk>(row, k, Z, L, mag1, mag2, meta, l * Z + k,
-                                                                ssh.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
+        check_update_exact<LT, MT, SAT, false, kServeChunk>(row, k, Z, L, mag1, mag2, meta, l * Z + k,
+                                                            ssh.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
         // the next row's table and record are ready before the barrier
         const int ln = l + 1 < m ? l + 1 : 0;
         row = load_row<kServeChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
