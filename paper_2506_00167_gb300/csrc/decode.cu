@@ -151,8 +151,8 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_kernel(const De
       RowIn<kChunk> row = load_row<kChunk>(s_tab, rows[0], mag1, mag2, meta, k);
       for (;; ++it) {
         for (int l = 0; l < m; ++l) {
-          check_update_by_degree<LT, MT, SAT, true, kChunk>(row, k, Z, L, mag1, mag2, meta, l * Z + k,
-                                                      item.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
+          check_update_exact<LT, MT, SAT, true, kChunk>(row, k, Z, L, mag1, mag2, meta, l * Z + k,
+                                                        item.dummy_base + k, a.beta, a.msg_sat, a.post_sat);
           // the next row's table and record are ready before the barrier
           const int ln = l + 1 < m ? l + 1 : 0;
           row = load_row<kChunk>(s_tab, rows[ln], mag1, mag2, meta, ln * Z + k);
