@@ -307,7 +307,11 @@ __device__ __forceinline__ void check_update_by_degree(const RowIn<CH>& in, int 
 }
 
 // The update with the row's exact degree as a compile-time constant (DEG
-// from 2 to the largest degree): no padding edge and no tail.
+// from 2 to the largest degree): no padding edge and no tail.  A LEAN caller's
+// rows of degree up to kRegQMaxDeg keep their Q values in registers all the
+// same (few enough not to raise the kernel's register count): one shared
+// store and load less per edge.
+constexpr int kRegQMaxDeg = 10;
 template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2>
 __device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                                    MT* __restrict__ mag1, MT* __restrict__ mag2,
@@ -320,7 +324,8 @@ __device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, i
       return;
     }
   }
-  check_update<LT, MT, SAT, LEAN, CH, -1, DEG>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
+  constexpr bool lean = LEAN && DEG > kRegQMaxDeg;
+  check_update<LT, MT, SAT, lean, CH, -1, DEG>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
