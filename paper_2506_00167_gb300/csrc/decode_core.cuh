@@ -309,9 +309,11 @@ __device__ __forceinline__ void check_update_by_degree(const RowIn<CH>& in, int 
 // The update with the row's exact degree as a compile-time constant (DEG
 // from 2 to the largest degree): no padding edge and no tail.  A LEAN caller's
 // rows of degree up to kRegQMaxDeg keep their Q values in registers all the
-// same (few enough not to raise the kernel's register count): one shared
-// store and load less per edge.
-constexpr int kRegQMaxDeg = 10;
+// same: one shared store and load less per edge.  With the degree fixed at
+// compile time the compiler fits rows of degree 22 in the 80-register budget
+// of two 384-thread blocks per SM (one rarely used variant, INT16 with the
+// code-block CRC exit, spills 8 bytes); beyond that the Q values park.
+constexpr int kRegQMaxDeg = 22;
 template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2>
 __device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                                    MT* __restrict__ mag1, MT* __restrict__ mag2,
