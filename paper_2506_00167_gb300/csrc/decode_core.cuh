@@ -519,6 +519,10 @@ __device__ __forceinline__ __half2 small_pair(uint32_t a, uint32_t b) {
   return __hsub2(as_h2((0x6400u + a) | ((0x6400u + b) << 16)), __float2half2_rn(1024.0f));
 }
 
+// Rows up to this degree keep their Q pairs in registers for pass 2 as well
+// (beyond it the 80-register budget spills).
+constexpr int kRegQ2MaxDeg = 12;
+
 // one pair check (l, k); `dummy` is this thread's dummy slot.  Pass 1 parks
 // each Q_j pair in its posterior's slot and pass 2 reads it back (the check
 // owns those slots during the layer), which keeps the row's Q values out of
@@ -568,6 +572,9 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   // edges are processed; otherwise a padding edge completes the last chunk
   // (on this thread's dummy slot, which can never be a minimum)
   constexpr bool EXACT = DEG >= 0;
+  // rows of degree up to kRegQ2MaxDeg also keep their Q pairs in registers for
+  // pass 2 (the parked copies still serve the argmin rewrite)
+  constexpr bool REGQ = EXACT && DEG <= kRegQ2MaxDeg;
   if constexpr (!EXACT) L[dummy] = as_u32(post);
   const uint32_t* tab = in.tab;
   const int deg = EXACT ? DEG : in.deg;
@@ -585,6 +592,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const int nch = (deg + kChunk - 1) / kChunk;
 
   int addr[kMaxChunks * kChunk];
+  uint32_t qr[REGQ ? kMaxChunks * kChunk : 1];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
   uint32_t acc1 = 0, acc2 = 0;  // Q signs: each new edge enters at bits 15 / 31
 #pragma unroll
@@ -611,6 +619,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
       __half2 Q = __hsub2(as_h2(lv[i]), as_h2(rb));
       Q = __hmin2(__hmax2(Q, npost), post);
       L[addr[j]] = as_u32(Q);
+      if constexpr (REGQ) qr[j] = as_u32(Q);
       if (j < 16)
         acc1 = ((acc1 >> 1) & 0x7FFF7FFFu) | (as_u32(Q) & 0x80008000u);
       else
@@ -640,7 +649,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
     uint32_t qv[kChunk];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i)
-      if (!EXACT || kChunk * c + i < DEG) qv[i] = L[addr[kChunk * c + i]];
+      if (!EXACT || kChunk * c + i < DEG) qv[i] = REGQ ? qr[REGQ ? kChunk * c + i : 0] : L[addr[kChunk * c + i]];
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) {
       if (EXACT && kChunk * c + i >= DEG) continue;
