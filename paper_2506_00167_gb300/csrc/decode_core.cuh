@@ -168,8 +168,9 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
 // LEAN: pass 1 parks each Q_j in its posterior's slot (the check owns those
 // slots during the layer) and pass 2 reads it back, instead of holding the
 // row's Q values in registers: one shared store and load more per edge for
-// about 30 fewer registers, which lets two 384-thread blocks share an SM.
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int NF = -1, int DEG = -1>
+// about 30 fewer registers, which lets two 384-thread blocks share an SM
+// (check_update_exact parks only rows above kRegQMaxDeg).
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = -1>
 __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
@@ -199,7 +200,7 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
   // padding edge sees Q = dummy + |R|, large and positive)
   uint32_t sgn = (PAD && SAT) ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u))
                               : ((mo ^ par_o) << (32 - deg));
-  const int nfull = EXACT ? (DEG + CH - 1) / CH : (NF >= 0 ? NF : (PAD ? (deg + CH - 1) / CH : deg / CH));
+  const int nfull = EXACT ? (DEG + CH - 1) / CH : (PAD ? (deg + CH - 1) / CH : deg / CH);
   const int ntail = (PAD || EXACT) ? 0 : deg - CH * nfull;
 
   float q[LEAN ? 1 : MaxChunks<CH>::value * CH];
@@ -287,25 +288,6 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
   meta[rec] = (PAD ? qs >> (CH * nfull - deg) : qs) | (static_cast<uint32_t>(idx) << 27);
 }
 
-// The update with the row's number of chunks (whole chunks for LEAN, padded
-// ones otherwise) as a compile-time constant: one dispatch per row instead of
-// a compare and branch per chunk in each pass, and each row's passes run as
-// straight-line code.
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int NF = 1>
-__device__ __forceinline__ void check_update_by_degree(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
-                                                       MT* __restrict__ mag1, MT* __restrict__ mag2,
-                                                       uint32_t* __restrict__ meta, int rec, int dummy, float beta,
-                                                       float msg_sat, float post_sat) {
-  if constexpr (NF < MaxChunks<CH>::value) {
-    if ((LEAN ? in.deg / CH : (in.deg + CH - 1) / CH) != NF) {
-      check_update_by_degree<LT, MT, SAT, LEAN, CH, NF + 1>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta,
-                                                            msg_sat, post_sat);
-      return;
-    }
-  }
-  check_update<LT, MT, SAT, LEAN, CH, NF>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
-}
-
 // The update with the row's exact degree as a compile-time constant (DEG
 // from 2 to the largest degree): no padding edge and no tail.  A LEAN caller's
 // rows of degree up to kRegQMaxDeg keep their Q values in registers all the
@@ -327,7 +309,7 @@ __device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, i
     }
   }
   constexpr bool lean = LEAN && DEG > kRegQMaxDeg;
-  check_update<LT, MT, SAT, lean, CH, -1, DEG>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
+  check_update<LT, MT, SAT, lean, CH, DEG>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
