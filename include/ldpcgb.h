@@ -353,11 +353,13 @@ typedef struct {
 #define LDPC_SERVE_PAIRED 4
 
 typedef struct {
-  int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16;
-                                 * redundancy version 0 */
+  int32_t bg, Z, Qm, E, n_cb;   /* one shape for all of the TB's code blocks; n_cb in 1..16 */
   int32_t n_sc, payload_bits;   /* n_e; payload_bits = n_cb * kb * Z - 24, or, for n_cb > 1 with a CRC
                                  * per code block (LDPC_CB_CRC24B), n_cb * (kb * Z - 24) - 24 */
   float inv_sigma2;
+  int32_t rv;                   /* redundancy version of every code block, 0..3, as LDPC_CB_RV in the
+                                 * batch descriptors (1-3 need a buffer of 66 Z or 50 Z positions) */
+  int32_t reserved;             /* 0 */
   int64_t sym_offset;           /* bytes into host_pool (8-aligned): n_cb * E/Qm float2, block after block */
   int64_t mask_offset;          /* bytes into host_pool (4-aligned): n_cb * ceil(E/Qm/32) words */
   int64_t result_offset;        /* bytes into result_pool (4-aligned) for n_cb * kb*Z/32 words, or -1 */

@@ -95,7 +95,8 @@ SERVE_PAIRED = 4  # ldpc_serve_desc.flags: INT8 requests always in the paired fo
 class ServeTbC(ctypes.Structure):
     _fields_ = [("bg", ctypes.c_int32), ("Z", ctypes.c_int32), ("Qm", ctypes.c_int32), ("E", ctypes.c_int32),
                 ("n_cb", ctypes.c_int32), ("n_sc", ctypes.c_int32), ("payload_bits", ctypes.c_int32),
-                ("inv_sigma2", ctypes.c_float), ("sym_offset", ctypes.c_int64), ("mask_offset", ctypes.c_int64),
+                ("inv_sigma2", ctypes.c_float), ("rv", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sym_offset", ctypes.c_int64), ("mask_offset", ctypes.c_int64),
                 ("result_offset", ctypes.c_int64), ("tag", ctypes.c_uint64)]
 
 

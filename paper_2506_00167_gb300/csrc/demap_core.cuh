@@ -95,12 +95,14 @@ __device__ __noinline__ float bit_llr(int e, int n_re, int interleave, float inv
 }
 
 // Resource element r of a code block (symbol y, punctured or not) into its
-// codeword positions, `out` pointing at the block's position t0.
+// codeword positions, `out` pointing at the block's position t0: bit e of the
+// rate-matched stream lands on buffer offset (k0 + e) mod Ncb, and a bit
+// repeated at e + Ncb (E > Ncb) is added there by the owner of e.
 // `out` is an LT* or any type whose out[e] takes an LT.
 template <typename LT, int Qm, typename Out, typename LoadSym, typename LoadMask>
 __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, Out out, int r, int n_re,
-                                              int E, int ncb, int interleave, float q_scale, float llr_sat,
-                                              LoadSym ld_sym, LoadMask ld_msk) {
+                                              int E, int ncb, int k0, int interleave, float q_scale,
+                                              float llr_sat, LoadSym ld_sym, LoadMask ld_msk) {
   float lam[Qm];
   axis_llr<Qm / 2>(y.x, inv_sigma2, lam, 0);
   axis_llr<Qm / 2>(y.y, inv_sigma2, lam, 1);
@@ -110,7 +112,8 @@ __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_si
     if (e >= ncb) continue;  // a repetition: added by the owner of e - ncb
     float v = punct ? 0.0f : lam[i];
     if (e + ncb < E) v += bit_llr<Qm>(e + ncb, n_re, interleave, inv_sigma2, ld_sym, ld_msk);
-    out[e] = to_llr<LT>(v, q_scale, llr_sat);
+    const int q = k0 + e;  // the redundancy version's buffer offset
+    out[q >= ncb ? q - ncb : q] = to_llr<LT>(v, q_scale, llr_sat);
   }
 }
 

@@ -193,7 +193,11 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
   using namespace demapcore;
   const int ncb = cb.n_eff * Z - cb.t0;  // circular buffer: E > ncb repeats it
   for (int p = k; p < cb.t0; p += Z) L[p] = LT(0);
-  for (int p = cb.t0 + min(cb.E, ncb) + k; p < cb.n_eff * Z; p += Z) L[p] = LT(0);
+  // buffer offsets k0 + j (mod ncb), j from E to ncb: those the version does not reach
+  for (int j = min(cb.E, ncb) + k; j < ncb; j += Z) {
+    const int q = cb.k0 + j;
+    L[cb.t0 + (q >= ncb ? q - ncb : q)] = LT(0);
+  }
   const float2* sym = reinterpret_cast<const float2*>(a.host_pool) + cb.re_off;
   const uint32_t* msk = reinterpret_cast<const uint32_t*>(a.host_pool) + cb.mask_off;
   const Out out = L.shift(cb.t0);
@@ -204,10 +208,10 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
     auto ls = [&](int i) { return ld_pool_f2(sym + i); };
     auto lm = [&](int w) { return ld_pool_u32(msk + w); };
     switch (cb.Qm) {
-      case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
-      case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
-      case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
-      default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
     }
   }
 }
@@ -792,6 +796,16 @@ int ensure_running(ldpc_server* v) {
   return launch_loop(v);
 }
 
+// Start of redundancy version rv in a shape's circular buffer (NR's table for
+// buffers of 66 Z and 50 Z positions), -1 where the buffer has neither length.
+int serve_k0(const ShapeDev& sd, int rv, int Z) {
+  static const int units66[4] = {0, 17, 33, 56}, units50[4] = {0, 13, 25, 43};
+  if (rv == 0) return 0;
+  if (sd.nb - sd.npc == 66) return units66[rv] * Z;
+  if (sd.nb - sd.npc == 50) return units50[rv] * Z;
+  return -1;
+}
+
 template <typename T>
 int host_alloc(T** p, size_t n) {
   const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
@@ -1067,6 +1081,9 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       return srv_fail(LDPC_EINVAL, at + "code-block CRCs need a service started with LDPC_SERVE_CB_CRC");
     if (static_cast<int64_t>(tb.n_cb) * (K / 32) >= static_cast<int64_t>(kServeXpowWords))
       return srv_fail(LDPC_EINVAL, at + "transport block too large");
+    if (tb.rv < 0 || tb.rv > 3 || tb.reserved != 0) return srv_fail(LDPC_EINVAL, at + "rv must be 0..3");
+    if (tb.rv != 0 && serve_k0(sd, tb.rv, tb.Z) < 0)
+      return srv_fail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
     if (tb.sym_offset < 0 || tb.sym_offset % 8 || tb.mask_offset < 0 || tb.mask_offset % 4 ||
@@ -1091,7 +1108,10 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const int K = sd.kb * tb.Z;
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
-    const int cols = (tb.E + t0 + tb.Z - 1) / tb.Z;
+    // columns up to the last position sent; a version that wraps the buffer reaches them all
+    const int k0 = serve_k0(sd, tb.rv, tb.Z);
+    const int ncb = sd.nb * tb.Z - t0;
+    const int cols = k0 + tb.E > ncb ? sd.nb : (t0 + k0 + tb.E + tb.Z - 1) / tb.Z;
     const int m_eff = std::min(sd.mb, std::max(sd.mc, cols - sd.kb));
     // the form: paired when the service pairs always, when only that form fits, or by load:
     // pairing starts once the items in flight with this request's single-form items would
@@ -1140,7 +1160,8 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       c.n_eff = sd.kb + m_eff;
       c.n_re = n_re;
       c.kb = sd.kb;
-      c.flags = rq.seg ? LDPC_CB_CRC24B : 0;
+      c.flags = (rq.seg ? LDPC_CB_CRC24B : 0) | LDPC_CB_RV(tb.rv);
+      c.k0 = k0;
       c.re_off = tb.sym_offset / 8 + static_cast<int64_t>(j) * n_re;
       c.mask_off = tb.mask_offset / 4 + static_cast<int64_t>(j) * mw;
       c.llr_off = rq.status_off + j;  // status word index in the arena

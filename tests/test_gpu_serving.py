@@ -248,6 +248,43 @@ def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(form):
         srv.stop()
 
 
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_redundancy_versions_through_the_service_match_the_batch_path(form):
+    """Code blocks of redundancy versions 0-3 (k0 inside the circular buffer, wrapping it, repetition):
+    the service's fused demap lands every bit on (k0 + e) mod Ncb and decodes the same columns as the
+    batch path, bit for bit."""
+    from workload.configs import cb_rv, redundancy_versions
+    w = redundancy_versions(n_per=2, rates=(0.5, 0.3, 0.2), seed=15)
+    assert sorted({cb_rv(c) for c in w.cbs}) == [0, 1, 2, 3]
+    raw, mask_base = pool_bytes(w)
+    host = torch.from_numpy(raw).pin_memory()
+    n = w.n_tb
+    words = [_tb_words(w, t) for t in range(n)]
+    offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
+    res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
+    s = session_for(w, "i8")
+    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, paired=form[0], pair_threshold=form[1])
+    try:
+        recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
+        assert sorted(set(recs["rv"].tolist())) == [0, 1, 2, 3]
+        bad = recs[:1].copy()
+        bad["rv"] = 4
+        with pytest.raises(LdpcError, match="rv"):
+            srv.submit(bad)
+        done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
+        assert sorted(done["tag"].tolist()) == list(range(n))
+        _check_forms(srv, form[2])
+        d_ref, bits_ref, it_ref = _batch_reference(w, range(n))
+        for r in done:
+            t = int(r["tag"])
+            assert int(r["d"]) == int(d_ref[t]), t
+            assert int(r["max_iters"]) == it_ref[t], t
+            assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
+        assert 0 < int(done["d"].sum()) < n  # versions 1-2 at these rates are not all self-decodable
+    finally:
+        srv.stop()
+
+
 def test_two_loops_per_sm_is_withdrawn(pool):
     w, host, mask_base = pool
     with pytest.raises(LdpcError, match="withdrawn"):

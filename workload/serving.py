@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .configs import N_MINISLOT, N_SYM, TBSpec, build, default_bgs, draw_tb_shape, es_n0_sigma2, \
+from .configs import N_MINISLOT, N_SYM, TBSpec, build, cb_rv, default_bgs, draw_tb_shape, es_n0_sigma2, \
     operating_point_db
 from .rng import np_stream
 
@@ -91,11 +91,15 @@ def tb_records(w, mask_base: int, serve_dtype, pool_index=None, tags=None, resul
     for j, t in enumerate(idx):
         tb = w.tbs[t]
         c = w.cbs[int(tb["first_cb"])]
-        out[j] = (int(c["bg"]), int(c["Z"]), int(c["Qm"]), int(c["E"]), int(tb["n_cb"]), int(tb["n_sc"]),
-                  int(tb["payload_bits"]), float(c["inv_sigma2"]), int(c["re_offset"]) * 8,
-                  mask_base + int(c["mask_word_offset"]) * 4,
-                  -1 if result_offsets is None else int(result_offsets[j]),
-                  j if tags is None else int(tags[j]))
+        r = out[j:j + 1]
+        for name in ("bg", "Z", "Qm", "E", "inv_sigma2"):
+            r[name] = c[name]
+        r["n_cb"], r["n_sc"], r["payload_bits"] = tb["n_cb"], tb["n_sc"], tb["payload_bits"]
+        r["rv"] = cb_rv(c)
+        r["sym_offset"] = int(c["re_offset"]) * 8
+        r["mask_offset"] = mask_base + int(c["mask_word_offset"]) * 4
+        r["result_offset"] = -1 if result_offsets is None else int(result_offsets[j])
+        r["tag"] = j if tags is None else int(tags[j])
     return out
 
 
