@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "arena.h"
+#include "host_rules.h"
 #include "crc_core.cuh"
 #include "decode_core.cuh"
 #include "demap_core.cuh"
@@ -710,11 +711,8 @@ struct ldpc_server {
   uint32_t* xpow32 = nullptr;
   uint32_t* crc_table = nullptr;
   uint8_t* rscratch = nullptr;
-  bool pairs = false;        // INT8: items may run in the paired form (two code blocks per thread group)
-  bool always_pair = false;  // LDPC_SERVE_PAIRED: every item whose shape allows it
-  int64_t pair_threshold = 0;  // otherwise: pair when the items in flight would exceed this,
-  int64_t pair_release = 0;    // and keep pairing until they fall to this
-  bool pairing = false;        // the current state of that choice
+  bool pairs = false;  // INT8: items may run in the paired form (two code blocks per thread group)
+  PairPolicy policy;   // which requests take it
   // requests, items single, items paired, loop launches; the last replay's longest pass of its
   // host loop (ns) and its passes longer than 1 ms
   int64_t stats[6] = {0, 0, 0, 0, 0, 0};
@@ -796,16 +794,6 @@ int ensure_running(ldpc_server* v) {
   return launch_loop(v);
 }
 
-// Start of redundancy version rv in a shape's circular buffer (NR's table for
-// buffers of 66 Z and 50 Z positions), -1 where the buffer has neither length.
-int serve_k0(const ShapeDev& sd, int rv, int Z) {
-  static const int units66[4] = {0, 17, 33, 56}, units50[4] = {0, 13, 25, 43};
-  if (rv == 0) return 0;
-  if (sd.nb - sd.npc == 66) return units66[rv] * Z;
-  if (sd.nb - sd.npc == 50) return units50[rv] * Z;
-  return -1;
-}
-
 template <typename T>
 int host_alloc(T** p, size_t n) {
   const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
@@ -864,7 +852,8 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
                        &sms);
     cudaGetDevice(&v->device);
     v->pairs = v->mode == LDPC_I8 && !(d->flags & LDPC_SERVE_UNPAIRED);
-    v->always_pair = v->pairs && (d->flags & LDPC_SERVE_PAIRED);
+    v->policy.pairs = v->pairs;
+    v->policy.always = v->pairs && (d->flags & LDPC_SERVE_PAIRED);
     const int esz = v->mode == LDPC_F32 ? 4 : (v->mode == LDPC_I8 ? 1 : 2);
     // ---- per-shape tables and layouts, sized for the largest block of the shape: the single
     // form (four-edge chunks, check messages in shared memory) and, for INT8, the paired form
@@ -931,8 +920,8 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     }
     v->grid = per_sm * sms;
     // by default pairing starts above two items in flight per loop and stops at one
-    v->pair_threshold = d->pair_threshold > 0 ? d->pair_threshold : 2 * static_cast<int64_t>(v->grid);
-    v->pair_release = std::min<int64_t>(d->pair_release > 0 ? d->pair_release : v->grid, v->pair_threshold);
+    v->policy.threshold = d->pair_threshold > 0 ? d->pair_threshold : 2 * static_cast<int64_t>(v->grid);
+    v->policy.release = std::min<int64_t>(d->pair_release > 0 ? d->pair_release : v->grid, v->policy.threshold);
     int gmax = 0;  // paired-form group slots per loop
     for (auto& ss : v->hshapes)
       if (ss.feasible_p) gmax = std::max(gmax, ss.Gp);
@@ -1082,7 +1071,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     if (static_cast<int64_t>(tb.n_cb) * (K / 32) >= static_cast<int64_t>(kServeXpowWords))
       return srv_fail(LDPC_EINVAL, at + "transport block too large");
     if (tb.rv < 0 || tb.rv > 3 || tb.reserved != 0) return srv_fail(LDPC_EINVAL, at + "rv must be 0..3");
-    if (tb.rv != 0 && serve_k0(sd, tb.rv, tb.Z) < 0)
+    if (rv_k0(sd.nb - sd.npc, tb.rv, tb.Z) < 0)
       return srv_fail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
@@ -1109,18 +1098,12 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
     // columns up to the last position sent; a version that wraps the buffer reaches them all
-    const int k0 = serve_k0(sd, tb.rv, tb.Z);
-    const int ncb = sd.nb * tb.Z - t0;
-    const int cols = k0 + tb.E > ncb ? sd.nb : (t0 + k0 + tb.E + tb.Z - 1) / tb.Z;
+    const int k0 = rv_k0(sd.nb - sd.npc, tb.rv, tb.Z);
+    const int cols = decoded_cols(sd.nb, tb.Z, t0, k0, tb.E);
     const int m_eff = std::min(sd.mb, std::max(sd.mc, cols - sd.kb));
-    // the form: paired when the service pairs always, when only that form fits, or by load:
-    // pairing starts once the items in flight with this request's single-form items would
-    // exceed the threshold and stops once they fall to the release level
     const int n_single = ss.feasible ? (tb.n_cb + ss.G - 1) / ss.G : 0;
-    const int64_t load = static_cast<int64_t>(v->items_inflight) + n_single;
-    if (load > v->pair_threshold) v->pairing = true;
-    else if (load <= v->pair_release) v->pairing = false;
-    const bool pair = v->pairs && ss.feasible_p && (v->always_pair || !ss.feasible || v->pairing);
+    const bool pair = v->policy.choose(static_cast<int64_t>(v->items_inflight), n_single, ss.feasible != 0,
+                                       ss.feasible_p != 0);
     const int G = std::max(1, std::min(pair ? 2 * ss.Gp : ss.G, tb.n_cb));  // code blocks per item
     const int n_items = (tb.n_cb + G - 1) / G;
     if (v->free_slots.empty() || v->items_inflight + n_items > v->item_cap || v->cbs_inflight + tb.n_cb > v->cb_cap)

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "host_rules.h"
 #include "internal.cuh"
 
 struct ldpc_session {
@@ -699,22 +700,13 @@ int ldpc_batch_create(ldpc_session* s, const ldpc_cb_desc* cbs, int32_t n_cb, co
         return bail(LDPC_EINVAL, at + "negative offset or unknown flag");
       // start of the redundancy version: NR's table for buffers of 66 Z and 50 Z positions
       const int rv = (c.flags & LDPC_CB_RV_MASK) >> LDPC_CB_RV_SHIFT;
-      const int ncb = g.nb * c.Z - t0;
-      int k0 = 0;
-      if (rv != 0) {
-        static const int units66[4] = {0, 17, 33, 56}, units50[4] = {0, 13, 25, 43};
-        if (g.nb - g.npc == 66)
-          k0 = units66[rv] * c.Z;
-        else if (g.nb - g.npc == 50)
-          k0 = units50[rv] * c.Z;
-        else
-          return bail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
-      }
+      const int k0 = rv_k0(g.nb - g.npc, rv, c.Z);
+      if (k0 < 0) return bail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
       if ((c.llr_offset * esz) % 16) return bail(LDPC_EINVAL, at + "llr_offset must be 16-byte aligned");
       if ((g.kb * c.Z) % 32) return bail(LDPC_EINVAL, at + "kb*Z must be a multiple of 32");
       if (!(c.inv_sigma2 >= 0.f)) return bail(LDPC_EINVAL, at + "inv_sigma2 must be >= 0");
       // columns up to the last position sent; a version that wraps the buffer reaches them all
-      const int cols = k0 + c.E > ncb ? g.nb : (t0 + k0 + c.E + c.Z - 1) / c.Z;
+      const int cols = decoded_cols(g.nb, c.Z, t0, k0, c.E);
       const int m_eff = std::min(g.mb, std::max(g.mc, cols - g.kb));
       if (g.maxcol_upto[m_eff - 1] >= g.kb + m_eff)
         return bail(LDPC_EINVAL, at + "a decoded row uses a column beyond the decoded ones (base graph order)");
