@@ -13,6 +13,11 @@
 // the TB CRC-24, copies the decoded bits to the host result pool and writes a
 // completion record to a host ring, sequence number last after a system
 // fence.  All waits are bounded by %globaltimer.
+//
+// INT8 items come in two forms, chosen per request at admission by load
+// (host_rules.h): single (one code block per thread group, check messages in
+// shared memory) or paired (two blocks per thread group in half2, messages in
+// a device-memory slot per group); one loop kernel holds both bodies.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
