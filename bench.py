@@ -204,6 +204,13 @@ def load_peaks():
     return 6800.0, "fallback", 2070.0
 
 
+def workload_desc(args) -> str:
+    """The workload named in both arms' JSON lines."""
+    return {"large": "4096 x BG1-shaped Z=384 K=8448 R=1/2 16-QAM, Es/N0 6-12 dB, <=10 iter + ET",
+            "mixed": "512 slots x 8 UEs mixed BG/Z/R/Qm" + (", CRC-24B per code block" if args.cb_crc else ""),
+            "tiny": "8x16 Z=16 QPSK"}[args.config]
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     if rank != 0:
@@ -229,7 +236,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.config},
+            "data": "synthetic", "config": {"workload": workload_desc(args), "cb_crc": bool(args.cb_crc)},
             "cpu_baseline": {"value": v, "unit": "Gbit/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -889,11 +896,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"f32": "f32", "i8": "i8", "i16": "i16"}[mode],
             "data": "synthetic (seeded Tx chain: CRC-24, QC-LDPC encode, 16-QAM, AWGN, URLLC puncture masks)",
-            "config": {"workload": {"large": "4096 x BG1-shaped Z=384 K=8448 R=1/2 16-QAM, Es/N0 6-12 dB, "
-                                             "<=10 iter + ET",
-                                    "mixed": "512 slots x 8 UEs mixed BG/Z/R/Qm"
-                                             + (", CRC-24B per code block" if args.cb_crc else ""),
-                                    "tiny": "8x16 Z=16 QPSK"}[args.config],
+            "config": {"workload": workload_desc(args),
                        "cb_crc": bool(args.cb_crc),
                        "code_blocks": w.n_cb, "transport_blocks": w.n_tb, "info_bits_per_step": info_bits,
                        "mean_iters": float(np.mean(status & 0xFFFF)),
