@@ -49,11 +49,11 @@ def _wait(srv, n, timeout=20.0):
     return np.concatenate(got)
 
 
-def _batch_reference(w, idx):
+def _batch_reference(w, idx, mode="i8"):
     """The same TBs through the batch path (puncture_demap + decode_batch + tb_crc_goodput): d_e, bits and
     the most iterations of any code block, per TB."""
     sub = subset(w, idx)
-    s = session_for(sub, "i8")
+    s = session_for(sub, mode)
     b = s.batch(sub.cbs, sub.tbs, sub.slot_N)
     sym, mask = device_inputs(sub)
     out = s.run(b, sym, mask, b.alloc_outputs())
@@ -283,6 +283,47 @@ def test_redundancy_versions_through_the_service_match_the_batch_path(form):
         assert 0 < int(done["d"].sum()) < n  # versions 1-2 at these rates are not all self-decodable
     finally:
         srv.stop()
+
+
+@pytest.mark.parametrize("mode", ["f32", "i16"])
+def test_float_and_int16_services_match_the_batch_path(mode):
+    """The FP32 and INT16 serving loops (single form, messages in shared memory; shapes up to Z = 128 so
+    that FP32 fits): bits, d_e and iteration counts equal the batch path in the same arithmetic; a shape
+    whose FP32 state does not fit shared memory is refused."""
+    w = tb_pool(24, seed=19, max_cb=5, zs=(32, 64, 128))
+    raw, mask_base = pool_bytes(w)
+    host = torch.from_numpy(raw).pin_memory()
+    n = w.n_tb
+    words = [_tb_words(w, t) for t in range(n)]
+    offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
+    res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
+    s = session_for(w, mode)
+    srv = Server(s, host, res, arena_bytes=1 << 26, max_inflight=64)
+    try:
+        recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
+        done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
+        assert sorted(done["tag"].tolist()) == list(range(n))
+        st = srv.stats()
+        assert st["items_paired"] == 0 and st["items_single"] > 0
+        d_ref, bits_ref, it_ref = _batch_reference(w, range(n), mode)
+        for r in done:
+            t = int(r["tag"])
+            assert int(r["d"]) == int(d_ref[t]), t
+            assert int(r["max_iters"]) == it_ref[t], t
+            assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
+        assert 0 < int(done["d"].sum()) <= n
+    finally:
+        srv.stop()
+    if mode == "f32":  # Z = 384 in FP32 (either base graph): too large for the loop's shared memory
+        big = tb_pool(2, seed=3, max_cb=1, zs=(384,))
+        raw2, mb2 = pool_bytes(big)
+        host2 = torch.from_numpy(raw2).pin_memory()
+        srv2 = Server(session_for(big, "f32"), host2, None, arena_bytes=1 << 24, max_inflight=8)
+        try:
+            with pytest.raises(LdpcError, match="shared memory"):
+                srv2.submit(tb_records(big, mb2, abi.SERVE_TB_NP)[:1])
+        finally:
+            srv2.stop()
 
 
 def test_two_loops_per_sm_is_withdrawn(pool):

@@ -342,12 +342,13 @@ def operating_point_db(R: float, Qm: int) -> float:
     return float(10.0 * np.log10(2.0 ** (R * Qm) - 1.0) + 3.0)
 
 
-def draw_tb_shape(rng, bgs):
-    """One TB's (bg, Z, R, Qm, E) for the mixed workload.  Rates below kb/(nb-2) (BG1-shaped: 1/3)
-    send more bits than the circular buffer holds, so their rate matching wraps it (repetition)."""
+def draw_tb_shape(rng, bgs, zs=MIX_Z):
+    """One TB's (bg, Z, R, Qm, E) for the mixed workload (Z from ``zs``).  Rates below kb/(nb-2)
+    (BG1-shaped: 1/3) send more bits than the circular buffer holds, so their rate matching wraps it
+    (repetition)."""
     b = int(rng.integers(0, 2))
     bg = bgs[b]
-    Z = int(MIX_Z[int(rng.integers(0, len(MIX_Z)))])
+    Z = int(zs[int(rng.integers(0, len(zs)))])
     Qm = int(MIX_QM[int(rng.integers(0, len(MIX_QM)))])
     R = float(rng.uniform(0.3, 0.9))
     K = bg.kb * Z

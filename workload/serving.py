@@ -46,9 +46,9 @@ def draw_pattern_id(rng) -> int:
 
 
 def tb_pool(n_tb: int, seed: int = 5, max_cb: int = 16, snr_range_db=(0.0, 3.0), noiseless: bool = False,
-            cb_crc: bool = False):
+            cb_crc: bool = False, zs=None):
     """A Workload of n_tb independent TBs (one per 'slot'), codebook-punctured; ``cb_crc``: multi-block TBs
-    carry a CRC per code block.
+    carry a CRC per code block; ``zs``: the lifting sizes drawn from (default: the mixed workload's).
 
     Es/N0 per TB ~ U[op + snr_range_db[0], op + snr_range_db[1]] with op the
     shape's operating point: the served stream is link-adapted to sit at or
@@ -58,7 +58,7 @@ def tb_pool(n_tb: int, seed: int = 5, max_cb: int = 16, snr_range_db=(0.0, 3.0),
     rng = np_stream(seed, 3)
     specs, widths, punct, snrs = [], [], [], []
     for t in range(n_tb):
-        b, Z, R, Qm, E = draw_tb_shape(rng, bgs)
+        b, Z, R, Qm, E = draw_tb_shape(rng, bgs) if zs is None else draw_tb_shape(rng, bgs, zs)
         n_cb = 1 + int(rng.integers(0, max_cb))
         n_prb = -(-n_cb * (E // Qm) // (12 * N_SYM))
         snr = operating_point_db(R, Qm) + float(rng.uniform(*snr_range_db))
