@@ -290,7 +290,7 @@ def test_float_and_int16_services_match_the_batch_path(mode):
     """The FP32 and INT16 serving loops (single form, messages in shared memory; shapes up to Z = 128 so
     that FP32 fits): bits, d_e and iteration counts equal the batch path in the same arithmetic; a shape
     whose FP32 state does not fit shared memory is refused."""
-    w = tb_pool(24, seed=19, max_cb=5, zs=(32, 64, 128))
+    w = tb_pool(24, seed=19, max_cb=5, zs=(32, 64, 128), snr_range_db=(3.0, 6.0))  # oracle: 3 of 24 pass
     raw, mask_base = pool_bytes(w)
     host = torch.from_numpy(raw).pin_memory()
     n = w.n_tb
@@ -311,7 +311,7 @@ def test_float_and_int16_services_match_the_batch_path(mode):
             assert int(r["d"]) == int(d_ref[t]), t
             assert int(r["max_iters"]) == it_ref[t], t
             assert np.array_equal(res[offs[t]:offs[t + 1]].numpy().view(np.uint32), bits_ref[t]), t
-        assert 0 < int(done["d"].sum()) <= n
+        assert 0 < int(done["d"].sum()) < n
     finally:
         srv.stop()
     if mode == "f32":  # Z = 384 in FP32 (either base graph): too large for the loop's shared memory
