@@ -70,3 +70,60 @@ def test_product_path_has_no_cpu_fallback():
     src = open(os.path.join(ROOT, "paper_2506_00167_gb300", "session.py")).read()
     src += open(os.path.join(ROOT, "paper_2506_00167_gb300", "abi.py")).read()
     assert "oracle" not in src and "workload" not in src
+
+
+# every public struct of the header and its ctypes mirror in the binding
+_STRUCTS = [("ldpc_base_graph", "BaseGraphC"), ("ldpc_session_desc", "SessionDescC"), ("ldpc_cb_desc", "CbDescC"),
+            ("ldpc_tb_desc", "TbDescC"), ("ldpc_batch_info", "BatchInfoC"), ("ldpc_tile", "TileC"),
+            ("ldpc_launch_info", "LaunchInfoC"), ("ldpc_serve_desc", "ServeDescC"), ("ldpc_serve_tb", "ServeTbC"),
+            ("ldpc_serve_done", "ServeDoneC")]
+
+
+def _header_fields(struct_text):
+    """Member names of a typedef'd struct body, in order (comments stripped)."""
+    body = re.sub(r"/\*.*?\*/", "", struct_text, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            m = re.search(r"(\w+)\s*(\[\s*\w+\s*\])?\s*$", part.strip())
+            names.append(m.group(1))
+    return names
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """sizeof / offsetof of every member as the C compiler lays the header out, against ctypes."""
+    import shutil
+    import subprocess
+    from paper_2506_00167_gb300 import abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    txt = open(HEADER).read()
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ldpcgb.h"', "int main(void) {"]
+    members = {}
+    for cname, _ in _STRUCTS:
+        m = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r";", txt)
+        assert m, cname
+        members[cname] = _header_fields(m.group(1))
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in members[cname]:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n"):
+        if ln:
+            s, f, v = ln.split()
+            got[(s, f)] = int(v)
+    for cname, pyname in _STRUCTS:
+        cls = getattr(abi, pyname)
+        assert [f for f, _ in cls._fields_] == members[cname], cname
+        assert ctypes.sizeof(cls) == got[(cname, "size")], cname
+        for f in members[cname]:
+            assert getattr(cls, f).offset == got[(cname, f)], (cname, f)
