@@ -4,6 +4,8 @@
 
 #include <stdint.h>
 
+#include <atomic>
+
 namespace ldpcgb {
 
 // Start k0 of redundancy version rv (0..3) in a circular buffer of buf_cols
@@ -49,5 +51,30 @@ struct PairPolicy {
     return pairs && fits_pair && (always || !fits_single || pairing);
   }
 };
+
+// Consumer of a device -> host completion ring: record number q (from 1)
+// sits in slot (q - 1) mod cap and is complete once its sequence word reads q
+// (the writer stores it last, after a system fence).  Records are taken in
+// order from number rd + 1; a slot whose word is not the next number -- not
+// yet written, left from the previous lap, or corrupted -- ends the drain, and
+// so does a record whose contents `take` rejects (returns false): then *bad is
+// set and rd stays on that record.  Returns the records taken.
+template <typename Rec, typename Take>
+int drain_ring(volatile Rec* ring, uint32_t cap, uint32_t& rd, int max, Take take, bool* bad) {
+  int n = 0;
+  *bad = false;
+  while (n < max) {
+    volatile Rec* r = ring + (rd % cap);
+    if (r->seq != rd + 1u) break;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    if (!take(r)) {
+      *bad = true;
+      break;
+    }
+    ++rd;
+    ++n;
+  }
+  return n;
+}
 
 }  // namespace ldpcgb

@@ -736,6 +736,7 @@ struct ldpc_server {
     int64_t arena_off = 0, arena_words = 0;
     int32_t n_items = 0, n_cb = 0;
     int64_t t_submit = 0;
+    bool busy = false;  // admitted and not yet completed
   };
   std::vector<Slot> slot_info;
   uint32_t tail = 0;
@@ -1124,6 +1125,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     si.n_items = n_items;
     si.n_cb = tb.n_cb;
     si.t_submit = t;
+    si.busy = true;
     ServeReq& rq = v->reqs[slot];
     rq.tag = tb.tag;
     rq.n_cb = tb.n_cb;
@@ -1185,11 +1187,11 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
 int ldpc_serve_poll(ldpc_server* v, ldpc_serve_done* out, int32_t cap, int32_t* n_out) {
   if (!v || !n_out || cap < 0 || (cap > 0 && !out)) return srv_fail(LDPC_EINVAL, "bad poll arguments");
   int n = 0;
-  while (n < cap) {
-    volatile ServeDone* rec = v->done + (v->rd % v->done_cap);
-    if (rec->seq != v->rd + 1u) break;
-    std::atomic_thread_fence(std::memory_order_acquire);
+  bool bad = false;
+  // a completion must name a request slot that is in flight (a corrupt or repeated record does not)
+  drain_ring(v->done, v->done_cap, v->rd, cap, [&](volatile ServeDone* rec) {
     const int slot = rec->req;
+    if (slot < 0 || slot >= v->max_inflight || !v->slot_info[slot].busy) return false;
     auto& si = v->slot_info[slot];
     ldpc_serve_done o{};
     o.tag = rec->tag;
@@ -1205,10 +1207,12 @@ int ldpc_serve_poll(ldpc_server* v, ldpc_serve_done* out, int32_t cap, int32_t* 
     v->alloc->release(si.arena_off, si.arena_words);
     v->items_inflight -= si.n_items;
     v->cbs_inflight -= si.n_cb;
+    si.busy = false;
     v->free_slots.push_back(slot);
-    ++v->rd;
-  }
+    return true;
+  }, &bad);
   *n_out = n;
+  if (bad) return srv_fail(LDPC_ECUDA, "serve: a completion record names no request in flight");
   if (v->items_inflight > 0) return ensure_running(v);  // a loop that idled out while items were pending
   return LDPC_OK;
 }

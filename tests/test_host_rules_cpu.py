@@ -1,6 +1,7 @@
 """Host rules shared by the batch session and the serving loop (csrc/host_rules.h), compiled with the
-host compiler: the redundancy versions' start and decoded columns against the oracle's geometry, and
-the serving loop's choice of the INT8 decode form (pairing by load, with hysteresis)."""
+host compiler: the redundancy versions' start and decoded columns against the oracle's geometry, the
+serving loop's choice of the INT8 decode form (pairing by load, with hysteresis), and its completion-ring
+consumer under injected faults (records missing, stale, corrupted or repeated)."""
 import os
 import shutil
 import subprocess
@@ -131,3 +132,100 @@ def test_pairing_policy_hysteresis_by_hand(driver):
     assert list(map(int, driver(lines))) == [0, 0, 1, 1, 1, 0, 0, 1]
     # only the paired form fits: paired at any load; only the single form fits: never paired
     assert list(map(int, driver(["p 1 0 300 150", "c 0 1 0 1", "c 999 1 1 0"]))) == [1, 0]
+
+
+RING_DRIVER = r"""
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include "host_rules.h"
+
+struct Rec { unsigned long long tag; int req; unsigned seq; };
+
+// A ring of 4 records.  Commands: "w q req" writes record number q (slot (q-1) % 4, sequence word
+// last); "x slot word" overwrites a slot's sequence word; "d max" drains up to max records and prints
+// "n rd bad taken-tags..."; a record is rejected when its request is not in flight, and taking one
+// ends its request ("s req" puts a request in flight).
+int main() {
+  Rec ring[4];
+  std::memset(ring, 0, sizeof ring);
+  unsigned rd = 0;
+  std::set<int> inflight;
+  char op[4];
+  while (std::scanf("%3s", op) == 1) {
+    if (!std::strcmp(op, "s")) {
+      int req;
+      if (std::scanf("%d", &req) != 1) return 2;
+      inflight.insert(req);
+    } else if (!std::strcmp(op, "w")) {
+      unsigned q;
+      int req;
+      if (std::scanf("%u %d", &q, &req) != 2) return 2;
+      Rec& r = ring[(q - 1) % 4];
+      r.tag = 1000 + q;
+      r.req = req;
+      r.seq = q;
+    } else if (!std::strcmp(op, "x")) {
+      unsigned slot, word;
+      if (std::scanf("%u %u", &slot, &word) != 2) return 2;
+      ring[slot].seq = word;
+    } else if (!std::strcmp(op, "d")) {
+      int max;
+      if (std::scanf("%d", &max) != 1) return 2;
+      bool bad = false;
+      unsigned long long tags[16];
+      int k = 0;
+      const int n = ldpcgb::drain_ring(static_cast<volatile Rec*>(ring), 4u, rd, max, [&](volatile Rec* r) {
+        const int req = r->req;
+        if (!inflight.count(req)) return false;
+        inflight.erase(req);
+        tags[k++] = r->tag;
+        return true;
+      }, &bad);
+      std::printf("%d %u %d", n, rd, bad ? 1 : 0);
+      for (int i = 0; i < k; ++i) std::printf(" %llu", tags[i]);
+      std::printf("\n");
+    } else {
+      return 2;
+    }
+  }
+  return 0;
+}
+"""
+
+
+def test_completion_ring_under_injected_faults(tmp_path):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "ring.cpp"
+    src.write_text(RING_DRIVER)
+    exe = tmp_path / "ring"
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    script = [
+        "s 0", "s 1", "s 2", "s 3", "s 4", "s 5", "s 6",
+        "d 8",                 # nothing written yet
+        "w 1 0", "w 2 1", "w 4 3",
+        "d 8",                 # 1 and 2; record 3 is missing, so 4 waits
+        "w 3 2",
+        "d 1",                 # at most one per call
+        "d 8",                 # then 4
+        "d 8",                 # slot 0 still holds record 1 from the previous lap: not record 5
+        "x 0 4294967295",      # a corrupted sequence word in the slot of record 5
+        "d 8",
+        "w 5 4", "w 6 1",      # record 6 repeats request 1, completed long ago
+        "d 8",                 # 5 is taken, 6 is rejected and stays
+        "d 8",                 # still rejected: the ring does not move past it
+    ]
+    r = subprocess.run([str(exe)], input="\n".join(script) + "\n", capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split("\n")[:-1] == [
+        "0 0 0",
+        "2 2 0 1001 1002",
+        "1 3 0 1003",
+        "1 4 0 1004",
+        "0 4 0",
+        "0 4 0",
+        "1 5 1 1005",
+        "0 5 1",
+    ]
