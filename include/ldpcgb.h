@@ -383,7 +383,8 @@ typedef struct {
 LDPC_API int ldpc_serve_start(ldpc_session *s, const ldpc_serve_desc *d, ldpc_server **out);
 /* Admit requests in order until one does not fit; *n_admitted says how many were taken. */
 LDPC_API int ldpc_serve_submit(ldpc_server *srv, const ldpc_serve_tb *tbs, int32_t n, int32_t *n_admitted);
-/* Collect up to cap completions (frees their arena space). */
+/* Collect up to cap completions (frees their arena space), in the order the loop wrote them.  A completion
+ * record that names no request in flight (corrupt or repeated) is refused with LDPC_ECUDA and left in place. */
 LDPC_API int ldpc_serve_poll(ldpc_server *srv, ldpc_serve_done *out, int32_t cap, int32_t *n_out);
 /* Replay an arrival schedule: submit tbs[i] at arrival_ns[i] (ns after the call starts, non-decreasing),
  * retrying admission as space frees, and collect every completion into out[0..n) in completion order.
