@@ -115,9 +115,9 @@ struct ServeArgs {
   int32_t hdr_bytes, interleave, max_iter, early_term;
   float q_scale, llr_sat, beta, msg_sat, post_sat;
   uint64_t idle_ns;
-  uint8_t* rscratch;       // message records: one slot per (resident block, group)
+  uint8_t* rscratch;       // paired form's message words: one slot per (loop block, group)
   int64_t rscratch_group;  // bytes per group slot
-  int32_t groups;          // group slots per block
+  int32_t groups;          // group slots per loop block (the most groups of any paired shape)
   // sizes the checked build tests indices against
   int32_t n_shapes, n_req;
   int64_t arena_words, pool_f2, pool_words;
