@@ -32,7 +32,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "decoded info Gbit/s + % HBM roofline; served p99 slot latency vs 125 µs, INT8 vs FP32"
-ALU_OPS_PER_EDGE = 8   # minimal ALU-pipe lane-ops per lifted edge update
+ALU_OPS_PER_EDGE = 8   # minimal ALU-pipe lane-ops per lifted edge update: R select + sign (2), min1/min2 (3),
+                       # sign parity (1), new magnitude select (1), new sign (1)
 ALU_LANES_PER_SM = 64  # ALU pipe (min/max/compare/select/logic): 64 lanes per clock per SM
 SAT = {"f32": None, "i8": (63, 63, 127), "i16": (1023, 1023, 32767)}
 
@@ -332,86 +333,95 @@ def _pct(x, q):
     return float(np.percentile(x, q)) if len(x) else None
 
 
-def run_serving(args):
-    """Replay config 5's request stream through the decode service; latency vs the 125 us slot.
+def serve_measure(pool_n: int, slots: int, loads, forms, thresholds=(0,), releases=(0,), loops=(1,),
+                  plain_n: int = 400, cb_crc: bool = False, punct_sample: int = 0, verbose: bool = True) -> dict:
+    """Replay the served request stream through the decode service; latency vs the 125 us slot.
 
-    40 UEs, Poisson TB requests per 125 us slot (args.serve_load TBs per UE per
-    slot, 1.0 = the configuration's rate), TBs of 1-16 code blocks of the mixed
-    shapes drawn from a pool of pre-encoded TBs with codebook URLLC puncturing;
-    INT8 service.  Beside it, the FP32 unbatched plain path: one TB at a time
-    through puncture_demap + decode_batch + tb_crc_goodput, synchronised.
+    40 UEs, Poisson TB requests per 125 us slot (``loads``: TBs per UE per slot, 1.0 = the configuration's
+    rate), TBs of 1-16 code blocks of the mixed shapes drawn from a pool of pre-encoded TBs; per slot one
+    URLLC codebook entry on the slot's shared subcarrier grid, expanded on the device; INT8 service.
+    Beside it, the FP32 unbatched plain path: one TB at a time through puncture_demap + decode_batch +
+    tb_crc_goodput, synchronised, on the first requests of the stream at the last load (masks expanded on
+    the host).
     """
     import torch
     from paper_2506_00167_gb300 import Server, Session, abi
     from workload.configs import subset
-    from workload.serving import SLOT_NS, arrivals, pool_bytes, tb_pool, tb_records
+    from workload.serving import (CODEBOOK_PRB, SLOT_NS, codebook_bitmaps, expand_mask, pool_bytes,
+                                  served_workload, slot_stream, tb_pool, tb_records)
 
     torch.cuda.set_device(0)
     t_gen = time.perf_counter()
-    w = tb_pool(args.serve_pool, seed=5, cb_crc=args.cb_crc)
+    w = tb_pool(pool_n, seed=5, cb_crc=cb_crc)
+    book = codebook_bitmaps()
     raw, mask_base = pool_bytes(w)
     host = torch.from_numpy(raw).pin_memory()
     gen_s = time.perf_counter() - t_gen
-    kbits = np.array([w.bgs[int(w.cbs[int(tb["first_cb"])]["bg"])].kb * int(w.cbs[int(tb["first_cb"])]["Z"])
-                      * int(tb["n_cb"]) for tb in w.tbs], dtype=np.int64)
+    first = w.tbs["first_cb"].astype(np.int64)
+    kbits = np.array([w.bgs[int(b)].kb for b in w.cbs["bg"][first]], np.int64) * \
+        w.cbs["Z"][first].astype(np.int64) * w.tbs["n_cb"].astype(np.int64)
     sess = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
-    base_recs = tb_records(w, mask_base, abi.SERVE_TB_NP)
     curves = {}
-    runs = [(f, lp, th, rl) for f in args.serve_form for lp in args.serve_loops
-            for th in (args.serve_pair_threshold if f == "auto" else [0])
-            for rl in (args.serve_pair_release if f == "auto" else [0])]
-    for form, loops, thr, rel in runs:
+    streams = {load: slot_stream(slots, w.tbs["n_sc"], n_ue=40, tb_per_slot=load, seed=6) for load in loads}
+    runs = [(f, lp, th, rl) for f in forms for lp in loops
+            for th in (thresholds if f == "auto" else [0])
+            for rl in (releases if f == "auto" else [0])]
+    for form, lps, thr, rel in runs:
         srv = Server(sess, host, None, arena_bytes=8 << 30, max_inflight=16384, idle_timeout_us=200000,
-                     loops_per_sm=loops, cb_crc=args.cb_crc, paired=SERVE_FORMS[form], pair_threshold=thr,
-                     pair_release=rel)
+                     loops_per_sm=lps, cb_crc=cb_crc, paired=SERVE_FORMS[form], pair_threshold=thr,
+                     pair_release=rel, codebook=(book, CODEBOOK_PRB))
         # warm-up
-        warm = base_recs[:64].copy()
-        warm["tag"] = np.arange(warm.size)
+        st0 = streams[loads[0]]
+        warm = tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=st0["pool"][:64], pattern=st0["pattern"][:64],
+                          grid_sc=st0["grid_sc"][:64])
         srv.replay(warm, np.zeros(warm.size, np.int64), timeout_ms=30000)
-        loads = []
-        for load in args.serve_loads:
-            t_arr, pidx = arrivals(args.serve_slots, n_ue=40, tb_per_slot=load, n_pool=w.n_tb, seed=6)
-            recs = base_recs[pidx].copy()
-            recs["tag"] = np.arange(recs.size)
-            st0 = srv.stats()
+        pts = []
+        for load in loads:
+            st = streams[load]
+            recs = tb_records(w, mask_base, abi.SERVE_TB_NP, pool_index=st["pool"], pattern=st["pattern"],
+                              grid_sc=st["grid_sc"])
+            c0 = srv.stats()
             t0 = time.perf_counter()
-            done = srv.replay(recs, t_arr, timeout_ms=60000)
+            done = srv.replay(recs, st["t_ns"], timeout_ms=60000)
             wall = time.perf_counter() - t0
-            st1 = srv.stats()
-            n_single = st1["items_single"] - st0["items_single"]
-            n_paired = st1["items_paired"] - st0["items_paired"]
+            c1 = srv.stats()
             lat_us = (done["t_complete_ns"] - done["t_submit_ns"]) / 1e3
-            bits = int(kbits[pidx].sum())
-            loads.append({"form": form, "pair_threshold": thr, "pair_release": rel, "loops_per_sm": loops, "tb_per_ue_per_slot": load, "requests": int(recs.size),
-                          "code_blocks": int(recs["n_cb"].sum()),
-                          "offered_gbps": bits / (args.serve_slots * SLOT_NS / 1e9) / 1e9,
-                          "served_gbps": bits / wall / 1e9, "wall_s": wall,
-                          "p50_us": _pct(lat_us, 50), "p99_us": _pct(lat_us, 99), "p999_us": _pct(lat_us, 99.9),
-                          "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
-                          "tb_crc_ok_frac": float(np.mean(done["d"])),
-                          "mean_max_iters": float(np.mean(done["max_iters"])),
-                          "items_single": int(n_single), "items_paired": int(n_paired),
-                          "loop_launches": int(st1["launches"] - st0["launches"]),
-                          "host_longest_pass_us": st1["replay_longest_pass_ns"] / 1e3,
-                          "host_passes_over_1ms": int(st1["replay_passes_over_1ms"]),
-                          **_stall_stats(done)})
-            print(json.dumps({"serving_point": loads[-1]}), flush=True)
+            bits = int(kbits[st["pool"]].sum())
+            pts.append({"form": form, "pair_threshold": thr, "pair_release": rel, "loops_per_sm": lps,
+                        "tb_per_ue_per_slot": load, "slots": slots, "requests": int(recs.size),
+                        "code_blocks": int(recs["n_cb"].sum()),
+                        "offered_gbps": bits / (slots * SLOT_NS / 1e9) / 1e9,
+                        "served_gbps": bits / wall / 1e9, "wall_s": wall,
+                        "p50_us": _pct(lat_us, 50), "p99_us": _pct(lat_us, 99), "p999_us": _pct(lat_us, 99.9),
+                        "max_us": float(lat_us.max()), "within_slot_frac": float(np.mean(lat_us <= 125.0)),
+                        "tb_crc_ok_frac": float(np.mean(done["d"])),
+                        "mean_max_iters": float(np.mean(done["max_iters"])),
+                        "items_single": int(c1["items_single"] - c0["items_single"]),
+                        "items_paired": int(c1["items_paired"] - c0["items_paired"]),
+                        "loop_launches": int(c1["launches"] - c0["launches"]),
+                        "host_longest_pass_us": c1["replay_longest_pass_ns"] / 1e3,
+                        "host_passes_over_1ms": int(c1["replay_passes_over_1ms"]),
+                        **_stall_stats(done)})
+            if verbose:
+                print(json.dumps({"serving_point": pts[-1]}), flush=True)
         srv.stop()
-        curves[f"{form}{thr or ''}{'-' + str(rel) if rel else ''}_{loops}_loops_per_sm"] = loads
+        curves[f"{form}{thr or ''}{'-' + str(rel) if rel else ''}_{lps}_loops_per_sm"] = pts
     # FP32 unbatched plain path: one TB at a time, synchronised
+    st = streams[loads[-1]]
+    n_plain = min(plain_n, st["pool"].size)
+    sw = served_workload(w, st["pool"][:n_plain], st["pattern"][:n_plain], st["grid_sc"][:n_plain], book)
     sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
-    n_plain = min(args.serve_plain, w.n_tb)
     per = []
     for t in range(n_plain):
-        sub = subset(w, [t])
+        sub = subset(sw, [t])
         b = sess32.batch(sub.cbs, sub.tbs, sub.slot_N)
         sym = torch.from_numpy(sub.sym.astype(np.complex64)).cuda()
         mask = torch.from_numpy(sub.mask.view(np.int32)).cuda()
-        per.append((b, sym, mask, b.alloc_outputs(), int(kbits[t])))
+        per.append((b, sym, mask, b.alloc_outputs(), int(kbits[st["pool"][t]])))
     for b, sym, mask, out, _ in per[:8]:
         sess32.run(b, sym, mask, out)
     torch.cuda.synchronize()
-    lat = []
+    lat, oks = [], []
     tot_bits = 0
     t0 = time.perf_counter()
     for b, sym, mask, out, kb in per:
@@ -421,18 +431,48 @@ def run_serving(args):
         lat.append((time.perf_counter() - t1) * 1e6)
         tot_bits += kb
     wall = time.perf_counter() - t0
+    for b, sym, mask, out, _ in per:
+        oks.append(int(out["d"][0].item()))
     plain = {"mode": "f32", "tbs": n_plain, "gbps": tot_bits / wall / 1e9, "p50_us": _pct(lat, 50),
-             "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9)}
+             "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9), "tb_crc_ok_frac": float(np.mean(oks))}
+    res = {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the mixed "
+                       "shapes; per slot one entry of a 128-entry URLLC codebook (7 mini-slot bits, "
+                       "q = 1 - 0.92^12; 4-12-PRB runs on a 66-PRB period) on the slot's shared grid, "
+                       "expanded on the device; INT8 service",
+           "cb_crc": bool(cb_crc), "forms": list(forms), "slots_per_load": slots, "pool_tbs": w.n_tb,
+           "pool_gen_s": gen_s, "loads": curves, "fp32_unbatched_plain": plain}
+    if punct_sample:
+        st = streams[loads[-1]]
+        hit = tot = 0
+        for t, p_, g in zip(st["pool"][:punct_sample], st["pattern"][:punct_sample], st["grid_sc"][:punct_sample]):
+            for words in expand_mask(w, int(t), int(p_), int(g), book):
+                hit += int(np.unpackbits(words.view(np.uint8)).sum())
+            c = w.cbs[int(w.tbs[t]["first_cb"])]
+            tot += int(w.tbs[t]["n_cb"]) * (int(c["E"]) // int(c["Qm"]))
+        res["punctured_re_frac"] = {"value": hit / tot, "sample_requests": int(punct_sample)}
     if os.environ.get("LDPCGB_CHECKED") == "1":  # checked library: the first failed device index check, if any
         log = (ctypes.c_uint32 * 8)()
         abi.check(abi.load().ldpc_check_log(log), "ldpc_check_log")
-        print(json.dumps({"check_log": list(log)}), flush=True)
-    res = {"serving": {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the "
-                                   "mixed shapes, 128-entry URLLC codebook, INT8 service",
-                       "cb_crc": bool(args.cb_crc), "forms": args.serve_form,
-                       "slots_per_load": args.serve_slots, "pool_tbs": w.n_tb, "pool_gen_s": gen_s,
-                       "loads": curves, "fp32_unbatched_plain": plain}}
-    print(json.dumps(res), flush=True)
+        res["check_log"] = list(log)
+    return res
+
+
+def run_serving(args):
+    res = serve_measure(args.serve_pool, args.serve_slots, args.serve_loads, args.serve_form,
+                        args.serve_pair_threshold, args.serve_pair_release, args.serve_loops, args.serve_plain,
+                        args.cb_crc, punct_sample=1000)
+    print(json.dumps({"serving": res}), flush=True)
+
+
+def serve_summary(res: dict) -> dict:
+    """The bench line's serving key: the configured load's latency against the 125 us slot."""
+    pt = next(iter(res["loads"].values()))[-1]
+    keep = ("tb_per_ue_per_slot", "slots", "requests", "offered_gbps", "served_gbps", "p50_us", "p99_us",
+            "p999_us", "max_us", "within_slot_frac", "tb_crc_ok_frac", "mean_max_iters", "items_single",
+            "items_paired")
+    return {"workload": res["workload"], "form": pt["form"], **{k: pt[k] for k in keep},
+            "slot_us": 125.0, "p99_within_slot": pt["p99_us"] <= 125.0,
+            "fp32_unbatched_plain": res["fp32_unbatched_plain"], "pool_tbs": res["pool_tbs"]}
 
 
 SERVE_FORMS = {"auto": "auto", "paired": True, "single": False}
@@ -668,12 +708,14 @@ def main():
                     help="mixed / served TBs of several code blocks carry a CRC per code block (CRC-aided exit)")
     ap.add_argument("--policy", action="store_true", help="time the puncturing allocations (RP, SeF, enforcer)")
     ap.add_argument("--policy-tti", type=int, default=5000)
-    ap.add_argument("--serve-slots", type=int, default=8000)
+    ap.add_argument("--serve-slots", type=int, default=100000)
     ap.add_argument("--serve-pool", type=int, default=1024)
     ap.add_argument("--serve-plain", type=int, default=400)
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.25, 0.5, 0.75, 1.0])
     ap.add_argument("--serve-loops", type=int, nargs="+", default=[1],
                     help="device loops per SM for the service (1; 2 is withdrawn)")
+    ap.add_argument("--bench-serve-slots", type=int, default=4000,
+                    help="slots of the served stream in the default benchmark line (0: no serving key)")
     ap.add_argument("--sweep", default=None, choices=["precision"],
                     help="run a measurement sweep instead of the benchmark line")
     ap.add_argument("--sweep-n", type=int, default=100000, help="code blocks per SNR point (GPU)")
@@ -875,6 +917,12 @@ def main():
                 "mean_iters": float(np.mean(st8 & 0xFFFF))}
         del s8, b8, out8
 
+    # ---- the served stream at the configured load (short): latency against the 125 us slot
+    serve = None
+    if world == 1 and args.bench_serve_slots > 0:
+        serve = serve_summary(serve_measure(256, args.bench_serve_slots, [1.0], ["auto"], plain_n=200,
+                                            verbose=False))
+
     # ---- CPU baseline: the oracle on a bounded sample, all host cores
     cpu = None
     if pool is not None:
@@ -907,7 +955,7 @@ def main():
             "graph": {"ms_per_step": ms_graph / args.steps,
                       "value": world * info_bits * args.steps / (ms_graph / 1e3) / 1e9, "unit": "Gbit/s",
                       "decoder_launches": len(b.plan())},
-            "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "int8": int8,
+            "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "int8": int8, "serve": serve,
             "e2e": {"value": e2e_val, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "pipeline": "steps alternate over 2 streams: one step's host copies overlap the other's kernels"},
             "gpu_launches": gpu_launches, "clocks": clocks}

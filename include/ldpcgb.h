@@ -272,9 +272,10 @@ LDPC_API int ldpc_graph_destroy(ldpc_graph *g);
 /*
  * Decode n_cb code blocks of one shape WITHOUT ALLOCATING any memory (the
  * paper has no counterpart; this is a deployment entry point).  For callers
- * that cannot call cudaMalloc: code running while a CUDA graph is captured or
- * replayed, under a memory pool that forbids growth, or in a real-time loop
- * where an allocation's latency or failure is unacceptable.  It needs no
+ * that cannot call cudaMalloc: code under a memory pool or budget that
+ * forbids growth once set up, a real-time receive loop where an allocation's
+ * latency or failure is unacceptable, or a host application that owns all
+ * device memory and hands the library only its buffers.  It needs no
  * session or batch: the base graph `g` (host arrays) and the decoder settings
  * are passed directly, with the same meaning and limits as in
  * ldpc_session_desc and ldpc_cb_desc.  Code block i's n_eff * Z LLRs start at
@@ -296,6 +297,15 @@ LDPC_API int decode_uniform_noalloc(const ldpc_base_graph *g, int32_t Z, int32_t
                                     float offset_f32, int32_t offset_lsb, int32_t msg_sat,
                                     int32_t post_sat, const void *llr_dev, uint32_t *bits_dev,
                                     int32_t *status_dev, void *cuda_stream);
+/* The no-allocation decoder's device error word on the current device (LDPC_DEVERR_* bits): each
+ * decode_uniform_noalloc call clears it before it decodes; a work item whose bounded bulk-copy wait gave
+ * up sets LDPC_DEVERR_TMA_TIMEOUT and leaves its blocks' bits and status unwritten.  Waits for
+ * `cuda_stream`, stores the word in *flags_out (host) and clears it.  Allocates nothing. */
+LDPC_API int decode_uniform_noalloc_errors(uint32_t *flags_out, void *cuda_stream);
+/* Runs the decoder's bounded bulk-copy wait on an mbarrier that nothing completes, giving up after
+ * `limit` polls (1..65536): it sets LDPC_DEVERR_TMA_TIMEOUT in the word above, exactly as a decode whose
+ * copy never landed would.  For tests of the failure report; enqueued on `cuda_stream`. */
+LDPC_API int decode_uniform_noalloc_wait_check(int32_t limit, void *cuda_stream);
 
 /* ------------------------------------------------------------------ serving
  * Continuous batching of TB decode requests (the paper's per-TTI receiver
@@ -347,6 +357,17 @@ typedef struct {
                               * number of loop thread blocks (one per SM) */
   int32_t pair_release;      /* once pairing, keep pairing until the items in flight fall to this many
                               * (hysteresis); 0: the number of loop thread blocks; at most pair_threshold */
+  /* URLLC puncturing codebook (Sec. III-A: URLLC packets preempt eMBB subcarriers for one mini-slot of
+   * two OFDM symbols, seven mini-slots per slot).  A request names one entry and its band's place on
+   * its slot's subcarrier grid; the loop expands the entry into the punctured resource elements of
+   * the request's code blocks while it demaps them, so one slot's URLLC bursts hit exactly the users
+   * whose bands lie under them.  codebook (host, copied at start; NULL when codebook_n = 0):
+   * [codebook_n][7][ceil(codebook_prb / 32)] uint32 bitmaps; bit p % 32 of word p / 32 of
+   * bitmap [id][m] set = PRB p (12 subcarriers) of the pattern grid is preempted in mini-slot m
+   * (symbols 2m, 2m + 1).  The pattern repeats every codebook_prb PRBs along the slot's grid. */
+  int32_t codebook_n;        /* entries, 0..65536 */
+  int32_t codebook_prb;      /* pattern period in PRBs, 1..65536 (ignored when codebook_n = 0) */
+  const uint32_t *codebook;
 } ldpc_serve_desc;
 #define LDPC_SERVE_CB_CRC 1
 #define LDPC_SERVE_UNPAIRED 2
@@ -359,11 +380,18 @@ typedef struct {
   float inv_sigma2;
   int32_t rv;                   /* redundancy version of every code block, 0..3, as LDPC_CB_RV in the
                                  * batch descriptors (1-3 need a buffer of 66 Z or 50 Z positions) */
-  int32_t reserved;             /* 0 */
+  int32_t pattern;              /* which resource elements URLLC punctured: -1 = bit r % 32 of mask word
+                                 * r / 32 at mask_offset, per code block; 0..codebook_n-1 = that codebook
+                                 * entry on the slot's grid (mask_offset unused) */
   int64_t sym_offset;           /* bytes into host_pool (8-aligned): n_cb * E/Qm float2, block after block */
-  int64_t mask_offset;          /* bytes into host_pool (4-aligned): n_cb * ceil(E/Qm/32) words */
+  int64_t mask_offset;          /* pattern -1: bytes into host_pool (4-aligned), n_cb * ceil(E/Qm/32) words */
   int64_t result_offset;        /* bytes into result_pool (4-aligned) for n_cb * kb*Z/32 words, or -1 */
   uint64_t tag;                 /* echoed in the completion */
+  int32_t grid_sc;              /* pattern >= 0: the first subcarrier of the TB's band on its slot's grid.
+                                 * Resource element i of the TB (code block i / (E/Qm), block after block)
+                                 * sits on OFDM symbol i / n_sc and subcarrier grid_sc + i % n_sc; the TB
+                                 * must fit its band in one slot: n_cb * E/Qm <= 14 * n_sc */
+  int32_t reserved;             /* 0 */
 } ldpc_serve_tb;
 
 typedef struct {
@@ -383,11 +411,15 @@ typedef struct {
 LDPC_API int ldpc_serve_start(ldpc_session *s, const ldpc_serve_desc *d, ldpc_server **out);
 /* Admit requests in order until one does not fit; *n_admitted says how many were taken. */
 LDPC_API int ldpc_serve_submit(ldpc_server *srv, const ldpc_serve_tb *tbs, int32_t n, int32_t *n_admitted);
-/* Collect up to cap completions (frees their arena space), in the order the loop wrote them.  A completion
- * record that names no request in flight (corrupt or repeated) is refused with LDPC_ECUDA and left in place. */
+/* Collect up to cap completions (frees their arena space), in the order the loop wrote them; out[0..*n_out)
+ * is valid whatever the return code.  A completion record that names no request in flight (corrupt or
+ * repeated) stops the collection: the good records before it are returned with LDPC_OK, and the call that
+ * starts on it returns LDPC_ECUDA with *n_out = 0 and leaves it in place -- the ring cannot advance past it,
+ * so the caller stops the service (ldpc_serve_stop) and starts a new one. */
 LDPC_API int ldpc_serve_poll(ldpc_server *srv, ldpc_serve_done *out, int32_t cap, int32_t *n_out);
 /* Replay an arrival schedule: submit tbs[i] at arrival_ns[i] (ns after the call starts, non-decreasing),
- * retrying admission as space frees, and collect every completion into out[0..n) in completion order.
+ * retrying admission as space frees, and collect every completion into out[0..n) in completion order
+ * (on an error return, the completions collected so far are in out, zeros after them).
  * Latency = t_complete_ns - t_submit_ns with t_submit_ns the scheduled arrival.  Gives up with
  * LDPC_ETIMEOUT if nothing completes for timeout_ms. */
 LDPC_API int ldpc_serve_replay(ldpc_server *srv, const ldpc_serve_tb *tbs, const int64_t *arrival_ns, int32_t n,

@@ -27,6 +27,7 @@ EXPORTED = [
     "ldpc_batch_create", "ldpc_batch_destroy", "ldpc_batch_info_get",
     "puncture_demap", "decode_batch", "tb_crc_goodput",
     "ldpc_device_errors", "ldpc_check_log", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
+    "decode_uniform_noalloc_errors", "decode_uniform_noalloc_wait_check",
     "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
     "ldpc_graph_create", "ldpc_graph_launch", "ldpc_graph_destroy",
     "ldpc_serve_start", "ldpc_serve_submit", "ldpc_serve_poll", "ldpc_serve_replay", "ldpc_serve_stats",
@@ -84,7 +85,8 @@ class ServeDescC(ctypes.Structure):
                 ("idle_timeout_us", ctypes.c_int32), ("host_pool", ctypes.c_void_p),
                 ("host_pool_bytes", ctypes.c_uint64), ("result_pool", ctypes.c_void_p),
                 ("result_pool_bytes", ctypes.c_uint64), ("loops_per_sm", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("pair_threshold", ctypes.c_int32), ("pair_release", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("pair_threshold", ctypes.c_int32), ("pair_release", ctypes.c_int32),
+                ("codebook_n", ctypes.c_int32), ("codebook_prb", ctypes.c_int32), ("codebook", ctypes.c_void_p)]
 
 
 SERVE_CB_CRC = 1  # ldpc_serve_desc.flags: accept TBs with code-block CRCs
@@ -95,9 +97,10 @@ SERVE_PAIRED = 4  # ldpc_serve_desc.flags: INT8 requests always in the paired fo
 class ServeTbC(ctypes.Structure):
     _fields_ = [("bg", ctypes.c_int32), ("Z", ctypes.c_int32), ("Qm", ctypes.c_int32), ("E", ctypes.c_int32),
                 ("n_cb", ctypes.c_int32), ("n_sc", ctypes.c_int32), ("payload_bits", ctypes.c_int32),
-                ("inv_sigma2", ctypes.c_float), ("rv", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("inv_sigma2", ctypes.c_float), ("rv", ctypes.c_int32), ("pattern", ctypes.c_int32),
                 ("sym_offset", ctypes.c_int64), ("mask_offset", ctypes.c_int64),
-                ("result_offset", ctypes.c_int64), ("tag", ctypes.c_uint64)]
+                ("result_offset", ctypes.c_int64), ("tag", ctypes.c_uint64), ("grid_sc", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServeDoneC(ctypes.Structure):
@@ -170,6 +173,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ldpc_check_log.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
     lib.decode_uniform_noalloc.argtypes = [ctypes.POINTER(BaseGraphC), i32, i32, i32, i32, i32, i32,
                                            ctypes.c_float, i32, i32, i32, vp, vp, vp, vp]
+    lib.decode_uniform_noalloc_errors.argtypes = [ctypes.POINTER(ctypes.c_uint32), vp]
+    lib.decode_uniform_noalloc_wait_check.argtypes = [i32, vp]
     lib.ldpc_session_set_tiles.argtypes = [vp, ctypes.POINTER(TileC), i32]
     lib.ldpc_session_set_strategy.argtypes = [vp, i32]
     lib.ldpc_batch_plan_get.argtypes = [vp, ctypes.POINTER(LaunchInfoC), i32, ctypes.POINTER(i32)]

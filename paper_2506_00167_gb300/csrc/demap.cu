@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kDemapBlock) demap_repeat_kernel(const DemapAr
   const float2* sym = a.sym + cb.re_off;
   const uint32_t* msk = a.mask + cb.mask_off;
   auto ls = [&](int i) { return __ldg(sym + i); };
-  auto lm = [&](int w) { return __ldg(msk + w); };
+  auto lm = [&](int r) { return ((__ldg(msk + (r >> 5)) >> (r & 31)) & 1u) != 0u; };
   float v;
   switch (cb.Qm) {
     case 2: v = bit_llr<2>(e2 - ncb, cb.n_re, a.interleave, cb.inv_sigma2, ls, lm) +

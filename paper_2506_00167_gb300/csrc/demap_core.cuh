@@ -76,13 +76,14 @@ __device__ __forceinline__ LT to_llr(float lam, float q_scale, float sat) {
 // taken in the same order.
 
 // Max-log LLR of rate-matched bit e (0 for a punctured resource element);
-// sym/msk point at the code block's symbols and mask words.
-template <int Qm, typename LoadSym, typename LoadMask>
+// ld_sym(r) loads the code block's symbol r, punct(r) tells whether resource
+// element r is punctured.
+template <int Qm, typename LoadSym, typename Punct>
 __device__ __noinline__ float bit_llr(int e, int n_re, int interleave, float inv_sigma2, LoadSym ld_sym,
-                                     LoadMask ld_msk) {
+                                     Punct punct) {
   const int r = interleave ? e % n_re : e / Qm;
   const int i = interleave ? e / n_re : e % Qm;
-  if ((ld_msk(r >> 5) >> (r & 31)) & 1u) return 0.0f;
+  if (punct(r)) return 0.0f;
   const float2 y = ld_sym(r);
   float lam[Qm];
   axis_llr<Qm / 2>(y.x, inv_sigma2, lam, 0);
@@ -99,10 +100,10 @@ __device__ __noinline__ float bit_llr(int e, int n_re, int interleave, float inv
 // rate-matched stream lands on buffer offset (k0 + e) mod Ncb, and a bit
 // repeated at e + Ncb (E > Ncb) is added there by the owner of e.
 // `out` is an LT* or any type whose out[e] takes an LT.
-template <typename LT, int Qm, typename Out, typename LoadSym, typename LoadMask>
+template <typename LT, int Qm, typename Out, typename LoadSym, typename Punct>
 __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, Out out, int r, int n_re,
                                               int E, int ncb, int k0, int interleave, float q_scale,
-                                              float llr_sat, LoadSym ld_sym, LoadMask ld_msk) {
+                                              float llr_sat, LoadSym ld_sym, Punct punct_of) {
   float lam[Qm];
   axis_llr<Qm / 2>(y.x, inv_sigma2, lam, 0);
   axis_llr<Qm / 2>(y.y, inv_sigma2, lam, 1);
@@ -111,7 +112,7 @@ __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_si
     const int e = interleave ? i * n_re + r : r * Qm + i;
     if (e >= ncb) continue;  // a repetition: added by the owner of e - ncb
     float v = punct ? 0.0f : lam[i];
-    if (e + ncb < E) v += bit_llr<Qm>(e + ncb, n_re, interleave, inv_sigma2, ld_sym, ld_msk);
+    if (e + ncb < E) v += bit_llr<Qm>(e + ncb, n_re, interleave, inv_sigma2, ld_sym, punct_of);
     const int q = k0 + e;  // the redundancy version's buffer offset
     out[q >= ncb ? q - ncb : q] = to_llr<LT>(v, q_scale, llr_sat);
   }

@@ -2,9 +2,10 @@
 // one shape with no device-memory allocation at all.
 //
 // Who needs it: callers that cannot call cudaMalloc -- for example code that
-// runs while a CUDA graph is being captured or replayed, under a memory pool
-// that forbids new allocations, or inside a real-time loop where an
-// allocation's latency or failure is not acceptable.  Everything the
+// runs under a memory pool or budget that forbids new allocations once set
+// up, inside a real-time receive loop where an allocation's latency or
+// failure is not acceptable, or in a host application that owns all device
+// memory and hands the library only its buffers.  Everything the
 // decoder needs beyond the caller's input and output buffers lives in one
 // file-scope __device__ array of fixed size (kScratchBytes below), which every
 // GPU that loads this library holds until the process exits.
@@ -75,6 +76,22 @@ __global__ void noalloc_setup_kernel(const SetupArgs a) {
       reinterpret_cast<DecodeItem*>(base + kOffItems)[i / a.G] = it;
     }
   }
+}
+
+// A bulk-copy-style wait on an mbarrier that nothing completes: the bounded
+// wait the decoder uses gives up after `limit` polls and records
+// LDPC_DEVERR_TMA_TIMEOUT in the error word, as a decode whose copy never
+// landed would.  Lets a caller check that a wait running out is reported
+// (decode_uniform_noalloc_errors) and leaves the context usable.
+__global__ void noalloc_wait_check_kernel(uint32_t limit, uint8_t* scratch) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, limit))
+    atomicOr(reinterpret_cast<uint32_t*>(scratch + kOffErr), LDPC_DEVERR_TMA_TIMEOUT);
 }
 
 // Device address of g_scratch per device, looked up once per device.
@@ -243,6 +260,8 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     while (G > 1 && G * Z > kDecodeMaxBlock) --G;
     const int region = L_bytes + hb_bytes;
     while (G > 1 && hdr_bytes + G * region > kMaxSmem) --G;
+    // Z = 16: two groups share a warp, so an even group count keeps every warp whole (as the batch planner)
+    if (Z == 16 && G > 1 && (G & 1)) --G;
     if (hdr_bytes + G * region > kMaxSmem) {
       set_error("decode_uniform_noalloc: code block too large for shared memory");
       return LDPC_EINVAL;
@@ -265,7 +284,7 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int block = G * Z;
+    const int block = (G * Z + 31) & ~31;
     const int smem = hdr_bytes + G * region;
     cudaError_t e = decode_occupancy(mode, kKindGlobal, block, smem, &per_sm);
     if (e != cudaSuccess || per_sm < 1) {
@@ -347,4 +366,58 @@ extern "C" LDPC_API int decode_uniform_noalloc(const ldpc_base_graph* g, int32_t
     set_error("decode_uniform_noalloc: unexpected host exception");
     return LDPC_EINVAL;
   }
+}
+
+/* The device error word of the no-allocation decoder on the current device: each decode_uniform_noalloc
+ * call clears it before it decodes, and a decoder work item whose bounded bulk-copy wait gave up sets
+ * LDPC_DEVERR_TMA_TIMEOUT there (that item's bits and status are then not written).  Waits for
+ * `cuda_stream`, reads the word into *flags_out and clears it; allocates nothing. */
+extern "C" LDPC_API int decode_uniform_noalloc_errors(uint32_t* flags_out, void* cuda_stream) {
+  if (!flags_out) {
+    set_error("decode_uniform_noalloc_errors: null output");
+    return LDPC_EINVAL;
+  }
+  uint8_t* scratch = nullptr;
+  std::string err;
+  int rc = scratch_for_current_device(&scratch, &err);
+  if (rc) {
+    set_error("decode_uniform_noalloc_errors: " + err);
+    return rc;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, scratch + kOffErr, sizeof(v), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kOffErr, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error(std::string("decode_uniform_noalloc_errors: ") + cudaGetErrorString(e));
+    return LDPC_ECUDA;
+  }
+  *flags_out = v;
+  return LDPC_OK;
+}
+
+/* Run the decoder's bounded bulk-copy wait on an mbarrier that nothing completes, with a limit of
+ * `limit` polls (1..65536): the wait gives up and sets LDPC_DEVERR_TMA_TIMEOUT in the word that
+ * decode_uniform_noalloc_errors reads.  For tests of the failure report; enqueued on `cuda_stream`. */
+extern "C" LDPC_API int decode_uniform_noalloc_wait_check(int32_t limit, void* cuda_stream) {
+  if (limit < 1 || limit > 65536) {
+    set_error("decode_uniform_noalloc_wait_check: limit must be 1..65536");
+    return LDPC_EINVAL;
+  }
+  uint8_t* scratch = nullptr;
+  std::string err;
+  int rc = scratch_for_current_device(&scratch, &err);
+  if (rc) {
+    set_error("decode_uniform_noalloc_wait_check: " + err);
+    return rc;
+  }
+  noalloc_wait_check_kernel<<<1, 32, 0, static_cast<cudaStream_t>(cuda_stream)>>>(static_cast<uint32_t>(limit),
+                                                                                   scratch);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("decode_uniform_noalloc_wait_check: ") + cudaGetErrorString(e));
+    return LDPC_ECUDA;
+  }
+  return LDPC_OK;
 }

@@ -55,6 +55,10 @@ struct ServeReq {  // host record per request slot
   int64_t bits_off;    // arena word offset of the TB's decoded bits (contiguous)
   int64_t status_off;  // arena word offset of its status words
   int64_t result_off;  // byte offset into the result pool, -1 for none
+  int32_t pattern;     // URLLC codebook entry puncturing the TB, -1: mask words in the host pool
+  int32_t grid_sc;     // pattern >= 0: first SC of the TB's band on its slot's grid
+  int32_t n_sc;        // the band's width in SCs (TB resource element i: symbol i / n_sc, SC i % n_sc)
+  int32_t pad;
 };
 
 struct ServeDone {  // device -> host completion record
@@ -112,6 +116,8 @@ struct ServeArgs {
   const uint32_t* crc_table_b;  // code-block CRC: byte table, x^(32 m) mod g_B, position tables
   const uint32_t* xpow32_b;
   const uint32_t* cbcrc;
+  const uint32_t* book;  // URLLC codebook: per entry 7 mini-slot bitmaps of book_wpm words
+  int32_t book_wpm, book_prb, book_n;  // words per mini-slot bitmap, pattern period in PRBs, entries
   int32_t hdr_bytes, interleave, max_iter, early_term;
   float q_scale, llr_sat, beta, msg_sat, post_sat;
   uint64_t idle_ns;
@@ -194,8 +200,47 @@ struct PairLaneOut {
   __device__ Ref operator[](int i) const { return Ref{p + 2 * i + lane}; }
 };
 
+// Which resource elements of a code block URLLC punctured: bit r of the
+// block's mask words in the host pool, or, for a request that names a
+// codebook entry, the entry's bitmap at the element's place on the slot's
+// grid.  TB resource element i = re0 + r (re0 = block index * n_re) sits on
+// OFDM symbol i / n_sc (mini-slot symbol / 2) and SC grid_sc + i % n_sc,
+// i.e. PRB (SC / 12); the entry's bitmaps repeat every book_prb PRBs.
+struct PunctSrc {
+  const uint32_t* words;  // mask words (book == nullptr)
+  const uint32_t* book;   // the entry's 7 bitmaps
+  int wpm, prb_period, re0, n_sc, grid_sc;
+  __device__ __forceinline__ bool operator()(int r) const {
+    if (book == nullptr) return ((ld_pool_u32(words + (r >> 5)) >> (r & 31)) & 1u) != 0u;
+    const int i = re0 + r;
+    const int sym = i / n_sc;
+    const int prb = ((grid_sc + (i - sym * n_sc)) / 12) % prb_period;
+    return ((__ldg(book + (sym >> 1) * wpm + (prb >> 5)) >> (prb & 31)) & 1u) != 0u;
+  }
+};
+
+struct ReqPunct {  // a request's puncturing, read once per item
+  int pattern, grid_sc, n_sc, slot;
+};
+
+__device__ __forceinline__ PunctSrc punct_src(const ServeArgs& a, const ReqPunct& rp, const CbDev& cb, int cb_index) {
+  PunctSrc ps{};
+  if (rp.pattern < 0) {
+    ps.words = reinterpret_cast<const uint32_t*>(a.host_pool) + cb.mask_off;
+    return ps;
+  }
+  ps.book = a.book + static_cast<int64_t>(rp.pattern) * 7 * a.book_wpm;
+  ps.wpm = a.book_wpm;
+  ps.prb_period = a.book_prb;
+  ps.re0 = (cb_index - rp.slot * kMaxTbCb) * cb.n_re;  // each request slot owns kMaxTbCb block records
+  ps.n_sc = rp.n_sc;
+  ps.grid_sc = rp.grid_sc;
+  return ps;
+}
+
 template <typename LT, typename Out>
-__device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, Out L, int k, int Z) {
+__device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, const PunctSrc& ps, Out L, int k,
+                                                int Z) {
   using namespace demapcore;
   const int ncb = cb.n_eff * Z - cb.t0;  // circular buffer: E > ncb repeats it
   for (int p = k; p < cb.t0; p += Z) L[p] = LT(0);
@@ -205,14 +250,13 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
     L[cb.t0 + (q >= ncb ? q - ncb : q)] = LT(0);
   }
   const float2* sym = reinterpret_cast<const float2*>(a.host_pool) + cb.re_off;
-  const uint32_t* msk = reinterpret_cast<const uint32_t*>(a.host_pool) + cb.mask_off;
   const Out out = L.shift(cb.t0);
 #pragma unroll 4
   for (int r = k; r < cb.n_re; r += Z) {
     const float2 y = ld_pool_f2(sym + r);
-    const bool punct = (ld_pool_u32(msk + (r >> 5)) >> (r & 31)) & 1u;
+    const bool punct = ps(r);
     auto ls = [&](int i) { return ld_pool_f2(sym + i); };
-    auto lm = [&](int w) { return ld_pool_u32(msk + w); };
+    auto lm = [&](int i) { return ps(i); };
     switch (cb.Qm) {
       case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
       case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
@@ -348,8 +392,8 @@ __device__ __forceinline__ void finish_item(const ServeArgs& a, int req, int n_i
 // false if the table copy did not complete within its bounded wait.
 template <typename LT, typename MT, bool SAT, bool CRC>
 __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape& ssh, const CbDev& cb_first,
-                                            int cb0, int count, uint32_t& phase, uint32_t* s_tab, uint64_t* s_bar,
-                                            uint8_t* regions) {
+                                            const ReqPunct& rp, int cb0, int count, uint32_t& phase,
+                                            uint32_t* s_tab, uint64_t* s_bar, uint8_t* regions) {
   using namespace core;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -381,8 +425,9 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
                         static_cast<int>(a.arena_words)) &&
                check_ok(cb.re_off >= 0 && cb.re_off + cb.n_re <= a.pool_f2, 16, static_cast<int>(cb.re_off),
                         static_cast<int>(a.pool_f2)) &&
-               check_ok(cb.mask_off >= 0 && cb.mask_off + ((cb.n_re + 31) >> 5) <= a.pool_words, 17,
-                        static_cast<int>(cb.mask_off), static_cast<int>(a.pool_words));
+               check_ok(rp.pattern >= 0 || (cb.mask_off >= 0 && cb.mask_off + ((cb.n_re + 31) >> 5) <= a.pool_words),
+                        17, static_cast<int>(cb.mask_off), static_cast<int>(a.pool_words)) &&
+               check_ok(rp.pattern < a.book_n && rp.n_sc > 0, 21, rp.pattern, a.book_n);
     }
   }
   if (active) {
@@ -391,7 +436,9 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
       st_val(L, ssh.dummy_base + k, a.post_sat);
     else
       L[ssh.dummy_base + k] = LT(kBigF);
-    demap_into_smem<LT>(a, cb, PlainOut<LT>{L}, k, Z);  // puncture flushing + max-log, straight into shared memory
+    // puncture flushing + max-log, straight into shared memory
+    const int ci = static_cast<int>(static_cast<uint32_t>(cb0 + g) % a.cb_cap);
+    demap_into_smem<LT>(a, cb, punct_src(a, rp, cb, ci), PlainOut<LT>{L}, k, Z);
   }
   const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
   phase ^= 1u;
@@ -463,9 +510,9 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
 // (block, group); the table (the shape's two-edge-chunk copy), posteriors and
 // both bitmaps in shared memory.
 template <bool CRC>
-__device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& ssh, const CbDev& cb_first, int cb0,
-                                          int count, uint32_t& phase, uint32_t* s_tab, uint64_t* s_bar,
-                                          uint8_t* regions) {
+__device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& ssh, const CbDev& cb_first,
+                                          const ReqPunct& rp, int cb0, int count, uint32_t& phase, uint32_t* s_tab,
+                                          uint64_t* s_bar, uint8_t* regions) {
   using namespace core;
   const int tid = threadIdx.x;
   const ShapeDev& sh = ssh.shp;
@@ -507,8 +554,10 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
                           static_cast<int>(a.arena_words)) &&
                  check_ok(c.re_off >= 0 && c.re_off + c.n_re <= a.pool_f2, 16, static_cast<int>(c.re_off),
                           static_cast<int>(a.pool_f2)) &&
-                 check_ok(c.mask_off >= 0 && c.mask_off + ((c.n_re + 31) >> 5) <= a.pool_words, 17,
-                          static_cast<int>(c.mask_off), static_cast<int>(a.pool_words));
+                 check_ok(rp.pattern >= 0 ||
+                              (c.mask_off >= 0 && c.mask_off + ((c.n_re + 31) >> 5) <= a.pool_words),
+                          17, static_cast<int>(c.mask_off), static_cast<int>(a.pool_words)) &&
+                 check_ok(rp.pattern < a.book_n && rp.n_sc > 0, 21, rp.pattern, a.book_n);
       }
     }
   }
@@ -520,9 +569,10 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
     }
     // both blocks' LLRs into the two halves of the posterior words (B's half 0 without a second block)
     __half* Lh = reinterpret_cast<__half*>(L);
-    demap_into_smem<int8_t>(a, A, PairLaneOut{Lh, 0}, k, Z);
+    const int ciA = static_cast<int>(static_cast<uint32_t>(cb0 + 2 * g) % a.cb_cap);
+    demap_into_smem<int8_t>(a, A, punct_src(a, rp, A, ciA), PairLaneOut{Lh, 0}, k, Z);
     if (hasB) {
-      demap_into_smem<int8_t>(a, B, PairLaneOut{Lh, 1}, k, Z);
+      demap_into_smem<int8_t>(a, B, punct_src(a, rp, B, ciA + 1), PairLaneOut{Lh, 1}, k, Z);
     } else {
       for (int p = k; p < A.n_eff * Z; p += Z) Lh[2 * p + 1] = __float2half(0.0f);
     }
@@ -632,12 +682,14 @@ __global__ void __launch_bounds__(kServeBlock, 1) serve_kernel(const ServeArgs a
       continue;
     }
     const ServeShape ssh = a.shapes[cb_first.shape];
+    const ServeReq* rq = a.reqs + req;
+    const ReqPunct rp{ld_sys(&rq->pattern), ld_sys(&rq->grid_sc), ld_sys(&rq->n_sc), req};
     bool fine;
     if constexpr (PAIRS) {
-      fine = paired ? pair_item<CRC>(a, ssh, cb_first, cb0, count, phase, s_tab, s_bar, regions)
-                    : single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, cb0, count, phase, s_tab, s_bar, regions);
+      fine = paired ? pair_item<CRC>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions)
+                    : single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions);
     } else {
-      fine = single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, cb0, count, phase, s_tab, s_bar, regions);
+      fine = single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions);
     }
     if (!fine) break;
     finish_item(a, req, n_items, tid, lane, &s_last, s_res);
@@ -716,6 +768,8 @@ struct ldpc_server {
   uint32_t* xpow32 = nullptr;
   uint32_t* crc_table = nullptr;
   uint8_t* rscratch = nullptr;
+  uint32_t* book = nullptr;  // URLLC codebook bitmaps
+  int32_t book_n = 0, book_prb = 0;
   bool pairs = false;  // INT8: items may run in the paired form (two code blocks per thread group)
   PairPolicy policy;   // which requests take it
   // requests, items single, items paired, loop launches; the last replay's longest pass of its
@@ -767,6 +821,7 @@ void free_server(ldpc_server* v) {
   cudaFree(v->xpow32);
   cudaFree(v->crc_table);
   cudaFree(v->rscratch);
+  cudaFree(v->book);
   if (v->done_ev) cudaEventDestroy(v->done_ev);
   if (v->stream) cudaStreamDestroy(v->stream);
   delete v->alloc;
@@ -840,6 +895,9 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
         d->pair_threshold < 0 || d->pair_release < 0 || (d->flags & ~(LDPC_SERVE_CB_CRC | LDPC_SERVE_UNPAIRED | LDPC_SERVE_PAIRED)) ||
         ((d->flags & LDPC_SERVE_UNPAIRED) && (d->flags & LDPC_SERVE_PAIRED)))
       return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad descriptor");
+    if (d->codebook_n < 0 || d->codebook_n > 65536 ||
+        (d->codebook_n > 0 && (!d->codebook || d->codebook_prb < 1 || d->codebook_prb > 65536)))
+      return srv_fail(LDPC_EINVAL, "ldpc_serve_start: bad URLLC codebook (codebook_n, codebook_prb, codebook)");
     *out = nullptr;
     auto* v = new (std::nothrow) ldpc_server();
     if (!v) return srv_fail(LDPC_ENOMEM, "host allocation");
@@ -970,8 +1028,13 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       return ee == cudaSuccess ? LDPC_OK : srv_fail(LDPC_ENOMEM, std::string("serve: ") + cudaGetErrorString(ee));
     };
     std::vector<uint32_t> zeros4(4, 0u), zcount(d->max_inflight, 0u);
+    const int book_wpm = d->codebook_n > 0 ? (d->codebook_prb + 31) / 32 : 0;
+    std::vector<uint32_t> book;
+    if (d->codebook_n > 0) book.assign(d->codebook, d->codebook + static_cast<size_t>(d->codebook_n) * 7 * book_wpm);
+    v->book_n = d->codebook_n;
+    v->book_prb = d->codebook_prb;
     if ((rc = up(&v->shapes, v->hshapes)) || (rc = up(&v->tabs, tabs)) || (rc = up(&v->xpow32, xp)) ||
-        (rc = up(&v->dctl, zeros4)) || (rc = up(&v->counts, zcount))) {
+        (rc = up(&v->dctl, zeros4)) || (rc = up(&v->counts, zcount)) || (rc = up(&v->book, book))) {
       free_server(v);
       return rc;
     }
@@ -1019,6 +1082,10 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     a.crc_table = session_crc_table(s);
     a.xpow32 = v->xpow32;
     session_cb_crc_tables(s, &a.crc_table_b, &a.xpow32_b, &a.cbcrc);
+    a.book = v->book;
+    a.book_wpm = book_wpm;
+    a.book_prb = std::max(1, d->codebook_prb);
+    a.book_n = d->codebook_n;
     a.hdr_bytes = hdr;
     a.interleave = interleave;
     a.max_iter = max_iter;
@@ -1076,15 +1143,26 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       return srv_fail(LDPC_EINVAL, at + "code-block CRCs need a service started with LDPC_SERVE_CB_CRC");
     if (static_cast<int64_t>(tb.n_cb) * (K / 32) >= static_cast<int64_t>(kServeXpowWords))
       return srv_fail(LDPC_EINVAL, at + "transport block too large");
-    if (tb.rv < 0 || tb.rv > 3 || tb.reserved != 0) return srv_fail(LDPC_EINVAL, at + "rv must be 0..3");
+    if (tb.rv < 0 || tb.rv > 3) return srv_fail(LDPC_EINVAL, at + "rv must be 0..3");
+    if (tb.reserved != 0) return srv_fail(LDPC_EINVAL, at + "reserved must be 0");
     if (rv_k0(sd.nb - sd.npc, tb.rv, tb.Z) < 0)
       return srv_fail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
-    if (tb.sym_offset < 0 || tb.sym_offset % 8 || tb.mask_offset < 0 || tb.mask_offset % 4 ||
-        static_cast<uint64_t>(tb.sym_offset) + static_cast<uint64_t>(tb.n_cb) * n_re * 8 > v->host_pool_bytes ||
-        static_cast<uint64_t>(tb.mask_offset) + static_cast<uint64_t>(tb.n_cb) * mw * 4 > v->host_pool_bytes)
-      return srv_fail(LDPC_EINVAL, at + "symbols/masks outside the host pool or misaligned");
+    if (tb.sym_offset < 0 || tb.sym_offset % 8 ||
+        static_cast<uint64_t>(tb.sym_offset) + static_cast<uint64_t>(tb.n_cb) * n_re * 8 > v->host_pool_bytes)
+      return srv_fail(LDPC_EINVAL, at + "symbols outside the host pool or misaligned");
+    if (tb.pattern < 0) {
+      if (tb.pattern != -1 || tb.mask_offset < 0 || tb.mask_offset % 4 ||
+          static_cast<uint64_t>(tb.mask_offset) + static_cast<uint64_t>(tb.n_cb) * mw * 4 > v->host_pool_bytes)
+        return srv_fail(LDPC_EINVAL, at + "masks outside the host pool or misaligned");
+    } else {
+      // the TB's resource elements fill its band symbol after symbol within the slot's 14 symbols
+      if (tb.pattern >= v->book_n || tb.n_sc < 1 || tb.grid_sc < 0 ||
+          static_cast<int64_t>(tb.grid_sc) + tb.n_sc > (int64_t{1} << 30) ||
+          static_cast<int64_t>(tb.n_cb) * n_re > 14 * static_cast<int64_t>(tb.n_sc))
+        return srv_fail(LDPC_EINVAL, at + "pattern not in the codebook, or the TB does not fit its band in one slot");
+    }
     if (tb.result_offset >= 0 &&
         (!v->result_pool || tb.result_offset % 4 ||
          static_cast<uint64_t>(tb.result_offset) + static_cast<uint64_t>(tb.n_cb) * K / 8 > v->result_pool_bytes))
@@ -1135,6 +1213,9 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
     rq.bits_off = off;
     rq.status_off = off + static_cast<int64_t>(tb.n_cb) * (K / 32);
     rq.result_off = tb.result_offset;
+    rq.pattern = tb.pattern;
+    rq.grid_sc = tb.grid_sc;
+    rq.n_sc = tb.n_sc;
     // each request slot owns kMaxTbCb code-block records: requests complete
     // out of order, so a ring in submission order could hand the records of
     // a request still waiting for its items to a newer one
@@ -1153,7 +1234,7 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
       c.flags = (rq.seg ? LDPC_CB_CRC24B : 0) | LDPC_CB_RV(tb.rv);
       c.k0 = k0;
       c.re_off = tb.sym_offset / 8 + static_cast<int64_t>(j) * n_re;
-      c.mask_off = tb.mask_offset / 4 + static_cast<int64_t>(j) * mw;
+      c.mask_off = tb.pattern < 0 ? tb.mask_offset / 4 + static_cast<int64_t>(j) * mw : 0;
       c.llr_off = rq.status_off + j;  // status word index in the arena
       c.bits_off = off + static_cast<int64_t>(j) * (K / 32);
       c.inv_sigma2 = tb.inv_sigma2;
@@ -1212,7 +1293,9 @@ int ldpc_serve_poll(ldpc_server* v, ldpc_serve_done* out, int32_t cap, int32_t* 
     return true;
   }, &bad);
   *n_out = n;
-  if (bad) return srv_fail(LDPC_ECUDA, "serve: a completion record names no request in flight");
+  // the good completions before a bad record are handed out first; the bad record stays where it is
+  // and the next call, which starts on it, refuses it
+  if (bad && n == 0) return srv_fail(LDPC_ECUDA, "serve: a completion record names no request in flight");
   if (v->items_inflight > 0) return ensure_running(v);  // a loop that idled out while items were pending
   return LDPC_OK;
 }
@@ -1252,13 +1335,13 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
     }
     int32_t k = 0;
     const int rc = ldpc_serve_poll(v, buf.data(), static_cast<int32_t>(buf.size()), &k);
-    if (rc) return rc;
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < k; ++i) {  // completions taken are kept even when the poll reports an error
       ldpc_serve_done o = buf[i];
       auto f = by_tag.find(o.tag);
       if (f != by_tag.end()) o.t_submit_ns = sched[f->second];
       out[got++] = o;
     }
+    if (rc) return rc;
     if (k > 0 || due > next) last_progress = now_ns();
     if (now_ns() - last_progress > static_cast<int64_t>(timeout_ms) * 1000000ll)
       return srv_fail(LDPC_ETIMEOUT, "replay: no completion within the timeout");

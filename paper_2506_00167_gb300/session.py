@@ -268,13 +268,14 @@ class Server:
     work items would be in flight -- 0: two per loop thread block -- and until
     they fall to ``pair_release`` -- 0: one per loop thread block; single
     otherwise), ``True`` (always paired where the shape allows) or ``False``
-    (always single).
+    (always single).  ``codebook``: ``(bitmaps, prb)``, the URLLC puncturing codebook that requests
+    with ``pattern >= 0`` name (``bitmaps``: uint32 [entries][7][ceil(prb / 32)], copied at start).
     """
 
     def __init__(self, session: Session, host_pool: torch.Tensor, result_pool: torch.Tensor | None = None,
                  arena_bytes: int = 8 << 30, max_inflight: int = 4096, idle_timeout_us: int = 200000,
                  loops_per_sm: int = 1, cb_crc: bool = False, paired: bool | str = "auto",
-                 pair_threshold: int = 0, pair_release: int = 0):
+                 pair_threshold: int = 0, pair_release: int = 0, codebook: np.ndarray | None = None):
         for t, name in ((host_pool, "host_pool"), (result_pool, "result_pool")):
             if t is not None and not (t.device.type == "cpu" and t.is_pinned() and t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous pinned CPU tensor")
@@ -282,12 +283,20 @@ class Server:
         if paired not in ("auto", True, False):
             raise ValueError("paired must be 'auto', True or False")
         form = 0 if paired == "auto" else (abi.SERVE_PAIRED if paired is True else abi.SERVE_UNPAIRED)
+        book_n = book_prb = 0
+        book_ptr = None
+        if codebook is not None:
+            book, book_prb = codebook
+            book = np.ascontiguousarray(book, dtype=np.uint32)
+            if book.ndim != 3 or book.shape[1] != 7 or book.shape[2] != -(-int(book_prb) // 32):
+                raise ValueError("codebook bitmaps must be [entries][7][ceil(prb / 32)] uint32")
+            book_n, book_ptr = book.shape[0], book.ctypes.data
         d = abi.ServeDescC(int(arena_bytes), int(max_inflight), int(idle_timeout_us), host_pool.data_ptr(),
                            host_pool.numel() * host_pool.element_size(),
                            result_pool.data_ptr() if result_pool is not None else None,
                            result_pool.numel() * result_pool.element_size() if result_pool is not None else 0,
                            int(loops_per_sm), (abi.SERVE_CB_CRC if cb_crc else 0) | form, int(pair_threshold),
-                           int(pair_release))
+                           int(pair_release), int(book_n), int(book_prb), book_ptr)
         h = ctypes.c_void_p()
         abi.check(abi.load().ldpc_serve_start(session.handle, ctypes.byref(d), ctypes.byref(h)), "ldpc_serve_start")
         self.handle = h.value

@@ -9,12 +9,13 @@ from workload.serving import pool_bytes, tb_pool, tb_records
 
 def test_record_layout_matches_the_header():
     dt = abi.SERVE_TB_NP
-    # int32 bg, Z, Qm, E, n_cb, n_sc, payload_bits; float inv_sigma2; int32 rv, reserved; int64 offsets; u64 tag
+    # int32 bg, Z, Qm, E, n_cb, n_sc, payload_bits; float inv_sigma2; int32 rv, pattern; int64 offsets;
+    # u64 tag; int32 grid_sc, reserved
     want = [("bg", 0), ("Z", 4), ("Qm", 8), ("E", 12), ("n_cb", 16), ("n_sc", 20), ("payload_bits", 24),
-            ("inv_sigma2", 28), ("rv", 32), ("reserved", 36), ("sym_offset", 40), ("mask_offset", 48),
-            ("result_offset", 56), ("tag", 64)]
+            ("inv_sigma2", 28), ("rv", 32), ("pattern", 36), ("sym_offset", 40), ("mask_offset", 48),
+            ("result_offset", 56), ("tag", 64), ("grid_sc", 72), ("reserved", 76)]
     assert [(n, dt.fields[n][1]) for n, _ in want] == want
-    assert dt.itemsize == 72
+    assert dt.itemsize == 80
 
 
 def _check(w):
@@ -32,7 +33,7 @@ def _check(w):
         assert np.float32(r["inv_sigma2"]) == np.float32(c["inv_sigma2"])
         assert (int(r["n_cb"]), int(r["n_sc"]), int(r["payload_bits"])) == (n, int(tb["n_sc"]),
                                                                             int(tb["payload_bits"]))
-        assert int(r["rv"]) == cb_rv(c) and int(r["reserved"]) == 0
+        assert int(r["rv"]) == cb_rv(c) and int(r["pattern"]) == -1 and int(r["reserved"]) == 0
         assert (int(r["tag"]), int(r["result_offset"])) == (100 + t, 64 * t)
         # the blocks' symbols and mask words lie back to back where the record says
         n_re = int(c["E"]) // int(c["Qm"])
@@ -49,7 +50,7 @@ def _check(w):
 
 
 def test_pool_requests_carry_their_blocks():
-    _check(tb_pool(12, seed=21, max_cb=6))
+    _check(tb_pool(12, seed=21, max_cb=6, own_band_masks=True))
 
 
 def test_redundancy_versions_reach_the_records():

@@ -114,6 +114,35 @@ class BaseGraph:
     def n_eff(self, Z: int, E: int, rv: int = 0) -> int:
         return self.kb + self.m_eff(Z, E, rv)
 
+    def peels_to_information(self, Z: int, E: int, rv: int = 0) -> bool:
+        """Whether the rate-matched code can recover every information bit at all: erasure peeling on the
+        lifted decoded rows (the noiseless limit of message passing), with the never-sent positions --
+        the punctured leading columns and the buffer positions this transmission does not reach --
+        erased.  A check with exactly one erased variable recovers it; peeling repeats until nothing
+        changes.  False means some information bits stay erased at any SNR (for example, when every
+        decoded row holds both punctured columns)."""
+        m = self.m_eff(Z, E, rv)
+        n = self.kb + m
+        t0, ncb, k0 = self.t0(Z), self.ncb(Z), self.k0(Z, rv)
+        known = np.zeros(n * Z, dtype=bool)
+        e = np.arange(min(E, ncb))
+        pos = t0 + (k0 + e) % ncb
+        known[pos[pos < n * Z]] = True
+        lanes = np.arange(Z)
+        rows = [(c.astype(np.int64) * Z, v.astype(np.int64) % Z)
+                for c, v in (self.row_edges(r) for r in range(m))]
+        changed = True
+        while changed and not known[:self.kb * Z].all():
+            changed = False
+            for base, shift in rows:
+                idx = base[:, None] + (lanes[None, :] + shift[:, None]) % Z   # (edges, lanes)
+                unk = ~known[idx]
+                one = unk.sum(axis=0) == 1
+                if one.any():
+                    known[idx[:, one][unk[:, one]]] = True
+                    changed = True
+        return bool(known[:self.kb * Z].all())
+
 
 SHAPES = {
     # name: (mb, nb, kb, mc, n_punct_cols, p_core, force01, deg_ext)

@@ -342,18 +342,32 @@ def operating_point_db(R: float, Qm: int) -> float:
     return float(10.0 * np.log10(2.0 ** (R * Qm) - 1.0) + 3.0)
 
 
+_PEELS: dict = {}
+
+
+def _peels(bg, Z: int, E: int) -> bool:
+    key = (bg.sha256(), Z, E)
+    if key not in _PEELS:
+        _PEELS[key] = bg.peels_to_information(Z, E)
+    return _PEELS[key]
+
+
 def draw_tb_shape(rng, bgs, zs=MIX_Z):
     """One TB's (bg, Z, R, Qm, E) for the mixed workload (Z from ``zs``).  Rates below kb/(nb-2)
     (BG1-shaped: 1/3) send more bits than the circular buffer holds, so their rate matching wraps it
-    (repetition)."""
+    (repetition).  R is redrawn while the rate-matched code cannot recover its information bits even
+    without noise (``BaseGraph.peels_to_information``: at the highest rates every decoded row of the
+    seeded graphs holds both punctured columns -- BG1-shaped R >= 0.88, BG2-shaped R >= 0.83)."""
     b = int(rng.integers(0, 2))
     bg = bgs[b]
     Z = int(zs[int(rng.integers(0, len(zs)))])
     Qm = int(MIX_QM[int(rng.integers(0, len(MIX_QM)))])
-    R = float(rng.uniform(0.3, 0.9))
     K = bg.kb * Z
-    E = Qm * int(round(K / (R * Qm)))
-    return b, Z, R, Qm, E
+    while True:
+        R = float(rng.uniform(0.3, 0.9))
+        E = Qm * int(round(K / (R * Qm)))
+        if _peels(bg, Z, E):
+            return b, Z, R, Qm, E
 
 
 def mixed(n_slots: int = 512, ues_per_slot: int = 8, max_cb: int = 8, seed: int = 3,
