@@ -614,74 +614,14 @@ def run_policy(args):
     print(json.dumps({"policy": out}), flush=True)
 
 
-def masks_to_host(mask: "torch.Tensor", n_sc: int) -> list:
-    """int32 [T, 14, words] SC bitmaps -> list of (14, n_sc) bool arrays."""
-    a = mask.cpu().numpy().astype("<u4")
-    bits = np.unpackbits(a.view(np.uint8), bitorder="little").reshape(a.shape[0], a.shape[1], -1)
-    return [bits[t, :, :n_sc].astype(bool) for t in range(a.shape[0])]
-
-
-def run_casestudy(args):
-    """The paper's reward under the two benchmark policies (Sec. VII-A) on link-level TTIs of its
-    case-study setting: per TTI an eMBB schedule and URLLC arrivals (``workload.policy.schedules``), the
-    policy's SCs per mini-slot and SC masks computed on the GPU, each user's band carrying one TB
-    (BG2-shaped, rate 1/2, 16-QAM), then puncture_demap + decode_batch + tb_crc_goodput on the GPU.
-    Both policies see the same schedules, payloads and noise."""
-    import torch
-    from paper_2506_00167_gb300 import Session
-    from paper_2506_00167_gb300 import policy as GP
-    from workload.policy import N_SC, case_study, schedules
-
-    torch.cuda.set_device(0)
-    T = args.policy_tti
-    alloc_np, demand_np = schedules(T)
-    alloc = torch.from_numpy(alloc_np.astype(np.int32)).cuda()
-    demand = torch.from_numpy(demand_np.astype(np.int32)).cuda()
-    res = {"workload": f"{T} TTIs of the case-study setting (N = 780 SCs, 10 eMBB users, 300-SC URLLC packets, "
-                       "Bernoulli(0.08) arrivals of 12 URLLC users per mini-slot); one BG2-shaped rate-1/2 16-QAM "
-                       "TB per user band, Es/N0 in [op, op + 3 dB]", "mode": args.mode or "f32", "policies": {}}
-    for pol in ["rp", "sef"]:
-        pm, st = GP.puncture_alloc(alloc, demand, pol)
-        masks = masks_to_host(GP.sc_mask(alloc, pm, (N_SC + 31) // 32), N_SC)
-        t0 = time.perf_counter()
-        w = case_study(alloc_np, masks)
-        gen_s = time.perf_counter() - t0
-        mode = args.mode or "f32"
-        s = Session(w.bgs, w.z_set, mode=mode, max_iter=10, early_term=True, sat=SAT[mode])
-        b = s.batch(w.cbs, w.tbs, w.slot_N)
-        sym = torch.from_numpy(np.ascontiguousarray(w.sym, dtype=np.complex64)).cuda()
-        mask = torch.from_numpy(np.ascontiguousarray(w.mask).view(np.int32)).cuda()
-        out = b.alloc_outputs(0)
-        for _ in range(args.warmup):
-            s.run(b, sym, mask, out)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            s.run(b, sym, mask, out)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        d = out["d"].cpu().numpy()
-        reward = out["reward"].cpu().numpy()
-        gbits = out["goodput_bits"].cpu().numpy().astype(np.float64)
-        res["policies"][pol] = {
-            "status_bad": int((st != 0).sum().item()),
-            "punctured_sc_fraction": float(pm.sum().item() / (T * 7 * N_SC)),
-            "tb_success": float(d.mean()), "mean_reward": float(reward.mean()),
-            "goodput_mbps": float(gbits.mean() / 125e-6 / 1e6),
-            "code_blocks": w.n_cb, "ms_per_step": ms, "tx_chain_s": gen_s,
-            "decoded_gbps": float(w.cbs.shape[0] and (w.tbs["payload_bits"].sum() + 24 * w.n_tb) / (ms / 1e3) / 1e9)}
-    print(json.dumps({"case_study": res}), flush=True)
-
-
+# ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="large", choices=["large", "mixed", "tiny", "casestudy"])
+    ap.add_argument("--config", default="large", choices=["large", "mixed", "tiny"])
     ap.add_argument("--mode", default=None, choices=["f32", "i8", "i16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-int8", action="store_true")
@@ -727,8 +667,6 @@ def main():
         return run_serving(args)
     if args.policy:
         return run_policy(args)
-    if args.config == "casestudy":
-        return run_casestudy(args)
     if args.sweep == "precision":
         return run_precision_sweep(args)
     if args.warmup < 3 and args.impl == "ours":

@@ -28,7 +28,12 @@ Readings where the paper is silent (each fixed here and in the CUDA path):
   n_e; equal priorities go to the lower index.
 * Precision: the paper does not fix one; quotas, priorities and the KL
   projection are float32 (the policy network's output type), every operation
-  rounded once and taken in a fixed order.
+  rounded once and taken in a fixed order.  ``kl_project64``, ``hh_round64``
+  and ``enforce64`` state the same enforcer plainly in float64 (the
+  projection from the optimality conditions of eq. 7, plain sums); the float32
+  form is tested against them (equal to float32 rounding, integer vectors
+  within one unit per user, exact sums), and against closed forms, the KKT
+  form and a convex solver.
 * KL projection: users with m_e > 0 take m^_e = min(n_e, c m_e) with one
   scale c >= 0 (the KKT conditions of eq. 7); users with m_e = 0 take 0 unless
   the others' allocations cannot hold jL, in which case the remainder is
@@ -145,6 +150,67 @@ def enforce(m, n, j: int, L: int) -> np.ndarray:
     """Feasible integer puncturing vector for branch j (demand j*L SCs)."""
     x = kl_project(m, n, j * L)
     return hh_round(x, j * L, np.asarray(n, dtype=np.int64))
+
+
+# ---------------------------------------------------------------------------- float64 reference of the enforcer
+def kl_project64(m, n, total) -> np.ndarray:
+    """The KL projection of eq. 6 / eq. 7 in float64, written from its optimality conditions.
+
+    Minimise sum_e m_e log(m_e / x_e) over 0 <= x_e <= n_e, sum_e x_e = total.
+    Stationarity of the Lagrangian gives m_e / x_e = lambda for every user whose
+    x_e is strictly inside its box, so x_e = min(n_e, c m_e) with one c = 1 /
+    lambda for the users with m_e > 0; c is the value at which these sum to
+    the total (the sum is continuous and increasing in c, so it is found
+    exactly by walking the breakpoints c = n_e / m_e in increasing order).
+    Users with m_e <= 0 contribute nothing to the objective and get 0 unless
+    the others' boxes cannot hold the total; then the rest is split over them
+    in proportion to n_e.
+    """
+    m = np.asarray(m, dtype=np.float64)
+    n = np.asarray(n, dtype=np.float64)
+    total = float(total)
+    if total > n.sum():
+        raise ValueError("total exceeds the allocations")
+    pos = m > 0
+    x = np.zeros(m.size)
+    if n[pos].sum() <= total:
+        x[pos] = n[pos]
+        rest = total - n[pos].sum()
+        if rest > 0 and n[~pos].sum() > 0:
+            x[~pos] = rest * n[~pos] / n[~pos].sum()
+        return x
+    idx = np.flatnonzero(pos)
+    brk = n[idx] / m[idx]                     # c beyond which user e is capped
+    order = idx[np.argsort(brk, kind="stable")]
+    for k in range(order.size):
+        capped, free = order[:k], order[k:]
+        c = (total - n[capped].sum()) / m[free].sum()
+        if c * m[order[k]] <= n[order[k]]:  # the k-th user stays inside its box: consistent
+            break
+    x[idx] = np.minimum(n[idx], c * m[idx])
+    return x
+
+
+def hh_round64(quota, total: int, cap=None) -> np.ndarray:
+    """Huntington-Hill rounding in float64: floors first, then one unit at a time to the largest
+    q / sqrt(a (a + 1)) among values below their ceiling and cap (a = 0: infinite; lower index on ties)."""
+    q = np.asarray(quota, dtype=np.float64)
+    cap = np.full(q.size, np.iinfo(np.int64).max, dtype=np.int64) if cap is None else np.asarray(cap, np.int64)
+    a = np.minimum(np.floor(q).astype(np.int64), cap)
+    hi = np.minimum(np.ceil(q).astype(np.int64), cap)
+    left = int(total) - int(a.sum())
+    if left < 0 or left > int((hi - a).sum()):
+        raise ValueError("no rounding of these quotas sums to the total")
+    for _ in range(left):
+        pri = np.where(a == 0, np.inf, q / np.sqrt(np.maximum(a * (a + 1.0), 1.0)))
+        pri[a >= hi] = -np.inf
+        a[int(np.argmax(pri))] += 1            # argmax: first (lowest) index among equal priorities
+    return a
+
+
+def enforce64(m, n, j: int, L: int) -> np.ndarray:
+    """The feasibility enforcer (Sec. V-B) in float64: KL projection, then Huntington-Hill rounding."""
+    return hh_round64(kl_project64(m, n, j * L), j * L, np.asarray(n, dtype=np.int64))
 
 
 def sc_mask(n, m_per_minislot) -> np.ndarray:

@@ -18,8 +18,9 @@ from gpu_helpers import device_inputs, session_for
 pytestmark = pytest.mark.gpu
 
 # INT8 decode forms of the service: (paired, pair_threshold, which item counters must be nonzero).
-# "auto" with a threshold of 4 items: a burst starts single and pairs once 4 items are in flight.
-FORMS = [("auto", 4, ("items_single", "items_paired")), (True, 0, ("items_paired",)),
+# "auto" with a threshold of 16 items: a burst starts single (a TB of at most 16 code blocks never has
+# more single-form items) and pairs once more than 16 items are in flight.
+FORMS = [("auto", 16, ("items_single", "items_paired")), (True, 0, ("items_paired",)),
          (False, 0, ("items_single",))]
 FORM_IDS = ["auto", "paired", "single"]
 BOOK = codebook_bitmaps()

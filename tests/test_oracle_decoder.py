@@ -161,3 +161,67 @@ def test_float32_run_close_to_float64():
     w64, s64 = decoder.decode_workload(w, llr, 10, True, decoder.F64)
     w32, s32 = decoder.decode_workload(w, llr.astype(np.float32), 10, True, decoder.F32)
     assert np.array_equal(w64, w32)
+
+
+def _star3():
+    """Three degree-2 checks sharing variable 0: rows {0,1}, {0,2}, {0,3}; Z = 1 (every shift 0)."""
+    from workload.basegraph import custom_base_graph
+    return custom_base_graph("star3", 3, 4, 1, 3, 0, {(0, 0): 0, (0, 1): 0, (1, 0): 0, (1, 2): 0,
+                                                       (2, 0): 0, (2, 3): 0})
+
+
+def _final_L(arith, llr, iters):
+    _, _, _, L = decoder.layered_oms(np.array([llr], dtype=np.int64), _star3(), 1, 3, iters, False, arith,
+                                     return_L=True)
+    return L[0].tolist()
+
+
+def test_int8_saturation_worked_by_hand():
+    """INT8 rule (precision configuration: 6-bit saturated magnitude, offset 1 LSB): Q = sat127(L - R),
+    |Q| clamped to 63 for the minima, R' = sgn * max(m - 1, 0), L = sat127(Q + R').  Channel [10, -30, 63, 63].
+
+    Iteration 1 (R = 0):
+      row {0,1}: Q = [10, -30]; |Q| = [10, 30]; m1 = 10 (edge 0), m2 = 30; one negative -> parity 1.
+                 R' = [-(30-1), +(10-1)] = [-29, 9];  L0 = 10 - 29 = -19, L1 = -30 + 9 = -21.
+      row {0,2}: Q = [-19, 63]; m1 = 19 (edge 0), m2 = 63; parity 1.  R' = [+62, -18]; L0 = 43, L2 = 45.
+      row {0,3}: Q = [43, 63]; m1 = 43, m2 = 63; parity 0.  R' = [62, 42]; L0 = 105, L3 = 105.
+      -> L = [105, -21, 45, 105].
+    Iteration 2:
+      row {0,1} (R = [-29, 9]): Q = [sat127(105 + 29), -21 - 9] = [127, -30]   <- Q saturates
+                 |Q| clamped: [63, 30] -> m1 = 30 (edge 1), m2 = 63; parity 1.
+                 R' = [-(30-1), +(63-1)] = [-29, 62]   <- the clamped |Q| feeds edge 1's message
+                 L0 = 127 - 29 = 98, L1 = -30 + 62 = 32.
+      row {0,2} (R = [62, -18]): Q = [98 - 62, 45 + 18] = [36, 63]; m1 = 36, m2 = 63; parity 0.
+                 R' = [62, 35]; L0 = 98, L2 = 98.
+      row {0,3} (R = [62, 42]): Q = [36, 63]; R' = [62, 35]; L0 = 98, L3 = 98.
+      -> L = [98, 32, 98, 98].
+    Plausible slips and what they would give: no Q saturation -> L0 = 105 after iteration 2; Q saturated
+    at 63 -> L0 = 34; |Q| not clamped -> R'_1 = 126, L1 = 96; the message R' clamped to 63 instead of |Q|
+    -> L1 = 33; L saturated at 63 -> L0 = 63 after iteration 1.  (Clamping |Q| before or after taking
+    the minima gives the same messages: the clamp is monotone, so it commutes with min and second min.)
+    """
+    assert _final_L(decoder.INT8, [10, -30, 63, 63], 1) == [105, -21, 45, 105]
+    assert _final_L(decoder.INT8, [10, -30, 63, 63], 2) == [98, 32, 98, 98]
+
+
+def test_int16_saturation_worked_by_hand():
+    """INT16 rule: Q and L saturate at +-32767, |Q| clamped to 1023, offset 1.  Channel [32000, -500, 2000,
+    2000] (large inputs reach the posterior limit within two iterations).
+
+    Iteration 1:
+      row {0,1}: Q = [32000, -500]; |Q| = [1023, 500] -> m1 = 500 (edge 1), m2 = 1023; parity 1.
+                 R' = [-(500-1), +(1023-1)] = [-499, 1022]; L0 = 31501, L1 = 522.
+      row {0,2}: Q = [31501, 2000]; |Q| = [1023, 1023] -> m1 = m2 = 1023; parity 0.  R' = [1022, 1022];
+                 L0 = 32523, L2 = 3022.
+      row {0,3}: Q = [32523, 2000]; R' = [1022, 1022]; L0 = sat(33545) = 32767   <- L saturates
+                 L3 = 3022.   -> L = [32767, 522, 3022, 3022].
+    Iteration 2:
+      row {0,1} (R = [-499, 1022]): Q = [sat(32767 + 499), 522 - 1022] = [32767, -500]   <- Q saturates
+                 R' = [-499, 1022]; L0 = 32268, L1 = 522.
+      row {0,2} (R = [1022, 1022]): Q = [31246, 2000]; R' = [1022, 1022]; L0 = 32268, L2 = 3022.
+      row {0,3}: the same; L3 = 3022.   -> L = [32268, 522, 3022, 3022].
+    Slips: no Q saturation -> L0 = 32767 after iteration 2; |Q| not clamped -> R'_1 = 31999 in iteration 1;
+    the INT8 limits -> every value differs.
+    """
+    assert _final_L(decoder.INT16, [32000, -500, 2000, 2000], 1) == [32767, 522, 3022, 3022]
+    assert _final_L(decoder.INT16, [32000, -500, 2000, 2000], 2) == [32268, 522, 3022, 3022]

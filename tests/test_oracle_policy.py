@@ -134,6 +134,79 @@ def test_kl_projection_kkt_form_and_zero_users():
     assert np.allclose(x, [60.0, 20.0, 40.0, 70.0], rtol=1e-6, atol=0)
 
 
+def test_float64_kl_projection_closed_forms_and_convex_solver():
+    """The float64 projection (eq. 6 / eq. 7 from its optimality conditions) against closed forms and SLSQP."""
+    m = np.array([3.0, 1.0, 0.0, 4.0])
+    assert np.allclose(P.kl_project64(m, np.full(4, 100.0), 40.0), 40.0 * m / m.sum(), rtol=1e-14, atol=0)
+    m = np.array([50.0, 0.0, 200.0, 10.0])
+    n = np.array([60.0, 30.0, 40.0, 70.0])
+    assert np.allclose(P.kl_project64(m, n, 90.0), [50 * 50 / 60, 0.0, 40.0, 10 * 50 / 60], rtol=1e-14, atol=0)
+    assert np.allclose(P.kl_project64(m, n, 190.0), [60.0, 20.0, 40.0, 70.0], rtol=1e-14, atol=0)
+    opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(17)
+    for _ in range(40):
+        E = int(rng.integers(2, 8))
+        n = rng.integers(10, 120, E).astype(float)
+        m = rng.uniform(0, 150, E)
+        T = float(rng.integers(1, int(n.sum())))
+        x = P.kl_project64(m, n, T)
+        assert math.isclose(x.sum(), T, rel_tol=1e-12) and np.all(x >= 0) and np.all(x <= n)
+
+        def f(v):
+            v = np.maximum(np.asarray(v, dtype=np.float64), 1e-12)
+            return float(np.sum(m * np.log(m / v)))
+        res = opt.minimize(f, np.full(E, T / E).clip(0, n), method="SLSQP", bounds=list(zip([1e-9] * E, n)),
+                           constraints=[{"type": "eq", "fun": lambda v: v.sum() - T}],
+                           options={"ftol": 1e-12, "maxiter": 500})
+        assert f(x) <= res.fun + 1e-6 * max(1.0, abs(res.fun))
+
+
+def test_float64_hh_round_is_the_minimum_of_its_objective_by_brute_force():
+    rng = np.random.default_rng(19)
+    for _ in range(60):
+        E = int(rng.integers(2, 5))
+        q = rng.uniform(0.2, 9.0, E)
+        total = int(round(q.sum()))
+        a = P.hh_round64(q, total)
+        best = None
+        for cand in itertools.product(*[range(int(math.floor(v)), int(math.ceil(v)) + 1) for v in q]):
+            cand = np.array(cand)
+            if cand.sum() != total or np.any(cand == 0):
+                continue
+            obj = float(np.sum(q * q / cand))
+            best = obj if best is None else min(best, obj)
+        if best is not None and np.all(a > 0):
+            assert float(np.sum(q * q / a)) <= best + 1e-9
+
+
+def test_float32_enforcer_follows_the_float64_reference():
+    """The float32 restatement (the arithmetic the CUDA kernel reproduces bit for bit) against the float64
+    reference: projections equal to float32 rounding, integer vectors within one unit per user, both
+    summing exactly to the demand."""
+    rng = np.random.default_rng(23)
+    exact = 0
+    trials = 0
+    for _ in range(400):
+        E = int(rng.integers(2, 16))
+        n = rng.integers(12, 150, E)
+        L = int(rng.integers(20, 120))
+        j = int(rng.integers(1, max(2, n.sum() // L) + 1))
+        if j * L > n.sum():
+            continue
+        m = rng.uniform(-0.2, 1.5, E) * n
+        m[rng.random(E) < 0.15] = 0.0
+        x32 = P.kl_project(m.astype(np.float32), n, j * L).astype(np.float64)
+        x64 = P.kl_project64(m.astype(np.float32).astype(np.float64), n, j * L)
+        assert np.allclose(x32, x64, rtol=2e-5, atol=2e-5 * j * L)
+        a32 = P.enforce(m.astype(np.float32), n, j, L)
+        a64 = P.enforce64(m.astype(np.float32).astype(np.float64), n, j, L)
+        assert a32.sum() == j * L == a64.sum()
+        assert np.all(np.abs(a32 - a64) <= 1) and np.all(a64 <= n) and np.all(a64 >= 0)
+        exact += int(np.array_equal(a32, a64))
+        trials += 1
+    assert exact >= 0.95 * trials, (exact, trials)
+
+
 def test_enforcer_returns_a_feasible_integer_vector_and_keeps_feasible_ones():
     rng = np.random.default_rng(8)
     for _ in range(200):
