@@ -255,57 +255,77 @@ def _oracle_errors(args):
 def run_precision_sweep(args):
     """BLER per Es/N0 point: GPU float32 / INT8 / INT16 against the float64 oracle, 95 % Wilson intervals.
 
-    A pool of noiseless code blocks (the large workload's shape, URLLC masks
-    included) is encoded once; every batch draws fresh seeded AWGN for the
-    whole pool.  The GPU decodes args.sweep_n code blocks per point in all
-    three modes; the oracle decodes the first args.sweep_oracle_n of them.
+    A pool of noiseless code blocks (URLLC masks included) is encoded once;
+    every batch draws fresh seeded AWGN for the whole pool.  The GPU decodes
+    args.sweep_n code blocks per point in all three modes; the oracle decodes
+    the first args.sweep_oracle_n of them.  ``--config large``: the large
+    workload's shape, points in absolute Es/N0.  ``--config mixed``: the mixed
+    workload's shapes (BG, Z, R, Qm per TB), each code block at its shape's
+    operating point + the point's offset.
     """
     import torch
     from oracle.stats import wilson
     from paper_2506_00167_gb300 import Session
-    from workload import large_fp32
-    from workload.configs import es_n0_sigma2, subset
+    from workload import large_fp32, mixed
+    from workload.configs import es_n0_sigma2, operating_point_db, subset
     from workload.rng import np_stream
 
     cores = os.cpu_count() or 1
     pool = mp.get_context("spawn").Pool(cores)
     torch.cuda.set_device(0)
-    n_pool = args.sweep_pool
-    w0 = large_fp32(n_cw=n_pool, noiseless=True, seed=40)
+    is_mixed = args.config == "mixed"
+    if is_mixed:
+        w0 = mixed(n_slots=args.sweep_pool, noiseless=True, seed=41)
+        K = np.array([w0.bgs[int(c["bg"])].kb * int(c["Z"]) for c in w0.cbs], np.float64)
+        op = np.array([operating_point_db(k / int(c["E"]), int(c["Qm"])) for k, c in zip(K, w0.cbs)])
+        points = [float(v) for v in np.arange(args.sweep_lo, args.sweep_lo + 0.5 * 10, 0.5)]
+    else:
+        w0 = large_fp32(n_cw=args.sweep_pool, noiseless=True, seed=40)
+        op = np.zeros(w0.n_cb)
+        points = [float(v) for v in np.arange(args.sweep_lo, args.sweep_lo + 0.5 * 10, 0.5)]
+    n_pool = w0.n_cb
     mi, et = w0.meta["max_iter"], bool(w0.meta["early_term"])
     x = w0.sym.astype(np.complex128)
-    info = torch.from_numpy(w0.info_words.view(np.int32)).cuda().view(n_pool, -1)
+    n_re = (w0.cbs["E"] // w0.cbs["Qm"]).astype(np.int64)
+    info = torch.from_numpy(w0.info_words.view(np.int32)).cuda()
+    words_per_cb = np.array([w0.bgs[int(c["bg"])].kb * int(c["Z"]) // 32 for c in w0.cbs], np.int64)
+    word_cb = torch.from_numpy(np.repeat(np.arange(n_pool), words_per_cb)).cuda()
+    assert np.array_equal(w0.cbs["bits_word_offset"], np.concatenate([[0], np.cumsum(words_per_cb)[:-1]]))
     mask = torch.from_numpy(w0.mask.view(np.int32)).cuda()
     sess = {m: Session(w0.bgs, w0.z_set, mode=m, max_iter=mi, early_term=et, sat=SAT[m]) for m in ("f32", "i8", "i16")}
-    points = [float(v) for v in np.arange(args.sweep_lo, args.sweep_lo + 0.5 * 10, 0.5)]
     rows = []
     t_start = time.perf_counter()
-    for pi, snr in enumerate(points):
-        s2 = float(es_n0_sigma2(snr))
+    for pi, pt in enumerate(points):
+        s2_cb = es_n0_sigma2(op + pt)
+        s2_re = np.repeat(s2_cb, n_re)
         cbs = w0.cbs.copy()
-        cbs["inv_sigma2"] = np.float32(1.0 / s2)
+        cbs["inv_sigma2"] = (1.0 / s2_cb).astype(np.float32)
         batches = {m: sess[m].batch(cbs) for m in sess}
         outs = {m: batches[m].alloc_outputs() for m in sess}
         err = {m: 0 for m in sess}
         iters = {m: 0 for m in sess}
         n_done = 0
-        rng = np_stream(40, 7, pi)
+        rng = np_stream(40 + is_mixed, 7, pi)
         oracle_jobs = []
         while n_done < args.sweep_n:
             noise = rng.standard_normal((2, x.size))
-            y = (x + np.sqrt(s2 / 2.0) * (noise[0] + 1j * noise[1])).astype(np.complex64)
+            y = (x + np.sqrt(s2_re / 2.0) * (noise[0] + 1j * noise[1])).astype(np.complex64)
             sym = torch.from_numpy(y).cuda()
             for m in sess:
                 s, b, o = sess[m], batches[m], outs[m]
                 s.puncture_demap(b, sym, mask, o["llr"])
                 s.decode_batch(b, o["llr"], o["bits"], o["status"])
-                err[m] += int((o["bits"].view(n_pool, -1) != info).any(dim=1).sum())
+                bad_w = (o["bits"] != info).to(torch.int32)
+                per_cb = torch.zeros(n_pool, dtype=torch.int32, device="cuda").index_add_(0, word_cb, bad_w)
+                err[m] += int((per_cb > 0).sum())
                 iters[m] += int((o["status"] & 0xFFFF).sum())
             if n_done < args.sweep_oracle_n:
-                wn = subset(w0, range(min(n_pool, args.sweep_oracle_n - n_done)))
+                n_take = min(n_pool, args.sweep_oracle_n - n_done)
+                tb_take = int(np.searchsorted(w0.tbs["first_cb"] + w0.tbs["n_cb"], n_take, side="left")) + 1
+                wn = subset(w0, range(min(w0.n_tb, tb_take)))
                 wn.sym = y[:wn.sym.size].copy()
-                wn.cbs["inv_sigma2"] = np.float32(1.0 / s2)
-                per = max(1, wn.n_tb // cores)
+                wn.cbs["inv_sigma2"] = cbs["inv_sigma2"][:wn.n_cb]
+                per = max(1, wn.n_tb // (4 * cores))
                 oracle_jobs.append(pool.map_async(_oracle_errors, [
                     (subset(wn, range(i, min(wn.n_tb, i + per))), mi, et) for i in range(0, wn.n_tb, per)]))
             n_done += n_pool
@@ -314,7 +334,7 @@ def run_precision_sweep(args):
             for e_, n_ in job.get():
                 o_err += e_
                 o_n += n_
-        row = {"es_n0_db": snr, "n_gpu": n_done, "n_oracle": o_n}
+        row = {("es_n0_offset_db" if is_mixed else "es_n0_db"): pt, "n_gpu": n_done, "n_oracle": o_n}
         for m in sess:
             row[m] = {"bler": err[m] / n_done, "ci95": wilson(err[m], n_done), "mean_iters": iters[m] / n_done}
         row["f64_oracle"] = {"bler": o_err / max(o_n, 1), "ci95": wilson(o_err, o_n)}
@@ -323,7 +343,10 @@ def run_precision_sweep(args):
         rows.append(row)
         print(json.dumps({"point": row}), flush=True)
     pool.close()
-    res = {"sweep": "precision", "workload": "BG1-shaped Z=384 K=8448 R=1/2 16-QAM with URLLC masks",
+    desc = ("mixed workload shapes (BG1/BG2-shaped, Z 32..384, R 0.3..0.9, QPSK..256-QAM, URLLC masks), "
+            "each code block at its shape's operating point + offset" if is_mixed else
+            "BG1-shaped Z=384 K=8448 R=1/2 16-QAM with URLLC masks")
+    res = {"sweep": "precision", "config": args.config, "workload": desc, "pool_code_blocks": n_pool,
            "points": rows, "wall_s": time.perf_counter() - t_start, "oracle_cores": cores}
     print(json.dumps(res), flush=True)
 
@@ -660,7 +683,8 @@ def main():
                     help="run a measurement sweep instead of the benchmark line")
     ap.add_argument("--sweep-n", type=int, default=100000, help="code blocks per SNR point (GPU)")
     ap.add_argument("--sweep-oracle-n", type=int, default=2048, help="code blocks per SNR point (oracle)")
-    ap.add_argument("--sweep-pool", type=int, default=4096, help="distinct encoded code blocks")
+    ap.add_argument("--sweep-pool", type=int, default=4096,
+                    help="distinct encoded code blocks (large) or slots of the mixed workload (mixed)")
     ap.add_argument("--sweep-lo", type=float, default=5.5, help="lowest Es/N0 point, dB (10 points, 0.5 dB apart)")
     args = ap.parse_args()
     if args.serve:
