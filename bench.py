@@ -245,11 +245,11 @@ def run_reference(args, world, rank):
 
 # ----------------------------------------------------------------------------- precision sweep
 def _oracle_errors(args):
-    """Worker: block errors of the float64 oracle on one noisy sub-batch."""
+    """Worker: per-block errors of the float64 oracle on one noisy sub-batch."""
     w, mi, et = args
     from oracle import path as opath
     out = opath.run(w, "f64", mi, et)
-    return int(opath.block_errors(w, out["words"]).sum()), w.n_cb
+    return opath.block_errors(w, out["words"])
 
 
 def run_precision_sweep(args):
@@ -304,6 +304,7 @@ def run_precision_sweep(args):
         outs = {m: batches[m].alloc_outputs() for m in sess}
         err = {m: 0 for m in sess}
         iters = {m: 0 for m in sess}
+        same = {m: [] for m in sess}  # per-block errors on the blocks the oracle also decodes (same noise)
         n_done = 0
         rng = np_stream(40 + is_mixed, 7, pi)
         oracle_jobs = []
@@ -319,24 +320,28 @@ def run_precision_sweep(args):
                 per_cb = torch.zeros(n_pool, dtype=torch.int32, device="cuda").index_add_(0, word_cb, bad_w)
                 err[m] += int((per_cb > 0).sum())
                 iters[m] += int((o["status"] & 0xFFFF).sum())
+                if n_done < args.sweep_oracle_n:
+                    same[m].append(per_cb > 0)
             if n_done < args.sweep_oracle_n:
                 n_take = min(n_pool, args.sweep_oracle_n - n_done)
                 tb_take = int(np.searchsorted(w0.tbs["first_cb"] + w0.tbs["n_cb"], n_take, side="left")) + 1
                 wn = subset(w0, range(min(w0.n_tb, tb_take)))
+                for m in sess:
+                    same[m][-1] = same[m][-1][:wn.n_cb].cpu().numpy()
                 wn.sym = y[:wn.sym.size].copy()
                 wn.cbs["inv_sigma2"] = cbs["inv_sigma2"][:wn.n_cb]
                 per = max(1, wn.n_tb // (4 * cores))
                 oracle_jobs.append(pool.map_async(_oracle_errors, [
                     (subset(wn, range(i, min(wn.n_tb, i + per))), mi, et) for i in range(0, wn.n_tb, per)]))
             n_done += n_pool
-        o_err = o_n = 0
-        for job in oracle_jobs:
-            for e_, n_ in job.get():
-                o_err += e_
-                o_n += n_
+        o_blk = np.concatenate([np.concatenate(job.get()) for job in oracle_jobs]).astype(bool)
+        o_err, o_n = int(o_blk.sum()), int(o_blk.size)
         row = {("es_n0_offset_db" if is_mixed else "es_n0_db"): pt, "n_gpu": n_done, "n_oracle": o_n}
         for m in sess:
-            row[m] = {"bler": err[m] / n_done, "ci95": wilson(err[m], n_done), "mean_iters": iters[m] / n_done}
+            g_blk = np.concatenate(same[m]).astype(bool)
+            assert g_blk.size == o_n
+            row[m] = {"bler": err[m] / n_done, "ci95": wilson(err[m], n_done), "mean_iters": iters[m] / n_done,
+                      "same_noise": {"bler": float(g_blk.mean()), "outcome_equal_frac": float(np.mean(g_blk == o_blk))}}
         row["f64_oracle"] = {"bler": o_err / max(o_n, 1), "ci95": wilson(o_err, o_n)}
         lo, hi = row["f64_oracle"]["ci95"]
         row["f32_inside_oracle_ci"] = bool(lo <= row["f32"]["bler"] <= hi)

@@ -17,13 +17,16 @@ from gpu_helpers import device_inputs, session_for
 
 pytestmark = pytest.mark.gpu
 
-# INT8 decode forms of the service: (paired, pair_threshold, which item counters must be nonzero).
-# "auto" with a threshold of 16 items: a burst starts single (a TB of at most 16 code blocks never has
-# more single-form items) and pairs once more than 16 items are in flight.
-FORMS = [("auto", 16, ("items_single", "items_paired")), (True, 0, ("items_paired",)),
-         (False, 0, ("items_single",))]
+# INT8 decode forms of the service: (paired, which item counters must be nonzero).  "auto" runs with a
+# pair threshold equal to the first request's code blocks (see _thr): that request stays single (it never
+# has more single-form items than blocks) and the burst behind it pairs once more items are in flight.
+FORMS = [("auto", ("items_single", "items_paired")), (True, ("items_paired",)), (False, ("items_single",))]
 FORM_IDS = ["auto", "paired", "single"]
 BOOK = codebook_bitmaps()
+
+
+def _thr(form, recs):
+    return int(recs["n_cb"][0]) if form[0] == "auto" else 0
 
 
 def _check_forms(srv, must):
@@ -210,7 +213,7 @@ def _oracle_parity(st, mode, srv_kw):
 
 @pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
 def test_int8_service_matches_the_oracle(stream, form):
-    got, ref = _oracle_parity(stream, "i8", dict(paired=form[0], pair_threshold=form[1]))
+    got, ref = _oracle_parity(stream, "i8", dict(paired=form[0], pair_threshold=_thr(form, stream.records())))
     assert 0 < int(ref["d"].sum()) < stream.n
 
 
@@ -292,12 +295,12 @@ def test_repetition_blocks_through_the_service_match_the_batch_path(form):
     offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
     res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
     s = session_for(w, "i8")
-    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, paired=form[0], pair_threshold=form[1])
+    recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
+    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, paired=form[0], pair_threshold=_thr(form, recs))
     try:
-        recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
-        _check_forms(srv, form[2])
+        _check_forms(srv, form[1])
         d_ref, bits_ref, _, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
@@ -313,11 +316,12 @@ def test_every_form_matches_the_batch_path(stream, form):
     iteration counts equal the batch path's on every request."""
     st = stream
     n = st.n
-    srv, res = st.server(arena_bytes=1 << 26, max_inflight=256, paired=form[0], pair_threshold=form[1])
+    srv, res = st.server(arena_bytes=1 << 26, max_inflight=256, paired=form[0],
+                         pair_threshold=_thr(form, st.records()))
     try:
         done = srv.replay(st.records(), np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
-        _check_forms(srv, form[2])
+        _check_forms(srv, form[1])
         stats = srv.stats()
         assert stats["requests"] == n and stats["launches"] >= 1
         d_ref, bits_ref, it_ref, _ = _batch_reference(st.sw, range(n))
@@ -363,11 +367,11 @@ def test_segmented_tbs_with_code_block_crcs_match_the_batch_path(seg_stream, for
     finally:
         plain.stop()
     srv, res = st.server(arena_bytes=1 << 26, max_inflight=64, cb_crc=True, paired=form[0],
-                         pair_threshold=form[1])
+                         pair_threshold=_thr(form, st.records()))
     try:
         done = srv.replay(st.records(), np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
-        _check_forms(srv, form[2])
+        _check_forms(srv, form[1])
         d_ref, bits_ref, _, _ = _batch_reference(st.sw, range(n))
         for r in done:
             t = int(r["tag"])
@@ -393,9 +397,9 @@ def test_redundancy_versions_through_the_service_match_the_batch_path(form):
     offs = np.concatenate([[0], np.cumsum(words)]).astype(np.int64)
     res = torch.zeros(int(offs[-1]), dtype=torch.int32).pin_memory()
     s = session_for(w, "i8")
-    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, paired=form[0], pair_threshold=form[1])
+    recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
+    srv = Server(s, host, res, arena_bytes=1 << 24, max_inflight=64, paired=form[0], pair_threshold=_thr(form, recs))
     try:
-        recs = tb_records(w, mask_base, abi.SERVE_TB_NP, tags=np.arange(n), result_offsets=4 * offs[:-1])
         assert sorted(set(recs["rv"].tolist())) == [0, 1, 2, 3]
         bad = recs[:1].copy()
         bad["rv"] = 4
@@ -403,7 +407,7 @@ def test_redundancy_versions_through_the_service_match_the_batch_path(form):
             srv.submit(bad)
         done = srv.replay(recs, np.zeros(n, np.int64), timeout_ms=20000)
         assert sorted(done["tag"].tolist()) == list(range(n))
-        _check_forms(srv, form[2])
+        _check_forms(srv, form[1])
         d_ref, bits_ref, it_ref, _ = _batch_reference(w, range(n))
         for r in done:
             t = int(r["tag"])
