@@ -27,6 +27,7 @@
 #include <set>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "arena.h"
@@ -1305,8 +1306,9 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
   if (!v || n < 0 || (n > 0 && (!tbs || !arrival_ns || !out)) || timeout_ms < 1)
     return srv_fail(LDPC_EINVAL, "bad replay arguments");
   std::vector<int64_t> sched(n);
-  std::map<uint64_t, int> by_tag;
-  for (int i = 0; i < n; ++i) by_tag[tbs[i].tag] = i;
+  std::unordered_map<uint64_t, int> by_tag;
+  by_tag.reserve(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) by_tag.emplace(tbs[i].tag, i);
   if (static_cast<int>(by_tag.size()) != n) return srv_fail(LDPC_EINVAL, "replay: tags must be unique");
   const int64_t t0 = now_ns();
   for (int i = 0; i < n; ++i) sched[i] = t0 + arrival_ns[i];
