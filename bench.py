@@ -486,10 +486,72 @@ def serve_measure(pool_n: int, slots: int, loads, forms, thresholds=(0,), releas
     return res
 
 
+def latency_floor(reps: int = 20) -> dict:
+    """One code block alone on the GPU, running all 10 iterations: the per-block decode latency that bounds the
+    service's tail.  BG1-shaped Z=384 at R=1/3 (all 46 rows) and R=1/2 (24 rows), QPSK below the waterfall so
+    that no early exit happens; through the batch decoder (FP32, INT16, INT8) and as a lone request to the INT8
+    service in each form (symbols demapped from pinned host memory, CRC included)."""
+    import torch
+    from paper_2506_00167_gb300 import Server, Session, abi
+    from workload.configs import TBSpec, build, default_bgs, es_n0_sigma2
+    from workload.serving import pool_bytes, tb_records
+
+    bgs = default_bgs()
+    out = {}
+    for R, snr in ((1 / 3, -2.0), (0.5, 2.0)):
+        Z, Qm = 384, 2
+        E = Qm * int(round(bgs[0].kb * Z / (R * Qm)))
+        width = 12 * (-(-(E // Qm) // 168))
+        w = build("one", bgs, [TBSpec(0, 0, Z, Qm, E, 1, float(es_n0_sigma2(snr)), 0, width)], [width],
+                  [np.zeros((14, width), bool)], seed=5)
+        m_eff = bgs[0].m_eff(Z, E)
+        sym = torch.from_numpy(w.sym.astype(np.complex64)).cuda()
+        mask = torch.from_numpy(w.mask.view(np.int32)).cuda()
+        tag = f"R{R:.2f}"
+        for mode in ("f32", "i16", "i8"):
+            s = Session(w.bgs, w.z_set, mode=mode, max_iter=10, early_term=True, sat=SAT[mode])
+            b = s.batch(w.cbs, w.tbs, w.slot_N)
+            o = b.alloc_outputs()
+            s.puncture_demap(b, sym, mask, o["llr"])
+            for _ in range(5):
+                s.decode_batch(b, o["llr"], o["bits"], o["status"])
+            torch.cuda.synchronize()
+            st = torch.cuda.current_stream()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                s.decode_batch(b, o["llr"], o["bits"], o["status"])
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3)
+            it = int(o["status"][0].item()) & 0xFFFF
+            us = float(np.median(ts))
+            out[f"{tag}_{mode}_batch"] = {"us": us, "iters": it, "rows": m_eff, "us_per_iter": us / it,
+                                          "us_per_layer": us / it / m_eff}
+        raw, mb = pool_bytes(w)
+        host = torch.from_numpy(raw).pin_memory()
+        s8 = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
+        for paired in (False, True):
+            srv = Server(s8, host, None, arena_bytes=1 << 24, max_inflight=8, paired=paired)
+            rec = tb_records(w, mb, abi.SERVE_TB_NP)
+            lat = []
+            for i in range(reps + 5):
+                rec["tag"] = i
+                d = srv.replay(rec, np.zeros(1, np.int64), timeout_ms=5000)
+                lat.append((int(d["t_complete_ns"][0]) - int(d["t_submit_ns"][0])) / 1e3)
+                time.sleep(0.002)
+            srv.stop()
+            out[f"{tag}_i8_serve_{'paired' if paired else 'single'}"] = {
+                "p50_us": float(np.median(lat[5:])), "min_us": float(np.min(lat[5:])), "iters": int(d["max_iters"][0])}
+    return out
+
+
 def run_serving(args):
     res = serve_measure(args.serve_pool, args.serve_slots, args.serve_loads, args.serve_form,
                         args.serve_pair_threshold, args.serve_pair_release, args.serve_loops, args.serve_plain,
                         args.cb_crc, punct_sample=1000)
+    res["single_block_latency"] = latency_floor()
     print(json.dumps({"serving": res}), flush=True)
 
 
