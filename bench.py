@@ -529,6 +529,21 @@ def latency_floor(reps: int = 20) -> dict:
             us = float(np.median(ts))
             out[f"{tag}_{mode}_batch"] = {"us": us, "iters": it, "rows": m_eff, "us_per_iter": us / it,
                                           "us_per_layer": us / it / m_eff}
+            for C in (2, 4):  # the same block on a cluster of C CTAs
+                for _ in range(3):
+                    s.decode_cluster(b, o["llr"], o["bits"], o["status"], C)
+                torch.cuda.synchronize()
+                tc = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    s.decode_cluster(b, o["llr"], o["bits"], o["status"], C)
+                    e1.record(st)
+                    torch.cuda.synchronize()
+                    tc.append(e0.elapsed_time(e1) * 1e3)
+                uc = float(np.median(tc))
+                out[f"{tag}_{mode}_cluster{C}"] = {"us": uc, "iters": int(o["status"][0].item()) & 0xFFFF,
+                                                   "us_per_layer": uc / it / m_eff}
         raw, mb = pool_bytes(w)
         host = torch.from_numpy(raw).pin_memory()
         s8 = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])

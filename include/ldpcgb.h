@@ -238,6 +238,21 @@ LDPC_API int decode_batch(ldpc_session *s, const ldpc_batch *b, const void *llr_
                  uint32_t *bits_dev, int32_t *status_dev);
 
 /*
+ * decode_batch's latency form: each code block is decoded by a thread-block
+ * cluster of cluster_ctas (2 or 4) CTAs on as many SMs, each CTA owning
+ * Z / cluster_ctas of every layer's lifted checks and keeping a replica of the
+ * block's posteriors (every new posterior is written into all replicas; a
+ * cluster barrier separates the layers).  The same algorithm and arithmetic as
+ * decode_batch (the paper's receiver decode, Sec. VI-D "UE"), so bits and
+ * status are identical; for callers that decode one or a few large blocks and
+ * want them back soonest.  Needs Z % (32 * cluster_ctas) == 0 and blocks
+ * without LDPC_CB_CRC24B (LDPC_EINVAL otherwise); the first call per cluster
+ * size builds the batch's cluster plan in device memory the batch owns.
+ */
+LDPC_API int ldpc_decode_cluster(ldpc_session *s, ldpc_batch *b, const void *llr_dev, uint32_t *bits_dev,
+                                 int32_t *status_dev, int32_t cluster_ctas);
+
+/*
  * Transport-block CRC-24 check and per-slot goodput and reward.  d_e = 1 iff
  * the TB's (payload_bits + 24) decoded bits are a multiple of
  * g(x) = 0x1864CFB (register from 0, first bit highest degree) -- the same

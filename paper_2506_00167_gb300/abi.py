@@ -25,7 +25,7 @@ ERRORS = {-1: "LDPC_EINVAL", -2: "LDPC_ENOMEM", -3: "LDPC_ECUDA", -4: "LDPC_ETIM
 EXPORTED = [
     "ldpc_session_create", "ldpc_session_destroy", "ldpc_session_set_stream",
     "ldpc_batch_create", "ldpc_batch_destroy", "ldpc_batch_info_get",
-    "puncture_demap", "decode_batch", "tb_crc_goodput",
+    "puncture_demap", "decode_batch", "ldpc_decode_cluster", "tb_crc_goodput",
     "ldpc_device_errors", "ldpc_check_log", "ldpc_last_error", "ldpc_version", "decode_uniform_noalloc",
     "decode_uniform_noalloc_errors", "decode_uniform_noalloc_wait_check",
     "ldpc_session_set_tiles", "ldpc_session_set_strategy", "ldpc_batch_plan_get",
@@ -168,6 +168,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.ldpc_batch_info_get.argtypes = [vp, ctypes.POINTER(BatchInfoC)]
     lib.puncture_demap.argtypes = [vp, vp, vp, vp, vp]
     lib.decode_batch.argtypes = [vp, vp, vp, vp, vp]
+    lib.ldpc_decode_cluster.argtypes = [vp, vp, vp, vp, vp, i32]
     lib.tb_crc_goodput.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.ldpc_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     lib.ldpc_check_log.argtypes = [ctypes.POINTER(ctypes.c_uint32)]

@@ -19,7 +19,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libldpcgb.so")
 LIB_CHECKED = os.path.join(HERE, "libldpcgb_checked.so")
 
-SOURCES = ["session.cu", "decode.cu", "demap.cu", "crc.cu", "noalloc.cu", "serve.cu", "policy.cu"]
+SOURCES = ["session.cu", "decode.cu", "decode_cluster.cu", "demap.cu", "crc.cu", "noalloc.cu", "serve.cu",
+           "policy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

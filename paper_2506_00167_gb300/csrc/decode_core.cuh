@@ -135,11 +135,27 @@ __device__ __forceinline__ float pass1_edge(LT* __restrict__ L, int a, float lv,
   return Q;
 }
 
+// A posterior written into another CTA's replica (cluster decoder): `a` is a
+// shared::cluster address from mapa.
+template <typename LT>
+__device__ __forceinline__ void st_cluster(uint32_t a, float v) {
+  if constexpr (sizeof(LT) == 4) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  } else if constexpr (sizeof(LT) == 2) {
+    asm volatile("st.shared::cluster.b16 [%0], %1;" ::"r"(a), "h"(static_cast<unsigned short>(f2i_exact(v)))
+                 : "memory");
+  } else {
+    asm volatile("st.shared::cluster.b8 [%0], %1;" ::"r"(a), "r"(f2i_exact(v)) : "memory");
+  }
+}
+
 // Pass 2 for edge j: L = Q_j + R'_j, R'_j the other edges' minimum carrying
-// the parity and Q_j's sign.
-template <typename LT, bool SAT>
+// the parity and Q_j's sign.  NREP > 1 (cluster decoder): the posterior is
+// also written into the NREP - 1 other CTAs' replicas, whose shared::cluster
+// base addresses are rep[0 .. NREP-2].
+template <typename LT, bool SAT, int NREP = 1>
 __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, int j, int& idx, float min1,
-                                           float n1s, float n2s, float post_sat) {
+                                           float n1s, float n2s, float post_sat, const uint32_t* rep = nullptr) {
   bool is_min;
   if (SAT) {
     is_min = (j == idx);
@@ -152,6 +168,10 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
   float v = qv + __uint_as_float(rb);
   if (SAT) v = fminf(fmaxf(v, -post_sat), post_sat);
   st_val(L, a, v);
+  if constexpr (NREP > 1) {
+#pragma unroll
+    for (int r = 0; r < NREP - 1; ++r) st_cluster<LT>(rep[r] + static_cast<uint32_t>(a) * sizeof(LT), v);
+  }
 }
 
 // One lifted check (l, k): row data in `in` (chunk c at tab[2 CH c ..]).
@@ -170,11 +190,11 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
 // row's Q values in registers: one shared store and load more per edge for
 // about 30 fewer registers, which lets two 384-thread blocks share an SM
 // (check_update_exact parks only rows above kRegQMaxDeg).
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = -1>
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = -1, int NREP = 1>
 __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                              MT* __restrict__ mag1, MT* __restrict__ mag2,
                                              uint32_t* __restrict__ meta, int rec, int dummy, float beta,
-                                             float msg_sat, float post_sat) {
+                                             float msg_sat, float post_sat, const uint32_t* rep = nullptr) {
   // checked builds: every posterior index stays inside the group's region
   // (dummy - k + Z elements: the columns, then one dummy slot per thread)
   const int lim = dummy - k + Z;
@@ -269,15 +289,15 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
     for (int i = 0; i < CH; ++i) {
       const int j = CH * c + i;
       if (EXACT && j >= DEG) continue;
-      pass2_edge<LT, SAT>(L, addr[j], qv[i], j, idx, min1, n1s, n2s, post_sat);
+      pass2_edge<LT, SAT, NREP>(L, addr[j], qv[i], j, idx, min1, n1s, n2s, post_sat, rep);
     }
   }
   if (ntail) {
 #pragma unroll
     for (int i = 0; i < CH - 1; ++i)
       if (i < ntail)
-        pass2_edge<LT, SAT>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : qt[i], CH * nfull + i, idx, min1, n1s,
-                            n2s, post_sat);
+        pass2_edge<LT, SAT, NREP>(L, addr_t[i], LEAN ? ld_val(L, addr_t[i]) : qt[i], CH * nfull + i, idx, min1,
+                                  n1s, n2s, post_sat, rep);
   }
   if constexpr (sizeof(MT) == 4) {
     reinterpret_cast<float2*>(mag1)[rec] = make_float2(n1, n2);
@@ -296,20 +316,21 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
 // of two 384-thread blocks per SM (one rarely used variant, INT16 with the
 // code-block CRC exit, spills 8 bytes); beyond that the Q values park.
 constexpr int kRegQMaxDeg = 22;
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2>
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2, int NREP = 1>
 __device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                                    MT* __restrict__ mag1, MT* __restrict__ mag2,
                                                    uint32_t* __restrict__ meta, int rec, int dummy, float beta,
-                                                   float msg_sat, float post_sat) {
+                                                   float msg_sat, float post_sat, const uint32_t* rep = nullptr) {
   if constexpr (DEG < kMaxDeg) {
     if (in.deg != DEG) {
-      check_update_exact<LT, MT, SAT, LEAN, CH, DEG + 1>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat,
-                                                         post_sat);
+      check_update_exact<LT, MT, SAT, LEAN, CH, DEG + 1, NREP>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta,
+                                                               msg_sat, post_sat, rep);
       return;
     }
   }
   constexpr bool lean = LEAN && DEG > kRegQMaxDeg;
-  check_update<LT, MT, SAT, lean, CH, DEG>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat);
+  check_update<LT, MT, SAT, lean, CH, DEG, NREP>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat,
+                                                 rep);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2

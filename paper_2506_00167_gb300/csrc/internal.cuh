@@ -95,6 +95,25 @@ struct DecodeArgs {
   const uint32_t* cbcrc;    // code-block CRC byte tables (ShapeDev::crc_off), for LDPC_CB_CRC24B blocks
 };
 
+// The cluster decoder (decode_cluster.cu): one code block per cluster of C
+// CTAs; cb_list names the launch's blocks in cluster order.  Per-CTA shared
+// layout: table (tab_bytes), mbarrier and flags (32 bytes), the block's
+// posterior replica (L_bytes), its hard-decision bitmap (hb_bytes), the
+// messages of the CTA's own checks (rec_cap records).
+struct ClusterArgs {
+  const ShapeDev* shapes;  // indexed by the session's shape index
+  const uint32_t* tabs;
+  const CbDev* cbs;
+  const int32_t* cb_list;
+  const void* llr;
+  uint32_t* bits;
+  int32_t* status;
+  uint32_t* err;
+  int32_t tab_bytes, L_bytes, hb_bytes, rec_cap;
+  int32_t max_iter, early_term;
+  float beta, msg_sat, post_sat;
+};
+
 struct DemapArgs {
   const CbDev* cbs;
   const DemapTile* tiles;
@@ -149,6 +168,8 @@ cudaError_t decode_prepare(int mode);  // raise the dynamic shared-memory limit
 cudaError_t launch_demap(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
 cudaError_t launch_demap_repeat(int mode, int n_tiles, cudaStream_t st, const DemapArgs& a);
 cudaError_t launch_crc(int n_slots, cudaStream_t st, const CrcArgs& a);
+cudaError_t launch_cluster_decode(int mode, int C, int n_clusters, int block, int smem, cudaStream_t st,
+                                  const ClusterArgs& a);
 // Checked builds: the first failed device check of the decoder and of the
 // serving loop (4 words each; zeros when none failed or checks are off).
 cudaError_t read_check_log_decode(uint32_t* out4);

@@ -85,6 +85,19 @@ struct ldpc_batch {
   uint32_t* d_xpow32 = nullptr;
   std::vector<void*> owned;
   uint64_t bytes = 0;
+  // the cluster decoder's plan per cluster size (2 and 4 CTAs), built at its first call
+  struct ClusterLaunch {
+    int n = 0, list_off = 0, block = 0, smem = 0;
+    int tab_bytes = 0, L_bytes = 0, hb_bytes = 0, rec_cap = 0;
+  };
+  struct ClusterPlan {
+    bool built = false;
+    uint32_t* d_tabs = nullptr;
+    ldpcgb::ShapeDev* d_shapes = nullptr;
+    int32_t* d_list = nullptr;
+    std::vector<ClusterLaunch> launches;
+  };
+  ClusterPlan cplan[2];
 };
 
 namespace ldpcgb {
@@ -984,6 +997,115 @@ int decode_batch(ldpc_session* s, const ldpc_batch* b, const void* llr_dev, uint
     if (e != cudaSuccess) return cuda_fail(e, "decode_batch launch");
   }
   return LDPC_OK;
+}
+
+int ldpc_decode_cluster(ldpc_session* s, ldpc_batch* b, const void* llr_dev, uint32_t* bits_dev, int32_t* status_dev,
+                        int32_t cluster_ctas) {
+  try {
+    if (!s || !b || b->s != s) return fail(LDPC_EINVAL, "batch does not belong to this session");
+    if (cluster_ctas != 2 && cluster_ctas != 4) return fail(LDPC_EINVAL, "ldpc_decode_cluster: cluster_ctas must be 2 or 4");
+    if (b->info.n_cb == 0) return LDPC_OK;
+    if (!llr_dev || !bits_dev || !status_dev) return fail(LDPC_EINVAL, "null buffer");
+    if (reinterpret_cast<uintptr_t>(llr_dev) % 16) return fail(LDPC_EINVAL, "LLR buffer must be 16-byte aligned");
+    const int C = cluster_ctas;
+    ldpc_batch::ClusterPlan& P = b->cplan[C == 2 ? 0 : 1];
+    if (!P.built) {
+      const int esz = s->mode == LDPC_F32 ? 4 : (s->mode == LDPC_I8 ? 1 : 2);
+      std::map<int, std::vector<int>> by_z;  // one launch per lifting size (the CTA's threads are Z / C)
+      std::map<int, std::pair<int, int>> shape_nm;  // session shape -> largest n_eff, m_eff in the batch
+      for (int i = 0; i < b->info.n_cb; ++i) {
+        const CbDev& c = b->cbs[i];
+        if (c.Z % (32 * C) != 0)
+          return fail(LDPC_EINVAL, "ldpc_decode_cluster: Z = " + std::to_string(c.Z) + " does not split into " +
+                                       std::to_string(C) + " CTAs of whole warps");
+        if (c.flags & LDPC_CB_CRC24B) return fail(LDPC_EINVAL, "ldpc_decode_cluster: code-block CRCs are not supported");
+        by_z[c.Z].push_back(i);
+        auto& nm = shape_nm[c.shape];
+        nm.first = std::max(nm.first, c.n_eff);
+        nm.second = std::max(nm.second, c.m_eff);
+      }
+      std::vector<uint32_t> tabs;
+      std::vector<ShapeDev> shapes(s->shapes.size());
+      for (auto& kv : shape_nm) {
+        ShapeDev d = s->shapes[kv.first];
+        build_table(s->bgs[d.bg], d.Z, kv.second.first * d.Z, tabs, d, kChunk);
+        shapes[kv.first] = d;
+      }
+      std::vector<int32_t> list;
+      for (auto& kv : by_z) {
+        ldpc_batch::ClusterLaunch L;
+        const int Z = kv.first;
+        L.n = static_cast<int>(kv.second.size());
+        L.list_off = static_cast<int>(list.size());
+        L.block = Z / C;
+        int tw = 0, max_n = 0, max_m = 0;
+        for (int i : kv.second) {
+          const CbDev& c = b->cbs[i];
+          tw = std::max(tw, shapes[c.shape].tab_words);
+          max_n = std::max(max_n, c.n_eff);
+          max_m = std::max(max_m, c.m_eff);
+          list.push_back(i);
+        }
+        const int msz = esz;
+        L.tab_bytes = align16(tw * 4);
+        L.L_bytes = align16((max_n + 1) * Z * esz);
+        L.hb_bytes = align16(max_n * (Z / 32) * 4);
+        L.rec_cap = max_m * L.block;
+        L.smem = L.tab_bytes + 32 + L.L_bytes + L.hb_bytes + 2 * align16(L.rec_cap * msz) + align16(L.rec_cap * 4);
+        if (L.smem > kMaxSmem)
+          return fail(LDPC_EINVAL, "ldpc_decode_cluster: a Z = " + std::to_string(Z) + " block needs " +
+                                       std::to_string(L.smem) + " B of shared memory per CTA");
+        P.launches.push_back(L);
+      }
+      auto up = [&](auto** p, const auto& vec) -> cudaError_t {
+        using T = std::remove_reference_t<decltype(vec[0])>;
+        const size_t nbytes = std::max<size_t>(vec.size(), 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), nbytes);
+        if (e == cudaSuccess) {
+          b->owned.push_back(*p);
+          b->bytes += nbytes;
+          if (!vec.empty()) e = cudaMemcpy(*p, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
+        }
+        return e;
+      };
+      cudaError_t e = up(&P.d_tabs, tabs);
+      if (e == cudaSuccess) e = up(&P.d_shapes, shapes);
+      if (e == cudaSuccess) e = up(&P.d_list, list);
+      if (e != cudaSuccess) return cuda_fail(e, "ldpc_decode_cluster plan");
+      P.built = true;
+    }
+    for (const auto& L : P.launches) {
+      ClusterArgs a{};
+      a.shapes = P.d_shapes;
+      a.tabs = P.d_tabs;
+      a.cbs = b->d_cbs;
+      a.cb_list = P.d_list + L.list_off;
+      a.llr = llr_dev;
+      a.bits = bits_dev;
+      a.status = status_dev;
+      a.err = s->d_err;
+      a.tab_bytes = L.tab_bytes;
+      a.L_bytes = L.L_bytes;
+      a.hb_bytes = L.hb_bytes;
+      a.rec_cap = L.rec_cap;
+      a.max_iter = s->max_iter;
+      a.early_term = s->early_term;
+      if (s->mode == LDPC_F32) {
+        a.beta = s->beta_f32;
+        a.msg_sat = 3.0e38f;
+        a.post_sat = 3.0e38f;
+      } else {
+        a.beta = static_cast<float>(s->offset_lsb);
+        a.msg_sat = static_cast<float>(s->msg_sat);
+        a.post_sat = static_cast<float>(s->post_sat);
+      }
+      const cudaError_t e = launch_cluster_decode(s->mode, C, L.n, L.block, L.smem, s->stream, a);
+      if (e != cudaSuccess) return cuda_fail(e, "ldpc_decode_cluster launch");
+    }
+    return LDPC_OK;
+  } catch (...) {
+    return fail(LDPC_EINVAL, "unexpected host exception");
+  }
 }
 
 int tb_crc_goodput(ldpc_session* s, const ldpc_batch* b, const uint32_t* bits_dev, uint8_t* d_dev,

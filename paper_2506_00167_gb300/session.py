@@ -172,6 +172,17 @@ class Session:
         self._bind_stream()
         abi.check(abi.load().decode_batch(self.handle, b.handle, pl, pb, pst), "decode_batch")
 
+    def decode_cluster(self, b: Batch, llr: torch.Tensor, bits: torch.Tensor, status: torch.Tensor,
+                       cluster_ctas: int = 2) -> None:
+        """decode_batch with each code block on a cluster of 2 or 4 CTAs (the latency form; same results)."""
+        i = b.info
+        pl = _check_tensor(llr, LLR_TORCH[self.mode], i.llr_elems, "llr", self.device)
+        pb = _check_tensor(bits, torch.int32, i.bits_words, "bits", self.device)
+        pst = _check_tensor(status, torch.int32, i.n_cb, "status", self.device)
+        self._bind_stream()
+        abi.check(abi.load().ldpc_decode_cluster(self.handle, b.handle, pl, pb, pst, int(cluster_ctas)),
+                  "ldpc_decode_cluster")
+
     def tb_crc_goodput(self, b: Batch, bits: torch.Tensor, d: torch.Tensor, goodput_bits: torch.Tensor,
                        goodput_sc: torch.Tensor, reward: torch.Tensor) -> None:
         i = b.info
