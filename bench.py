@@ -570,6 +570,47 @@ def run_serving(args):
     print(json.dumps({"serving": res}), flush=True)
 
 
+def mixed_measure(steps: int = 10, world: int = 1) -> dict:
+    """The uneven batch (S1): the mixed workload's 512 slots (BG1/BG2-shaped, Z 32-384, R 0.3-0.9, QPSK-256-QAM,
+    1-8 code blocks per TB, URLLC arrivals) as one CUDA graph per step -- demap, one persistent decoder launch
+    over every shape (work queue, autotuned tiles), CRC/goodput -- in INT8 (paired) and FP32."""
+    import torch
+    from paper_2506_00167_gb300 import Graph, Session
+
+    w = make_workload("mixed")
+    mi, et = w.meta["max_iter"], bool(w.meta["early_term"])
+    sym = torch.from_numpy(np.ascontiguousarray(w.sym, dtype=np.complex64)).cuda()
+    mask = torch.from_numpy(np.ascontiguousarray(w.mask).view(np.int32)).cuda()
+    res = {"workload": "mixed: 512 slots x 8 UEs, TBs of 1-8 code blocks, BG1/BG2-shaped, Z 32-384, R 0.3-0.9, "
+                       "QPSK-256-QAM, 1-4 URLLC arrivals per slot", "code_blocks": w.n_cb,
+           "shapes": len({(int(c["bg"]), int(c["Z"])) for c in w.cbs}), "info_bits_per_step": w.info_bits_total()}
+    for mode in ("i8", "f32"):
+        s = Session(w.bgs, w.z_set, mode=mode, max_iter=mi, early_term=et, sat=SAT[mode])
+        tiles = apply_tiles(s, w, mode, "auto", world)
+        b = s.batch(w.cbs, w.tbs, w.slot_N)
+        out = b.alloc_outputs()
+        g = Graph(s, b, sym, mask, out)
+        for _ in range(3):
+            g.launch()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            g.launch()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        g.close()
+        status = out["status"].cpu().numpy()
+        res[mode] = {"value": w.info_bits_total() / (ms / 1e3) / 1e9, "unit": "Gbit/s", "ms_per_step": ms,
+                     "decoder_launches": len(b.plan()), "mean_iters": float(np.mean(status & 0xFFFF)),
+                     "tiles": tiles.get("source")}
+        if s.device_errors():
+            raise RuntimeError("device error word set in the mixed leg")
+    return res
+
+
 def serve_summary(res: dict) -> dict:
     """The bench line's serving key: the configured load's latency against the 125 us slot."""
     pt = next(iter(res["loads"].values()))[-1]
@@ -760,6 +801,8 @@ def main():
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.25, 0.5, 0.75, 1.0])
     ap.add_argument("--serve-loops", type=int, nargs="+", default=[1],
                     help="device loops per SM for the service (1; 2 is withdrawn)")
+    ap.add_argument("--no-bench-mixed", dest="bench_mixed", action="store_false",
+                    help="leave out the mixed-shape batch key of the benchmark line")
     ap.add_argument("--bench-serve-slots", type=int, default=4000,
                     help="slots of the served stream in the default benchmark line (0: no serving key)")
     ap.add_argument("--sweep", default=None, choices=["precision"],
@@ -962,7 +1005,8 @@ def main():
                 "mean_iters": float(np.mean(st8 & 0xFFFF))}
         del s8, b8, out8
 
-    # ---- the served stream at the configured load (short): latency against the 125 us slot
+    # ---- the uneven batch (mixed shapes) as one graph per step, and the served stream at the configured load
+    mixed_res = mixed_measure(world=world) if (world == 1 and args.config == "large" and args.bench_mixed) else None
     serve = None
     if world == 1 and args.bench_serve_slots > 0:
         serve = serve_summary(serve_measure(256, args.bench_serve_slots, [1.0], ["auto"], plain_n=200,
@@ -1000,7 +1044,8 @@ def main():
             "graph": {"ms_per_step": ms_graph / args.steps,
                       "value": world * info_bits * args.steps / (ms_graph / 1e3) / 1e9, "unit": "Gbit/s",
                       "decoder_launches": len(b.plan())},
-            "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "int8": int8, "serve": serve,
+            "kernels": kernels, "roofline": roof, "cpu_baseline": cpu, "int8": int8, "mixed": mixed_res,
+            "serve": serve,
             "e2e": {"value": e2e_val, "unit": "Gbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "pipeline": "steps alternate over 2 streams: one step's host copies overlap the other's kernels"},
             "gpu_launches": gpu_launches, "clocks": clocks}
