@@ -313,24 +313,38 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
 // rows of degree up to kRegQMaxDeg keep their Q values in registers all the
 // same: one shared store and load less per edge.  With the degree fixed at
 // compile time the compiler fits rows of degree 22 in the 80-register budget
-// of two 384-thread blocks per SM (one rarely used variant, INT16 with the
-// code-block CRC exit, spills 8 bytes); beyond that the Q values park.
+// of two 384-thread blocks per SM without spilling; beyond that the Q values
+// park.
 constexpr int kRegQMaxDeg = 22;
-template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2, int NREP = 1>
+//
+// The degree is found by bisection of [DEG, HI]: first at 8 (most rows of the
+// base graphs have degree 3-8), then by halves, so a row of degree 20 takes 6
+// compares instead of the 19 of a chain from degree 2 upward.  (The paired
+// INT8 update keeps its chain, check_update_x2_by_degree: there bisection
+// measured slower.)
+template <int LO, int HI>
+constexpr int degree_split() {
+  return (LO <= 8 && HI > 8) ? 8 : (LO + HI) / 2;
+}
+
+template <typename LT, typename MT, bool SAT, bool LEAN, int CH, int DEG = 2, int NREP = 1, int HI = kMaxDeg>
 __device__ __forceinline__ void check_update_exact(const RowIn<CH>& in, int k, int Z, LT* __restrict__ L,
                                                    MT* __restrict__ mag1, MT* __restrict__ mag2,
                                                    uint32_t* __restrict__ meta, int rec, int dummy, float beta,
                                                    float msg_sat, float post_sat, const uint32_t* rep = nullptr) {
-  if constexpr (DEG < kMaxDeg) {
-    if (in.deg != DEG) {
-      check_update_exact<LT, MT, SAT, LEAN, CH, DEG + 1, NREP>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta,
-                                                               msg_sat, post_sat, rep);
-      return;
-    }
+  if constexpr (DEG < HI) {
+    constexpr int MID = degree_split<DEG, HI>();
+    if (in.deg <= MID)
+      check_update_exact<LT, MT, SAT, LEAN, CH, DEG, NREP, MID>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta,
+                                                                msg_sat, post_sat, rep);
+    else
+      check_update_exact<LT, MT, SAT, LEAN, CH, MID + 1, NREP, HI>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta,
+                                                                   msg_sat, post_sat, rep);
+  } else {
+    constexpr bool lean = LEAN && DEG > kRegQMaxDeg;
+    check_update<LT, MT, SAT, lean, CH, DEG, NREP>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat,
+                                                   post_sat, rep);
   }
-  constexpr bool lean = LEAN && DEG > kRegQMaxDeg;
-  check_update<LT, MT, SAT, lean, CH, DEG, NREP>(in, k, Z, L, mag1, mag2, meta, rec, dummy, beta, msg_sat, post_sat,
-                                                 rep);
 }
 
 // R = 0 for the first n check records (float: the magnitudes are one float2
