@@ -51,10 +51,12 @@ __device__ __forceinline__ bool group_any(int Z, int g, uint32_t wmask, bool pre
   return named_bar_or(1 + g, Z, pred);
 }
 
-// (k + s) mod Z for 0 <= k, s < Z: the unsigned minimum of k + s and k + s - Z.
+// (k + s) mod Z for 0 <= k, s < Z: the unsigned minimum of k + s and k + s - Z
+// (k + s - Z wraps around when k + s < Z), as one fused add-and-minimum (DPX)
+// on the sum.
 __device__ __forceinline__ int rot(int k, uint32_t s, int Z) {
   const uint32_t t = static_cast<uint32_t>(k) + s;
-  return static_cast<int>(umin(t, t - static_cast<uint32_t>(Z)));
+  return static_cast<int>(__viaddmin_u32(t, 0u - static_cast<uint32_t>(Z), t));
 }
 
 // What a check update needs before it touches the posteriors: the row's edge

@@ -380,3 +380,66 @@ def test_extreme_row_degrees_match_oracle(mode):
     assert np.array_equal(to_np_u32(bits), want_bits)
     assert np.array_equal(status.cpu().numpy(), want_status)
     assert s.device_errors() == 0
+
+
+def _every_degree_graph():
+    """26 x 30 base matrix with one row of every degree the decoders accept, 2 .. 27, in a shuffled order, so
+    that every leaf of the degree dispatch runs (no code structure: the decoders only see LLRs)."""
+    from workload.basegraph import custom_base_graph
+    rng = np.random.default_rng(78)
+    degrees = rng.permutation(np.arange(2, 28))
+    ent = {}
+    for r, d in enumerate(degrees):
+        for c in rng.choice(30, size=int(d), replace=False):
+            ent[(r, int(c))] = int(rng.integers(0, 384))
+    return custom_base_graph("every_degree", 26, 30, 4, 26, 0, ent)
+
+
+def _every_degree_workload(zs, seed):
+    from workload.configs import TBSpec, build
+    bg = _every_degree_graph()
+    assert sorted(np.bincount(bg.row).tolist()) == list(range(2, 28))
+    specs, widths, punct = [], [], []
+    for i, Z in enumerate(zs):
+        E = bg.nb * Z
+        width = 12 * -(-(E // 2) // (12 * 14))
+        specs.append(TBSpec(i, 0, Z, 2, E, 1, 1.2, 0, width))
+        widths.append(width)
+        punct.append(np.zeros((14, width), bool))
+    return build("every_degree", [bg], specs, widths, punct, seed=seed, z_set=sorted(set(zs)))
+
+
+@pytest.mark.parametrize("mode", ["f32", "i8", "i16"])
+def test_every_row_degree_matches_oracle(mode):
+    # every degree from 2 to 27 in one graph, every row decoded; Z = 16 (the single-block INT8 form) and
+    # 32/64 (the paired INT8 form), an odd block count
+    w = _every_degree_workload([16, 32, 64, 32, 16, 64, 32], seed=6)
+    assert all(int(c["Z"]) * 26 <= int(c["E"]) for c in w.cbs)
+    llr = _oracle_llr_for_mode(w, mode)
+    want_bits, want_status = odec.decode_workload(w, llr, 5, False, ARITH[mode])
+    s = session_for(w, mode, max_iter=5, early_term=False)
+    b = s.batch(w.cbs)
+    bits = torch.zeros(b.info.bits_words, dtype=torch.int32, device="cuda")
+    status = torch.zeros(b.n_cb, dtype=torch.int32, device="cuda")
+    s.decode_batch(b, torch.from_numpy(llr.astype(LLR_NP[mode])).cuda(), bits, status)
+    assert np.array_equal(to_np_u32(bits), want_bits)
+    assert np.array_equal(status.cpu().numpy(), want_status)
+    assert s.device_errors() == 0
+
+
+@pytest.mark.parametrize("mode", ["f32", "i8"])
+def test_every_row_degree_cluster_matches_oracle(mode):
+    # the cluster decoder's copy of the update on the same graph: Z = 64 on 2 CTAs, Z = 128 on 4
+    for zs, C in (([64, 64, 64], 2), ([128, 128], 4)):
+        w = _every_degree_workload(zs, seed=7 + C)
+        llr = _oracle_llr_for_mode(w, mode)
+        want_bits, want_status = odec.decode_workload(w, llr, 5, False, ARITH[mode])
+        s = session_for(w, mode, max_iter=5, early_term=False)
+        b = s.batch(w.cbs)
+        bits = torch.zeros(b.info.bits_words, dtype=torch.int32, device="cuda")
+        status = torch.zeros(b.n_cb, dtype=torch.int32, device="cuda")
+        s.decode_cluster(b, torch.from_numpy(llr.astype(LLR_NP[mode])).cuda(), bits, status, C)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_np_u32(bits), want_bits), (zs, C)
+        assert np.array_equal(status.cpu().numpy(), want_status), (zs, C)
+        assert s.device_errors() == 0
