@@ -616,7 +616,8 @@ def serve_summary(res: dict) -> dict:
     pt = next(iter(res["loads"].values()))[-1]
     keep = ("tb_per_ue_per_slot", "slots", "requests", "offered_gbps", "served_gbps", "p50_us", "p99_us",
             "p999_us", "max_us", "within_slot_frac", "tb_crc_ok_frac", "mean_max_iters", "items_single",
-            "items_paired")
+            "items_paired", "host_longest_pass_us", "host_passes_over_1ms", "max_gap_device_us", "max_gap_host_us",
+            "max_admit_wait_us")
     return {"workload": res["workload"], "form": pt["form"], **{k: pt[k] for k in keep},
             "slot_us": 125.0, "p99_within_slot": pt["p99_us"] <= 125.0,
             "fp32_unbatched_plain": res["fp32_unbatched_plain"], "pool_tbs": res["pool_tbs"]}

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
   int* s_item = reinterpret_cast<int*>(smem + a.hdr_bytes - 8);
   uint8_t* regions = smem + a.hdr_bytes;
   const int tid = threadIdx.x;
-  const int beta = static_cast<int>(a.beta);
+  const __half2 beta = __float2half2_rn(a.beta);
   const __half2 msg = __float2half2_rn(a.msg_sat);
   const __half2 post = __float2half2_rn(a.post_sat);
 

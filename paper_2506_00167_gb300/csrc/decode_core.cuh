@@ -533,11 +533,6 @@ __device__ __forceinline__ uint32_t as_u32(__half2 h) {
   return u;
 }
 
-// half2 (1024 + a, 1024 + b) - 1024 for 0 <= a, b < 1024
-__device__ __forceinline__ __half2 small_pair(uint32_t a, uint32_t b) {
-  return __hsub2(as_h2((0x6400u + a) | ((0x6400u + b) << 16)), __float2half2_rn(1024.0f));
-}
-
 // Rows up to this degree keep their Q pairs in registers for pass 2 as well
 // (beyond it the 80-register budget spills).
 constexpr int kRegQ2MaxDeg = 12;
@@ -585,7 +580,7 @@ __device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int 
 template <int DEG = -1>
 __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
                                                 uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
-                                                uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
+                                                uint32_t* __restrict__ sg2, int rec, int dummy, __half2 beta,
                                                 __half2 msg, __half2 post) {
   // DEG >= 0: the row's degree is a compile-time constant and only its DEG
   // edges are processed; otherwise a padding edge completes the last chunk
@@ -648,16 +643,23 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
       min1 = __hmin2(min1, key);
     }
   }
-  const float2 f1 = __half22float2(min1), f2 = __half22float2(min2);
-  const int kA1 = f2i_exact(f1.x), kB1 = f2i_exact(f1.y), kA2 = f2i_exact(f2.x), kB2 = f2i_exact(f2.y);
-  const uint32_t idxA = kA1 & 31, idxB = kB1 & 31;
-  const uint32_t nA1 = max((kA1 >> 5) - beta, 0), nB1 = max((kB1 >> 5) - beta, 0);
-  const uint32_t nA2 = max((kA2 >> 5) - beta, 0), nB2 = max((kB2 >> 5) - beta, 0);
+  // the keys decoded in half2, exactly (integers < 2048; the division by 32
+  // is a power-of-two scaling): magnitude = floor(key / 32), argmin = key - 32
+  // magnitude, new magnitudes max(magnitude - beta, 0)
+  const __half2 zero2 = __float2half2_rn(0.0f);
+  const __half2 m1 = h2floor(__hmul2(min1, __float2half2_rn(0.03125f)));
+  const __half2 m2 = h2floor(__hmul2(min2, __float2half2_rn(0.03125f)));
+  const __half2 h1 = __hmax2(__hsub2(m1, beta), zero2);
+  const __half2 h2 = __hmax2(__hsub2(m2, beta), zero2);
+  // 1024 + x (0 <= x < 1024) holds x in its low mantissa bits
+  const uint32_t iw = as_u32(__hadd2(__hfma2(m1, __float2half2_rn(-32.0f), min1), h1024)) & 0x001F001Fu;
+  const uint32_t idxA = iw & 0xFFFFu, idxB = iw >> 16;
+  const uint32_t mw = __byte_perm(as_u32(__hadd2(h1, h1024)), as_u32(__hadd2(h2, h1024)), 0x6420);
   const uint32_t xa = acc1 ^ acc2;  // every processed edge's sign once (padding edges are positive)
   const uint32_t pm = ((static_cast<uint32_t>(__popc(xa & 0xFFFFu)) & 1u) << 15) |
                       ((static_cast<uint32_t>(__popc(xa >> 16)) & 1u) << 31);
-  const uint32_t N1s = as_u32(small_pair(nA1, nB1)) | pm;
-  const uint32_t N2s = as_u32(small_pair(nA2, nB2)) | pm;
+  const uint32_t N1s = as_u32(h1) | pm;
+  const uint32_t N2s = as_u32(h2) | pm;
   // the two argmin edges and their Q values, before pass 2 overwrites them
   const int aA = checked(edge_addr(tab, static_cast<int>(idxA), k, Z), dummy - k + Z, dummy, 4);
   const int aB = checked(edge_addr(tab, static_cast<int>(idxB), k, Z), dummy - k + Z, dummy, 4);
@@ -687,10 +689,10 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const int n_all = EXACT ? DEG : kChunk * nch;
   const int n1 = n_all < 16 ? n_all : 16;
   const int n2 = n_all - 16;
-  mags[rec] = nA1 | (nB1 << 8) | (nA2 << 16) | (nB2 << 24);
+  mags[rec] = mw;
   sg1[rec] = acc1 >> (16 - n1);
   const uint32_t a2 = n2 <= 0 ? 0u : (n2 <= 11 ? acc2 >> (11 - n2) : acc2 << (n2 - 11));
-  sg2[rec] = (a2 & 0xFFE0FFE0u) | idxA | (idxB << 16);
+  sg2[rec] = (a2 & 0xFFE0FFE0u) | iw;
 }
 
 // check_update_x2 with the row's degree as a compile-time constant (no padding
@@ -698,7 +700,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
 template <int DEG = 2>
 __device__ __forceinline__ void check_update_x2_by_degree(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
                                                           uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
-                                                          uint32_t* __restrict__ sg2, int rec, int dummy, int beta,
+                                                          uint32_t* __restrict__ sg2, int rec, int dummy, __half2 beta,
                                                           __half2 msg, __half2 post) {
   if constexpr (DEG < kMaxDeg) {
     if (in.deg != DEG) {

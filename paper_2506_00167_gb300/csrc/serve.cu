@@ -520,7 +520,7 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
   const int Z = sh.Z;
   const int g = tid / Z;
   const int k = tid - g * Z;
-  const int beta = static_cast<int>(a.beta);
+  const __half2 beta = __float2half2_rn(a.beta);
   const __half2 msg = __float2half2_rn(a.msg_sat);
   const __half2 post = __float2half2_rn(a.post_sat);
   if (tid == 0) {
