@@ -181,11 +181,12 @@ __device__ __forceinline__ void pass2_edge(LT* __restrict__ L, int a, float qv, 
 // chunks run unrolled; the deg % CH edges of a last, partial chunk run
 // after them (the table's padding entries are never touched).
 //
-// The record keeps the signs of the Q_j of the last update (edge j at bit
-// deg-1-j) and the argmin edge in bits 27..31; the sign of the stored message
-// R_j is that bit XOR the parity of all of them (R'_j carries the sign
-// product over i != j), so the parity is recovered by one popcount and the
-// new signs cost nothing in the second pass.
+// The record keeps the signs of the stored messages R_j (edge j at bit
+// deg-1-j) and the argmin edge in bits 27..31.  R'_j carries the sign
+// product over i != j, i.e. sign(Q_j) XOR the parity of all Q signs: the
+// update collects the Q signs in pass 1, takes their parity with one
+// popcount, and stores them XOR the parity, so the next update reads R_j's
+// sign as it is.
 //
 // LEAN: pass 1 parks each Q_j in its posterior's slot (the check owns those
 // slots during the layer) and pass 2 reads it back, instead of holding the
@@ -216,12 +217,10 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
   const float r1 = in.r1, r2 = in.r2;
   const uint32_t mo = in.mo;
   const int idx_o = static_cast<int>(mo >> 27);
-  // sign of R_j = stored Q-sign bit ^ parity, edge 0's moved to bit 31
-  const uint32_t par_o = 0u - (static_cast<uint32_t>(__popc(mo << 5)) & 1u);
-  // (integer modes with PAD: positions past deg read as negative, so the
-  // padding edge sees Q = dummy + |R|, large and positive)
-  uint32_t sgn = (PAD && SAT) ? (((mo ^ par_o) << (32 - deg)) | ((1u << (32 - deg)) - 1u))
-                              : ((mo ^ par_o) << (32 - deg));
+  // signs of the R_j, edge 0's moved to bit 31 (integer modes with PAD:
+  // positions past deg read as negative, so the padding edge sees
+  // Q = dummy + |R|, large and positive)
+  uint32_t sgn = (PAD && SAT) ? ((mo << (32 - deg)) | ((1u << (32 - deg)) - 1u)) : (mo << (32 - deg));
   const int nfull = EXACT ? (DEG + CH - 1) / CH : (PAD ? (deg + CH - 1) / CH : deg / CH);
   const int ntail = (PAD || EXACT) ? 0 : deg - CH * nfull;
 
@@ -307,7 +306,10 @@ __device__ __forceinline__ void check_update(const RowIn<CH>& in, int k, int Z, 
     st_val(mag1, rec, n1);
     st_val(mag2, rec, n2);
   }
-  meta[rec] = (PAD ? qs >> (CH * nfull - deg) : qs) | (static_cast<uint32_t>(idx) << 27);
+  // the new R signs: the Q signs XOR the parity, on the row's deg bits
+  const uint32_t pspread = static_cast<uint32_t>(static_cast<int32_t>(pm) >> 31);
+  const uint32_t dmask = (1u << deg) - 1u;
+  meta[rec] = ((PAD ? qs >> (CH * nfull - deg) : qs) ^ (pspread & dmask)) | (static_cast<uint32_t>(idx) << 27);
 }
 
 // The update with the row's exact degree as a compile-time constant (DEG
@@ -533,6 +535,12 @@ __device__ __forceinline__ uint32_t as_u32(__half2 h) {
   return u;
 }
 
+// 16-bit store into shared memory
+__device__ __forceinline__ void st_shared_b16(void* p, uint16_t v) {
+  asm volatile("st.shared.b16 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "h"(v)
+               : "memory");
+}
+
 // Rows up to this degree keep their Q pairs in registers for pass 2 as well
 // (beyond it the 80-register budget spills).
 constexpr int kRegQ2MaxDeg = 12;
@@ -568,11 +576,11 @@ __device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int 
   return static_cast<int>(t[0]) + rot(k, t[kChunk], Z);
 }
 
-// Stored form (v2): magnitudes as above; Q-sign history of the last update,
+// Stored form: magnitudes as above; the signs of the stored messages R_j,
 // edge j < 16 at bit j (A) and 16 + j (B) of s1, edges 16..26 at bits
 // 5 + (j-16) (A) and 21 + (j-16) (B) of s2, argmins in s2 bits 0..4 / 16..20.
-// The sign of the stored message R_j is that bit XOR the parity of the
-// block's Q signs (R'_j carries the sign product over i != j).
+// R'_j carries the sign product over i != j: the update stores each block's
+// Q signs XOR their parity.
 //
 // Pass 2 writes every edge with the smaller magnitude; the argmin edge of
 // each block, whose message takes the second magnitude instead, is then
@@ -594,13 +602,10 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const int deg = EXACT ? DEG : in.deg;
   const uint32_t mg = in.mg, s1 = in.s1, s2 = in.s2;
   const __half2 h1024 = __float2half2_rn(1024.0f);
-  // parity of each block's stored Q signs, as the two sign bits of a half2
-  const uint32_t xs = s1 ^ (s2 & 0xFFE0FFE0u);
-  const uint32_t pm_o = ((static_cast<uint32_t>(__popc(xs & 0xFFFFu)) & 1u) << 15) |
-                        ((static_cast<uint32_t>(__popc(xs >> 16)) & 1u) << 31);
-  const uint32_t M1s = as_u32(__hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5140)), h1024)) | pm_o;
-  const uint32_t M2s = as_u32(__hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5342)), h1024)) | pm_o;
-  const __half2 I = __hsub2(as_h2((s2 & 0x001F001Fu) | 0x64006400u), h1024);
+  const uint32_t M1s = as_u32(__hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5140)), h1024));
+  const uint32_t M2s = as_u32(__hsub2(as_h2(__byte_perm(mg, 0x64646464u, 0x5342)), h1024));
+  // the argmins as half2 1024 + index, compared with 1024 + j below
+  const __half2 I = as_h2((s2 & 0x001F001Fu) | 0x64006400u);
   const __half2 h32 = __float2half2_rn(32.0f);
   const __half2 npost = __hneg2(post);
   const int nch = (deg + kChunk - 1) / kChunk;
@@ -626,7 +631,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
       const int j = kChunk * c + i;
       if (EXACT && j >= DEG) continue;
       const __half2 J = __float2half2_rn(static_cast<float>(j));
-      const uint32_t eq = __heq2_mask(I, J);
+      const uint32_t eq = __heq2_mask(I, __float2half2_rn(static_cast<float>(1024 + j)));
       // (edge 27 can only be padding, whose sign does not matter)
       const uint32_t sw = j < 16 ? (s1 << (15 - j)) : (j <= 26 ? (s2 << (26 - j)) : 0u);
       const uint32_t rb = ((M2s & eq) | (M1s & ~eq)) ^ (sw & 0x80008000u);
@@ -683,15 +688,20 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   {
     const uint32_t rb = N2s ^ (qsel & 0x80008000u);
     const uint32_t v = as_u32(__hmin2(__hmax2(__hadd2(as_h2(qsel), as_h2(rb)), npost), post));
-    L[aA] = (L[aA] & 0xFFFF0000u) | (v & 0x0000FFFFu);
-    L[aB] = (L[aB] & 0x0000FFFFu) | (v & 0xFFFF0000u);
+    // block A's half of slot aA, block B's half of slot aB: one 16-bit store
+    // each (inline stores with a memory clobber, ordered after pass 2's)
+    st_shared_b16(reinterpret_cast<uint8_t*>(L + aA), static_cast<uint16_t>(v & 0xFFFFu));
+    st_shared_b16(reinterpret_cast<uint8_t*>(L + aB) + 2, static_cast<uint16_t>(v >> 16));
   }
   const int n_all = EXACT ? DEG : kChunk * nch;
   const int n1 = n_all < 16 ? n_all : 16;
   const int n2 = n_all - 16;
+  // the new R signs: each block's Q signs XOR its parity (bit 15 / 31 of pm
+  // spread over its half); bits past the row's degree are never read
+  const uint32_t spread = (pm >> 15) * 0xFFFFu;  // (bit 0, bit 16) = (A, B) parity, times 0xFFFF
   mags[rec] = mw;
-  sg1[rec] = acc1 >> (16 - n1);
-  const uint32_t a2 = n2 <= 0 ? 0u : (n2 <= 11 ? acc2 >> (11 - n2) : acc2 << (n2 - 11));
+  sg1[rec] = (acc1 ^ spread) >> (16 - n1);
+  const uint32_t a2 = n2 <= 0 ? 0u : (n2 <= 11 ? (acc2 ^ spread) >> (11 - n2) : (acc2 ^ spread) << (n2 - 11));
   sg2[rec] = (a2 & 0xFFE0FFE0u) | iw;
 }
 
