@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
     uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + item.L_bytes + item.hb_bytes);
     uint8_t* recs = reg + item.L_bytes + 2 * item.hb_bytes;
     if (RGLOBAL) recs = a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.G + g) * a.rscratch_group;
-    uint32_t* mags = reinterpret_cast<uint32_t*>(recs);
-    uint32_t* sg1 = mags + item.rec_cap;
-    uint32_t* sg2 = sg1 + item.rec_cap;
+    // per check: (magnitudes, s1) as one 8-byte pair, then s2
+    uint2* ms = reinterpret_cast<uint2*>(recs);
+    uint32_t* sg2 = reinterpret_cast<uint32_t*>(recs) + 2 * item.rec_cap;
 
     // ---- stage the table and (shared-message form) each pair's int8 LLRs
     // into its message area
@@ -320,8 +320,7 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
       }
       group_sync(Z, g, 0xFFFFFFFFu);
       for (int r = k; r < A.m_eff * Z; r += Z) {
-        mags[r] = 0u;
-        sg1[r] = 0u;
+        ms[r] = make_uint2(0u, 0u);
         sg2[r] = 0u;
       }
       group_sync(Z, g, 0xFFFFFFFFu);
@@ -329,13 +328,13 @@ __global__ void __launch_bounds__(kDecodeMaxBlock, 2) oms_decode_i8x2_kernel(con
       const uint32_t* rows = s_tab + sh.row_off;
       const int mA = A.m_eff, mB = hasB ? Bc.m_eff : 0;
       bool doneA = false, doneB = !hasB;
-      PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
+      PairIn prow = load_pair_row(s_tab, rows[0], ms, sg2, k);
       for (int it = 1;; ++it) {
         for (int l = 0; l < mA; ++l) {
-          check_update_x2_by_degree(prow, k, Z, L, mags, sg1, sg2, l * Z + k, item.dummy_base + k, beta, msg, post);
+          check_update_x2_by_degree(prow, k, Z, L, ms, sg2, l * Z + k, item.dummy_base + k, beta, msg, post);
           // the next row's table entry and message words are loaded before the barrier
           const int ln = l + 1 < mA ? l + 1 : 0;
-          prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
+          prow = load_pair_row(s_tab, rows[ln], ms, sg2, ln * Z + k);
           group_sync(Z, g, 0xFFFFFFFFu);
         }
         if (a.early_term || it == a.max_iter) {

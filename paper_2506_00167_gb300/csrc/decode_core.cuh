@@ -558,14 +558,17 @@ struct PairIn {
   uint32_t mg, s1, s2;
 };
 
+// The three message words of a check: (magnitudes, s1) as one 8-byte pair in
+// `ms`, s2 in its own array.
 __device__ __forceinline__ PairIn load_pair_row(const uint32_t* __restrict__ s_tab, uint32_t info,
-                                                const uint32_t* __restrict__ mags, const uint32_t* __restrict__ sg1,
-                                                const uint32_t* __restrict__ sg2, int rec) {
+                                                const uint2* __restrict__ ms, const uint32_t* __restrict__ sg2,
+                                                int rec) {
   PairIn r;
   r.tab = s_tab + (info & 0xFFFFu);
   r.deg = static_cast<int>(info >> 16);
-  r.mg = mags[rec];
-  r.s1 = sg1[rec];
+  const uint2 m = ms[rec];
+  r.mg = m.x;
+  r.s1 = m.y;
   r.s2 = sg2[rec];
   return r;
 }
@@ -580,16 +583,17 @@ __device__ __forceinline__ int edge_addr(const uint32_t* tab, int e, int k, int 
 // edge j < 16 at bit j (A) and 16 + j (B) of s1, edges 16..26 at bits
 // 5 + (j-16) (A) and 21 + (j-16) (B) of s2, argmins in s2 bits 0..4 / 16..20.
 // R'_j carries the sign product over i != j: the update stores each block's
-// Q signs XOR their parity.
+// Q signs XOR their parity, which it reads off bits 15 / 31 of the XOR of the
+// row's Q pairs.  The magnitude word and s1 sit side by side (one 8-byte
+// access), s2 in its own array.
 //
 // Pass 2 writes every edge with the smaller magnitude; the argmin edge of
 // each block, whose message takes the second magnitude instead, is then
 // rewritten from its Q, read before pass 2 (the check owns the slot).
 template <int DEG = -1>
 __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
-                                                uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
-                                                uint32_t* __restrict__ sg2, int rec, int dummy, __half2 beta,
-                                                __half2 msg, __half2 post) {
+                                                uint2* __restrict__ ms, uint32_t* __restrict__ sg2, int rec,
+                                                int dummy, __half2 beta, __half2 msg, __half2 post) {
   // DEG >= 0: the row's degree is a compile-time constant and only its DEG
   // edges are processed; otherwise a padding edge completes the last chunk
   // (on this thread's dummy slot, which can never be a minimum)
@@ -614,6 +618,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   uint32_t qr[REGQ ? kMaxChunks * kChunk : 1];
   __half2 min1 = __float2half2_rn(65504.0f), min2 = min1;
   uint32_t acc1 = 0, acc2 = 0;  // Q signs: each new edge enters at bits 15 / 31
+  uint32_t par = 0;              // XOR of the Q pairs: bits 15 / 31 are the sign parities
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     if (c >= nch) break;
@@ -639,6 +644,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
       Q = __hmin2(__hmax2(Q, npost), post);
       L[addr[j]] = as_u32(Q);
       if constexpr (REGQ) qr[j] = as_u32(Q);
+      par ^= as_u32(Q);
       if (j < 16)
         acc1 = ((acc1 >> 1) & 0x7FFF7FFFu) | (as_u32(Q) & 0x80008000u);
       else
@@ -660,9 +666,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   const uint32_t iw = as_u32(__hadd2(__hfma2(m1, __float2half2_rn(-32.0f), min1), h1024)) & 0x001F001Fu;
   const uint32_t idxA = iw & 0xFFFFu, idxB = iw >> 16;
   const uint32_t mw = __byte_perm(as_u32(__hadd2(h1, h1024)), as_u32(__hadd2(h2, h1024)), 0x6420);
-  const uint32_t xa = acc1 ^ acc2;  // every processed edge's sign once (padding edges are positive)
-  const uint32_t pm = ((static_cast<uint32_t>(__popc(xa & 0xFFFFu)) & 1u) << 15) |
-                      ((static_cast<uint32_t>(__popc(xa >> 16)) & 1u) << 31);
+  const uint32_t pm = par & 0x80008000u;
   const uint32_t N1s = as_u32(h1) | pm;
   const uint32_t N2s = as_u32(h2) | pm;
   // the two argmin edges and their Q values, before pass 2 overwrites them
@@ -699,8 +703,7 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
   // the new R signs: each block's Q signs XOR its parity (bit 15 / 31 of pm
   // spread over its half); bits past the row's degree are never read
   const uint32_t spread = (pm >> 15) * 0xFFFFu;  // (bit 0, bit 16) = (A, B) parity, times 0xFFFF
-  mags[rec] = mw;
-  sg1[rec] = (acc1 ^ spread) >> (16 - n1);
+  ms[rec] = make_uint2(mw, (acc1 ^ spread) >> (16 - n1));
   const uint32_t a2 = n2 <= 0 ? 0u : (n2 <= 11 ? (acc2 ^ spread) >> (11 - n2) : (acc2 ^ spread) << (n2 - 11));
   sg2[rec] = (a2 & 0xFFE0FFE0u) | iw;
 }
@@ -709,16 +712,15 @@ __device__ __forceinline__ void check_update_x2(const PairIn& in, int k, int Z, 
 // edge, straight-line passes).
 template <int DEG = 2>
 __device__ __forceinline__ void check_update_x2_by_degree(const PairIn& in, int k, int Z, uint32_t* __restrict__ L,
-                                                          uint32_t* __restrict__ mags, uint32_t* __restrict__ sg1,
-                                                          uint32_t* __restrict__ sg2, int rec, int dummy, __half2 beta,
-                                                          __half2 msg, __half2 post) {
+                                                          uint2* __restrict__ ms, uint32_t* __restrict__ sg2, int rec,
+                                                          int dummy, __half2 beta, __half2 msg, __half2 post) {
   if constexpr (DEG < kMaxDeg) {
     if (in.deg != DEG) {
-      check_update_x2_by_degree<DEG + 1>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
+      check_update_x2_by_degree<DEG + 1>(in, k, Z, L, ms, sg2, rec, dummy, beta, msg, post);
       return;
     }
   }
-  check_update_x2<DEG>(in, k, Z, L, mags, sg1, sg2, rec, dummy, beta, msg, post);
+  check_update_x2<DEG>(in, k, Z, L, ms, sg2, rec, dummy, beta, msg, post);
 }
 
 // hard decisions of both blocks of a pair into their bitmaps

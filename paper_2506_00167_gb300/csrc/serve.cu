@@ -535,10 +535,10 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
   uint32_t* L = reinterpret_cast<uint32_t*>(reg);
   uint32_t* hbA = reinterpret_cast<uint32_t*>(reg + ssh.Lp_bytes);
   uint32_t* hbB = reinterpret_cast<uint32_t*>(reg + ssh.Lp_bytes + ssh.hb_bytes);
-  uint32_t* mags = reinterpret_cast<uint32_t*>(a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) *
-                                                             a.rscratch_group);
-  uint32_t* sg1 = mags + ssh.rec_cap;
-  uint32_t* sg2 = sg1 + ssh.rec_cap;
+  // per check: (magnitudes, s1) as one 8-byte pair, then s2
+  uint2* ms = reinterpret_cast<uint2*>(a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) *
+                                                        a.rscratch_group);
+  uint32_t* sg2 = reinterpret_cast<uint32_t*>(ms) + 2 * ssh.rec_cap;
   CbDev A{}, B{};
   if (active) {
     A = load_cb(a.cbs + (static_cast<uint32_t>(cb0 + 2 * g) % a.cb_cap));
@@ -564,8 +564,7 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
   }
   if (active) {
     for (int r = k; r < A.m_eff * Z; r += Z) {
-      mags[r] = 0u;
-      sg1[r] = 0u;
+      ms[r] = make_uint2(0u, 0u);
       sg2[r] = 0u;
     }
     // both blocks' LLRs into the two halves of the posterior words (B's half 0 without a second block)
@@ -590,12 +589,12 @@ __device__ __forceinline__ bool pair_item(const ServeArgs& a, const ServeShape& 
     const int m = A.m_eff;
     const int dummy = ssh.dummy_base + k;
     bool doneA = false, doneB = !hasB;
-    PairIn prow = load_pair_row(s_tab, rows[0], mags, sg1, sg2, k);
+    PairIn prow = load_pair_row(s_tab, rows[0], ms, sg2, k);
     for (int it = 1;; ++it) {
       for (int l = 0; l < m; ++l) {
-        check_update_x2_by_degree(prow, k, Z, L, mags, sg1, sg2, l * Z + k, dummy, beta, msg, post);
+        check_update_x2_by_degree(prow, k, Z, L, ms, sg2, l * Z + k, dummy, beta, msg, post);
         const int ln = l + 1 < m ? l + 1 : 0;
-        prow = load_pair_row(s_tab, rows[ln], mags, sg1, sg2, ln * Z + k);
+        prow = load_pair_row(s_tab, rows[ln], ms, sg2, ln * Z + k);
         group_sync(Z, g, 0xFFFFFFFFu);
       }
       if (a.early_term || it == a.max_iter) {
