@@ -430,6 +430,11 @@ def serve_measure(pool_n: int, slots: int, loads, forms, thresholds=(0,), releas
                         "loop_launches": int(c1["launches"] - c0["launches"]),
                         "host_longest_pass_us": c1["replay_longest_pass_ns"] / 1e3,
                         "host_passes_over_1ms": int(c1["replay_passes_over_1ms"]),
+                        "host_longest_pass_at_ms": c1["replay_longest_pass_at_ns"] / 1e6,
+                        "host_involuntary_switches": int(c1["replay_involuntary_switches"]),
+                        "host_voluntary_switches": int(c1["replay_voluntary_switches"]),
+                        "host_minor_faults": int(c1["replay_minor_faults"]),
+                        "host_major_faults": int(c1["replay_major_faults"]),
                         **_stall_stats(done)})
             if verbose:
                 print(json.dumps({"serving_point": pts[-1]}), flush=True)
@@ -616,7 +621,8 @@ def serve_summary(res: dict) -> dict:
     pt = next(iter(res["loads"].values()))[-1]
     keep = ("tb_per_ue_per_slot", "slots", "requests", "offered_gbps", "served_gbps", "p50_us", "p99_us",
             "p999_us", "max_us", "within_slot_frac", "tb_crc_ok_frac", "mean_max_iters", "items_single",
-            "items_paired", "host_longest_pass_us", "host_passes_over_1ms", "max_gap_device_us", "max_gap_host_us",
+            "items_paired", "host_longest_pass_us", "host_passes_over_1ms", "host_longest_pass_at_ms",
+            "host_involuntary_switches", "host_minor_faults", "max_gap_device_us", "max_gap_host_us",
             "max_admit_wait_us")
     return {"workload": res["workload"], "form": pt["form"], **{k: pt[k] for k in keep},
             "slot_us": 125.0, "p99_within_slot": pt["p99_us"] <= 125.0,

@@ -441,7 +441,10 @@ LDPC_API int ldpc_serve_replay(ldpc_server *srv, const ldpc_serve_tb *tbs, const
                                ldpc_serve_done *out, int32_t timeout_ms);
 /* Counters, out[0..n): since start, requests admitted, work items admitted in the single form, in
  * the paired form, device loop launches; then, for the last ldpc_serve_replay, the longest pass of
- * its host loop in ns and the number of passes longer than 1 ms (later entries 0). */
+ * its host loop in ns, the number of passes longer than 1 ms, when the longest pass began (ns after
+ * the replay started), and the replaying thread's involuntary and voluntary context switches and its
+ * minor and major page faults during the replay (getrusage of the thread; 0 where unavailable).
+ * Entries past these are 0. */
 LDPC_API int ldpc_serve_stats(ldpc_server *srv, int64_t *out, int32_t n);
 /* Stop the device loop (bounded wait) and free the server. */
 LDPC_API int ldpc_serve_stop(ldpc_server *srv);

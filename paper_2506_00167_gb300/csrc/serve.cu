@@ -30,6 +30,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <sys/resource.h>
+
 #include "arena.h"
 #include "host_rules.h"
 #include "crc_core.cuh"
@@ -40,6 +42,7 @@ namespace ldpcgb {
 namespace {
 
 constexpr int kServeBlock = 384;
+constexpr int kServeStats = 11;  // entries of ldpc_serve_stats
 constexpr int kMaxTbCb = 16;
 constexpr int kServeXpowWords = kMaxTbCb * 8448 / 32 * 2;  // TB CRC shift table: words of the largest TB
 
@@ -772,9 +775,11 @@ struct ldpc_server {
   int32_t book_n = 0, book_prb = 0;
   bool pairs = false;  // INT8: items may run in the paired form (two code blocks per thread group)
   PairPolicy policy;   // which requests take it
-  // requests, items single, items paired, loop launches; the last replay's longest pass of its
-  // host loop (ns) and its passes longer than 1 ms
-  int64_t stats[6] = {0, 0, 0, 0, 0, 0};
+  // requests, items single, items paired, loop launches; for the last replay: the longest pass of
+  // its host loop (ns), its passes longer than 1 ms, when the longest pass began (ns after the
+  // replay started), and the replaying thread's involuntary and voluntary context switches and
+  // minor and major page faults during it
+  int64_t stats[kServeStats] = {};
   bool cb_crc = false;  // LDPC_SERVE_CB_CRC: TBs with code-block CRCs accepted
   std::vector<ServeShape> hshapes;
   ServeArgs args{};
@@ -1043,7 +1048,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       free_server(v);
       return srv_fail(LDPC_ENOMEM, std::string("serve arena: ") + cudaGetErrorString(e));
     }
-    v->alloc = new Arena(arena_words);
+    v->alloc = new Arena(arena_words, 2 * static_cast<size_t>(d->max_inflight) + 8);
     for (int i = d->max_inflight - 1; i >= 0; --i) v->free_slots.push_back(i);
     v->slot_info.resize(d->max_inflight);
     v->host_pool = static_cast<const uint8_t*>(d->host_pool);
@@ -1125,49 +1130,50 @@ int ldpc_serve_submit(ldpc_server* v, const ldpc_serve_tb* tbs, int32_t n, int32
   // ---- validate every request before admitting any
   for (int i = 0; i < n; ++i) {
     const ldpc_serve_tb& tb = tbs[i];
-    const std::string at = "serve request " + std::to_string(i) + ": ";
+    // (the message is built only on a refusal: the admission loop allocates nothing)
+    const auto at = [i](const char* why) { return "serve request " + std::to_string(i) + ": " + why; };
     const int shape = session_shape_lookup(v->s, tb.bg, tb.Z);
-    if (shape < 0) return srv_fail(LDPC_EINVAL, at + "unknown (bg, Z)");
+    if (shape < 0) return srv_fail(LDPC_EINVAL, at("unknown (bg, Z)"));
     const ServeShape& ss = v->hshapes[shape];
     if (!ss.feasible && !(v->pairs && ss.feasible_p))
-      return srv_fail(LDPC_EINVAL, at + "shape does not fit the serving loop's shared memory");
+      return srv_fail(LDPC_EINVAL, at("shape does not fit the serving loop's shared memory"));
     const ShapeDev& sd = ss.sh;
     const int t0 = sd.npc * tb.Z;
     if (tb.n_cb < 1 || tb.n_cb > kMaxTbCb || (tb.Qm != 2 && tb.Qm != 4 && tb.Qm != 6 && tb.Qm != 8) || tb.E <= 0 ||
         tb.E % tb.Qm || tb.E > 2 * (sd.nb * tb.Z - t0))  // the circular buffer may wrap once
-      return srv_fail(LDPC_EINVAL, at + "bad n_cb, Qm or E");
+      return srv_fail(LDPC_EINVAL, at("bad n_cb, Qm or E"));
     const int K = sd.kb * tb.Z;
     const bool seg = tb.n_cb > 1 && tb.payload_bits == tb.n_cb * (K - 24) - 24;
-    if (K % 32 || (tb.payload_bits != tb.n_cb * K - 24 && !seg)) return srv_fail(LDPC_EINVAL, at + "payload_bits");
+    if (K % 32 || (tb.payload_bits != tb.n_cb * K - 24 && !seg)) return srv_fail(LDPC_EINVAL, at("payload_bits"));
     if (seg && !v->cb_crc)
-      return srv_fail(LDPC_EINVAL, at + "code-block CRCs need a service started with LDPC_SERVE_CB_CRC");
+      return srv_fail(LDPC_EINVAL, at("code-block CRCs need a service started with LDPC_SERVE_CB_CRC"));
     if (static_cast<int64_t>(tb.n_cb) * (K / 32) >= static_cast<int64_t>(kServeXpowWords))
-      return srv_fail(LDPC_EINVAL, at + "transport block too large");
-    if (tb.rv < 0 || tb.rv > 3) return srv_fail(LDPC_EINVAL, at + "rv must be 0..3");
-    if (tb.reserved != 0) return srv_fail(LDPC_EINVAL, at + "reserved must be 0");
+      return srv_fail(LDPC_EINVAL, at("transport block too large"));
+    if (tb.rv < 0 || tb.rv > 3) return srv_fail(LDPC_EINVAL, at("rv must be 0..3"));
+    if (tb.reserved != 0) return srv_fail(LDPC_EINVAL, at("reserved must be 0"));
     if (rv_k0(sd.nb - sd.npc, tb.rv, tb.Z) < 0)
-      return srv_fail(LDPC_EINVAL, at + "redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions");
+      return srv_fail(LDPC_EINVAL, at("redundancy versions 1-3 need a buffer of 66 Z or 50 Z positions"));
     const int n_re = tb.E / tb.Qm;
     const int mw = (n_re + 31) / 32;
     if (tb.sym_offset < 0 || tb.sym_offset % 8 ||
         static_cast<uint64_t>(tb.sym_offset) + static_cast<uint64_t>(tb.n_cb) * n_re * 8 > v->host_pool_bytes)
-      return srv_fail(LDPC_EINVAL, at + "symbols outside the host pool or misaligned");
+      return srv_fail(LDPC_EINVAL, at("symbols outside the host pool or misaligned"));
     if (tb.pattern < 0) {
       if (tb.pattern != -1 || tb.mask_offset < 0 || tb.mask_offset % 4 ||
           static_cast<uint64_t>(tb.mask_offset) + static_cast<uint64_t>(tb.n_cb) * mw * 4 > v->host_pool_bytes)
-        return srv_fail(LDPC_EINVAL, at + "masks outside the host pool or misaligned");
+        return srv_fail(LDPC_EINVAL, at("masks outside the host pool or misaligned"));
     } else {
       // the TB's resource elements fill its band symbol after symbol within the slot's 14 symbols
       if (tb.pattern >= v->book_n || tb.n_sc < 1 || tb.grid_sc < 0 ||
           static_cast<int64_t>(tb.grid_sc) + tb.n_sc > (int64_t{1} << 30) ||
           static_cast<int64_t>(tb.n_cb) * n_re > 14 * static_cast<int64_t>(tb.n_sc))
-        return srv_fail(LDPC_EINVAL, at + "pattern not in the codebook, or the TB does not fit its band in one slot");
+        return srv_fail(LDPC_EINVAL, at("pattern not in the codebook, or the TB does not fit its band in one slot"));
     }
     if (tb.result_offset >= 0 &&
         (!v->result_pool || tb.result_offset % 4 ||
          static_cast<uint64_t>(tb.result_offset) + static_cast<uint64_t>(tb.n_cb) * K / 8 > v->result_pool_bytes))
-      return srv_fail(LDPC_EINVAL, at + "result outside the result pool or misaligned");
-    if (!(tb.inv_sigma2 >= 0.f)) return srv_fail(LDPC_EINVAL, at + "inv_sigma2");
+      return srv_fail(LDPC_EINVAL, at("result outside the result pool or misaligned"));
+    if (!(tb.inv_sigma2 >= 0.f)) return srv_fail(LDPC_EINVAL, at("inv_sigma2"));
   }
   // ---- admit in order while the request slots, rings and arena have room
   const int64_t t = now_ns();
@@ -1314,12 +1320,29 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
   int next = 0, got = 0;
   int64_t last_progress = t0;
   std::vector<ldpc_serve_done> buf(1024);
-  v->stats[4] = 0;
-  v->stats[5] = 0;
+  for (int i = 4; i < kServeStats; ++i) v->stats[i] = 0;
+  rusage ru0{};
+  const bool have_ru = getrusage(RUSAGE_THREAD, &ru0) == 0;
+  struct RuDelta {  // the thread's scheduling and paging counts since the replay began, on every return
+    ldpc_server* v;
+    const rusage& r0;
+    bool ok;
+    ~RuDelta() {
+      rusage r1{};
+      if (!ok || getrusage(RUSAGE_THREAD, &r1) != 0) return;
+      v->stats[7] = r1.ru_nivcsw - r0.ru_nivcsw;
+      v->stats[8] = r1.ru_nvcsw - r0.ru_nvcsw;
+      v->stats[9] = r1.ru_minflt - r0.ru_minflt;
+      v->stats[10] = r1.ru_majflt - r0.ru_majflt;
+    }
+  } ru_delta{v, ru0, have_ru};
   int64_t prev = t0;
   while (got < n) {
     const int64_t now = now_ns();
-    if (now - prev > v->stats[4]) v->stats[4] = now - prev;
+    if (now - prev > v->stats[4]) {
+      v->stats[4] = now - prev;
+      v->stats[6] = prev - t0;
+    }
     if (now - prev > 1000000) ++v->stats[5];
     prev = now;
     int due = next;
@@ -1352,7 +1375,7 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
 
 int ldpc_serve_stats(ldpc_server* v, int64_t* out, int32_t n) {
   if (!v || n < 0 || (n > 0 && !out)) return srv_fail(LDPC_EINVAL, "bad stats arguments");
-  for (int i = 0; i < n; ++i) out[i] = i < 6 ? v->stats[i] : 0;
+  for (int i = 0; i < n; ++i) out[i] = i < kServeStats ? v->stats[i] : 0;
   return LDPC_OK;
 }
 

@@ -336,11 +336,14 @@ class Server:
 
     def stats(self) -> dict:
         """Counters since start (requests, items admitted single / paired, loop launches) and, for the last
-        replay, its host loop's longest pass (ns) and passes longer than 1 ms."""
-        out = (ctypes.c_int64 * 6)()
-        abi.check(abi.load().ldpc_serve_stats(self.handle, ctypes.cast(out, ctypes.c_void_p), 6), "ldpc_serve_stats")
+        replay, its host loop's longest pass (ns, and when it began), passes longer than 1 ms, and the
+        replaying thread's context switches and page faults."""
+        out = (ctypes.c_int64 * 11)()
+        abi.check(abi.load().ldpc_serve_stats(self.handle, ctypes.cast(out, ctypes.c_void_p), 11), "ldpc_serve_stats")
         return {"requests": out[0], "items_single": out[1], "items_paired": out[2], "launches": out[3],
-                "replay_longest_pass_ns": out[4], "replay_passes_over_1ms": out[5]}
+                "replay_longest_pass_ns": out[4], "replay_passes_over_1ms": out[5],
+                "replay_longest_pass_at_ns": out[6], "replay_involuntary_switches": out[7],
+                "replay_voluntary_switches": out[8], "replay_minor_faults": out[9], "replay_major_faults": out[10]}
 
     def stop(self) -> None:
         if getattr(self, "handle", 0):

@@ -71,3 +71,63 @@ def test_arena_best_fit_invariants(tmp_path):
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+DRIVER_NOALLOC = r"""
+#include <cstdio>
+#include <cstdlib>
+#include <new>
+#include <random>
+#include <vector>
+#include "arena.h"
+
+static bool counting = false;
+static long heap_calls = 0;
+void* operator new(std::size_t n) {
+  if (counting) ++heap_calls;
+  if (void* p = std::malloc(n ? n : 1)) return p;
+  throw std::bad_alloc();
+}
+void operator delete(void* p) noexcept { std::free(p); }
+void operator delete(void* p, std::size_t) noexcept { std::free(p); }
+
+int main() {
+  const int max_live = 4000;
+  ldpcgb::Arena a(1 << 24, 2 * max_live + 8);
+  std::mt19937_64 rng(11);
+  std::vector<std::pair<long long, long long>> live;
+  live.reserve(max_live);
+  for (int step = 0; step < 300000; ++step) {
+    if (live.empty() || (live.size() < static_cast<size_t>(max_live) && rng() % 100 < 52)) {
+      const long long n = 1 + static_cast<long long>(rng() % 3000);
+      counting = true;
+      const long long off = a.alloc(n);
+      counting = false;
+      if (off >= 0) live.emplace_back(off, n);
+    } else {
+      const size_t i = static_cast<size_t>(rng() % live.size());  // out of order
+      counting = true;
+      a.release(live[i].first, live[i].second);
+      counting = false;
+      live[i] = live.back();
+      live.pop_back();
+    }
+  }
+  std::printf("%ld\n", heap_calls);
+  return 0;
+}
+"""
+
+
+def test_arena_steady_state_allocates_nothing(tmp_path):
+    """With its node pool sized for the requests in flight (two tree nodes per free block), admitting and
+    releasing requests never calls the heap: the serving loop's host side stays allocation-free."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "arena_noalloc.cpp"
+    src.write_text(DRIVER_NOALLOC)
+    exe = tmp_path / "arena_noalloc"
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "0", r.stdout + r.stderr
