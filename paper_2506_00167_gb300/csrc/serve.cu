@@ -1310,16 +1310,23 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
                       ldpc_serve_done* out, int32_t timeout_ms) {
   if (!v || n < 0 || (n > 0 && (!tbs || !arrival_ns || !out)) || timeout_ms < 1)
     return srv_fail(LDPC_EINVAL, "bad replay arguments");
-  std::vector<int64_t> sched(n);
+  // the schedule and the tag index are built before the loop (which then allocates nothing)
+  std::vector<int64_t> sched;
   std::unordered_map<uint64_t, int> by_tag;
-  by_tag.reserve(static_cast<size_t>(n));
-  for (int i = 0; i < n; ++i) by_tag.emplace(tbs[i].tag, i);
+  std::vector<ldpc_serve_done> buf;
+  try {
+    sched.resize(static_cast<size_t>(n));
+    by_tag.reserve(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) by_tag.emplace(tbs[i].tag, i);
+    buf.resize(1024);
+  } catch (const std::bad_alloc&) {
+    return srv_fail(LDPC_ENOMEM, "replay: host memory for the schedule");
+  }
   if (static_cast<int>(by_tag.size()) != n) return srv_fail(LDPC_EINVAL, "replay: tags must be unique");
   const int64_t t0 = now_ns();
   for (int i = 0; i < n; ++i) sched[i] = t0 + arrival_ns[i];
   int next = 0, got = 0;
   int64_t last_progress = t0;
-  std::vector<ldpc_serve_done> buf(1024);
   for (int i = 4; i < kServeStats; ++i) v->stats[i] = 0;
   rusage ru0{};
   const bool have_ru = getrusage(RUSAGE_THREAD, &ru0) == 0;
