@@ -737,9 +737,6 @@ int64_t now_ns() {
 
 int align16s(int x) { return (x + 15) & ~15; }
 
-// First-fit allocator over arena words with coalescing frees.
-
-
 }  // namespace
 }  // namespace ldpcgb
 
