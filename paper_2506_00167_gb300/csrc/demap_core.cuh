@@ -54,14 +54,19 @@ __device__ __forceinline__ void axis_llr(float y, float inv_s2, float* out, int 
   for (int t = 0; t < q; ++t) out[2 * t + off] = (m1[t] - m0[t]) * inv_s2;
 }
 
-template <typename LT>
+// Q: quantise (the integer modes); a float LT with Q holds the quantised
+// integer as a float.
+template <typename LT, bool Q = (sizeof(LT) < 4)>
 __device__ __forceinline__ LT to_llr(float lam, float q_scale, float sat) {
-  if constexpr (sizeof(LT) == 4) {
+  if constexpr (!Q) {
     return lam;
   } else {
     float x = roundf(lam * q_scale);  // round half away from zero
     x = fminf(fmaxf(x, -sat), sat);
-    return static_cast<LT>(__float2int_rn(x));
+    if constexpr (sizeof(LT) == 4)
+      return x;
+    else
+      return static_cast<LT>(__float2int_rn(x));
   }
 }
 
@@ -100,7 +105,7 @@ __device__ __noinline__ float bit_llr(int e, int n_re, int interleave, float inv
 // rate-matched stream lands on buffer offset (k0 + e) mod Ncb, and a bit
 // repeated at e + Ncb (E > Ncb) is added there by the owner of e.
 // `out` is an LT* or any type whose out[e] takes an LT.
-template <typename LT, int Qm, typename Out, typename LoadSym, typename Punct>
+template <typename LT, int Qm, bool Q = (sizeof(LT) < 4), typename Out, typename LoadSym, typename Punct>
 __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_sigma2, Out out, int r, int n_re,
                                               int E, int ncb, int k0, int interleave, float q_scale,
                                               float llr_sat, LoadSym ld_sym, Punct punct_of) {
@@ -114,7 +119,7 @@ __device__ __forceinline__ void demap_re_into(float2 y, bool punct, float inv_si
     float v = punct ? 0.0f : lam[i];
     if (e + ncb < E) v += bit_llr<Qm>(e + ncb, n_re, interleave, inv_sigma2, ld_sym, punct_of);
     const int q = k0 + e;  // the redundancy version's buffer offset
-    out[q >= ncb ? q - ncb : q] = to_llr<LT>(v, q_scale, llr_sat);
+    out[q >= ncb ? q - ncb : q] = to_llr<LT, Q>(v, q_scale, llr_sat);
   }
 }
 

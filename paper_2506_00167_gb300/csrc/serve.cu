@@ -242,7 +242,7 @@ __device__ __forceinline__ PunctSrc punct_src(const ServeArgs& a, const ReqPunct
   return ps;
 }
 
-template <typename LT, typename Out>
+template <typename LT, bool Q = (sizeof(LT) < 4), typename Out>
 __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev& cb, const PunctSrc& ps, Out L, int k,
                                                 int Z) {
   using namespace demapcore;
@@ -262,10 +262,10 @@ __device__ __forceinline__ void demap_into_smem(const ServeArgs& a, const CbDev&
     auto ls = [&](int i) { return ld_pool_f2(sym + i); };
     auto lm = [&](int i) { return ps(i); };
     switch (cb.Qm) {
-      case 2: demap_re_into<LT, 2>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
-      case 4: demap_re_into<LT, 4>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
-      case 6: demap_re_into<LT, 6>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
-      default: demap_re_into<LT, 8>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 2: demap_re_into<LT, 2, Q>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 4: demap_re_into<LT, 4, Q>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      case 6: demap_re_into<LT, 6, Q>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
+      default: demap_re_into<LT, 8, Q>(y, punct, cb.inv_sigma2, out, r, cb.n_re, cb.E, ncb, cb.k0, a.interleave, a.q_scale, a.llr_sat, ls, lm); break;
     }
   }
 }
@@ -442,7 +442,7 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
       L[ssh.dummy_base + k] = LT(kBigF);
     // puncture flushing + max-log, straight into shared memory
     const int ci = static_cast<int>(static_cast<uint32_t>(cb0 + g) % a.cb_cap);
-    demap_into_smem<LT>(a, cb, punct_src(a, rp, cb, ci), PlainOut<LT>{L}, k, Z);
+    demap_into_smem<LT, SAT>(a, cb, punct_src(a, rp, cb, ci), PlainOut<LT>{L}, k, Z);
   }
   const bool got = mbar_wait_bounded(s_bar, phase, 1u << 22);
   phase ^= 1u;
@@ -713,9 +713,12 @@ template <bool CRC>
 const void* serve_kernel_for(int mode, bool pairs) {
   switch (mode) {
     case LDPC_F32: return reinterpret_cast<const void*>(&serve_kernel<float, float, false, CRC, false>);
+    // INT8: the single form keeps its posteriors as floats holding the
+    // quantised integers (no int8 conversion per edge access; the same
+    // values and arithmetic), its messages as bytes
     case LDPC_I8:
-      return pairs ? reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, CRC, true>)
-                   : reinterpret_cast<const void*>(&serve_kernel<int8_t, uint8_t, true, CRC, false>);
+      return pairs ? reinterpret_cast<const void*>(&serve_kernel<float, uint8_t, true, CRC, true>)
+                   : reinterpret_cast<const void*>(&serve_kernel<float, uint8_t, true, CRC, false>);
     default: return reinterpret_cast<const void*>(&serve_kernel<int16_t, uint16_t, true, CRC, false>);
   }
 }
@@ -941,7 +944,7 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       tw = std::max(tw, sd.tab_words);
       ss.rec_cap = sd.mb * Z;
       ss.hb_bytes = (Z % 32 == 0) ? align16s(sd.nb * (Z / 32) * 4) : 0;
-      ss.L_bytes = align16s((sd.nb + 1) * Z * esz);
+      ss.L_bytes = align16s((sd.nb + 1) * Z * (v->mode == LDPC_I8 ? 4 : esz));  // INT8: float posteriors
       ss.region_bytes = ss.L_bytes + ss.hb_bytes + 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
       ss.G = std::max(1, kServeBlock / Z);
       if (Z > 32) ss.G = std::min(ss.G, 15);
