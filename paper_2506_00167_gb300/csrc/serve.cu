@@ -1310,15 +1310,21 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
                       ldpc_serve_done* out, int32_t timeout_ms) {
   if (!v || n < 0 || (n > 0 && (!tbs || !arrival_ns || !out)) || timeout_ms < 1)
     return srv_fail(LDPC_EINVAL, "bad replay arguments");
-  // the schedule and the tag index are built before the loop (which then allocates nothing)
+  // The schedule, the tag index, the requests and the completions are set up
+  // in memory of this call's own before the loop, which then allocates nothing
+  // and touches no page of the caller's arrays (which may be subject to
+  // transparent huge-page collapsing, whose page faults stall the loop).
   std::vector<int64_t> sched;
   std::unordered_map<uint64_t, int> by_tag;
-  std::vector<ldpc_serve_done> buf;
+  std::vector<ldpc_serve_done> buf, done;
+  std::vector<ldpc_serve_tb> req;
   try {
     sched.resize(static_cast<size_t>(n));
     by_tag.reserve(static_cast<size_t>(n));
     for (int i = 0; i < n; ++i) by_tag.emplace(tbs[i].tag, i);
     buf.resize(1024);
+    req.assign(tbs, tbs + n);
+    done.resize(static_cast<size_t>(n));
   } catch (const std::bad_alloc&) {
     return srv_fail(LDPC_ENOMEM, "replay: host memory for the schedule");
   }
@@ -1327,6 +1333,14 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
   for (int i = 0; i < n; ++i) sched[i] = t0 + arrival_ns[i];
   int next = 0, got = 0;
   int64_t last_progress = t0;
+  // (declared before the counters' guard, so the copy comes after they are read)
+  struct CopyOut {  // the completions collected (zeros after them) reach the caller on every return
+    const std::vector<ldpc_serve_done>& done;
+    ldpc_serve_done* out;
+    ~CopyOut() {
+      if (!done.empty()) std::memcpy(out, done.data(), done.size() * sizeof(ldpc_serve_done));
+    }
+  } copy_out{done, out};
   for (int i = 4; i < kServeStats; ++i) v->stats[i] = 0;
   rusage ru0{};
   const bool have_ru = getrusage(RUSAGE_THREAD, &ru0) == 0;
@@ -1359,7 +1373,7 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
     while (due > next) {
       const int32_t chunk = std::min(due - next, 64);
       int32_t adm = 0;
-      const int rc = ldpc_serve_submit(v, tbs + next, chunk, &adm);
+      const int rc = ldpc_serve_submit(v, req.data() + next, chunk, &adm);
       if (rc) return rc;
       next += adm;
       if (adm < chunk) break;
@@ -1370,7 +1384,7 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
       ldpc_serve_done o = buf[i];
       auto f = by_tag.find(o.tag);
       if (f != by_tag.end()) o.t_submit_ns = sched[f->second];
-      out[got++] = o;
+      done[got++] = o;
     }
     if (rc) return rc;
     if (k > 0 || due > next) last_progress = now_ns();
