@@ -1310,73 +1310,37 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
                       ldpc_serve_done* out, int32_t timeout_ms) {
   if (!v || n < 0 || (n > 0 && (!tbs || !arrival_ns || !out)) || timeout_ms < 1)
     return srv_fail(LDPC_EINVAL, "bad replay arguments");
-  // The schedule, the tag index, the requests and the completions live in one
-  // page-locked host block of this call's own, set up before the loop: the
-  // loop then allocates nothing and touches no pageable memory of this size.
-  // (The kernel's background compaction migrates pageable pages; an access to
-  // a page being migrated faults and waits, which stalled the loop for up to
-  // ~100 ms.  Page-locked pages are not migrated.)
-  struct TagSlot {
-    uint64_t tag;
-    int32_t idx;  // -1: empty
-    int32_t pad;
-  };
-  int hbits = 1;
-  while ((int64_t{1} << hbits) < 2 * static_cast<int64_t>(n) + 2) ++hbits;
-  const size_t hcap = size_t{1} << hbits;
-  const size_t off_req = 0;
-  const size_t off_done = off_req + ((static_cast<size_t>(n) * sizeof(ldpc_serve_tb) + 255) & ~size_t{255});
-  const size_t off_sched = off_done + ((static_cast<size_t>(n) * sizeof(ldpc_serve_done) + 255) & ~size_t{255});
-  const size_t off_hash = off_sched + ((static_cast<size_t>(n) * sizeof(int64_t) + 255) & ~size_t{255});
-  const size_t off_buf = off_hash + hcap * sizeof(TagSlot);
-  const size_t total = off_buf + 1024 * sizeof(ldpc_serve_done);
-  void* block = nullptr;
-  const cudaError_t he = cudaHostAlloc(&block, total, cudaHostAllocDefault);
-  if (he != cudaSuccess) return srv_fail(LDPC_ENOMEM, std::string("replay: cudaHostAlloc: ") + cudaGetErrorString(he));
-  struct FreeBlock {
-    void* p;
-    ~FreeBlock() { cudaFreeHost(p); }
-  } free_block{block};
-  uint8_t* base = static_cast<uint8_t*>(block);
-  ldpc_serve_tb* req = reinterpret_cast<ldpc_serve_tb*>(base + off_req);
-  ldpc_serve_done* done = reinterpret_cast<ldpc_serve_done*>(base + off_done);
-  int64_t* sched = reinterpret_cast<int64_t*>(base + off_sched);
-  TagSlot* tagix = reinterpret_cast<TagSlot*>(base + off_hash);
-  ldpc_serve_done* buf = reinterpret_cast<ldpc_serve_done*>(base + off_buf);
-  if (n > 0) std::memcpy(req, tbs, static_cast<size_t>(n) * sizeof(ldpc_serve_tb));
-  std::memset(done, 0, static_cast<size_t>(n) * sizeof(ldpc_serve_done));
-  for (size_t i = 0; i < hcap; ++i) tagix[i] = TagSlot{0, -1, 0};
-  const auto slot_of = [&](uint64_t tag) {
-    return static_cast<size_t>((tag * 0x9E3779B97F4A7C15ull) >> (64 - hbits));
-  };
-  for (int i = 0; i < n; ++i) {  // open addressing, linear probing
-    size_t h = slot_of(req[i].tag);
-    while (tagix[h].idx >= 0) {
-      if (tagix[h].tag == req[i].tag) return srv_fail(LDPC_EINVAL, "replay: tags must be unique");
-      h = (h + 1) & (hcap - 1);
-    }
-    tagix[h] = TagSlot{req[i].tag, i, 0};
+  // The schedule, the tag index, the requests and the completions are set up
+  // in memory of this call's own before the loop, which then allocates nothing
+  // and touches no page of the caller's arrays (which may be subject to
+  // transparent huge-page collapsing, whose page faults stall the loop).
+  std::vector<int64_t> sched;
+  std::unordered_map<uint64_t, int> by_tag;
+  std::vector<ldpc_serve_done> buf, done;
+  std::vector<ldpc_serve_tb> req;
+  try {
+    sched.resize(static_cast<size_t>(n));
+    by_tag.reserve(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) by_tag.emplace(tbs[i].tag, i);
+    buf.resize(1024);
+    req.assign(tbs, tbs + n);
+    done.resize(static_cast<size_t>(n));
+  } catch (const std::bad_alloc&) {
+    return srv_fail(LDPC_ENOMEM, "replay: host memory for the schedule");
   }
-  const auto find_tag = [&](uint64_t tag) {
-    for (size_t h = slot_of(tag);; h = (h + 1) & (hcap - 1)) {
-      if (tagix[h].idx < 0) return -1;
-      if (tagix[h].tag == tag) return static_cast<int>(tagix[h].idx);
-    }
-  };
+  if (static_cast<int>(by_tag.size()) != n) return srv_fail(LDPC_EINVAL, "replay: tags must be unique");
   const int64_t t0 = now_ns();
   for (int i = 0; i < n; ++i) sched[i] = t0 + arrival_ns[i];
   int next = 0, got = 0;
   int64_t last_progress = t0;
-  // (declared after the block's guard and before the counters' guard: the copy
-  // comes after the counters are read and before the block is freed)
+  // (declared before the counters' guard, so the copy comes after they are read)
   struct CopyOut {  // the completions collected (zeros after them) reach the caller on every return
-    const ldpc_serve_done* done;
-    size_t n;
+    const std::vector<ldpc_serve_done>& done;
     ldpc_serve_done* out;
     ~CopyOut() {
-      if (n) std::memcpy(out, done, n * sizeof(ldpc_serve_done));
+      if (!done.empty()) std::memcpy(out, done.data(), done.size() * sizeof(ldpc_serve_done));
     }
-  } copy_out{done, static_cast<size_t>(n), out};
+  } copy_out{done, out};
   for (int i = 4; i < kServeStats; ++i) v->stats[i] = 0;
   rusage ru0{};
   const bool have_ru = getrusage(RUSAGE_THREAD, &ru0) == 0;
@@ -1409,17 +1373,17 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
     while (due > next) {
       const int32_t chunk = std::min(due - next, 64);
       int32_t adm = 0;
-      const int rc = ldpc_serve_submit(v, req + next, chunk, &adm);
+      const int rc = ldpc_serve_submit(v, req.data() + next, chunk, &adm);
       if (rc) return rc;
       next += adm;
       if (adm < chunk) break;
     }
     int32_t k = 0;
-    const int rc = ldpc_serve_poll(v, buf, 1024, &k);
+    const int rc = ldpc_serve_poll(v, buf.data(), static_cast<int32_t>(buf.size()), &k);
     for (int i = 0; i < k; ++i) {  // completions taken are kept even when the poll reports an error
       ldpc_serve_done o = buf[i];
-      const int f = find_tag(o.tag);
-      if (f >= 0) o.t_submit_ns = sched[f];
+      auto f = by_tag.find(o.tag);
+      if (f != by_tag.end()) o.t_submit_ns = sched[f->second];
       done[got++] = o;
     }
     if (rc) return rc;
