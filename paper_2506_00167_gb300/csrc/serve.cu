@@ -1312,8 +1312,8 @@ int ldpc_serve_replay(ldpc_server* v, const ldpc_serve_tb* tbs, const int64_t* a
     return srv_fail(LDPC_EINVAL, "bad replay arguments");
   // The schedule, the tag index, the requests and the completions are set up
   // in memory of this call's own before the loop, which then allocates nothing
-  // and touches no page of the caller's arrays (which may be subject to
-  // transparent huge-page collapsing, whose page faults stall the loop).
+  // and touches none of the caller's arrays (a page fault in the loop stalls
+  // every request due meanwhile).
   std::vector<int64_t> sched;
   std::unordered_map<uint64_t, int> by_tag;
   std::vector<ldpc_serve_done> buf, done;
