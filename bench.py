@@ -362,7 +362,8 @@ def _pct(x, q):
 
 
 def serve_measure(pool_n: int, slots: int, loads, forms, thresholds=(0,), releases=(0,), loops=(1,),
-                  plain_n: int = 400, cb_crc: bool = False, punct_sample: int = 0, verbose: bool = True) -> dict:
+                  plain_n: int = 400, cb_crc: bool = False, punct_sample: int = 0, verbose: bool = True,
+                  mode: str = "i8") -> dict:
     """Replay the served request stream through the decode service; latency vs the 125 us slot.
 
     40 UEs, Poisson TB requests per 125 us slot (``loads``: TBs per UE per slot, 1.0 = the configuration's
@@ -388,7 +389,7 @@ def serve_measure(pool_n: int, slots: int, loads, forms, thresholds=(0,), releas
     first = w.tbs["first_cb"].astype(np.int64)
     kbits = np.array([w.bgs[int(b)].kb for b in w.cbs["bg"][first]], np.int64) * \
         w.cbs["Z"][first].astype(np.int64) * w.tbs["n_cb"].astype(np.int64)
-    sess = Session(w.bgs, w.z_set, mode="i8", max_iter=10, early_term=True, sat=SAT["i8"])
+    sess = Session(w.bgs, w.z_set, mode=mode, max_iter=10, early_term=True, sat=SAT[mode])
     curves = {}
     streams = {load: slot_stream(slots, w.tbs["n_sc"], n_ue=40, tb_per_slot=load, seed=6) for load in loads}
     runs = [(f, lp, th, rl) for f in forms for lp in loops
@@ -440,39 +441,41 @@ def serve_measure(pool_n: int, slots: int, loads, forms, thresholds=(0,), releas
                 print(json.dumps({"serving_point": pts[-1]}), flush=True)
         srv.stop()
         curves[f"{form}{thr or ''}{'-' + str(rel) if rel else ''}_{lps}_loops_per_sm"] = pts
-    # FP32 unbatched plain path: one TB at a time, synchronised
-    st = streams[loads[-1]]
-    n_plain = min(plain_n, st["pool"].size)
-    sw = served_workload(w, st["pool"][:n_plain], st["pattern"][:n_plain], st["grid_sc"][:n_plain], book)
-    sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
-    per = []
-    for t in range(n_plain):
-        sub = subset(sw, [t])
-        b = sess32.batch(sub.cbs, sub.tbs, sub.slot_N)
-        sym = torch.from_numpy(sub.sym.astype(np.complex64)).cuda()
-        mask = torch.from_numpy(sub.mask.view(np.int32)).cuda()
-        per.append((b, sym, mask, b.alloc_outputs(), int(kbits[st["pool"][t]])))
-    for b, sym, mask, out, _ in per[:8]:
-        sess32.run(b, sym, mask, out)
-    torch.cuda.synchronize()
-    lat, oks = [], []
-    tot_bits = 0
-    t0 = time.perf_counter()
-    for b, sym, mask, out, kb in per:
-        t1 = time.perf_counter()
-        sess32.run(b, sym, mask, out)
+    # FP32 unbatched plain path: one TB at a time, synchronised (plain_n = 0: not run)
+    plain = None
+    if plain_n > 0:
+        st = streams[loads[-1]]
+        n_plain = min(plain_n, st["pool"].size)
+        sw = served_workload(w, st["pool"][:n_plain], st["pattern"][:n_plain], st["grid_sc"][:n_plain], book)
+        sess32 = Session(w.bgs, w.z_set, mode="f32", max_iter=10, early_term=True)
+        per = []
+        for t in range(n_plain):
+            sub = subset(sw, [t])
+            b = sess32.batch(sub.cbs, sub.tbs, sub.slot_N)
+            sym = torch.from_numpy(sub.sym.astype(np.complex64)).cuda()
+            mask = torch.from_numpy(sub.mask.view(np.int32)).cuda()
+            per.append((b, sym, mask, b.alloc_outputs(), int(kbits[st["pool"][t]])))
+        for b, sym, mask, out, _ in per[:8]:
+            sess32.run(b, sym, mask, out)
         torch.cuda.synchronize()
-        lat.append((time.perf_counter() - t1) * 1e6)
-        tot_bits += kb
-    wall = time.perf_counter() - t0
-    for b, sym, mask, out, _ in per:
-        oks.append(int(out["d"][0].item()))
-    plain = {"mode": "f32", "tbs": n_plain, "gbps": tot_bits / wall / 1e9, "p50_us": _pct(lat, 50),
-             "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9), "tb_crc_ok_frac": float(np.mean(oks))}
+        lat, oks = [], []
+        tot_bits = 0
+        t0 = time.perf_counter()
+        for b, sym, mask, out, kb in per:
+            t1 = time.perf_counter()
+            sess32.run(b, sym, mask, out)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t1) * 1e6)
+            tot_bits += kb
+        wall = time.perf_counter() - t0
+        for b, sym, mask, out, _ in per:
+            oks.append(int(out["d"][0].item()))
+        plain = {"mode": "f32", "tbs": n_plain, "gbps": tot_bits / wall / 1e9, "p50_us": _pct(lat, 50),
+                 "p99_us": _pct(lat, 99), "p999_us": _pct(lat, 99.9), "tb_crc_ok_frac": float(np.mean(oks))}
     res = {"workload": "40 UEs, Poisson TB requests per 125 us slot, TBs of 1-16 code blocks of the mixed "
                        "shapes; per slot one entry of a 128-entry URLLC codebook (7 mini-slot bits, "
                        "q = 1 - 0.92^12; 4-12-PRB runs on a 66-PRB period) on the slot's shared grid, "
-                       "expanded on the device; INT8 service",
+                       f"expanded on the device; {dict(i8='INT8', f32='FP32', i16='INT16')[mode]} service",
            "cb_crc": bool(cb_crc), "forms": list(forms), "slots_per_load": slots, "pool_tbs": w.n_tb,
            "pool_gen_s": gen_s, "loads": curves, "fp32_unbatched_plain": plain}
     if punct_sample:
@@ -570,7 +573,8 @@ def latency_floor(reps: int = 20) -> dict:
 def run_serving(args):
     res = serve_measure(args.serve_pool, args.serve_slots, args.serve_loads, args.serve_form,
                         args.serve_pair_threshold, args.serve_pair_release, args.serve_loops, args.serve_plain,
-                        args.cb_crc, punct_sample=1000)
+                        args.cb_crc, punct_sample=1000, mode=args.serve_mode)
+    res["mode"] = args.serve_mode
     res["single_block_latency"] = latency_floor()
     print(json.dumps({"serving": res}), flush=True)
 
@@ -789,6 +793,8 @@ def main():
                     help="keep warming up (untimed) at least this long so clocks settle and are sampled")
     ap.add_argument("--ref-tb", type=int, default=192, help="TBs per step of the reference arm")
     ap.add_argument("--serve", action="store_true", help="replay the served request stream instead")
+    ap.add_argument("--serve-mode", choices=["i8", "f32", "i16"], default="i8",
+                    help="arithmetic of the decode service (the paired form is INT8 only)")
     ap.add_argument("--serve-form", choices=sorted(SERVE_FORMS), nargs="+", default=["auto"],
                     help="INT8 service: pair code blocks by load (auto), always, or never (single); "
                          "several run one after the other")
@@ -1018,6 +1024,11 @@ def main():
     if world == 1 and args.bench_serve_slots > 0:
         serve = serve_summary(serve_measure(256, args.bench_serve_slots, [1.0], ["auto"], plain_n=200,
                                             verbose=False))
+        # the same stream through an FP32 service (one code block per thread group; no paired form)
+        s32 = serve_summary(serve_measure(256, args.bench_serve_slots, [1.0], ["auto"], plain_n=0, verbose=False,
+                                          mode="f32"))
+        serve["fp32_service"] = {k: s32[k] for k in ("served_gbps", "p50_us", "p99_us", "p999_us", "within_slot_frac",
+                                                     "tb_crc_ok_frac", "mean_max_iters", "host_longest_pass_us")}
 
     # ---- CPU baseline: the oracle on a bounded sample, all host cores
     cpu = None

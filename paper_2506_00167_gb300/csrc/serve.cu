@@ -125,9 +125,9 @@ struct ServeArgs {
   int32_t hdr_bytes, interleave, max_iter, early_term;
   float q_scale, llr_sat, beta, msg_sat, post_sat;
   uint64_t idle_ns;
-  uint8_t* rscratch;       // paired form's message words: one slot per (loop block, group)
+  uint8_t* rscratch;       // device-memory messages (paired form; FP32 single form): one slot per (loop block, group)
   int64_t rscratch_group;  // bytes per group slot
-  int32_t groups;          // group slots per loop block (the most groups of any paired shape)
+  int32_t groups;          // message slots per loop block (the most groups of any shape with device-memory messages)
   // sizes the checked build tests indices against
   int32_t n_shapes, n_req;
   int64_t arena_words, pool_f2, pool_words;
@@ -394,7 +394,10 @@ __device__ __forceinline__ void finish_item(const ServeArgs& a, int req, int n_i
 // Loads the shape's table (bulk copy), demaps straight into shared memory,
 // runs the layered decoder, writes bits and status to the arena.  Returns
 // false if the table copy did not complete within its bounded wait.
-template <typename LT, typename MT, bool SAT, bool CRC>
+// RG: the check messages live in a device-memory slot per (loop block, group),
+// as the paired form's do (FP32: a block's 12-byte records do not fit shared
+// memory beside its posteriors for the large shapes), else in shared memory.
+template <typename LT, typename MT, bool SAT, bool CRC, bool RG>
 __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape& ssh, const CbDev& cb_first,
                                             const ReqPunct& rp, int cb0, int count, uint32_t& phase,
                                             uint32_t* s_tab, uint64_t* s_bar, uint8_t* regions) {
@@ -414,7 +417,8 @@ __device__ __forceinline__ bool single_item(const ServeArgs& a, const ServeShape
   bool active = g < count && check_ok(count >= 1 && count <= ssh.G, 12, count, ssh.G);
   CbDev cb{};
   LT* L = reinterpret_cast<LT*>(regions + g * ssh.region_bytes);
-  uint8_t* rbase = regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
+  uint8_t* rbase = RG ? a.rscratch + (static_cast<int64_t>(blockIdx.x) * a.groups + g) * a.rscratch_group
+                      : regions + g * ssh.region_bytes + ssh.L_bytes + ssh.hb_bytes;
   MT* mag1 = reinterpret_cast<MT*>(rbase);
   MT* mag2 = mag1 + ssh.rec_cap;
   uint32_t* meta = reinterpret_cast<uint32_t*>(rbase + 2 * ((ssh.rec_cap * sizeof(MT) + 15) & ~15));
@@ -690,9 +694,9 @@ __global__ void __launch_bounds__(kServeBlock, 1) serve_kernel(const ServeArgs a
     bool fine;
     if constexpr (PAIRS) {
       fine = paired ? pair_item<CRC>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions)
-                    : single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions);
+                    : single_item<LT, MT, SAT, CRC, (sizeof(MT) == 4)>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions);
     } else {
-      fine = single_item<LT, MT, SAT, CRC>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions);
+      fine = single_item<LT, MT, SAT, CRC, (sizeof(MT) == 4)>(a, ssh, cb_first, rp, cb0, count, phase, s_tab, s_bar, regions);
     }
     if (!fine) break;
     finish_item(a, req, n_items, tid, lane, &s_last, s_res);
@@ -945,7 +949,10 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
       ss.rec_cap = sd.mb * Z;
       ss.hb_bytes = (Z % 32 == 0) ? align16s(sd.nb * (Z / 32) * 4) : 0;
       ss.L_bytes = align16s((sd.nb + 1) * Z * (v->mode == LDPC_I8 ? 4 : esz));  // INT8: float posteriors
-      ss.region_bytes = ss.L_bytes + ss.hb_bytes + 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
+      // FP32: the single form's messages in a device-memory slot per (loop block, group)
+      const int64_t rec_single = 2 * align16s(ss.rec_cap * esz) + align16s(ss.rec_cap * 4);
+      ss.region_bytes = ss.L_bytes + ss.hb_bytes + (v->mode == LDPC_F32 ? 0 : static_cast<int>(rec_single));
+      if (v->mode == LDPC_F32) rec_group = std::max<int64_t>(rec_group, rec_single);
       ss.G = std::max(1, kServeBlock / Z);
       if (Z > 32) ss.G = std::min(ss.G, 15);
       if (v->pairs && Z % 32 == 0) {
@@ -991,9 +998,11 @@ int ldpc_serve_start(ldpc_session* s, const ldpc_serve_desc* d, ldpc_server** ou
     // by default pairing starts above two items in flight per loop and stops at one
     v->policy.threshold = d->pair_threshold > 0 ? d->pair_threshold : 2 * static_cast<int64_t>(v->grid);
     v->policy.release = std::min<int64_t>(d->pair_release > 0 ? d->pair_release : v->grid, v->policy.threshold);
-    int gmax = 0;  // paired-form group slots per loop
-    for (auto& ss : v->hshapes)
+    int gmax = 0;  // message slots per loop: the paired form's groups, or FP32's single-form groups
+    for (auto& ss : v->hshapes) {
       if (ss.feasible_p) gmax = std::max(gmax, ss.Gp);
+      if (v->mode == LDPC_F32 && ss.feasible) gmax = std::max(gmax, ss.G);
+    }
     if (gmax > 0) {
       e = cudaMalloc(&v->rscratch, static_cast<size_t>(v->grid) * gmax * rec_group);
       if (e != cudaSuccess) {

@@ -219,7 +219,7 @@ def test_int8_service_matches_the_oracle(stream, form):
 
 @pytest.fixture(scope="module")
 def small_stream():
-    """Shapes up to Z = 128 so that the FP32 loop's state fits shared memory."""
+    """Shapes up to Z = 128 (messages in shared memory for INT16; FP32's are in device memory)."""
     return Stream(tb_pool(24, seed=19, max_cb=5, zs=(32, 64, 128)), n_slots=3, n_ue=10, seed=10)
 
 
@@ -227,6 +227,13 @@ def small_stream():
 def test_float_and_int16_services_match_the_oracle(small_stream, mode):
     got, ref = _oracle_parity(small_stream, mode, {})
     assert 0 < int(ref["d"].sum()) < small_stream.n
+
+
+def test_fp32_service_on_the_full_stream_matches_the_oracle(stream):
+    """FP32 on the served stream's shapes up to Z = 384 (its check messages in a device-memory slot per
+    loop group)."""
+    got, ref = _oracle_parity(stream, "f32", {})
+    assert 0 < int(ref["d"].sum()) < stream.n
 
 
 def test_admission_waits_for_memory(stream):
@@ -421,9 +428,8 @@ def test_redundancy_versions_through_the_service_match_the_batch_path(form):
 
 @pytest.mark.parametrize("mode", ["f32", "i16"])
 def test_float_and_int16_services_match_the_batch_path(small_stream, mode):
-    """The FP32 and INT16 serving loops (single form, messages in shared memory; shapes up to Z = 128 so
-    that FP32 fits): bits, d_e and iteration counts equal the batch path in the same arithmetic; a shape
-    whose FP32 state does not fit shared memory is refused."""
+    """The FP32 and INT16 serving loops (single form): bits, d_e and iteration counts equal the batch path
+    in the same arithmetic, on shapes up to Z = 128 and, in FP32, on Z = 384 shapes too."""
     st = small_stream
     n = st.n
     srv, res = st.server(mode, arena_bytes=1 << 26, max_inflight=64)
@@ -441,14 +447,18 @@ def test_float_and_int16_services_match_the_batch_path(small_stream, mode):
         assert 0 < int(done["d"].sum()) < n
     finally:
         srv.stop()
-    if mode == "f32":  # Z = 384 in FP32 (either base graph): too large for the loop's shared memory
-        big = tb_pool(2, seed=3, max_cb=1, zs=(384,))
-        raw2, mb2 = pool_bytes(big)
-        host2 = torch.from_numpy(raw2).pin_memory()
-        srv2 = Server(session_for(big, "f32"), host2, None, arena_bytes=1 << 24, max_inflight=8)
+    if mode == "f32":  # Z = 384 in FP32 (either base graph): the messages in device memory
+        big = Stream(tb_pool(6, seed=3, max_cb=2, zs=(384,)), n_slots=2, n_ue=4, seed=11)
+        srv2, res2 = big.server("f32", arena_bytes=1 << 26, max_inflight=16)
         try:
-            with pytest.raises(LdpcError, match="shared memory"):
-                srv2.submit(tb_records(big, mb2, abi.SERVE_TB_NP)[:1])
+            done = srv2.replay(big.records(), np.zeros(big.n, np.int64), timeout_ms=20000)
+            assert sorted(done["tag"].tolist()) == list(range(big.n))
+            d_ref, bits_ref, it_ref, _ = _batch_reference(big.sw, range(big.n), "f32")
+            for r in done:
+                t = int(r["tag"])
+                assert int(r["d"]) == int(d_ref[t]), t
+                assert int(r["max_iters"]) == it_ref[t], t
+                assert np.array_equal(big.bits(res2, t), bits_ref[t]), t
         finally:
             srv2.stop()
 
