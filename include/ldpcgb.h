@@ -340,7 +340,10 @@ LDPC_API int decode_uniform_noalloc_wait_check(int32_t limit, void *cuda_stream)
  * free space.  Every device wait is bounded: the loop exits after
  * idle_timeout_us without work (submit relaunches it) or when stopped.
  * Shapes whose decoder state does not fit shared memory are rejected
- * (LDPC_EINVAL); the integer modes fit every shape up to Z = 384.
+ * (LDPC_EINVAL); every mode fits every shape up to Z = 384 (an FP32 service
+ * keeps its check messages in a device-memory slot per loop group, the
+ * integer modes in shared memory; the INT8 single form holds its posteriors
+ * as floats carrying the quantised integers).
  */
 typedef struct ldpc_server ldpc_server;
 
@@ -352,7 +355,7 @@ typedef struct {
   uint64_t host_pool_bytes;
   void *result_pool;         /* pinned, mapped host memory receiving decoded bits (may be NULL) */
   uint64_t result_pool_bytes;
-  int32_t loops_per_sm;      /* 0 or 1: one device loop per SM, check messages in shared memory.  2 (two
+  int32_t loops_per_sm;      /* 0 or 1: one device loop per SM.  2 (two
                               * loops per SM, messages in device memory) is withdrawn and returns
                               * LDPC_EINVAL: under load it once made an illegal access and once returned
                               * corrupted status words, cause not yet found */
